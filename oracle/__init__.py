@@ -1,0 +1,15 @@
+"""FP64 CPU oracle of the LS/MRC receiver.
+
+TEST INFRASTRUCTURE: only the tests, the smoke check of ``__graft_entry__``
+and the CPU baseline legs of ``bench.py`` may use it.  It shares no code with
+the CUDA library.
+"""
+
+from .lsas_oracle import (Result, receive, strip_cp, dft, dft_matrix,
+                          ls_estimate, channel_energy, mrc, demap, slice_axis,
+                          thresholds, qam_axis, gray_bits, pack_bits,
+                          to_complex, data_symbols)
+
+__all__ = ["Result", "receive", "strip_cp", "dft", "dft_matrix", "ls_estimate",
+           "channel_energy", "mrc", "demap", "slice_axis", "thresholds",
+           "qam_axis", "gray_bits", "pack_bits", "to_complex", "data_symbols"]
