@@ -1,0 +1,350 @@
+"""Throughput benchmark of the fused LS/MRC receiver on GB300.
+
+One step = one ``lsas_run_frame`` over a batch of 1000 frames of the "scale"
+workload (64 antennas, N = 1024, CP 128, 1 pilot + 13 16-QAM data symbols,
+sc16 input; 4.13 GB of samples, larger than L2), i.e. the whole hot path:
+CP removal, FFT, LS estimate, MRC combine, demap and bit packing.
+
+Prints one JSON line (rank 0):
+  value      antenna*subcarrier samples/s  (F * M * S * N per step / time),
+             whole job over all ranks (each rank processes its own frames)
+  roofline   the fused kernel's algorithmic bytes (input + H + packed bits)
+             per launch / its CUDA-event time, against the measured HBM peak
+  e2e        the same metric through lsas_run_frame_host with pinned host
+             buffers, host<->device copies inside the timed region
+  cpu_baseline  the FP64 oracle timed on the host cores on a bounded sample
+  latency_ms p50/p99 of single-frame calls
+``--impl reference`` times the oracle instead (the CPU reference arm).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+FALLBACK_HBM_GBS = 6800.0
+KERNEL_SRC = os.path.join(ROOT, "paper_1901_07499_gb300", "csrc", "lsas_kernels.cuh")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "frame_kernel_traffic.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="lsas", choices=["lsas", "reference"])
+    ap.add_argument("--config", default="scale")
+    ap.add_argument("--frames", type=int, default=0, help="frames per step (default: config)")
+    ap.add_argument("--pool", type=int, default=32, help="distinct seeded frames tiled")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--latency-calls", type=int, default=200)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_hash():
+    with open(KERNEL_SRC, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def ncu_traffic(cfg, frames):
+    """DRAM bytes per launch from a committed ncu capture of this kernel
+    source, scaled by frames; None when absent or the kernel changed."""
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            d = json.load(fh)
+        if d.get("kernel_sha") != kernel_hash() or d.get("workload") != cfg.name:
+            return None
+        return float(d["dram_bytes_per_frame"]) * frames
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi SM clock and throttle reasons sampled during a window."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t0 = time.time()
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append((time.time(), [c.strip() for c in line.split(",")]))
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for _, r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for n, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(n)
+            except Exception:
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ CPU oracle
+
+def time_oracle(cfg, seconds, min_frames=1):
+    """Run the FP64 oracle on seeded frames until ``seconds`` have elapsed;
+    returns (samples/s, frames, threads)."""
+    import oracle
+    frames = 0
+    t_used = 0.0
+    fid = 0
+    while t_used < seconds or frames < min_frames:
+        b = synth.generate(cfg, frame_ids=[fid])
+        t0 = time.perf_counter()
+        oracle.receive(b.frames, cfg.N, cfg.cp, cfg.S, cfg.pilot_idx, cfg.Q, b.pilot,
+                       keep_Y=False)
+        t_used += time.perf_counter() - t0
+        frames += 1
+        fid += 1
+    rate = frames * cfg.M * cfg.S * cfg.N / t_used
+    return rate, frames, blas_threads(), t_used
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [d.get("num_threads", 1) for d in threadpool_info() if d.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
+        if os.environ.get(var):
+            return int(os.environ[var])
+    return os.cpu_count() or 1
+
+
+def workload_config(cfg, F, pool):
+    return {"workload": f"{cfg.name}: {F} frames x {cfg.M} antennas x N={cfg.N} "
+                        f"(CP {cfg.cp}, {cfg.S} symbols, {cfg.Q}-QAM, {cfg.fmt})",
+            "frames": F, "M": cfg.M, "N": cfg.N, "cp": cfg.cp, "n_sym": cfg.S,
+            "qam": cfg.Q, "input": cfg.fmt, "distinct_frames": pool,
+            "l2": "inputs larger than L2 (no flush needed)"}
+
+
+def reference_arm(args, cfg):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    per_step = 2
+    times = []
+    for i in range(args.warmup + args.steps):
+        import oracle
+        b = synth.generate(cfg, frame_ids=range(i * per_step, (i + 1) * per_step))
+        t0 = time.perf_counter()
+        oracle.receive(b.frames, cfg.N, cfg.cp, cfg.S, cfg.pilot_idx, cfg.Q, b.pilot,
+                       keep_Y=False)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    t = sum(times)
+    value = args.steps * per_step * cfg.M * cfg.S * cfg.N / t
+    line = {
+        "impl": "reference", "metric": "antenna*subcarrier samples/s", "value": value,
+        "unit": "samples/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator)",
+        "config": workload_config(cfg, per_step, per_step),
+        "cpu_baseline": {"value": value, "unit": "samples/s", "cores": blas_threads(),
+                         "kind": "oracle",
+                         "sample": f"{per_step} frames per step, generation excluded"},
+        "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    cfg = synth.config_by_name(args.config)
+    if args.impl == "reference":
+        return reference_arm(args, cfg)
+
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_1901_07499_gb300.lsas as lsas
+
+    F = args.frames or cfg.F
+    pool = min(args.pool, F)
+    # each rank owns its own seeded frames (independent units, no exchange)
+    b = synth.generate(cfg, frame_ids=range(rank * pool, (rank + 1) * pool))
+    plan = lsas.Plan(cfg.M, cfg.N, cfg.cp, cfg.S, cfg.pilot_idx, cfg.Q, fmt=cfg.fmt,
+                     max_frames=F, pilot=b.pilot)
+    xp = torch.from_numpy(np.ascontiguousarray(b.frames)).cuda()
+    reps = (F + pool - 1) // pool
+    x = xp.repeat(reps, 1, 1, 1)[:F].contiguous()
+    del xp
+    H = plan.empty_H(F)
+    bits = plan.empty_bits(F)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        plan.run_frame(x, H, bits)
+    plan.sync()
+    clk = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    time.sleep(0.3)   # let the sampler start before the timed region
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.run_frame(x, H, bits)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    barrier()
+    plan.sync()
+    ms = e0.elapsed_time(e1)
+    t_max = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t_max, op=torch.distributed.ReduceOp.MAX)
+    ms = float(t_max.item())
+    ms_step = ms / args.steps
+    samples = world * F * cfg.M * cfg.S * cfg.N
+    value = samples / (ms_step * 1e-3)
+
+    in_b, h_b, bit_b, eq_b = lsas.frame_bytes(cfg.M, cfg.N, cfg.cp, cfg.S, cfg.Q, cfg.fmt)
+    alg_bytes = F * (in_b + h_b + bit_b)
+    achieved = alg_bytes / (ms_step * 1e-3) / 1e9
+    peak, peak_src = measured_peaks()
+    traffic = ncu_traffic(cfg, F)
+
+    # single-frame latency
+    lat = []
+    x1, H1, b1 = x[:1], H[:1], bits[:1]
+    for i in range(args.latency_calls + 10):
+        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        plan.run_frame(x1, H1, b1)
+        c.record(stream)
+        c.synchronize()
+        if i >= 10:
+            lat.append(a.elapsed_time(c))
+    lat.sort()
+
+    # end to end through the host-buffer entry point
+    xh = x[:F].cpu().pin_memory()
+    Hh = torch.empty((F, cfg.M, cfg.N), dtype=torch.complex64).pin_memory()
+    bh = torch.empty((F, bits.shape[1]), dtype=torch.uint8).pin_memory()
+    plan.run_frame_host(xh, Hh, bh)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        plan.run_frame_host(xh, Hh, bh)
+    t_e2e = (time.perf_counter() - t0) / args.e2e_steps
+    te = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
+    t_e2e = float(te.item())
+    plan.sync()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, nfr, threads, used = time_oracle(cfg, args.cpu_seconds)
+        cpu = {"value": rate, "unit": "samples/s", "cores": threads, "kind": "oracle",
+               "sample": f"{nfr} frames of the same workload ({used:.1f} s), "
+                         "generation excluded"}
+
+    if rank == 0:
+        line = {
+            "metric": "antenna*subcarrier samples/s", "value": value, "unit": "samples/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded generator)",
+            "config": workload_config(cfg, F, pool),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": peak_src,
+                         "kernel": "frame_kernel (fused CP strip+FFT+LS+MRC+demap)",
+                         "algorithmic_bytes_per_frame": in_b + h_b + bit_b},
+            "e2e": {"value": world * F * cfg.M * cfg.S * cfg.N / t_e2e, "unit": "samples/s",
+                    "h2d_bytes_per_step": F * in_b, "d2h_bytes_per_step": F * (h_b + bit_b)},
+            "latency_ms": {"frames_per_call": 1, "p50": lat[len(lat) // 2],
+                           "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    plan.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,187 @@
+/*
+ * lsas.h -- C ABI of liblsas: LS channel estimation and MRC demodulation of
+ * uplink OFDM frames for large-scale antenna receivers, on one GB300 GPU.
+ *
+ * The operations are those of the paper "Accelerating Channel Estimation and
+ * Demodulation of Uplink OFDM symbols for Large Scale Antenna Systems using
+ * GPU" (arXiv 1901.07499):
+ *   - cyclic-prefix removal and an N-point FFT of every OFDM symbol of every
+ *     receive antenna (Sec. II-B, Sec. II-C: batched FFTs over antennas);
+ *   - block-type Least Squares estimation from the first (pilot) symbol,
+ *     H[m,k] = Y_pilot[m,k] / X_pilot[k] (Sec. II-B, Sec. II-C);
+ *   - Maximal Ratio Combining of each data symbol over the M antennas with the
+ *     conjugate channel and the channel-energy sum formed once per frame
+ *     (Sec. II-C, Sec. III);
+ *   - hard decision of the combined symbols to Gray-labelled QAM bits (the
+ *     demodulated output of Sec. II-B).
+ * The paper calls the antenna count N and the subcarrier count M; this ABI
+ * uses M = antennas and N = FFT length = subcarriers throughout.
+ *
+ * Conventions fixed by this library where the paper leaves them open:
+ *   - forward FFT kernel exp(-2j pi k n / N), unitary scale 1/sqrt(N);
+ *     subcarriers in natural order k = 0 .. N-1 (no fftshift);
+ *   - LS for a general pilot: H = Y conj(X) / |X|^2;
+ *   - normalised MRC: z[d,k] = sum_m conj(H[m,k]) Y[m,d,k] / sum_m |H[m,k]|^2;
+ *   - square Gray QAM of unit average energy: per axis L = sqrt(Q) levels at
+ *     (2i - (L-1)) A, A = 1/sqrt(2(Q-1)/3); the level of a value v is the
+ *     number of boundaries (2b - L) A, b = 1..L-1, with v >= boundary (a value
+ *     on a boundary goes to the upper level), compared in float32; level i
+ *     carries the Gray word i ^ (i >> 1), MSB first, I-axis bits before
+ *     Q-axis bits.  BPSK (Q = 2) uses the I axis only, boundary 0.
+ *
+ * Buffers (all contiguous, row-major; "d_" = device memory, "h_" = host):
+ *   input  [F][M][S*(N+CP)] interleaved IQ samples: int16 pairs (SC16, the
+ *          value is used as is, no rescaling) or float32 pairs (FC32)
+ *   H      [F][M][N]  complex float32 (re, im interleaved)
+ *   Y      [F][M][S][N] complex float32 (lsas_fft only)
+ *   eq     [F][D][N]  complex float32, the combined symbols z (optional)
+ *   bits   [F][D*N*q/8] bytes; bit t = (d*N + k)*q + j of a frame is bit
+ *          (7 - t%8) of byte t/8 (MSB first), d = data-symbol index in
+ *          ascending symbol order skipping the pilot, j = bit of the symbol.
+ * with F frames, M antennas, N subcarriers, S symbols per frame (one pilot
+ * at pilot_idx, D = S - 1 data symbols), q = log2(Q) bits per data symbol.
+ *
+ * Ownership: the caller owns every buffer passed in.  A plan owns only its own
+ * device tables (twiddles, pilot inverse, a status word) and, after the first
+ * lsas_run_frame_host call, its host-transfer staging buffers.
+ *
+ * Errors: argument checks run on the host before any launch; a failing check
+ * returns its code and enqueues nothing.  A CUDA launch or copy failure
+ * returns LSAS_ERR_CUDA.  Conditions found on the device (a zero or non-finite
+ * channel energy, a wait that timed out) are latched into the plan's status
+ * word and returned by lsas_plan_sync.  Calls on one plan from several host
+ * threads at once are not supported.
+ */
+#ifndef LSAS_H_
+#define LSAS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lsas_plan_s* lsas_plan;
+
+typedef enum {
+  LSAS_OK = 0,
+  LSAS_ERR_INVALID_ARG = 1,  /* bad size, null pointer, misuse */
+  LSAS_ERR_UNSUPPORTED = 2,  /* valid request this build does not handle */
+  LSAS_ERR_OOM = 3,          /* device or pinned-host allocation failed */
+  LSAS_ERR_CAPACITY = 4,     /* n_frames above the plan's max_frames */
+  LSAS_ERR_CUDA = 5,         /* a CUDA runtime call failed */
+  LSAS_ERR_TIMEOUT = 6,      /* a bounded device wait gave up (latched) */
+  LSAS_ERR_DEVICE = 7        /* zero / non-finite channel energy (latched) */
+} lsas_status;
+
+typedef enum { LSAS_IN_SC16 = 0, LSAS_IN_FC32 = 1 } lsas_input_fmt;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* lsas_status_str(lsas_status s);
+
+/*
+ * Host-only check of a receiver configuration; touches no GPU.
+ * Supported: 1 <= M <= 256; N a power of two in [64, 2048];
+ * 0 <= cp_len < N; 2 <= n_sym <= 64; 0 <= pilot_idx < n_sym;
+ * qam_order in {2, 4, 16, 64, 256}.  Returns LSAS_OK or LSAS_ERR_INVALID_ARG.
+ */
+lsas_status lsas_check_config(int M, int N, int cp_len, int n_sym,
+                              int pilot_idx, int qam_order);
+
+/*
+ * Host-only: bytes per frame of the input (for fmt), of H, of the packed bits
+ * and of eq, written to out[0..3].  Returns LSAS_ERR_INVALID_ARG for a bad
+ * configuration or a NULL out.
+ */
+lsas_status lsas_frame_bytes(int M, int N, int cp_len, int n_sym,
+                             int qam_order, lsas_input_fmt fmt,
+                             size_t out[4]);
+
+/*
+ * Create a plan on the current CUDA device: validates the configuration (as
+ * lsas_check_config), uploads the twiddle table and the default all-(+1)
+ * pilot, and prepares the kernels.  Defaults: SC16 input, max_frames = 1024.
+ * On success *out holds the plan; on failure *out is set to NULL.
+ */
+lsas_status lsas_plan_create(int M, int N, int cp_len, int n_sym,
+                             int pilot_idx, int qam_order, lsas_plan* out);
+
+/* Select the input sample format and the largest n_frames a call accepts. */
+lsas_status lsas_plan_set(lsas_plan plan, lsas_input_fmt fmt, int max_frames);
+
+/*
+ * Set the known pilot symbol X_pilot[k] (Sec. II-B channel-estimation
+ * symbol) from N interleaved (re, im) float pairs in host memory.  Every
+ * |X[k]| must be non-zero and finite, else LSAS_ERR_INVALID_ARG.
+ * Synchronous (the table is uploaded before return).
+ */
+lsas_status lsas_plan_set_pilot(lsas_plan plan, const float* host_pilot_iq);
+
+/*
+ * CP removal + unitary FFT of every symbol of every antenna (Sec. II-B,
+ * Sec. II-C): d_Y[f][m][s][k] = N^-1/2 sum_n r[f][m][s][n] exp(-2j pi k n/N).
+ * Asynchronous on stream (a cudaStream_t; NULL = legacy default stream).
+ */
+lsas_status lsas_fft(lsas_plan plan, const void* d_in, int n_frames,
+                     float* d_Y, void* stream);
+
+/*
+ * LS channel estimation from the pilot symbol (Sec. II-C):
+ * d_H[f][m][k] = Y[f][m][pilot_idx][k] conj(X[k]) / |X[k]|^2.  Asynchronous.
+ */
+lsas_status lsas_estimate(lsas_plan plan, const void* d_in, int n_frames,
+                          float* d_H, void* stream);
+
+/*
+ * MRC demodulation of the data symbols with a given channel d_H (Sec. II-C):
+ * writes d_bits and, if d_eq is not NULL, the combined symbols z.  d_H may
+ * come from lsas_estimate or from any other estimator.  Asynchronous.
+ */
+lsas_status lsas_demodulate(lsas_plan plan, const void* d_in,
+                            const float* d_H, int n_frames, uint8_t* d_bits,
+                            float* d_eq, void* stream);
+
+/*
+ * The whole receiver in one fused pass per frame: estimation (writes d_H)
+ * then demodulation (writes d_bits and optionally d_eq).  Asynchronous.
+ */
+lsas_status lsas_run_frame(lsas_plan plan, const void* d_in, int n_frames,
+                           float* d_H, uint8_t* d_bits, float* d_eq,
+                           void* stream);
+
+/*
+ * lsas_run_frame on HOST buffers: copies the input to the device, runs the
+ * receiver and copies H, bits and (if h_eq is not NULL) eq back, in chunks so
+ * that transfers overlap the kernels.  Host buffers should be page-locked
+ * (cudaHostAlloc / pinned) for full speed.  The first call on a plan
+ * allocates the plan's device staging buffers.  Returns after the results
+ * are in host memory (it synchronises stream).
+ */
+lsas_status lsas_run_frame_host(lsas_plan plan, const void* h_in,
+                                int n_frames, float* h_H, uint8_t* h_bits,
+                                float* h_eq, void* stream);
+
+/*
+ * Synchronise stream, then return and clear the plan's latched device status
+ * (LSAS_OK, LSAS_ERR_TIMEOUT or LSAS_ERR_DEVICE), or LSAS_ERR_CUDA.
+ */
+lsas_status lsas_plan_sync(lsas_plan plan, void* stream);
+
+/*
+ * Launch geometry of the plan, for tests and reports: out[0] antennas per
+ * step, out[1] threads per block of the fused kernel, out[2] its dynamic
+ * shared memory bytes, out[3] data-symbol groups per frame, out[4] staging
+ * slots, out[5] 1 if input is staged by bulk asynchronous copies (TMA),
+ * out[6] input format, out[7] max_frames.
+ */
+lsas_status lsas_plan_info(lsas_plan plan, int out[8]);
+
+/* Release the plan's device memory (synchronises its device first). */
+lsas_status lsas_plan_destroy(lsas_plan plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LSAS_H_ */

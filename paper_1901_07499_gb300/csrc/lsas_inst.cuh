@@ -1,0 +1,28 @@
+// lsas_inst.cuh -- launch wrapper of one FFT length; each lsas_inst_n*.cu
+// includes it once so that the six lengths compile in parallel.
+#pragma once
+#include "lsas_kernels.cuh"
+
+namespace lsas {
+
+template <int LOG2N, bool FC32>
+static cudaError_t launch_t(int kind, const KParams& p, int grid, int smem, cudaStream_t st) {
+  constexpr int T = Geo<LOG2N>::T;
+  void (*fn)(const KParams) = nullptr;
+  if (kind == kKindFrame) fn = frame_kernel<LOG2N, FC32>;
+  else if (kind == kKindEstimate) fn = estimate_kernel<LOG2N, FC32>;
+  else fn = fft_kernel<LOG2N, FC32>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  fn<<<grid, T, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <int LOG2N>
+cudaError_t launch_n(int kind, bool fc32, const KParams& p, int grid, int smem,
+                     cudaStream_t st) {
+  return fc32 ? launch_t<LOG2N, true>(kind, p, grid, smem, st)
+              : launch_t<LOG2N, false>(kind, p, grid, smem, st);
+}
+
+}  // namespace lsas

@@ -1,0 +1,743 @@
+// lsas_kernels.cuh -- device code of liblsas for sm_103a.
+//
+// Three kernels share one building block, the "team FFT": a team of
+// L = N/32 threads transforms one N-point OFDM symbol of one antenna, each
+// thread holding 32 complex points in registers.  A Stockham auto-sort FFT
+// (radix 32, then radix N/32; N = 2048 uses 32 x 8 x 8) runs its butterflies
+// in registers and exchanges data between passes through a swizzled
+// shared-memory buffer.  A block holds A teams = A antennas of one symbol.
+//
+// Input samples are staged by bulk asynchronous copies (cp.async.bulk, the
+// TMA engine) into a ring of shared-memory slots, one contiguous CP-stripped
+// symbol row per antenna, completion tracked by mbarriers; this is the CP
+// removal of Sec. II-B done as addressing.  Every wait on an mbarrier is
+// bounded: after ~2 s it latches LSAS_ERR_TIMEOUT and the block runs on
+// without waiting again, so a missing completion can never hang the GPU.
+//
+//   frame_kernel    one block per frame: pilot FFT -> LS estimate H (kept in
+//                   registers, written out) and the channel energy sum, then
+//                   every data symbol: FFT -> conj(H) Y -> sum over antennas
+//                   (shared-memory reduction) accumulated per subcarrier,
+//                   then z = sum / energy -> Gray slicer -> packed bits.
+//                   Sec. II-C (LS, MRC), Sec. III (conjugate and channel sum
+//                   formed once and reused for every data symbol).
+//   estimate_kernel one block per (frame, antenna chunk): pilot FFT -> H.
+//   fft_kernel      one block per (frame, antenna chunk): all symbols -> Y.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lsas {
+
+enum { kModeEstimate = 0, kModeDemod = 1, kModeRun = 2 };
+enum { kStOk = 0, kStTimeout = 6, kStDevice = 7 };
+
+constexpr int kMaxSlots = 4;
+constexpr int kSmemHeader = 128;     // mbarriers + flags
+constexpr int kMaxThresholds = 15;   // 256-QAM: 16 levels per axis
+
+struct KParams {
+  const void* in;        // [F][M][S][N+CP] samples (sc16 or fc32)
+  float2* H_out;         // [F][M][N]
+  const float2* H_in;    // [F][M][N] (demodulate)
+  uint8_t* bits;         // [F][D*N*q/8]
+  float2* eq;            // [F][D][N] or null
+  float2* Y_out;         // [F][M][S][N] (fft)
+  const float2* twN;     // W_N^i = exp(-2j pi i / N), i < N
+  const float2* xinv;    // conj(X[k]) / |X[k]|^2 / sqrt(N)
+  int* status;           // latched device status
+  int M, S, cp, pilot_idx, D;
+  int chunks;            // ceil(M / A)
+  int groups, dg;        // data-symbol groups per frame, symbols per group
+  int mode;              // kModeDemod or kModeRun (frame_kernel)
+  int use_tma, nslots;
+  int q, wbits, axes, nthr;
+  float inv_sqrtN;
+  float thr[kMaxThresholds];   // per-axis decision boundaries (float32)
+  float2 w32[32];              // W_32^e, small-DFT twiddles (param space)
+};
+
+// ---------------------------------------------------------------- geometry
+
+template <int LOG2N>
+struct Geo {
+  static constexpr int N = 1 << LOG2N;
+  static constexpr int L = N / 32;                       // threads per team
+  static constexpr int A = (N == 64) ? 16 : (N == 2048 ? 4 : 8);  // teams
+  static constexpr int T = A * L;                        // threads per block
+  static constexpr int SPAD = (L < 4) ? 4 : L;           // staging pad, samples
+  static constexpr int XS = N + 8;                       // exchange stride, float2
+};
+
+__host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
+
+struct Layout {
+  int team_stage;   // bytes per team per slot
+  int stage_off;    // slots
+  int ex_off;       // exchange / product buffer
+  int e_off;        // channel energy (float[N])
+  int p_off;        // combined sums (float2[dg][N])
+  int total;
+};
+
+__host__ __device__ inline Layout make_layout(int N, int A, int L, int bps,
+                                              int nslots, int dg, bool frame) {
+  Layout l;
+  const int spad = (L < 4) ? 4 : L;
+  l.team_stage = (N + spad) * bps;
+  l.stage_off = kSmemHeader;
+  l.ex_off = align_up(l.stage_off + nslots * A * l.team_stage, 128);
+  l.e_off = l.ex_off + A * (N + 8) * 8;
+  if (frame) {
+    l.p_off = align_up(l.e_off + N * 4, 128);
+    l.total = l.p_off + dg * N * 8;
+  } else {
+    l.p_off = l.e_off;
+    l.total = l.e_off;
+  }
+  return l;
+}
+
+#ifdef __CUDACC__
+
+// ------------------------------------------------------- PTX primitives
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src,
+                                          uint32_t bytes, uint32_t bar,
+                                          uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1], %2, [%3], %4;" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar), "l"(policy)
+      : "memory");
+}
+__device__ __forceinline__ uint64_t evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait: false after ~2 s without completion.
+static __device__ __noinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  for (;;) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (globaltimer() - t0 > 2000000000ull) return false;
+  }
+}
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// ------------------------------------------------------- complex helpers
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+  return make_float2(a.x + b.x, a.y + b.y);
+}
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+  return make_float2(a.x - b.x, a.y - b.y);
+}
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// conj(h) * y
+__device__ __forceinline__ float2 cmulc(float2 h, float2 y) {
+  return make_float2(h.x * y.x + h.y * y.y, h.x * y.y - h.y * y.x);
+}
+
+__host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x / 2); }
+__host__ __device__ constexpr int brev(int i, int bits) {
+  int r = 0;
+  for (int b = 0; b < bits; ++b) r |= ((i >> b) & 1) << (bits - 1 - b);
+  return r;
+}
+
+// b * W_32^e for a compile-time e in [0, 16)
+__device__ __forceinline__ float2 tw32(float2 b, int e, const KParams& p) {
+  constexpr float kS = 0.70710678118654752440f;  // 1/sqrt(2)
+  if (e == 0) return b;
+  if (e == 8) return make_float2(b.y, -b.x);                       // -j
+  if (e == 4) return make_float2((b.x + b.y) * kS, (b.y - b.x) * kS);   // (1-j)/sqrt2
+  if (e == 12) return make_float2((b.y - b.x) * kS, -(b.x + b.y) * kS); // (-1-j)/sqrt2
+  return cmul(b, p.w32[e]);
+}
+
+// One radix-2 decimation-in-time stage of half-span S on R registers.
+template <int R, int S>
+__device__ __forceinline__ void dit_stage(float2* a, const KParams& p) {
+#pragma unroll
+  for (int base = 0; base < R; base += 2 * S) {
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      const float2 b = tw32(a[base + i + S], i * (16 / S), p);
+      const float2 x = a[base + i];
+      a[base + i] = cadd(x, b);
+      a[base + i + S] = csub(x, b);
+    }
+  }
+}
+template <int R, int S>
+__device__ __forceinline__ void dit_stages(float2* a, const KParams& p) {
+  if constexpr (S < R) {
+    dit_stage<R, S>(a, p);
+    dit_stages<R, 2 * S>(a, p);
+  }
+}
+
+// In-register R-point DFT (R <= 32), natural order in and out: radix-2
+// decimation in time over bit-reversed register indices (free renaming).
+template <int R>
+__device__ __forceinline__ void dft(float2* v, const KParams& p) {
+  constexpr int LOGR = ilog2c(R);
+  float2 a[R];
+#pragma unroll
+  for (int i = 0; i < R; ++i) a[i] = v[brev(i, LOGR)];
+  dit_stages<R, 1>(a, p);
+#pragma unroll
+  for (int i = 0; i < R; ++i) v[i] = a[i];
+}
+
+// XOR swizzle of the exchange buffer: bits 0-4 of an index are flipped by
+// bits 5-9, which spreads both the row writes (t*32 + r) and the column
+// reads (j + 32 r) of the transposes over all banks.
+__device__ __forceinline__ int swz(int n) { return n ^ ((n >> 5) & 31); }
+
+template <int LOG2N>
+__device__ __forceinline__ void team_sync(int team) {
+  using G = Geo<LOG2N>;
+  if constexpr (G::L <= 32) {
+    __syncwarp();
+  } else {
+    named_sync(1 + team, G::L);
+  }
+}
+
+// Bin k held in register e after the last FFT pass, for team thread t.
+template <int LOG2N>
+__device__ __forceinline__ int bin_of(int t, int e) {
+  using G = Geo<LOG2N>;
+  if constexpr (G::N <= 1024) {
+    return t + (e / G::L) * G::L + 32 * (e % G::L);
+  } else {
+    return t + 64 * (e / 8) + 256 * (e % 8);
+  }
+}
+
+// Pass-1 inputs x[t + r L], r < 32, of one antenna-symbol row (N samples).
+template <int LOG2N, bool FC32>
+__device__ __forceinline__ void load_row(float2 (&v)[32], const void* row, int t,
+                                         bool from_global) {
+  using G = Geo<LOG2N>;
+  if constexpr (FC32) {
+    const float2* s = static_cast<const float2*>(row);
+#pragma unroll
+    for (int r = 0; r < 32; ++r) v[r] = from_global ? __ldg(s + t + r * G::L) : s[t + r * G::L];
+  } else {
+    const uint32_t* s = static_cast<const uint32_t*>(row);
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      const uint32_t w = from_global ? __ldg(s + t + r * G::L) : s[t + r * G::L];
+      v[r] = make_float2(static_cast<float>(static_cast<int16_t>(w & 0xffffu)),
+                         static_cast<float>(static_cast<int16_t>(w >> 16)));
+    }
+  }
+}
+
+// Remaining FFT passes of a team: v holds the radix-32 pass-1 outputs of
+// thread t (Y1[t*32 + r]); on return v[e] = Y[bin_of(t, e)] (unscaled).
+template <int LOG2N>
+__device__ __forceinline__ void team_fft_rest(float2 (&v)[32], float2* ex, int t,
+                                              int team, const KParams& p) {
+  using G = Geo<LOG2N>;
+  constexpr int L = G::L;
+#pragma unroll
+  for (int r = 0; r < 32; ++r) ex[swz(t * 32 + r)] = v[r];
+  team_sync<LOG2N>(team);
+  if constexpr (G::N <= 1024) {
+#pragma unroll
+    for (int i = 0; i < 32 / L; ++i) {
+      const int j = t + i * L;
+#pragma unroll
+      for (int r = 0; r < L; ++r) {
+        const float2 u = ex[swz(j + 32 * r)];
+        v[i * L + r] = (r == 0) ? u : cmul(u, __ldg(p.twN + (j & 31) * r));
+      }
+    }
+    team_sync<LOG2N>(team);
+#pragma unroll
+    for (int i = 0; i < 32 / L; ++i) dft<L>(v + i * L, p);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int j = t + 64 * i;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const float2 u = ex[swz(j + 256 * r)];
+        v[i * 8 + r] = (r == 0) ? u : cmul(u, __ldg(p.twN + 8 * (j & 31) * r));
+      }
+    }
+    team_sync<LOG2N>(team);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) dft<8>(v + i * 8, p);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int j = t + 64 * i;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) ex[swz((j >> 5) * 256 + (j & 31) + 32 * r)] = v[i * 8 + r];
+    }
+    team_sync<LOG2N>(team);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int j = t + 64 * i;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const float2 u = ex[swz(j + 256 * r)];
+        v[i * 8 + r] = (r == 0) ? u : cmul(u, __ldg(p.twN + j * r));
+      }
+    }
+    team_sync<LOG2N>(team);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) dft<8>(v + i * 8, p);
+  }
+}
+
+// ------------------------------------------------------- staging pipeline
+
+struct StepInfo {
+  int g, c, s, d;   // group, antenna chunk, symbol, data index (-1 = pilot)
+};
+
+// Steps of a frame block: group-major, chunk, then items (pilot first in
+// group 0 of the fused mode, then the group's data symbols).
+__device__ __forceinline__ int group_items(const KParams& p, int g) {
+  const int nd = min(p.dg, p.D - g * p.dg);
+  return nd + ((p.mode == kModeRun && g == 0) ? 1 : 0);
+}
+__device__ inline StepInfo frame_step(const KParams& p, int i) {
+  StepInfo si;
+  int g = 0;
+  for (;;) {
+    const int n = p.chunks * group_items(p, g);
+    if (i < n) break;
+    i -= n;
+    ++g;
+  }
+  const int items = group_items(p, g);
+  si.g = g;
+  si.c = i / items;
+  int it = i % items;
+  if (p.mode == kModeRun && g == 0) {
+    if (it == 0) {
+      si.s = p.pilot_idx;
+      si.d = -1;
+      return si;
+    }
+    --it;
+  }
+  si.d = g * p.dg + it;
+  si.s = si.d < p.pilot_idx ? si.d : si.d + 1;
+  return si;
+}
+
+template <int LOG2N, bool FC32>
+__device__ __forceinline__ const unsigned char* row_ptr(const KParams& p, int f, int m,
+                                                        int s) {
+  constexpr int bps = FC32 ? 8 : 4;
+  const size_t row = (static_cast<size_t>(f) * p.M + m) * p.S + s;
+  return static_cast<const unsigned char*>(p.in) +
+         (row * (Geo<LOG2N>::N + p.cp) + p.cp) * bps;
+}
+
+// Issue the bulk copies of one step (antennas of chunk c, symbol s) into a
+// slot; called by one thread.
+template <int LOG2N, bool FC32>
+__device__ __forceinline__ void issue_step(const KParams& p, int f, int c, int s,
+                                           unsigned char* slot, int team_stage,
+                                           uint32_t bar, uint64_t pol) {
+  using G = Geo<LOG2N>;
+  constexpr uint32_t bytes = G::N * (FC32 ? 8 : 4);
+  const int nvalid = min(G::A, p.M - c * G::A);
+  mbar_expect_tx(bar, bytes * nvalid);
+  for (int a = 0; a < nvalid; ++a)
+    bulk_load(smem_u32(slot + a * team_stage), row_ptr<LOG2N, FC32>(p, f, c * G::A + a, s),
+              bytes, bar, pol);
+}
+
+__device__ __forceinline__ void latch(int* status, int code) {
+  atomicCAS(status, 0, code);
+}
+
+// Wait for a slot; on timeout latch the status and stop waiting for good.
+__device__ __forceinline__ void wait_slot(uint32_t bar, uint32_t parity,
+                                          volatile int* abort_flag, int* status) {
+  if (*abort_flag) return;
+  if (!mbar_wait_bounded(bar, parity)) {
+    *abort_flag = 1;
+    latch(status, kStTimeout);
+  }
+}
+
+// Level of one axis value: boundaries at or below v (ties go up).
+__device__ __forceinline__ int axis_level(float v, const KParams& p) {
+  int l = 0;
+#pragma unroll
+  for (int b = 0; b < kMaxThresholds; ++b)
+    if (b < p.nthr) l += (v >= p.thr[b]) ? 1 : 0;
+  return l;
+}
+__device__ __forceinline__ uint32_t gray(int l) { return static_cast<uint32_t>(l ^ (l >> 1)); }
+
+// ======================================================= frame kernel
+
+template <int LOG2N, bool FC32>
+__global__ void __launch_bounds__(Geo<LOG2N>::T, 1) frame_kernel(const KParams p) {
+  using G = Geo<LOG2N>;
+  constexpr int N = G::N, L = G::L, A = G::A, T = G::T;
+  constexpr int BPT = N / T;  // bins per thread in the reduction
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int f = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int team = tid / L, t = tid % L;
+  const Layout lay = make_layout(N, A, L, FC32 ? 8 : 4, p.nslots, p.dg, true);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 64);
+  unsigned char* stage = smem + lay.stage_off;
+  float2* ex = reinterpret_cast<float2*>(smem + lay.ex_off);
+  float* E = reinterpret_cast<float*>(smem + lay.e_off);
+  float2* P = reinterpret_cast<float2*>(smem + lay.p_off);
+  float2* myex = ex + team * G::XS;
+  const int K = p.nslots;
+  const int slot_bytes = A * lay.team_stage;
+
+  int total = 0;
+  for (int g = 0; g < p.groups; ++g) total += p.chunks * group_items(p, g);
+
+  uint64_t pol = 0;
+  if (tid == 0) {
+    *abort_flag = 0;
+    if (p.use_tma) {
+      pol = evict_first_policy();
+      for (int s = 0; s < K; ++s) mbar_init(smem_u32(&bars[s]), 1);
+      fence_mbar_init();
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < BPT; ++b) E[tid + T * b] = 0.f;
+  __syncthreads();
+  if (tid == 0 && p.use_tma) {
+    for (int i = 0; i < K && i < total; ++i) {
+      const StepInfo si = frame_step(p, i);
+      issue_step<LOG2N, FC32>(p, f, si.c, si.s, stage + i * slot_bytes, lay.team_stage,
+                              smem_u32(&bars[i]), pol);
+    }
+  }
+
+  float2 h[32];
+  int step = 0;
+  for (int g = 0; g < p.groups; ++g) {
+    const int nd = min(p.dg, p.D - g * p.dg);
+    const int d0 = g * p.dg;
+#pragma unroll
+    for (int b = 0; b < BPT; ++b)
+      for (int dl = 0; dl < nd; ++dl) P[dl * N + tid + T * b] = make_float2(0.f, 0.f);
+
+    for (int c = 0; c < p.chunks; ++c) {
+      const int m = c * A + team;
+      const bool valid = m < p.M;
+      const size_t hrow = (static_cast<size_t>(f) * p.M + m) * N;
+      const bool need_fft_pilot = (p.mode == kModeRun && g == 0);
+      if (!need_fft_pilot) {
+        // channel from memory: given (demodulate) or written in group 0
+        const float2* Hs = (p.mode == kModeRun) ? p.H_out : p.H_in;
+#pragma unroll
+        for (int e = 0; e < 32; ++e)
+          h[e] = valid ? Hs[hrow + bin_of<LOG2N>(t, e)] : make_float2(0.f, 0.f);
+        if (g == 0) {
+          // channel energy of this chunk: |H|^2 summed over its antennas
+          __syncthreads();
+#pragma unroll
+          for (int e = 0; e < 32; ++e)
+            myex[swz(bin_of<LOG2N>(t, e))] = make_float2(h[e].x * h[e].x + h[e].y * h[e].y, 0.f);
+          __syncthreads();
+#pragma unroll
+          for (int b = 0; b < BPT; ++b) {
+            const int k = tid + T * b;
+            float s = 0.f;
+#pragma unroll
+            for (int a = 0; a < A; ++a) s += ex[a * G::XS + swz(k)].x;
+            E[k] += s;
+          }
+        }
+      }
+      const int items = group_items(p, g);
+      for (int it = 0; it < items; ++it, ++step) {
+        const bool is_pilot = need_fft_pilot && it == 0;
+        const int d = d0 + it - (need_fft_pilot ? 1 : 0);
+        const int s = is_pilot ? p.pilot_idx : (d < p.pilot_idx ? d : d + 1);
+        const int slot = step % K;
+        float2 v[32];
+        if (p.use_tma) {
+          wait_slot(smem_u32(&bars[slot]), (step / K) & 1, abort_flag, p.status);
+          if (valid) {
+            load_row<LOG2N, FC32>(v, stage + slot * slot_bytes + team * lay.team_stage, t, false);
+          } else {
+#pragma unroll
+            for (int r = 0; r < 32; ++r) v[r] = make_float2(0.f, 0.f);
+          }
+        } else {
+          if (valid) {
+            load_row<LOG2N, FC32>(v, row_ptr<LOG2N, FC32>(p, f, m, s), t, true);
+          } else {
+#pragma unroll
+            for (int r = 0; r < 32; ++r) v[r] = make_float2(0.f, 0.f);
+          }
+        }
+        dft<32>(v, p);
+        __syncthreads();  // staging slot consumed; products of the last step read
+        if (tid == 0 && p.use_tma && step + K < total) {
+          const StepInfo si = frame_step(p, step + K);
+          fence_proxy_async();
+          issue_step<LOG2N, FC32>(p, f, si.c, si.s, stage + slot * slot_bytes, lay.team_stage,
+                                  smem_u32(&bars[slot]), pol);
+        }
+        team_fft_rest<LOG2N>(v, myex, t, team, p);
+        if (is_pilot) {
+          // LS estimate H = Y conj(X) / |X|^2 (1/sqrt(N) folded into xinv)
+#pragma unroll
+          for (int e = 0; e < 32; ++e) {
+            const int k = bin_of<LOG2N>(t, e);
+            const float2 hv = cmul(v[e], __ldg(p.xinv + k));
+            h[e] = valid ? hv : make_float2(0.f, 0.f);
+            if (valid) p.H_out[hrow + k] = hv;
+            myex[swz(k)] = make_float2(h[e].x * h[e].x + h[e].y * h[e].y, 0.f);
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < 32; ++e) myex[swz(bin_of<LOG2N>(t, e))] = cmulc(h[e], v[e]);
+        }
+        __syncthreads();  // products of all antennas of the chunk are in place
+        if (is_pilot) {
+#pragma unroll
+          for (int b = 0; b < BPT; ++b) {
+            const int k = tid + T * b;
+            float s2 = 0.f;
+#pragma unroll
+            for (int a = 0; a < A; ++a) s2 += ex[a * G::XS + swz(k)].x;
+            E[k] += s2;
+          }
+        } else {
+          const int dl = d - d0;
+#pragma unroll
+          for (int b = 0; b < BPT; ++b) {
+            const int k = tid + T * b;
+            float2 s2 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int a = 0; a < A; ++a) s2 = cadd(s2, ex[a * G::XS + swz(k)]);
+            P[dl * N + k] = cadd(P[dl * N + k], s2);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (g == 0) {
+      // E -> 1 / (sqrt(N) E); zero or non-finite energy flags the frame
+#pragma unroll
+      for (int b = 0; b < BPT; ++b) {
+        const int k = tid + T * b;
+        const float e = E[k];
+        const bool ok = (e > 0.f) && (e <= 3.4028234663852886e38f);
+        if (!ok) latch(p.status, kStDevice);
+        E[k] = ok ? (1.0f / e) * p.inv_sqrtN : 0.f;
+      }
+      __syncthreads();
+    }
+    // demap + pack: 8 consecutive subcarriers -> q bytes
+    const int items8 = nd * (N / 8);
+    const size_t frame_bytes = static_cast<size_t>(p.D) * N * p.q / 8;
+    for (int it = tid; it < items8; it += T) {
+      const int dl = it / (N / 8);
+      const int k0 = (it % (N / 8)) * 8;
+      const int d = d0 + dl;
+      uint64_t acc = 0;
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        const int k = k0 + b;
+        const float ie = E[k];
+        const float2 sum = P[dl * N + k];
+        const float2 z = (ie != 0.f) ? make_float2(sum.x * ie, sum.y * ie) : make_float2(0.f, 0.f);
+        if (p.eq) p.eq[(static_cast<size_t>(f) * p.D + d) * N + k] = z;
+        uint32_t code = gray(axis_level(z.x, p));
+        if (p.axes == 2) code = (code << p.wbits) | gray(axis_level(z.y, p));
+        acc = (acc << p.q) | code;
+      }
+      uint8_t* dst = p.bits + f * frame_bytes + (static_cast<size_t>(d) * N + k0) * p.q / 8;
+      for (int j = 0; j < p.q; ++j) dst[j] = static_cast<uint8_t>(acc >> (8 * (p.q - 1 - j)));
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && p.use_tma && *abort_flag) {
+    // a wait gave up: give any copy still in flight a bounded chance to land
+    for (int s = 0; s < K && s < total; ++s) {
+      const int last = total - 1 - ((total - 1 - s) % K);
+      (void)mbar_wait_bounded(smem_u32(&bars[last % K]), (last / K) & 1);
+    }
+  }
+}
+
+// ======================================================= estimate kernel
+
+template <int LOG2N, bool FC32>
+__global__ void __launch_bounds__(Geo<LOG2N>::T) estimate_kernel(const KParams p) {
+  using G = Geo<LOG2N>;
+  constexpr int N = G::N, L = G::L, A = G::A;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int f = blockIdx.x / p.chunks;
+  const int c = blockIdx.x % p.chunks;
+  const int tid = threadIdx.x;
+  const int team = tid / L, t = tid % L;
+  const Layout lay = make_layout(N, A, L, FC32 ? 8 : 4, 1, 0, false);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 64);
+  unsigned char* stage = smem + lay.stage_off;
+  float2* myex = reinterpret_cast<float2*>(smem + lay.ex_off) + team * G::XS;
+  const int m = c * A + team;
+  const bool valid = m < p.M;
+  if (tid == 0) {
+    *abort_flag = 0;
+    if (p.use_tma) {
+      mbar_init(smem_u32(&bars[0]), 1);
+      fence_mbar_init();
+      issue_step<LOG2N, FC32>(p, f, c, p.pilot_idx, stage, lay.team_stage, smem_u32(&bars[0]),
+                              evict_first_policy());
+    }
+  }
+  __syncthreads();
+  float2 v[32];
+  if (p.use_tma) wait_slot(smem_u32(&bars[0]), 0, abort_flag, p.status);
+  if (valid) {
+    if (p.use_tma)
+      load_row<LOG2N, FC32>(v, stage + team * lay.team_stage, t, false);
+    else
+      load_row<LOG2N, FC32>(v, row_ptr<LOG2N, FC32>(p, f, m, p.pilot_idx), t, true);
+  } else {
+#pragma unroll
+    for (int r = 0; r < 32; ++r) v[r] = make_float2(0.f, 0.f);
+  }
+  dft<32>(v, p);
+  team_fft_rest<LOG2N>(v, myex, t, team, p);
+  if (valid) {
+    const size_t hrow = (static_cast<size_t>(f) * p.M + m) * N;
+#pragma unroll
+    for (int e = 0; e < 32; ++e) {
+      const int k = bin_of<LOG2N>(t, e);
+      p.H_out[hrow + k] = cmul(v[e], __ldg(p.xinv + k));
+    }
+  }
+}
+
+// ======================================================= fft kernel
+
+template <int LOG2N, bool FC32>
+__global__ void __launch_bounds__(Geo<LOG2N>::T) fft_kernel(const KParams p) {
+  using G = Geo<LOG2N>;
+  constexpr int N = G::N, L = G::L, A = G::A;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int f = blockIdx.x / p.chunks;
+  const int c = blockIdx.x % p.chunks;
+  const int tid = threadIdx.x;
+  const int team = tid / L, t = tid % L;
+  const Layout lay = make_layout(N, A, L, FC32 ? 8 : 4, p.nslots, 0, false);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 64);
+  unsigned char* stage = smem + lay.stage_off;
+  float2* myex = reinterpret_cast<float2*>(smem + lay.ex_off) + team * G::XS;
+  const int m = c * A + team;
+  const bool valid = m < p.M;
+  const int K = p.nslots;
+  const int slot_bytes = A * lay.team_stage;
+  uint64_t pol = 0;
+  if (tid == 0) {
+    *abort_flag = 0;
+    if (p.use_tma) {
+      pol = evict_first_policy();
+      for (int s = 0; s < K; ++s) mbar_init(smem_u32(&bars[s]), 1);
+      fence_mbar_init();
+      for (int s = 0; s < K && s < p.S; ++s)
+        issue_step<LOG2N, FC32>(p, f, c, s, stage + s * slot_bytes, lay.team_stage,
+                                smem_u32(&bars[s]), pol);
+    }
+  }
+  __syncthreads();
+  for (int s = 0; s < p.S; ++s) {
+    const int slot = s % K;
+    float2 v[32];
+    if (p.use_tma) wait_slot(smem_u32(&bars[slot]), (s / K) & 1, abort_flag, p.status);
+    if (valid) {
+      if (p.use_tma)
+        load_row<LOG2N, FC32>(v, stage + slot * slot_bytes + team * lay.team_stage, t, false);
+      else
+        load_row<LOG2N, FC32>(v, row_ptr<LOG2N, FC32>(p, f, m, s), t, true);
+    } else {
+#pragma unroll
+      for (int r = 0; r < 32; ++r) v[r] = make_float2(0.f, 0.f);
+    }
+    dft<32>(v, p);
+    __syncthreads();
+    if (tid == 0 && p.use_tma && s + K < p.S) {
+      fence_proxy_async();
+      issue_step<LOG2N, FC32>(p, f, c, s + K, stage + slot * slot_bytes, lay.team_stage,
+                              smem_u32(&bars[slot]), pol);
+    }
+    team_fft_rest<LOG2N>(v, myex, t, team, p);
+    if (valid) {
+      float2* out = p.Y_out + ((static_cast<size_t>(f) * p.M + m) * p.S + s) * N;
+#pragma unroll
+      for (int e = 0; e < 32; ++e)
+        out[bin_of<LOG2N>(t, e)] = make_float2(v[e].x * p.inv_sqrtN, v[e].y * p.inv_sqrtN);
+    }
+  }
+}
+
+#endif  // __CUDACC__
+
+// Host-side launch entry of one FFT length (defined in lsas_inst_n*.cu).
+using LaunchFn = cudaError_t (*)(int kind, bool fc32, const KParams& p, int grid,
+                                 int smem, cudaStream_t st);
+enum { kKindFrame = 0, kKindEstimate = 1, kKindFft = 2 };
+
+}  // namespace lsas

@@ -1,0 +1,556 @@
+// lsas_plan.cu -- host runtime and C ABI of liblsas (see include/lsas.h).
+//
+// A plan fixes one receiver configuration (M antennas, N subcarriers, CP,
+// S symbols, pilot position, QAM order, input format) and owns the device
+// tables its kernels read: the N-point twiddles W_N^i (computed here in
+// double precision and rounded once), the LS pilot inverse
+// conj(X)/|X|^2/sqrt(N) (Sec. II-C: LS is a division by the pilot), and a
+// status word the kernels latch device-side conditions into.  Every argument
+// is checked here before anything is enqueued.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/lsas.h"
+#include "lsas_kernels.cuh"
+
+namespace lsas {
+cudaError_t launch_n64(int, bool, const KParams&, int, int, cudaStream_t);
+cudaError_t launch_n128(int, bool, const KParams&, int, int, cudaStream_t);
+cudaError_t launch_n256(int, bool, const KParams&, int, int, cudaStream_t);
+cudaError_t launch_n512(int, bool, const KParams&, int, int, cudaStream_t);
+cudaError_t launch_n1024(int, bool, const KParams&, int, int, cudaStream_t);
+cudaError_t launch_n2048(int, bool, const KParams&, int, int, cudaStream_t);
+}  // namespace lsas
+
+using namespace lsas;
+
+namespace {
+
+constexpr int kSmemLimit = 232448;   // opt-in dynamic shared memory per block
+constexpr int kHostChunk = 64;       // frames per transfer chunk (host path)
+
+struct Geometry {
+  int A, L, T;
+  int nslots, groups, dg, smem_frame;
+  int smem_est, smem_fft, fft_slots;
+};
+
+}  // namespace
+
+struct lsas_plan_s {
+  int M, N, cp, S, pilot_idx, Q, q, D;
+  int wbits, axes, nthr;
+  float thr[kMaxThresholds];
+  lsas_input_fmt fmt;
+  int max_frames;
+  int device;
+  float2* d_twN = nullptr;
+  float2* d_xinv = nullptr;
+  int* d_status = nullptr;
+  float2 w32[32];
+  Geometry geo;
+  LaunchFn launch = nullptr;
+  // host-transfer staging (lsas_run_frame_host), allocated on first use
+  void* d_in_stage[2] = {nullptr, nullptr};
+  float2* d_H_stage[2] = {nullptr, nullptr};
+  uint8_t* d_bits_stage[2] = {nullptr, nullptr};
+  float2* d_eq_stage[2] = {nullptr, nullptr};
+  cudaStream_t up_stream = nullptr, down_stream = nullptr;
+  cudaEvent_t ev_up[2] = {nullptr, nullptr};
+  cudaEvent_t ev_k[2] = {nullptr, nullptr};
+  cudaEvent_t ev_down[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+int ilog2i(int x) {
+  int r = 0;
+  while ((1 << r) < x) ++r;
+  return r;
+}
+
+size_t in_bytes_per_frame(int M, int N, int cp, int S, lsas_input_fmt fmt) {
+  return static_cast<size_t>(M) * S * (N + cp) * (fmt == LSAS_IN_SC16 ? 4 : 8);
+}
+size_t bits_bytes_per_frame(int N, int S, int Q) {
+  return static_cast<size_t>(S - 1) * N * ilog2i(Q) / 8;
+}
+
+LaunchFn launcher_for(int N) {
+  switch (N) {
+    case 64: return launch_n64;
+    case 128: return launch_n128;
+    case 256: return launch_n256;
+    case 512: return launch_n512;
+    case 1024: return launch_n1024;
+    case 2048: return launch_n2048;
+    default: return nullptr;
+  }
+}
+
+// Antennas per step and team size for an FFT length (mirrors Geo<>).
+void team_shape(int N, int* A, int* L) {
+  *L = N / 32;
+  *A = (N == 64) ? 16 : (N == 2048 ? 4 : 8);
+}
+
+// Choose staging slots and data-symbol groups so that the fused kernel's
+// shared memory fits one block per SM.
+bool plan_geometry(int M, int N, int D, lsas_input_fmt fmt, Geometry* g) {
+  team_shape(N, &g->A, &g->L);
+  g->T = g->A * g->L;
+  const int bps = fmt == LSAS_IN_SC16 ? 4 : 8;
+  (void)M;
+  // fused frame kernel
+  int best_dg = 0, slots = 2;
+  for (slots = 2; slots >= 1; --slots) {
+    const Layout l0 = make_layout(N, g->A, g->L, bps, slots, 0, true);
+    const int room = kSmemLimit - l0.total;
+    best_dg = room / (N * 8);
+    if (best_dg >= 1) break;
+  }
+  if (best_dg < 1) return false;
+  g->groups = (D + best_dg - 1) / best_dg;
+  g->dg = (D + g->groups - 1) / g->groups;
+  g->nslots = slots;
+  while (g->nslots < kMaxSlots &&
+         make_layout(N, g->A, g->L, bps, g->nslots + 1, g->dg, true).total <= kSmemLimit)
+    ++g->nslots;
+  g->smem_frame = make_layout(N, g->A, g->L, bps, g->nslots, g->dg, true).total;
+  g->smem_est = make_layout(N, g->A, g->L, bps, 1, 0, false).total;
+  g->fft_slots = 2;
+  g->smem_fft = make_layout(N, g->A, g->L, bps, 2, 0, false).total;
+  return true;
+}
+
+void fill_w32(float2* w) {
+  for (int e = 0; e < 32; ++e) {
+    const double a = -2.0 * M_PI * e / 32.0;
+    w[e] = make_float2(static_cast<float>(std::cos(a)), static_cast<float>(std::sin(a)));
+  }
+}
+
+lsas_status upload_pilot(lsas_plan p, const double* re, const double* im) {
+  std::vector<float2> xi(p->N);
+  const double s = 1.0 / std::sqrt(static_cast<double>(p->N));
+  for (int k = 0; k < p->N; ++k) {
+    const double m2 = re[k] * re[k] + im[k] * im[k];
+    if (!(m2 > 0.0) || !std::isfinite(m2)) return LSAS_ERR_INVALID_ARG;
+    xi[k] = make_float2(static_cast<float>(re[k] / m2 * s), static_cast<float>(-im[k] / m2 * s));
+  }
+  if (cudaMemcpy(p->d_xinv, xi.data(), sizeof(float2) * p->N, cudaMemcpyHostToDevice) !=
+      cudaSuccess)
+    return LSAS_ERR_CUDA;
+  return LSAS_OK;
+}
+
+bool aligned16(const void* ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15u) == 0; }
+
+void base_params(lsas_plan p, KParams* k) {
+  std::memset(k, 0, sizeof(*k));
+  k->twN = p->d_twN;
+  k->xinv = p->d_xinv;
+  k->status = p->d_status;
+  k->M = p->M;
+  k->S = p->S;
+  k->cp = p->cp;
+  k->pilot_idx = p->pilot_idx;
+  k->D = p->D;
+  k->chunks = (p->M + p->geo.A - 1) / p->geo.A;
+  k->groups = p->geo.groups;
+  k->dg = p->geo.dg;
+  k->nslots = p->geo.nslots;
+  k->q = p->q;
+  k->wbits = p->wbits;
+  k->axes = p->axes;
+  k->nthr = p->nthr;
+  k->inv_sqrtN = static_cast<float>(1.0 / std::sqrt(static_cast<double>(p->N)));
+  for (int i = 0; i < kMaxThresholds; ++i) k->thr[i] = p->thr[i];
+  for (int i = 0; i < 32; ++i) k->w32[i] = p->w32[i];
+}
+
+// Bulk copies need 16-byte aligned rows: every row start
+// ((f M + m) S + s)(N + CP) + CP samples from a 16-byte aligned base.
+bool tma_ok(lsas_plan p, const void* d_in) {
+  const int bps = p->fmt == LSAS_IN_SC16 ? 4 : 8;
+  return aligned16(d_in) && ((p->N + p->cp) * bps) % 16 == 0 && (p->cp * bps) % 16 == 0;
+}
+
+lsas_status set_device(lsas_plan p) {
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) return LSAS_ERR_CUDA;
+  if (cur != p->device && cudaSetDevice(p->device) != cudaSuccess) return LSAS_ERR_CUDA;
+  return LSAS_OK;
+}
+
+lsas_status check_frames(lsas_plan p, int n_frames) {
+  if (n_frames < 0) return LSAS_ERR_INVALID_ARG;
+  if (n_frames > p->max_frames) return LSAS_ERR_CAPACITY;
+  return LSAS_OK;
+}
+
+lsas_status launch_frame(lsas_plan p, const void* d_in, int n_frames, float* d_H,
+                         const float* d_Hin, uint8_t* d_bits, float* d_eq, int mode,
+                         cudaStream_t st) {
+  KParams k;
+  base_params(p, &k);
+  k.in = d_in;
+  k.H_out = reinterpret_cast<float2*>(d_H);
+  k.H_in = reinterpret_cast<const float2*>(d_Hin);
+  k.bits = d_bits;
+  k.eq = reinterpret_cast<float2*>(d_eq);
+  k.mode = mode;
+  k.use_tma = tma_ok(p, d_in) ? 1 : 0;
+  if (p->launch(kKindFrame, p->fmt == LSAS_IN_FC32, k, n_frames, p->geo.smem_frame, st) !=
+      cudaSuccess)
+    return LSAS_ERR_CUDA;
+  return LSAS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lsas_status_str(lsas_status s) {
+  switch (s) {
+    case LSAS_OK: return "LSAS_OK";
+    case LSAS_ERR_INVALID_ARG: return "LSAS_ERR_INVALID_ARG";
+    case LSAS_ERR_UNSUPPORTED: return "LSAS_ERR_UNSUPPORTED";
+    case LSAS_ERR_OOM: return "LSAS_ERR_OOM";
+    case LSAS_ERR_CAPACITY: return "LSAS_ERR_CAPACITY";
+    case LSAS_ERR_CUDA: return "LSAS_ERR_CUDA";
+    case LSAS_ERR_TIMEOUT: return "LSAS_ERR_TIMEOUT";
+    case LSAS_ERR_DEVICE: return "LSAS_ERR_DEVICE";
+  }
+  return "LSAS_ERR_UNKNOWN";
+}
+
+lsas_status lsas_check_config(int M, int N, int cp_len, int n_sym, int pilot_idx,
+                              int qam_order) {
+  if (M < 1 || M > 256) return LSAS_ERR_INVALID_ARG;
+  if (!is_pow2(N) || N < 64 || N > 2048) return LSAS_ERR_INVALID_ARG;
+  if (cp_len < 0 || cp_len >= N) return LSAS_ERR_INVALID_ARG;
+  if (n_sym < 2 || n_sym > 64) return LSAS_ERR_INVALID_ARG;
+  if (pilot_idx < 0 || pilot_idx >= n_sym) return LSAS_ERR_INVALID_ARG;
+  if (qam_order != 2 && qam_order != 4 && qam_order != 16 && qam_order != 64 &&
+      qam_order != 256)
+    return LSAS_ERR_INVALID_ARG;
+  return LSAS_OK;
+}
+
+lsas_status lsas_frame_bytes(int M, int N, int cp_len, int n_sym, int qam_order,
+                             lsas_input_fmt fmt, size_t out[4]) {
+  if (!out) return LSAS_ERR_INVALID_ARG;
+  lsas_status s = lsas_check_config(M, N, cp_len, n_sym, 0, qam_order);
+  if (s != LSAS_OK) return s;
+  if (fmt != LSAS_IN_SC16 && fmt != LSAS_IN_FC32) return LSAS_ERR_INVALID_ARG;
+  out[0] = in_bytes_per_frame(M, N, cp_len, n_sym, fmt);
+  out[1] = static_cast<size_t>(M) * N * 8;
+  out[2] = bits_bytes_per_frame(N, n_sym, qam_order);
+  out[3] = static_cast<size_t>(n_sym - 1) * N * 8;
+  return LSAS_OK;
+}
+
+lsas_status lsas_plan_create(int M, int N, int cp_len, int n_sym, int pilot_idx,
+                             int qam_order, lsas_plan* out) {
+  if (!out) return LSAS_ERR_INVALID_ARG;
+  *out = nullptr;
+  lsas_status s = lsas_check_config(M, N, cp_len, n_sym, pilot_idx, qam_order);
+  if (s != LSAS_OK) return s;
+  lsas_plan p = new (std::nothrow) lsas_plan_s();
+  if (!p) return LSAS_ERR_OOM;
+  p->M = M;
+  p->N = N;
+  p->cp = cp_len;
+  p->S = n_sym;
+  p->pilot_idx = pilot_idx;
+  p->Q = qam_order;
+  p->q = ilog2i(qam_order);
+  p->D = n_sym - 1;
+  p->fmt = LSAS_IN_SC16;
+  p->max_frames = 1024;
+  // per-axis decision boundaries (2b - L) A of unit-energy Gray QAM
+  int L;
+  double A;
+  if (qam_order == 2) {
+    L = 2;
+    A = 1.0;
+    p->axes = 1;
+    p->wbits = 1;
+  } else {
+    L = static_cast<int>(std::lround(std::sqrt(static_cast<double>(qam_order))));
+    A = 1.0 / std::sqrt(2.0 * (qam_order - 1) / 3.0);
+    p->axes = 2;
+    p->wbits = ilog2i(L);
+  }
+  p->nthr = L - 1;
+  for (int b = 0; b < kMaxThresholds; ++b)
+    p->thr[b] = b < L - 1 ? static_cast<float>((2.0 * (b + 1) - L) * A) : 0.f;
+  fill_w32(p->w32);
+  p->launch = launcher_for(N);
+  if (!plan_geometry(M, N, p->D, p->fmt, &p->geo)) {
+    delete p;
+    return LSAS_ERR_UNSUPPORTED;
+  }
+  if (cudaGetDevice(&p->device) != cudaSuccess) {
+    delete p;
+    return LSAS_ERR_CUDA;
+  }
+  if (cudaMalloc(&p->d_twN, sizeof(float2) * N) != cudaSuccess ||
+      cudaMalloc(&p->d_xinv, sizeof(float2) * N) != cudaSuccess ||
+      cudaMalloc(&p->d_status, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    lsas_plan_destroy(p);
+    return LSAS_ERR_OOM;
+  }
+  std::vector<float2> tw(N);
+  for (int i = 0; i < N; ++i) {
+    const double a = -2.0 * M_PI * static_cast<double>(i) / N;
+    tw[i] = make_float2(static_cast<float>(std::cos(a)), static_cast<float>(std::sin(a)));
+  }
+  std::vector<double> one(N, 1.0), zero(N, 0.0);
+  if (cudaMemcpy(p->d_twN, tw.data(), sizeof(float2) * N, cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess ||
+      upload_pilot(p, one.data(), zero.data()) != LSAS_OK) {
+    lsas_plan_destroy(p);
+    return LSAS_ERR_CUDA;
+  }
+  *out = p;
+  return LSAS_OK;
+}
+
+lsas_status lsas_plan_set(lsas_plan p, lsas_input_fmt fmt, int max_frames) {
+  if (!p) return LSAS_ERR_INVALID_ARG;
+  if (fmt != LSAS_IN_SC16 && fmt != LSAS_IN_FC32) return LSAS_ERR_INVALID_ARG;
+  if (max_frames < 1) return LSAS_ERR_INVALID_ARG;
+  Geometry g;
+  if (!plan_geometry(p->M, p->N, p->D, fmt, &g)) return LSAS_ERR_UNSUPPORTED;
+  const bool realloc = fmt != p->fmt || max_frames != p->max_frames;
+  p->fmt = fmt;
+  p->max_frames = max_frames;
+  p->geo = g;
+  if (realloc) {
+    // host-transfer staging depends on both; drop it, the next host call
+    // allocates it again
+    if (set_device(p) != LSAS_OK) return LSAS_ERR_CUDA;
+    cudaDeviceSynchronize();
+    for (int i = 0; i < 2; ++i) {
+      cudaFree(p->d_in_stage[i]);
+      cudaFree(p->d_H_stage[i]);
+      cudaFree(p->d_bits_stage[i]);
+      cudaFree(p->d_eq_stage[i]);
+      p->d_in_stage[i] = nullptr;
+      p->d_H_stage[i] = nullptr;
+      p->d_bits_stage[i] = nullptr;
+      p->d_eq_stage[i] = nullptr;
+    }
+  }
+  return LSAS_OK;
+}
+
+lsas_status lsas_plan_set_pilot(lsas_plan p, const float* host_pilot_iq) {
+  if (!p || !host_pilot_iq) return LSAS_ERR_INVALID_ARG;
+  std::vector<double> re(p->N), im(p->N);
+  for (int k = 0; k < p->N; ++k) {
+    re[k] = host_pilot_iq[2 * k];
+    im[k] = host_pilot_iq[2 * k + 1];
+  }
+  if (set_device(p) != LSAS_OK) return LSAS_ERR_CUDA;
+  return upload_pilot(p, re.data(), im.data());
+}
+
+lsas_status lsas_fft(lsas_plan p, const void* d_in, int n_frames, float* d_Y, void* stream) {
+  if (!p) return LSAS_ERR_INVALID_ARG;
+  lsas_status s = check_frames(p, n_frames);
+  if (s != LSAS_OK) return s;
+  if (n_frames == 0) return LSAS_OK;
+  if (!d_in || !d_Y) return LSAS_ERR_INVALID_ARG;
+  if (set_device(p) != LSAS_OK) return LSAS_ERR_CUDA;
+  KParams k;
+  base_params(p, &k);
+  k.in = d_in;
+  k.Y_out = reinterpret_cast<float2*>(d_Y);
+  k.nslots = p->geo.fft_slots;
+  k.use_tma = tma_ok(p, d_in) ? 1 : 0;
+  const int grid = n_frames * k.chunks;
+  if (p->launch(kKindFft, p->fmt == LSAS_IN_FC32, k, grid, p->geo.smem_fft,
+                static_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return LSAS_ERR_CUDA;
+  return LSAS_OK;
+}
+
+lsas_status lsas_estimate(lsas_plan p, const void* d_in, int n_frames, float* d_H,
+                          void* stream) {
+  if (!p) return LSAS_ERR_INVALID_ARG;
+  lsas_status s = check_frames(p, n_frames);
+  if (s != LSAS_OK) return s;
+  if (n_frames == 0) return LSAS_OK;
+  if (!d_in || !d_H) return LSAS_ERR_INVALID_ARG;
+  if (set_device(p) != LSAS_OK) return LSAS_ERR_CUDA;
+  KParams k;
+  base_params(p, &k);
+  k.in = d_in;
+  k.H_out = reinterpret_cast<float2*>(d_H);
+  k.mode = kModeEstimate;
+  k.use_tma = tma_ok(p, d_in) ? 1 : 0;
+  const int grid = n_frames * k.chunks;
+  if (p->launch(kKindEstimate, p->fmt == LSAS_IN_FC32, k, grid, p->geo.smem_est,
+                static_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return LSAS_ERR_CUDA;
+  return LSAS_OK;
+}
+
+lsas_status lsas_demodulate(lsas_plan p, const void* d_in, const float* d_H, int n_frames,
+                            uint8_t* d_bits, float* d_eq, void* stream) {
+  if (!p) return LSAS_ERR_INVALID_ARG;
+  lsas_status s = check_frames(p, n_frames);
+  if (s != LSAS_OK) return s;
+  if (n_frames == 0) return LSAS_OK;
+  if (!d_in || !d_H || !d_bits) return LSAS_ERR_INVALID_ARG;
+  if (set_device(p) != LSAS_OK) return LSAS_ERR_CUDA;
+  return launch_frame(p, d_in, n_frames, nullptr, d_H, d_bits, d_eq, kModeDemod,
+                      static_cast<cudaStream_t>(stream));
+}
+
+lsas_status lsas_run_frame(lsas_plan p, const void* d_in, int n_frames, float* d_H,
+                           uint8_t* d_bits, float* d_eq, void* stream) {
+  if (!p) return LSAS_ERR_INVALID_ARG;
+  lsas_status s = check_frames(p, n_frames);
+  if (s != LSAS_OK) return s;
+  if (n_frames == 0) return LSAS_OK;
+  if (!d_in || !d_H || !d_bits) return LSAS_ERR_INVALID_ARG;
+  if (set_device(p) != LSAS_OK) return LSAS_ERR_CUDA;
+  return launch_frame(p, d_in, n_frames, d_H, nullptr, d_bits, d_eq, kModeRun,
+                      static_cast<cudaStream_t>(stream));
+}
+
+lsas_status lsas_run_frame_host(lsas_plan p, const void* h_in, int n_frames, float* h_H,
+                                uint8_t* h_bits, float* h_eq, void* stream) {
+  if (!p) return LSAS_ERR_INVALID_ARG;
+  lsas_status s = check_frames(p, n_frames);
+  if (s != LSAS_OK) return s;
+  if (n_frames == 0) return LSAS_OK;
+  if (!h_in || !h_H || !h_bits) return LSAS_ERR_INVALID_ARG;
+  if (set_device(p) != LSAS_OK) return LSAS_ERR_CUDA;
+  const int chunk = p->max_frames < kHostChunk ? p->max_frames : kHostChunk;
+  const size_t inb = in_bytes_per_frame(p->M, p->N, p->cp, p->S, p->fmt);
+  const size_t hb = static_cast<size_t>(p->M) * p->N * 8;
+  const size_t bb = bits_bytes_per_frame(p->N, p->S, p->Q);
+  const size_t eb = static_cast<size_t>(p->D) * p->N * 8;
+  if (!p->d_in_stage[0]) {
+    for (int i = 0; i < 2; ++i) {
+      if (cudaMalloc(&p->d_in_stage[i], inb * chunk) != cudaSuccess ||
+          cudaMalloc(&p->d_H_stage[i], hb * chunk) != cudaSuccess ||
+          cudaMalloc(&p->d_bits_stage[i], bb * chunk) != cudaSuccess ||
+          cudaMalloc(&p->d_eq_stage[i], eb * chunk) != cudaSuccess) {
+        cudaGetLastError();
+        return LSAS_ERR_OOM;
+      }
+    }
+    if (cudaStreamCreateWithFlags(&p->up_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&p->down_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return LSAS_ERR_CUDA;
+    for (int i = 0; i < 2; ++i)
+      if (cudaEventCreateWithFlags(&p->ev_up[i], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&p->ev_k[i], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&p->ev_down[i], cudaEventDisableTiming) != cudaSuccess)
+        return LSAS_ERR_CUDA;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // Chunk c uses staging buffer c % 2.  Uploads run on up_stream, kernels on
+  // the caller's stream, downloads on down_stream, so the upload of chunk
+  // c+1 and the download of chunk c-1 overlap the kernel of chunk c.  The
+  // upload into a buffer waits for the download of the chunk that used it
+  // last, which itself waited for that chunk's kernel.
+  const int nchunks = (n_frames + chunk - 1) / chunk;
+  for (int c = 0; c < nchunks; ++c) {
+    const int b = c % 2;
+    const int f0 = c * chunk;
+    const int nf = (n_frames - f0) < chunk ? (n_frames - f0) : chunk;
+    if (c >= 2 && cudaStreamWaitEvent(p->up_stream, p->ev_down[b], 0) != cudaSuccess)
+      return LSAS_ERR_CUDA;
+    if (cudaMemcpyAsync(p->d_in_stage[b], static_cast<const unsigned char*>(h_in) + inb * f0,
+                        inb * nf, cudaMemcpyHostToDevice, p->up_stream) != cudaSuccess ||
+        cudaEventRecord(p->ev_up[b], p->up_stream) != cudaSuccess ||
+        cudaStreamWaitEvent(st, p->ev_up[b], 0) != cudaSuccess)
+      return LSAS_ERR_CUDA;
+    lsas_status r = launch_frame(p, p->d_in_stage[b], nf, reinterpret_cast<float*>(p->d_H_stage[b]),
+                                 nullptr, p->d_bits_stage[b],
+                                 h_eq ? reinterpret_cast<float*>(p->d_eq_stage[b]) : nullptr,
+                                 kModeRun, st);
+    if (r != LSAS_OK) return r;
+    if (cudaEventRecord(p->ev_k[b], st) != cudaSuccess ||
+        cudaStreamWaitEvent(p->down_stream, p->ev_k[b], 0) != cudaSuccess)
+      return LSAS_ERR_CUDA;
+    if (cudaMemcpyAsync(h_H + hb / 4 * f0, p->d_H_stage[b], hb * nf, cudaMemcpyDeviceToHost,
+                        p->down_stream) != cudaSuccess ||
+        cudaMemcpyAsync(h_bits + bb * f0, p->d_bits_stage[b], bb * nf, cudaMemcpyDeviceToHost,
+                        p->down_stream) != cudaSuccess)
+      return LSAS_ERR_CUDA;
+    if (h_eq && cudaMemcpyAsync(h_eq + eb / 4 * f0, p->d_eq_stage[b], eb * nf,
+                                cudaMemcpyDeviceToHost, p->down_stream) != cudaSuccess)
+      return LSAS_ERR_CUDA;
+    if (cudaEventRecord(p->ev_down[b], p->down_stream) != cudaSuccess) return LSAS_ERR_CUDA;
+  }
+  if (cudaStreamSynchronize(p->down_stream) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return LSAS_ERR_CUDA;
+  return LSAS_OK;
+}
+
+lsas_status lsas_plan_sync(lsas_plan p, void* stream) {
+  if (!p) return LSAS_ERR_INVALID_ARG;
+  if (set_device(p) != LSAS_OK) return LSAS_ERR_CUDA;
+  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return LSAS_ERR_CUDA;
+  int st = 0;
+  if (cudaMemcpy(&st, p->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess)
+    return LSAS_ERR_CUDA;
+  return static_cast<lsas_status>(st);
+}
+
+lsas_status lsas_plan_info(lsas_plan p, int out[8]) {
+  if (!p || !out) return LSAS_ERR_INVALID_ARG;
+  out[0] = p->geo.A;
+  out[1] = p->geo.T;
+  out[2] = p->geo.smem_frame;
+  out[3] = p->geo.groups;
+  out[4] = p->geo.nslots;
+  const int bps = p->fmt == LSAS_IN_SC16 ? 4 : 8;
+  out[5] = (((p->N + p->cp) * bps) % 16 == 0 && (p->cp * bps) % 16 == 0) ? 1 : 0;
+  out[6] = static_cast<int>(p->fmt);
+  out[7] = p->max_frames;
+  return LSAS_OK;
+}
+
+lsas_status lsas_plan_destroy(lsas_plan p) {
+  if (!p) return LSAS_ERR_INVALID_ARG;
+  if (set_device(p) == LSAS_OK) cudaDeviceSynchronize();
+  cudaFree(p->d_twN);
+  cudaFree(p->d_xinv);
+  cudaFree(p->d_status);
+  for (int i = 0; i < 2; ++i) {
+    cudaFree(p->d_in_stage[i]);
+    cudaFree(p->d_H_stage[i]);
+    cudaFree(p->d_bits_stage[i]);
+    cudaFree(p->d_eq_stage[i]);
+  }
+  if (p->up_stream) cudaStreamDestroy(p->up_stream);
+  if (p->down_stream) cudaStreamDestroy(p->down_stream);
+  for (int i = 0; i < 2; ++i) {
+    if (p->ev_up[i]) cudaEventDestroy(p->ev_up[i]);
+    if (p->ev_k[i]) cudaEventDestroy(p->ev_k[i]);
+    if (p->ev_down[i]) cudaEventDestroy(p->ev_down[i]);
+  }
+  delete p;
+  return LSAS_OK;
+}
+
+}  // extern "C"

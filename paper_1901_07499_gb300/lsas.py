@@ -1,0 +1,231 @@
+"""ctypes binding of liblsas (include/lsas.h).
+
+Argument marshalling only: every step of the receiver runs in the CUDA
+library.  The raw entry points are exposed under their C names
+(``lsas_plan_create``, ``lsas_estimate`` ...); :class:`Plan` wraps them for
+PyTorch tensors, which supply device memory and streams.  Importing this
+module fails loudly when the library has not been built: there is no other
+implementation to fall back to.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+from .build import LIB
+
+if not os.path.exists(LIB):
+    raise ImportError(
+        f"liblsas is not built ({LIB} missing); run "
+        "`python -c 'import __graft_entry__ as g; g.build()'` first")
+
+_lib = C.CDLL(LIB)
+
+LSAS_OK = 0
+LSAS_ERR_INVALID_ARG = 1
+LSAS_ERR_UNSUPPORTED = 2
+LSAS_ERR_OOM = 3
+LSAS_ERR_CAPACITY = 4
+LSAS_ERR_CUDA = 5
+LSAS_ERR_TIMEOUT = 6
+LSAS_ERR_DEVICE = 7
+LSAS_IN_SC16 = 0
+LSAS_IN_FC32 = 1
+
+_vp, _i, _f = C.c_void_p, C.c_int, C.c_float
+
+
+def _proto(name, args, res=C.c_int):
+    fn = getattr(_lib, name)
+    fn.argtypes = args
+    fn.restype = res
+    return fn
+
+
+lsas_status_str = _proto("lsas_status_str", [_i], C.c_char_p)
+lsas_check_config = _proto("lsas_check_config", [_i] * 6)
+lsas_frame_bytes = _proto("lsas_frame_bytes", [_i] * 6 + [C.POINTER(C.c_size_t)])
+lsas_plan_create = _proto("lsas_plan_create", [_i] * 6 + [C.POINTER(_vp)])
+lsas_plan_set = _proto("lsas_plan_set", [_vp, _i, _i])
+lsas_plan_set_pilot = _proto("lsas_plan_set_pilot", [_vp, C.POINTER(_f)])
+lsas_fft = _proto("lsas_fft", [_vp, _vp, _i, _vp, _vp])
+lsas_estimate = _proto("lsas_estimate", [_vp, _vp, _i, _vp, _vp])
+lsas_demodulate = _proto("lsas_demodulate", [_vp, _vp, _vp, _i, _vp, _vp, _vp])
+lsas_run_frame = _proto("lsas_run_frame", [_vp, _vp, _i, _vp, _vp, _vp, _vp])
+lsas_run_frame_host = _proto("lsas_run_frame_host", [_vp, _vp, _i, _vp, _vp, _vp, _vp])
+lsas_plan_sync = _proto("lsas_plan_sync", [_vp, _vp])
+lsas_plan_info = _proto("lsas_plan_info", [_vp, C.POINTER(_i)])
+lsas_plan_destroy = _proto("lsas_plan_destroy", [_vp])
+
+EXPORTED = ["lsas_status_str", "lsas_check_config", "lsas_frame_bytes",
+            "lsas_plan_create", "lsas_plan_set", "lsas_plan_set_pilot",
+            "lsas_fft", "lsas_estimate", "lsas_demodulate", "lsas_run_frame",
+            "lsas_run_frame_host", "lsas_plan_sync", "lsas_plan_info",
+            "lsas_plan_destroy"]
+
+
+class LsasError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {lsas_status_str(code).decode()}")
+
+
+def check(code: int, what: str = "lsas") -> None:
+    if code != LSAS_OK:
+        raise LsasError(code, what)
+
+
+def frame_bytes(M, N, cp, n_sym, qam_order, fmt="sc16"):
+    out = (C.c_size_t * 4)()
+    check(lsas_frame_bytes(M, N, cp, n_sym, qam_order, _fmt(fmt), out), "lsas_frame_bytes")
+    return tuple(int(v) for v in out)
+
+
+def _fmt(fmt) -> int:
+    if fmt in ("sc16", LSAS_IN_SC16):
+        return LSAS_IN_SC16
+    if fmt in ("fc32", LSAS_IN_FC32):
+        return LSAS_IN_FC32
+    raise ValueError(f"unknown input format {fmt!r}")
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream or None
+
+
+class Plan:
+    """A receiver configuration bound to the current CUDA device.
+
+    Tensors: input ``[F][M][S*(N+CP)][2]`` int16 (sc16) or float32 (fc32);
+    H and eq complex64; bits uint8 ``[F][D*N*q/8]``.
+    """
+
+    def __init__(self, M: int, N: int, cp: int, n_sym: int, pilot_idx: int = 0,
+                 qam_order: int = 4, fmt: str = "sc16", max_frames: int = 1024,
+                 pilot=None):
+        self.M, self.N, self.cp, self.S = M, N, cp, n_sym
+        self.pilot_idx, self.Q, self.fmt = pilot_idx, qam_order, fmt
+        self.D = n_sym - 1
+        self.q = int(round(np.log2(qam_order)))
+        h = _vp()
+        check(lsas_plan_create(M, N, cp, n_sym, pilot_idx, qam_order, C.byref(h)),
+              "lsas_plan_create")
+        self._h = h
+        check(lsas_plan_set(self._h, _fmt(fmt), max_frames), "lsas_plan_set")
+        self.max_frames = max_frames
+        if pilot is not None:
+            self.set_pilot(pilot)
+
+    # ---- configuration
+    def set_pilot(self, pilot) -> None:
+        x = np.asarray(pilot, dtype=np.complex128)
+        iq = np.ascontiguousarray(np.stack([x.real, x.imag], -1).astype(np.float32))
+        check(lsas_plan_set_pilot(self._h, iq.ctypes.data_as(C.POINTER(_f))),
+              "lsas_plan_set_pilot")
+
+    def info(self) -> dict:
+        out = (_i * 8)()
+        check(lsas_plan_info(self._h, out), "lsas_plan_info")
+        keys = ["antennas_per_step", "threads", "smem_bytes", "groups", "slots",
+                "tma", "fmt", "max_frames"]
+        return dict(zip(keys, list(out)))
+
+    @property
+    def handle(self):
+        return self._h
+
+    # ---- buffers
+    def _frames(self, x) -> int:
+        if not x.is_contiguous():
+            raise ValueError("input must be contiguous")
+        want = np.int16 if self.fmt == "sc16" else np.float32
+        import torch
+        tdt = torch.int16 if want == np.int16 else torch.float32
+        if x.dtype != tdt:
+            raise TypeError(f"input dtype must be {tdt} for {self.fmt}")
+        per = self.M * self.S * (self.N + self.cp) * 2
+        if x.numel() % per:
+            raise ValueError("input size is not a whole number of frames")
+        return x.numel() // per
+
+    def empty_H(self, F, device="cuda"):
+        import torch
+        return torch.empty((F, self.M, self.N), dtype=torch.complex64, device=device)
+
+    def empty_bits(self, F, device="cuda"):
+        import torch
+        return torch.empty((F, self.D * self.N * self.q // 8), dtype=torch.uint8, device=device)
+
+    def empty_eq(self, F, device="cuda"):
+        import torch
+        return torch.empty((F, self.D, self.N), dtype=torch.complex64, device=device)
+
+    # ---- operations
+    def fft(self, x, Y=None, stream=None):
+        import torch
+        F = self._frames(x)
+        if Y is None:
+            Y = torch.empty((F, self.M, self.S, self.N), dtype=torch.complex64, device=x.device)
+        check(lsas_fft(self._h, _ptr(x), F, _ptr(Y), _stream(stream)), "lsas_fft")
+        return Y
+
+    def estimate(self, x, H=None, stream=None):
+        F = self._frames(x)
+        H = self.empty_H(F, x.device) if H is None else H
+        check(lsas_estimate(self._h, _ptr(x), F, _ptr(H), _stream(stream)), "lsas_estimate")
+        return H
+
+    def demodulate(self, x, H, bits=None, eq=None, want_eq=False, stream=None):
+        F = self._frames(x)
+        bits = self.empty_bits(F, x.device) if bits is None else bits
+        if eq is None and want_eq:
+            eq = self.empty_eq(F, x.device)
+        check(lsas_demodulate(self._h, _ptr(x), _ptr(H), F, _ptr(bits), _ptr(eq),
+                              _stream(stream)), "lsas_demodulate")
+        return bits, eq
+
+    def run_frame(self, x, H=None, bits=None, eq=None, want_eq=False, stream=None):
+        F = self._frames(x)
+        H = self.empty_H(F, x.device) if H is None else H
+        bits = self.empty_bits(F, x.device) if bits is None else bits
+        if eq is None and want_eq:
+            eq = self.empty_eq(F, x.device)
+        check(lsas_run_frame(self._h, _ptr(x), F, _ptr(H), _ptr(bits), _ptr(eq),
+                             _stream(stream)), "lsas_run_frame")
+        return H, bits, eq
+
+    def run_frame_host(self, x, H, bits, eq=None, stream=None):
+        """Host (pinned) tensors in and out; copies happen inside the call."""
+        F = self._frames(x)
+        check(lsas_run_frame_host(self._h, _ptr(x), F, _ptr(H), _ptr(bits), _ptr(eq),
+                                  _stream(stream)), "lsas_run_frame_host")
+        return H, bits, eq
+
+    def sync(self, stream=None) -> None:
+        """Synchronise and raise if a device-side condition was latched."""
+        check(lsas_plan_sync(self._h, _stream(stream)), "device status")
+
+    def sync_status(self, stream=None) -> int:
+        return lsas_plan_sync(self._h, _stream(stream))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lsas_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,259 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle
+on the same seeded synthetic frames.
+
+Covers the whole path (lsas_run_frame), each step alone (lsas_fft = CP
+removal + FFT, lsas_estimate = LS, lsas_demodulate = MRC + demap with the
+oracle's channel), the antenna-count x FFT-length grid, odd shapes (M not a
+multiple of the antennas per block, M = 1, pilot not first, the paper's
+CP 72, a CP that defeats the bulk-copy alignment, BPSK and 256-QAM, float32
+input), full-scale amplitudes, the zero-energy status, argument errors,
+the host-buffer entry point, determinism, and the 1000-frame 64-antenna
+N=1024 workload in the launch configuration the benchmark times.
+"""
+
+import numpy as np
+import pytest
+
+import synth
+from synth.frames import FrameConfig, sweep_config, paper_config
+from tests.parity_util import (check_frame_outputs, oracle_run, rel_err,
+                               to_torch_frames, unpack, TOL_REL)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_1901_07499_gb300.lsas as lsas
+    return lsas
+
+
+def make_plan(L, cfg, max_frames=1024):
+    return L.Plan(cfg.M, cfg.N, cfg.cp, cfg.S, cfg.pilot_idx, cfg.Q, fmt=cfg.fmt,
+                  max_frames=max_frames, pilot=synth.frames.pilot_sequence(cfg))
+
+
+def run_and_check(L, cfg, F=None, want_eq=True, pilot=None):
+    import torch
+    ids = range(F if F is not None else cfg.F)
+    b = synth.generate(cfg, frame_ids=ids, pilot=pilot)
+    plan = make_plan(L, cfg)
+    if pilot is not None:
+        plan.set_pilot(pilot)
+    x = to_torch_frames(b)
+    H, bits, eq = plan.run_frame(x, want_eq=want_eq)
+    plan.sync()
+    ref = oracle_run(cfg, b)
+    return check_frame_outputs(cfg, ref, H.cpu().numpy(), bits.cpu().numpy(),
+                               eq.cpu().numpy() if eq is not None else None), plan
+
+
+def test_tiny_config_full(L):
+    cfg = synth.CONFIGS["tiny"]
+    stats, plan = run_and_check(L, cfg)
+    assert plan.info()["tma"] == 1
+
+
+def test_scale_config_small_batch(L):
+    run_and_check(L, synth.CONFIGS["scale"], F=3)
+
+
+def test_precision_config_small_batch(L):
+    run_and_check(L, synth.CONFIGS["precision"], F=2)
+
+
+@pytest.mark.parametrize("M", [8, 16, 32, 64, 128])
+@pytest.mark.parametrize("N", [64, 256, 512, 1024, 2048])
+def test_sweep_grid(L, M, N):
+    run_and_check(L, sweep_config(M, N), F=2)
+
+
+@pytest.mark.parametrize("N", [128])
+@pytest.mark.parametrize("M", [1, 3, 13, 100])
+def test_odd_antenna_counts(L, M, N):
+    run_and_check(L, sweep_config(M, N).replace(M=M), F=3)
+
+
+@pytest.mark.parametrize("M,N", [(16, 64), (16, 1024), (5, 1024)])
+def test_paper_shapes(L, M, N):
+    run_and_check(L, paper_config(M, N, F=2))
+
+
+@pytest.mark.parametrize("pilot_idx", [1, 6, 13])
+def test_pilot_not_first(L, pilot_idx):
+    run_and_check(L, sweep_config(24, 512).replace(pilot_idx=pilot_idx), F=2)
+
+
+@pytest.mark.parametrize("Q", [2, 4, 64, 256])
+def test_qam_orders(L, Q):
+    run_and_check(L, sweep_config(16, 256).replace(Q=Q, snr_db=40.0), F=2)
+
+
+@pytest.mark.parametrize("cp", [17, 1, 0])
+def test_unaligned_cp_falls_back_to_plain_loads(L, cp):
+    cfg = sweep_config(12, 256).replace(cp=cp, taps=min(8, cp + 1))
+    stats, plan = run_and_check(L, cfg, F=2)
+    assert plan.info()["tma"] == (1 if (cp * 4) % 16 == 0 else 0)
+
+
+@pytest.mark.parametrize("N", [64, 1024, 2048])
+def test_fc32_input(L, N):
+    run_and_check(L, sweep_config(10, N).replace(fmt="fc32"), F=2)
+
+
+def test_complex_pilot(L):
+    cfg = sweep_config(8, 256)
+    rng = np.random.default_rng(5)
+    pilot = np.exp(2j * np.pi * rng.random(256)) * (0.5 + rng.random(256))
+    run_and_check(L, cfg, F=2, pilot=pilot)
+
+
+# ------------------------------------------------------- single steps ----
+
+@pytest.mark.parametrize("N", [64, 128, 256, 512, 1024, 2048])
+def test_fft_alone(L, N):
+    cfg = sweep_config(9, N).replace(S=5)
+    b = synth.generate(cfg, frame_ids=range(2))
+    plan = make_plan(L, cfg)
+    Y = plan.fft(to_torch_frames(b))
+    plan.sync()
+    ref = oracle_run(cfg, b, keep_Y=True)
+    e = rel_err(Y.cpu().numpy(), ref.Y, axes=(1, 2, 3))
+    assert e.max() <= TOL_REL, e
+
+
+def test_fft_full_scale_amplitudes(L):
+    cfg = sweep_config(8, 1024).replace(S=3)
+    b = synth.generate(cfg, frame_ids=range(1))
+    rng = np.random.default_rng(1)
+    b.frames[...] = rng.choice(np.array([-32767, 32767], np.int16), size=b.frames.shape)
+    plan = make_plan(L, cfg)
+    Y = plan.fft(to_torch_frames(b))
+    plan.sync()
+    ref = oracle_run(cfg, b, keep_Y=True)
+    assert rel_err(Y.cpu().numpy(), ref.Y, axes=(1, 2, 3)).max() <= TOL_REL
+
+
+@pytest.mark.parametrize("M,N", [(8, 64), (64, 1024), (13, 2048)])
+def test_estimate_alone(L, M, N):
+    cfg = sweep_config(M, N)
+    b = synth.generate(cfg, frame_ids=range(2))
+    plan = make_plan(L, cfg)
+    H = plan.estimate(to_torch_frames(b))
+    plan.sync()
+    ref = oracle_run(cfg, b)
+    assert rel_err(H.cpu().numpy(), ref.H, axes=(1, 2)).max() <= TOL_REL
+
+
+@pytest.mark.parametrize("M,N", [(8, 64), (64, 1024), (20, 2048)])
+def test_demodulate_with_oracle_channel(L, M, N):
+    import torch
+    cfg = sweep_config(M, N)
+    b = synth.generate(cfg, frame_ids=range(2))
+    ref = oracle_run(cfg, b)
+    plan = make_plan(L, cfg)
+    Hd = torch.from_numpy(ref.H.astype(np.complex64)).cuda()
+    bits, eq = plan.demodulate(to_torch_frames(b), Hd, want_eq=True)
+    plan.sync()
+    check_frame_outputs(cfg, ref, None, bits.cpu().numpy(), eq.cpu().numpy(), check_H=False)
+
+
+def test_zero_channel_energy_latches_status(L):
+    import torch
+    cfg = sweep_config(8, 256)
+    b = synth.generate(cfg, frame_ids=range(2))
+    ref = oracle_run(cfg, b)
+    H = ref.H.astype(np.complex64).copy()
+    H[1, :, 17] = 0
+    plan = make_plan(L, cfg)
+    bits, eq = plan.demodulate(to_torch_frames(b), torch.from_numpy(H).cuda(), want_eq=True)
+    assert plan.sync_status() == L.LSAS_ERR_DEVICE
+    assert plan.sync_status() == L.LSAS_OK          # cleared by the read
+    z = eq.cpu().numpy()
+    assert np.all(z[1, :, 17] == 0)
+    ref2 = oracle_run(cfg, b, H_given=H.astype(np.complex128))
+    assert ref2.bad[1] and not ref2.bad[0]
+    got = unpack(bits.cpu().numpy(), cfg.D, cfg.N, cfg.q)
+    assert np.array_equal(got[1, :, 17], ref2.bits[1, :, 17])
+
+
+def test_argument_errors(L):
+    import ctypes as C
+    import torch
+    cfg = sweep_config(8, 256)
+    plan = make_plan(L, cfg, max_frames=4)
+    x = torch.zeros((5, 8, cfg.T, 2), dtype=torch.int16, device="cuda")
+    H = plan.empty_H(5)
+    bits = plan.empty_bits(5)
+    s = torch.cuda.current_stream().cuda_stream
+    h = plan.handle
+    assert L.lsas_run_frame(h, x.data_ptr(), 5, H.data_ptr(), bits.data_ptr(), None, s) == L.LSAS_ERR_CAPACITY
+    assert L.lsas_run_frame(h, x.data_ptr(), 0, H.data_ptr(), bits.data_ptr(), None, s) == L.LSAS_OK
+    assert L.lsas_run_frame(h, None, 2, H.data_ptr(), bits.data_ptr(), None, s) == L.LSAS_ERR_INVALID_ARG
+    assert L.lsas_run_frame(h, x.data_ptr(), 2, None, bits.data_ptr(), None, s) == L.LSAS_ERR_INVALID_ARG
+    assert L.lsas_run_frame(h, x.data_ptr(), -1, H.data_ptr(), bits.data_ptr(), None, s) == L.LSAS_ERR_INVALID_ARG
+    bad = np.zeros(2 * 256, np.float32)
+    assert L.lsas_plan_set_pilot(h, bad.ctypes.data_as(C.POINTER(C.c_float))) == L.LSAS_ERR_INVALID_ARG
+    assert L.lsas_plan_set(h, 7, 4) == L.LSAS_ERR_INVALID_ARG
+    out = C.c_void_p()
+    assert L.lsas_plan_create(8, 1000, 16, 4, 0, 16, C.byref(out)) == L.LSAS_ERR_INVALID_ARG
+    assert out.value is None
+    assert plan.sync_status() == L.LSAS_OK
+
+
+def test_host_entry_point_matches_device_path(L):
+    import torch
+    cfg = sweep_config(32, 512)
+    b = synth.generate(cfg, frame_ids=range(150))   # > 2 transfer chunks
+    plan = make_plan(L, cfg)
+    xd = to_torch_frames(b)
+    H, bits, eq = plan.run_frame(xd, want_eq=True)
+    plan.sync()
+    xh = torch.from_numpy(b.frames).pin_memory()
+    Hh = torch.empty(H.shape, dtype=H.dtype).pin_memory()
+    bh = torch.empty(bits.shape, dtype=bits.dtype).pin_memory()
+    eh = torch.empty(eq.shape, dtype=eq.dtype).pin_memory()
+    plan.run_frame_host(xh, Hh, bh, eh)
+    plan.sync()
+    assert torch.equal(Hh, H.cpu()) and torch.equal(bh, bits.cpu()) and torch.equal(eh, eq.cpu())
+
+
+def test_deterministic(L):
+    import torch
+    cfg = sweep_config(64, 1024)
+    b = synth.generate(cfg, frame_ids=range(3))
+    plan = make_plan(L, cfg)
+    x = to_torch_frames(b)
+    r1 = plan.run_frame(x, want_eq=True)
+    r2 = plan.run_frame(x, want_eq=True)
+    plan.sync()
+    assert all(torch.equal(a, c) for a, c in zip(r1, r2))
+
+
+# ------------------------------------------------ full-size workload ----
+
+def test_scale_workload_full_size_sampled(L):
+    """1000 frames of 64 antennas x 1024 subcarriers in one launch, the
+    configuration the benchmark times: a pool of seeded frames is tiled to
+    1000 frames; sampled frames are checked against the oracle, and every
+    frame against the first copy of its pool frame."""
+    import torch
+    cfg = synth.CONFIGS["scale"]
+    pool = 8
+    b = synth.generate(cfg, frame_ids=range(pool))
+    plan = make_plan(L, cfg)
+    x = to_torch_frames(b).repeat(cfg.F // pool, 1, 1, 1)
+    H, bits, eq = plan.run_frame(x, want_eq=True)
+    plan.sync()
+    for f in (0, 517, 999):
+        p = f % pool
+        one = synth.generate(cfg, frame_ids=[p])
+        ref = oracle_run(cfg, one)
+        check_frame_outputs(cfg, ref, H[f:f + 1].cpu().numpy(), bits[f:f + 1].cpu().numpy(),
+                            eq[f:f + 1].cpu().numpy())
+    Hr = H.view(cfg.F // pool, pool, cfg.M, cfg.N)
+    assert torch.equal(Hr, Hr[:1].expand_as(Hr))
+    br = bits.view(cfg.F // pool, pool, -1)
+    assert torch.equal(br, br[:1].expand_as(br))
