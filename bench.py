@@ -62,6 +62,26 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def rank_frame_ids(rank, pool):
+    """Seeded frame indices owned by a rank: independent units, no exchange."""
+    return range(rank * pool, (rank + 1) * pool)
+
+
+def max_over_ranks(value, world, device):
+    """Largest value over all ranks (the slowest rank's time)."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_samples(world, frames, cfg):
+    """Antenna*subcarrier samples processed by the whole job in one step."""
+    return world * frames * cfg.M * cfg.S * cfg.N
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -236,7 +256,7 @@ def main():
     F = args.frames or cfg.F
     pool = min(args.pool, F)
     # each rank owns its own seeded frames (independent units, no exchange)
-    b = synth.generate(cfg, frame_ids=range(rank * pool, (rank + 1) * pool))
+    b = synth.generate(cfg, frame_ids=rank_frame_ids(rank, pool))
     plan = lsas.Plan(cfg.M, cfg.N, cfg.cp, cfg.S, cfg.pilot_idx, cfg.Q, fmt=cfg.fmt,
                      max_frames=F, pilot=b.pilot)
     xp = torch.from_numpy(np.ascontiguousarray(b.frames)).cuda()
@@ -268,13 +288,9 @@ def main():
     clocks = clk.stop()
     barrier()
     plan.sync()
-    ms = e0.elapsed_time(e1)
-    t_max = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t_max, op=torch.distributed.ReduceOp.MAX)
-    ms = float(t_max.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
     ms_step = ms / args.steps
-    samples = world * F * cfg.M * cfg.S * cfg.N
+    samples = job_samples(world, F, cfg)
     value = samples / (ms_step * 1e-3)
 
     in_b, h_b, bit_b, eq_b = lsas.frame_bytes(cfg.M, cfg.N, cfg.cp, cfg.S, cfg.Q, cfg.fmt)
@@ -305,11 +321,7 @@ def main():
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
         plan.run_frame_host(xh, Hh, bh)
-    t_e2e = (time.perf_counter() - t0) / args.e2e_steps
-    te = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
-    t_e2e = float(te.item())
+    t_e2e = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, world, "cuda")
     plan.sync()
 
     cpu = None
@@ -331,7 +343,7 @@ def main():
                          "peak_source": peak_src,
                          "kernel": "frame_kernel (fused CP strip+FFT+LS+MRC+demap)",
                          "algorithmic_bytes_per_frame": in_b + h_b + bit_b},
-            "e2e": {"value": world * F * cfg.M * cfg.S * cfg.N / t_e2e, "unit": "samples/s",
+            "e2e": {"value": samples / t_e2e, "unit": "samples/s",
                     "h2d_bytes_per_step": F * in_b, "d2h_bytes_per_step": F * (h_b + bit_b)},
             "latency_ms": {"frames_per_call": 1, "p50": lat[len(lat) // 2],
                            "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},

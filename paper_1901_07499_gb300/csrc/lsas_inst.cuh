@@ -12,8 +12,16 @@ static cudaError_t launch_t(int kind, const KParams& p, int grid, int smem, cuda
   if (kind == kKindFrame) fn = frame_kernel<LOG2N, FC32>;
   else if (kind == kKindEstimate) fn = estimate_kernel<LOG2N, FC32>;
   else fn = fft_kernel<LOG2N, FC32>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  // raise the kernel's dynamic shared memory limit once per device
+  static int limit[3][64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64 || smem > limit[kind][dev]) {
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) limit[kind][dev] = smem;
+  }
   fn<<<grid, T, smem, st>>>(p);
   return cudaGetLastError();
 }

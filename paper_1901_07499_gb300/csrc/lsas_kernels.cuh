@@ -44,7 +44,7 @@ struct KParams {
   uint8_t* bits;         // [F][D*N*q/8]
   float2* eq;            // [F][D][N] or null
   float2* Y_out;         // [F][M][S][N] (fft)
-  const float2* twN;     // W_N^i = exp(-2j pi i / N), i < N
+  const float2* twP;     // pass twiddles W (layout: pass_tw_count)
   const float2* xinv;    // conj(X[k]) / |X[k]|^2 / sqrt(N)
   int* status;           // latched device status
   int M, S, cp, pilot_idx, D;
@@ -55,40 +55,67 @@ struct KParams {
   int q, wbits, axes, nthr;
   float inv_sqrtN;
   float thr[kMaxThresholds];   // per-axis decision boundaries (float32)
-  float2 w32[32];              // W_32^e, small-DFT twiddles (param space)
+  float2 w32[16];              // W_32^e = {cos, -sin}(2 pi e / 32), e < 16
+  float2 w32n[16];             // {-Im, Re} of W_32^e (packed complex multiply)
 };
 
 // ---------------------------------------------------------------- geometry
+//
+// Thread mapping of every kernel: a warp's lanes hold A antennas x F = 32/A
+// sub-lanes (antenna alpha = lane % A, sub-lane q = lane / A).  The FFT team
+// of antenna alpha is the set of threads with that alpha across the W warps
+// of the block, team index jt = warp * F + q, L = W * F = N / 32 threads per
+// team, 32 complex points per thread.  Because the A antennas of one bin sit
+// in lanes of one warp, the sum over antennas of MRC is a warp-shuffle
+// reduction, and lanes of different antennas share pass twiddles.
 
 template <int LOG2N>
 struct Geo {
   static constexpr int N = 1 << LOG2N;
-  static constexpr int L = N / 32;                       // threads per team
-  static constexpr int A = (N == 64) ? 16 : (N == 2048 ? 4 : 8);  // teams
-  static constexpr int T = A * L;                        // threads per block
-  static constexpr int SPAD = (L < 4) ? 4 : L;           // staging pad, samples
-  static constexpr int XS = N + 8;                       // exchange stride, float2
+  static constexpr int L = N / 32;                                  // threads per team
+  static constexpr int A = (N == 64) ? 16 : (N == 2048 ? 4 : 8);    // antennas per step
+  static constexpr int F = 32 / A;                                  // sub-lanes per warp
+  static constexpr int W = L / F;                                   // warps per block
+  static constexpr int T = 32 * W;                                  // threads per block
+  static constexpr int ALOG = (A == 16) ? 4 : (A == 8 ? 3 : 2);
+  // exchange stride (float2): N plus one pad per 32, then rounded so that
+  // antenna regions start 16/A float2 apart modulo the 16 bank pairs
+  static constexpr int XB = N + N / 32;
+  static constexpr int XS = XB + ((16 / A - XB % 16) + 16) % 16;
 };
+
+__host__ __device__ constexpr int geo_A(int N) { return (N == 64) ? 16 : (N == 2048 ? 4 : 8); }
+__host__ __device__ constexpr int geo_T(int N) { return 32 * ((N / 32) / (32 / geo_A(N))); }
+__host__ __device__ constexpr int geo_XS(int N) {
+  return (N + N / 32) + ((16 / geo_A(N) - (N + N / 32) % 16) + 16) % 16;
+}
+// staging stride pad (samples) per antenna: rows start F (sc16) or F/2
+// (fc32) words of banks apart, and stay 16-byte aligned for bulk copies
+__host__ __device__ constexpr int geo_spad(int N, int bps) {
+  return bps == 4 ? ((32 / geo_A(N)) < 4 ? 4 : 32 / geo_A(N))
+                  : ((16 / geo_A(N)) < 2 ? 2 : 16 / geo_A(N));
+}
 
 __host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
 
 struct Layout {
-  int team_stage;   // bytes per team per slot
+  int team_stage;   // bytes per antenna per slot
   int stage_off;    // slots
-  int ex_off;       // exchange / product buffer
-  int e_off;        // channel energy (float[N])
-  int p_off;        // combined sums (float2[dg][N])
+  int ex_off;       // exchange buffer
+  int tw_off;       // pass twiddles (float2[N], N <= 1024)
+  int e_off;        // channel energy (float[N], owner layout)
+  int p_off;        // combined sums (float2[dg][N], owner layout)
   int total;
 };
 
-__host__ __device__ inline Layout make_layout(int N, int A, int L, int bps,
-                                              int nslots, int dg, bool frame) {
+__host__ __device__ inline Layout make_layout(int N, int bps, int nslots, int dg, bool frame) {
   Layout l;
-  const int spad = (L < 4) ? 4 : L;
-  l.team_stage = (N + spad) * bps;
+  const int A = geo_A(N);
+  l.team_stage = (N + geo_spad(N, bps)) * bps;
   l.stage_off = kSmemHeader;
   l.ex_off = align_up(l.stage_off + nslots * A * l.team_stage, 128);
-  l.e_off = l.ex_off + A * (N + 8) * 8;
+  l.tw_off = l.ex_off + A * geo_XS(N) * 8;
+  l.e_off = l.tw_off + (N <= 1024 ? N * 8 : 0);
   if (frame) {
     l.p_off = align_up(l.e_off + N * 4, 128);
     l.total = l.p_off + dg * N * 8;
@@ -98,6 +125,12 @@ __host__ __device__ inline Layout make_layout(int N, int A, int L, int bps,
   }
   return l;
 }
+
+// Number of pass twiddles in the host-built table (layout in pass_twiddles):
+// N <= 1024: [r][j] = W_N^(j r), r < N/32, j < 32 (second pass);
+// N = 2048:  [r][j] = W_2048^(8 j r), j < 32 (second pass), then
+//            [256 + r*256 + j] = W_2048^(j r), j < 256 (third pass).
+__host__ __device__ inline int pass_tw_count(int N) { return N <= 1024 ? N : 256 + 2048; }
 
 #ifdef __CUDACC__
 
@@ -166,11 +199,21 @@ __device__ __forceinline__ void named_sync(int id, int nthreads) {
 
 // ------------------------------------------------------- complex helpers
 
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) {
-  return make_float2(a.x + b.x, a.y + b.y);
-}
+// Complex arithmetic on {re, im} pairs with the packed f32x2 instructions:
+// one issue slot per complex add, two per complex multiply.
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) {
-  return make_float2(a.x - b.x, a.y - b.y);
+  float2 r;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+// a * w with w = {Re, Im} and wn = {-Im, Re}
+__device__ __forceinline__ float2 cmulw(float2 a, float2 w, float2 wn) {
+  return __ffma2_rn(make_float2(a.x, a.x), w, __fmul2_rn(make_float2(a.y, a.y), wn));
 }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -191,10 +234,10 @@ __host__ __device__ constexpr int brev(int i, int bits) {
 __device__ __forceinline__ float2 tw32(float2 b, int e, const KParams& p) {
   constexpr float kS = 0.70710678118654752440f;  // 1/sqrt(2)
   if (e == 0) return b;
-  if (e == 8) return make_float2(b.y, -b.x);                       // -j
-  if (e == 4) return make_float2((b.x + b.y) * kS, (b.y - b.x) * kS);   // (1-j)/sqrt2
-  if (e == 12) return make_float2((b.y - b.x) * kS, -(b.x + b.y) * kS); // (-1-j)/sqrt2
-  return cmul(b, p.w32[e]);
+  if (e == 8) return make_float2(b.y, -b.x);                                     // -j
+  if (e == 4) return __fmul2_rn(make_float2(b.x + b.y, b.y - b.x), make_float2(kS, kS));
+  if (e == 12) return __fmul2_rn(make_float2(b.y - b.x, -(b.x + b.y)), make_float2(kS, kS));
+  return cmulw(b, p.w32[e], p.w32n[e]);
 }
 
 // One radix-2 decimation-in-time stage of half-span S on R registers.
@@ -232,18 +275,18 @@ __device__ __forceinline__ void dft(float2* v, const KParams& p) {
   for (int i = 0; i < R; ++i) v[i] = a[i];
 }
 
-// XOR swizzle of the exchange buffer: bits 0-4 of an index are flipped by
-// bits 5-9, which spreads both the row writes (t*32 + r) and the column
-// reads (j + 32 r) of the transposes over all banks.
-__device__ __forceinline__ int swz(int n) { return n ^ ((n >> 5) & 31); }
+// Padded exchange index: one float2 of padding after every 32 entries, so
+// that both the row writes (t*32 + r) and the column reads (j + 32 r) of a
+// transpose hit distinct banks, and every address is a per-thread base plus
+// a compile-time offset.
+__device__ __forceinline__ int xpad(int n) { return n + (n >> 5); }
 
 template <int LOG2N>
-__device__ __forceinline__ void team_sync(int team) {
-  using G = Geo<LOG2N>;
-  if constexpr (G::L <= 32) {
+__device__ __forceinline__ void team_sync() {
+  if constexpr (Geo<LOG2N>::W == 1) {
     __syncwarp();
   } else {
-    named_sync(1 + team, G::L);
+    __syncthreads();
   }
 }
 
@@ -258,81 +301,153 @@ __device__ __forceinline__ int bin_of(int t, int e) {
   }
 }
 
-// Pass-1 inputs x[t + r L], r < 32, of one antenna-symbol row (N samples).
+// Owner of bin k after the antenna reduction: the thread (tid) whose
+// register e = alpha * (32/A) + c holds it, and the slot c.  Inverse of
+// bin_of with the thread mapping of Geo.
+template <int LOG2N>
+__device__ __forceinline__ void owner_of(int k, int& tid, int& c) {
+  using G = Geo<LOG2N>;
+  constexpr int OWN = 32 / G::A;
+  int jt, e;
+  if constexpr (G::N <= 1024) {
+    const int kl = k & 31;
+    jt = kl % G::L;
+    e = (kl / G::L) * G::L + (k >> 5);
+  } else {
+    jt = k & 63;
+    e = 8 * ((k >> 6) & 3) + (k >> 8);
+  }
+  const int alpha = e / OWN;
+  c = e % OWN;
+  tid = (jt / G::F) * 32 + (jt % G::F) * G::A + alpha;
+}
+
+// Pass-1 inputs x[jt + r L], r < 32, of one antenna-symbol row (N samples).
 template <int LOG2N, bool FC32>
-__device__ __forceinline__ void load_row(float2 (&v)[32], const void* row, int t,
+__device__ __forceinline__ void load_row(float2 (&v)[32], const void* row, int jt,
                                          bool from_global) {
   using G = Geo<LOG2N>;
   if constexpr (FC32) {
     const float2* s = static_cast<const float2*>(row);
 #pragma unroll
-    for (int r = 0; r < 32; ++r) v[r] = from_global ? __ldg(s + t + r * G::L) : s[t + r * G::L];
+    for (int r = 0; r < 32; ++r) v[r] = from_global ? __ldg(s + jt + r * G::L) : s[jt + r * G::L];
   } else {
     const uint32_t* s = static_cast<const uint32_t*>(row);
 #pragma unroll
     for (int r = 0; r < 32; ++r) {
-      const uint32_t w = from_global ? __ldg(s + t + r * G::L) : s[t + r * G::L];
+      const uint32_t w = from_global ? __ldg(s + jt + r * G::L) : s[jt + r * G::L];
       v[r] = make_float2(static_cast<float>(static_cast<int16_t>(w & 0xffffu)),
                          static_cast<float>(static_cast<int16_t>(w >> 16)));
     }
   }
 }
 
-// Remaining FFT passes of a team: v holds the radix-32 pass-1 outputs of
-// thread t (Y1[t*32 + r]); on return v[e] = Y[bin_of(t, e)] (unscaled).
+// Remaining FFT passes: v holds the radix-32 pass-1 outputs of team thread
+// jt (Y1[jt*32 + r]); on return v[e] = Y[bin_of(jt, e)] (unscaled).  ex is
+// this antenna's exchange region; tw the pass twiddles (shared memory for
+// N <= 1024, global for N = 2048).  Every thread of the block calls this.
 template <int LOG2N>
-__device__ __forceinline__ void team_fft_rest(float2 (&v)[32], float2* ex, int t,
-                                              int team, const KParams& p) {
+__device__ __forceinline__ void team_fft_rest(float2 (&v)[32], float2* ex, int jt,
+                                              const float2* tw, const KParams& p) {
   using G = Geo<LOG2N>;
   constexpr int L = G::L;
 #pragma unroll
-  for (int r = 0; r < 32; ++r) ex[swz(t * 32 + r)] = v[r];
-  team_sync<LOG2N>(team);
+  for (int r = 0; r < 32; ++r) ex[xpad(jt * 32 + r)] = v[r];
+  team_sync<LOG2N>();
   if constexpr (G::N <= 1024) {
 #pragma unroll
     for (int i = 0; i < 32 / L; ++i) {
-      const int j = t + i * L;
+      const int j = jt + i * L;
 #pragma unroll
       for (int r = 0; r < L; ++r) {
-        const float2 u = ex[swz(j + 32 * r)];
-        v[i * L + r] = (r == 0) ? u : cmul(u, __ldg(p.twN + (j & 31) * r));
+        const float2 u = ex[xpad(j + 32 * r)];
+        if (r == 0) {
+          v[i * L + r] = u;
+        } else {
+          v[i * L + r] = cmul(u, tw[r * 32 + j]);
+        }
       }
     }
-    team_sync<LOG2N>(team);
 #pragma unroll
     for (int i = 0; i < 32 / L; ++i) dft<L>(v + i * L, p);
   } else {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const int j = t + 64 * i;
+      const int j = jt + 64 * i;
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
-        const float2 u = ex[swz(j + 256 * r)];
-        v[i * 8 + r] = (r == 0) ? u : cmul(u, __ldg(p.twN + 8 * (j & 31) * r));
+        const float2 u = ex[xpad(j + 256 * r)];
+        if (r == 0) {
+          v[i * 8 + r] = u;
+        } else {
+          v[i * 8 + r] = cmul(u, __ldg(tw + r * 32 + (j & 31)));
+        }
       }
     }
-    team_sync<LOG2N>(team);
+    team_sync<LOG2N>();   // all reads done before the second exchange
 #pragma unroll
     for (int i = 0; i < 4; ++i) dft<8>(v + i * 8, p);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const int j = t + 64 * i;
+      const int j = jt + 64 * i;
 #pragma unroll
-      for (int r = 0; r < 8; ++r) ex[swz((j >> 5) * 256 + (j & 31) + 32 * r)] = v[i * 8 + r];
+      for (int r = 0; r < 8; ++r) ex[xpad((j >> 5) * 256 + (j & 31) + 32 * r)] = v[i * 8 + r];
     }
-    team_sync<LOG2N>(team);
+    team_sync<LOG2N>();
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const int j = t + 64 * i;
+      const int j = jt + 64 * i;
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
-        const float2 u = ex[swz(j + 256 * r)];
-        v[i * 8 + r] = (r == 0) ? u : cmul(u, __ldg(p.twN + j * r));
+        const float2 u = ex[xpad(j + 256 * r)];
+        if (r == 0) {
+          v[i * 8 + r] = u;
+        } else {
+          v[i * 8 + r] = cmul(u, __ldg(tw + 256 + r * 256 + j));
+        }
       }
     }
-    team_sync<LOG2N>(team);
 #pragma unroll
     for (int i = 0; i < 4; ++i) dft<8>(v + i * 8, p);
+  }
+}
+
+// Sum over the A antennas held in lane bits [0, log2 A): a reduce-scatter by
+// recursive halving with warp shuffles.  Each round the lane keeps the half
+// of its registers selected by one bit of alpha and adds the partner's copy
+// of it; on return v[c], c < 32/A, holds the sum for register index
+// e = alpha * (32/A) + c.
+template <int A, int HALF>
+__device__ __forceinline__ void reduce_scatter(float2* v, int alpha) {
+  if constexpr (A > 1) {
+    constexpr int m = A / 2;
+    const bool up = (alpha & m) != 0;
+#pragma unroll
+    for (int c = 0; c < HALF; ++c) {
+      const float2 lo = v[c], hi = v[c + HALF];
+      const float2 send = up ? lo : hi;
+      const float2 keep = up ? hi : lo;
+      float2 recv;
+      recv.x = __shfl_xor_sync(0xffffffffu, send.x, m);
+      recv.y = __shfl_xor_sync(0xffffffffu, send.y, m);
+      v[c] = cadd(keep, recv);
+    }
+    reduce_scatter<A / 2, HALF / 2>(v, alpha);
+  }
+}
+
+// Pass twiddles for the block: copied to shared memory when N <= 1024.
+template <int LOG2N>
+__device__ __forceinline__ const float2* load_pass_twiddles(const KParams& p,
+                                                            unsigned char* smem,
+                                                            const Layout& lay) {
+  using G = Geo<LOG2N>;
+  if constexpr (G::N <= 1024) {
+    float2* tws = reinterpret_cast<float2*>(smem + lay.tw_off);
+    for (int i = threadIdx.x; i < G::N; i += G::T) tws[i] = __ldg(p.twP + i);
+    return tws;
+  } else {
+    return p.twP;
   }
 }
 
@@ -427,20 +542,22 @@ __device__ __forceinline__ uint32_t gray(int l) { return static_cast<uint32_t>(l
 template <int LOG2N, bool FC32>
 __global__ void __launch_bounds__(Geo<LOG2N>::T, 1) frame_kernel(const KParams p) {
   using G = Geo<LOG2N>;
-  constexpr int N = G::N, L = G::L, A = G::A, T = G::T;
-  constexpr int BPT = N / T;  // bins per thread in the reduction
+  constexpr int N = G::N, A = G::A, T = G::T, F = G::F;
+  constexpr int OWN = 32 / A;  // bins per thread after the antenna reduction
   extern __shared__ __align__(128) unsigned char smem[];
   const int f = blockIdx.x;
   const int tid = threadIdx.x;
-  const int team = tid / L, t = tid % L;
-  const Layout lay = make_layout(N, A, L, FC32 ? 8 : 4, p.nslots, p.dg, true);
+  const int lane = tid & 31;
+  const int alpha = lane % A;
+  const int jt = (tid >> 5) * F + lane / A;
+  const Layout lay = make_layout(N, FC32 ? 8 : 4, p.nslots, p.dg, true);
+  const float2* tw = load_pass_twiddles<LOG2N>(p, smem, lay);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 64);
   unsigned char* stage = smem + lay.stage_off;
-  float2* ex = reinterpret_cast<float2*>(smem + lay.ex_off);
   float* E = reinterpret_cast<float*>(smem + lay.e_off);
   float2* P = reinterpret_cast<float2*>(smem + lay.p_off);
-  float2* myex = ex + team * G::XS;
+  float2* myex = reinterpret_cast<float2*>(smem + lay.ex_off) + alpha * G::XS;
   const int K = p.nslots;
   const int slot_bytes = A * lay.team_stage;
 
@@ -456,8 +573,7 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T, 1) frame_kernel(const KParams p
       fence_mbar_init();
     }
   }
-#pragma unroll
-  for (int b = 0; b < BPT; ++b) E[tid + T * b] = 0.f;
+  for (int k = tid; k < N; k += T) E[k] = 0.f;
   __syncthreads();
   if (tid == 0 && p.use_tma) {
     for (int i = 0; i < K && i < total; ++i) {
@@ -472,12 +588,11 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T, 1) frame_kernel(const KParams p
   for (int g = 0; g < p.groups; ++g) {
     const int nd = min(p.dg, p.D - g * p.dg);
     const int d0 = g * p.dg;
-#pragma unroll
-    for (int b = 0; b < BPT; ++b)
-      for (int dl = 0; dl < nd; ++dl) P[dl * N + tid + T * b] = make_float2(0.f, 0.f);
+    for (int i = tid; i < nd * N; i += T) P[i] = make_float2(0.f, 0.f);
+    __syncthreads();
 
     for (int c = 0; c < p.chunks; ++c) {
-      const int m = c * A + team;
+      const int m = c * A + alpha;
       const bool valid = m < p.M;
       const size_t hrow = (static_cast<size_t>(f) * p.M + m) * N;
       const bool need_fft_pilot = (p.mode == kModeRun && g == 0);
@@ -486,22 +601,15 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T, 1) frame_kernel(const KParams p
         const float2* Hs = (p.mode == kModeRun) ? p.H_out : p.H_in;
 #pragma unroll
         for (int e = 0; e < 32; ++e)
-          h[e] = valid ? Hs[hrow + bin_of<LOG2N>(t, e)] : make_float2(0.f, 0.f);
+          h[e] = valid ? Hs[hrow + bin_of<LOG2N>(jt, e)] : make_float2(0.f, 0.f);
         if (g == 0) {
           // channel energy of this chunk: |H|^2 summed over its antennas
-          __syncthreads();
+          float2 e2[32];
 #pragma unroll
-          for (int e = 0; e < 32; ++e)
-            myex[swz(bin_of<LOG2N>(t, e))] = make_float2(h[e].x * h[e].x + h[e].y * h[e].y, 0.f);
-          __syncthreads();
+          for (int e = 0; e < 32; ++e) e2[e] = make_float2(h[e].x * h[e].x + h[e].y * h[e].y, 0.f);
+          reduce_scatter<A, 16>(e2, alpha);
 #pragma unroll
-          for (int b = 0; b < BPT; ++b) {
-            const int k = tid + T * b;
-            float s = 0.f;
-#pragma unroll
-            for (int a = 0; a < A; ++a) s += ex[a * G::XS + swz(k)].x;
-            E[k] += s;
-          }
+          for (int cc = 0; cc < OWN; ++cc) E[cc * T + tid] += e2[cc].x;
         }
       }
       const int items = group_items(p, g);
@@ -514,71 +622,56 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T, 1) frame_kernel(const KParams p
         if (p.use_tma) {
           wait_slot(smem_u32(&bars[slot]), (step / K) & 1, abort_flag, p.status);
           if (valid) {
-            load_row<LOG2N, FC32>(v, stage + slot * slot_bytes + team * lay.team_stage, t, false);
+            load_row<LOG2N, FC32>(v, stage + slot * slot_bytes + alpha * lay.team_stage, jt, false);
           } else {
 #pragma unroll
             for (int r = 0; r < 32; ++r) v[r] = make_float2(0.f, 0.f);
           }
         } else {
           if (valid) {
-            load_row<LOG2N, FC32>(v, row_ptr<LOG2N, FC32>(p, f, m, s), t, true);
+            load_row<LOG2N, FC32>(v, row_ptr<LOG2N, FC32>(p, f, m, s), jt, true);
           } else {
 #pragma unroll
             for (int r = 0; r < 32; ++r) v[r] = make_float2(0.f, 0.f);
           }
         }
         dft<32>(v, p);
-        __syncthreads();  // staging slot consumed; products of the last step read
+        __syncthreads();  // staging slot consumed; exchange buffer free
         if (tid == 0 && p.use_tma && step + K < total) {
           const StepInfo si = frame_step(p, step + K);
           fence_proxy_async();
           issue_step<LOG2N, FC32>(p, f, si.c, si.s, stage + slot * slot_bytes, lay.team_stage,
                                   smem_u32(&bars[slot]), pol);
         }
-        team_fft_rest<LOG2N>(v, myex, t, team, p);
+        team_fft_rest<LOG2N>(v, myex, jt, tw, p);
         if (is_pilot) {
           // LS estimate H = Y conj(X) / |X|^2 (1/sqrt(N) folded into xinv)
 #pragma unroll
           for (int e = 0; e < 32; ++e) {
-            const int k = bin_of<LOG2N>(t, e);
+            const int k = bin_of<LOG2N>(jt, e);
             const float2 hv = cmul(v[e], __ldg(p.xinv + k));
             h[e] = valid ? hv : make_float2(0.f, 0.f);
             if (valid) p.H_out[hrow + k] = hv;
-            myex[swz(k)] = make_float2(h[e].x * h[e].x + h[e].y * h[e].y, 0.f);
+            v[e] = make_float2(h[e].x * h[e].x + h[e].y * h[e].y, 0.f);
           }
+          reduce_scatter<A, 16>(v, alpha);
+#pragma unroll
+          for (int cc = 0; cc < OWN; ++cc) E[cc * T + tid] += v[cc].x;
         } else {
+          // MRC numerator: conj(H) Y summed over the antennas of the chunk
 #pragma unroll
-          for (int e = 0; e < 32; ++e) myex[swz(bin_of<LOG2N>(t, e))] = cmulc(h[e], v[e]);
-        }
-        __syncthreads();  // products of all antennas of the chunk are in place
-        if (is_pilot) {
+          for (int e = 0; e < 32; ++e) v[e] = cmulc(h[e], v[e]);
+          reduce_scatter<A, 16>(v, alpha);
+          float2* Pd = P + (d - d0) * N + tid;
 #pragma unroll
-          for (int b = 0; b < BPT; ++b) {
-            const int k = tid + T * b;
-            float s2 = 0.f;
-#pragma unroll
-            for (int a = 0; a < A; ++a) s2 += ex[a * G::XS + swz(k)].x;
-            E[k] += s2;
-          }
-        } else {
-          const int dl = d - d0;
-#pragma unroll
-          for (int b = 0; b < BPT; ++b) {
-            const int k = tid + T * b;
-            float2 s2 = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int a = 0; a < A; ++a) s2 = cadd(s2, ex[a * G::XS + swz(k)]);
-            P[dl * N + k] = cadd(P[dl * N + k], s2);
-          }
+          for (int cc = 0; cc < OWN; ++cc) Pd[cc * T] = cadd(Pd[cc * T], v[cc]);
         }
       }
     }
     __syncthreads();
     if (g == 0) {
       // E -> 1 / (sqrt(N) E); zero or non-finite energy flags the frame
-#pragma unroll
-      for (int b = 0; b < BPT; ++b) {
-        const int k = tid + T * b;
+      for (int k = tid; k < N; k += T) {
         const float e = E[k];
         const bool ok = (e > 0.f) && (e <= 3.4028234663852886e38f);
         if (!ok) latch(p.status, kStDevice);
@@ -597,8 +690,10 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T, 1) frame_kernel(const KParams p
 #pragma unroll
       for (int b = 0; b < 8; ++b) {
         const int k = k0 + b;
-        const float ie = E[k];
-        const float2 sum = P[dl * N + k];
+        int otid, oc;
+        owner_of<LOG2N>(k, otid, oc);
+        const float ie = E[oc * T + otid];
+        const float2 sum = P[dl * N + oc * T + otid];
         const float2 z = (ie != 0.f) ? make_float2(sum.x * ie, sum.y * ie) : make_float2(0.f, 0.f);
         if (p.eq) p.eq[(static_cast<size_t>(f) * p.D + d) * N + k] = z;
         uint32_t code = gray(axis_level(z.x, p));
@@ -624,18 +719,21 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T, 1) frame_kernel(const KParams p
 template <int LOG2N, bool FC32>
 __global__ void __launch_bounds__(Geo<LOG2N>::T) estimate_kernel(const KParams p) {
   using G = Geo<LOG2N>;
-  constexpr int N = G::N, L = G::L, A = G::A;
+  constexpr int N = G::N, A = G::A, F = G::F;
   extern __shared__ __align__(128) unsigned char smem[];
   const int f = blockIdx.x / p.chunks;
   const int c = blockIdx.x % p.chunks;
   const int tid = threadIdx.x;
-  const int team = tid / L, t = tid % L;
-  const Layout lay = make_layout(N, A, L, FC32 ? 8 : 4, 1, 0, false);
+  const int lane = tid & 31;
+  const int alpha = lane % A;
+  const int jt = (tid >> 5) * F + lane / A;
+  const Layout lay = make_layout(N, FC32 ? 8 : 4, 1, 0, false);
+  const float2* tw = load_pass_twiddles<LOG2N>(p, smem, lay);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 64);
   unsigned char* stage = smem + lay.stage_off;
-  float2* myex = reinterpret_cast<float2*>(smem + lay.ex_off) + team * G::XS;
-  const int m = c * A + team;
+  float2* myex = reinterpret_cast<float2*>(smem + lay.ex_off) + alpha * G::XS;
+  const int m = c * A + alpha;
   const bool valid = m < p.M;
   if (tid == 0) {
     *abort_flag = 0;
@@ -651,20 +749,20 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T) estimate_kernel(const KParams p
   if (p.use_tma) wait_slot(smem_u32(&bars[0]), 0, abort_flag, p.status);
   if (valid) {
     if (p.use_tma)
-      load_row<LOG2N, FC32>(v, stage + team * lay.team_stage, t, false);
+      load_row<LOG2N, FC32>(v, stage + alpha * lay.team_stage, jt, false);
     else
-      load_row<LOG2N, FC32>(v, row_ptr<LOG2N, FC32>(p, f, m, p.pilot_idx), t, true);
+      load_row<LOG2N, FC32>(v, row_ptr<LOG2N, FC32>(p, f, m, p.pilot_idx), jt, true);
   } else {
 #pragma unroll
     for (int r = 0; r < 32; ++r) v[r] = make_float2(0.f, 0.f);
   }
   dft<32>(v, p);
-  team_fft_rest<LOG2N>(v, myex, t, team, p);
+  team_fft_rest<LOG2N>(v, myex, jt, tw, p);
   if (valid) {
     const size_t hrow = (static_cast<size_t>(f) * p.M + m) * N;
 #pragma unroll
     for (int e = 0; e < 32; ++e) {
-      const int k = bin_of<LOG2N>(t, e);
+      const int k = bin_of<LOG2N>(jt, e);
       p.H_out[hrow + k] = cmul(v[e], __ldg(p.xinv + k));
     }
   }
@@ -675,18 +773,21 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T) estimate_kernel(const KParams p
 template <int LOG2N, bool FC32>
 __global__ void __launch_bounds__(Geo<LOG2N>::T) fft_kernel(const KParams p) {
   using G = Geo<LOG2N>;
-  constexpr int N = G::N, L = G::L, A = G::A;
+  constexpr int N = G::N, A = G::A, F = G::F;
   extern __shared__ __align__(128) unsigned char smem[];
   const int f = blockIdx.x / p.chunks;
   const int c = blockIdx.x % p.chunks;
   const int tid = threadIdx.x;
-  const int team = tid / L, t = tid % L;
-  const Layout lay = make_layout(N, A, L, FC32 ? 8 : 4, p.nslots, 0, false);
+  const int lane = tid & 31;
+  const int alpha = lane % A;
+  const int jt = (tid >> 5) * F + lane / A;
+  const Layout lay = make_layout(N, FC32 ? 8 : 4, p.nslots, 0, false);
+  const float2* tw = load_pass_twiddles<LOG2N>(p, smem, lay);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 64);
   unsigned char* stage = smem + lay.stage_off;
-  float2* myex = reinterpret_cast<float2*>(smem + lay.ex_off) + team * G::XS;
-  const int m = c * A + team;
+  float2* myex = reinterpret_cast<float2*>(smem + lay.ex_off) + alpha * G::XS;
+  const int m = c * A + alpha;
   const bool valid = m < p.M;
   const int K = p.nslots;
   const int slot_bytes = A * lay.team_stage;
@@ -709,9 +810,9 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T) fft_kernel(const KParams p) {
     if (p.use_tma) wait_slot(smem_u32(&bars[slot]), (s / K) & 1, abort_flag, p.status);
     if (valid) {
       if (p.use_tma)
-        load_row<LOG2N, FC32>(v, stage + slot * slot_bytes + team * lay.team_stage, t, false);
+        load_row<LOG2N, FC32>(v, stage + slot * slot_bytes + alpha * lay.team_stage, jt, false);
       else
-        load_row<LOG2N, FC32>(v, row_ptr<LOG2N, FC32>(p, f, m, s), t, true);
+        load_row<LOG2N, FC32>(v, row_ptr<LOG2N, FC32>(p, f, m, s), jt, true);
     } else {
 #pragma unroll
       for (int r = 0; r < 32; ++r) v[r] = make_float2(0.f, 0.f);
@@ -723,12 +824,12 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T) fft_kernel(const KParams p) {
       issue_step<LOG2N, FC32>(p, f, c, s + K, stage + slot * slot_bytes, lay.team_stage,
                               smem_u32(&bars[slot]), pol);
     }
-    team_fft_rest<LOG2N>(v, myex, t, team, p);
+    team_fft_rest<LOG2N>(v, myex, jt, tw, p);
     if (valid) {
       float2* out = p.Y_out + ((static_cast<size_t>(f) * p.M + m) * p.S + s) * N;
 #pragma unroll
       for (int e = 0; e < 32; ++e)
-        out[bin_of<LOG2N>(t, e)] = make_float2(v[e].x * p.inv_sqrtN, v[e].y * p.inv_sqrtN);
+        out[bin_of<LOG2N>(jt, e)] = make_float2(v[e].x * p.inv_sqrtN, v[e].y * p.inv_sqrtN);
     }
   }
 }

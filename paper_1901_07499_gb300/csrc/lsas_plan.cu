@@ -14,7 +14,7 @@
 #include <new>
 #include <vector>
 
-#include "../../include/lsas.h"
+#include "lsas.h"
 #include "lsas_kernels.cuh"
 
 namespace lsas {
@@ -48,10 +48,10 @@ struct lsas_plan_s {
   lsas_input_fmt fmt;
   int max_frames;
   int device;
-  float2* d_twN = nullptr;
+  float2* d_twP = nullptr;
   float2* d_xinv = nullptr;
   int* d_status = nullptr;
-  float2 w32[32];
+  float2 w32[16], w32n[16];
   Geometry geo;
   LaunchFn launch = nullptr;
   // host-transfer staging (lsas_run_frame_host), allocated on first use
@@ -93,23 +93,18 @@ LaunchFn launcher_for(int N) {
   }
 }
 
-// Antennas per step and team size for an FFT length (mirrors Geo<>).
-void team_shape(int N, int* A, int* L) {
-  *L = N / 32;
-  *A = (N == 64) ? 16 : (N == 2048 ? 4 : 8);
-}
-
 // Choose staging slots and data-symbol groups so that the fused kernel's
 // shared memory fits one block per SM.
 bool plan_geometry(int M, int N, int D, lsas_input_fmt fmt, Geometry* g) {
-  team_shape(N, &g->A, &g->L);
-  g->T = g->A * g->L;
+  g->A = geo_A(N);
+  g->L = N / 32;
+  g->T = geo_T(N);
   const int bps = fmt == LSAS_IN_SC16 ? 4 : 8;
   (void)M;
   // fused frame kernel
   int best_dg = 0, slots = 2;
   for (slots = 2; slots >= 1; --slots) {
-    const Layout l0 = make_layout(N, g->A, g->L, bps, slots, 0, true);
+    const Layout l0 = make_layout(N, bps, slots, 0, true);
     const int room = kSmemLimit - l0.total;
     best_dg = room / (N * 8);
     if (best_dg >= 1) break;
@@ -119,20 +114,46 @@ bool plan_geometry(int M, int N, int D, lsas_input_fmt fmt, Geometry* g) {
   g->dg = (D + g->groups - 1) / g->groups;
   g->nslots = slots;
   while (g->nslots < kMaxSlots &&
-         make_layout(N, g->A, g->L, bps, g->nslots + 1, g->dg, true).total <= kSmemLimit)
+         make_layout(N, bps, g->nslots + 1, g->dg, true).total <= kSmemLimit)
     ++g->nslots;
-  g->smem_frame = make_layout(N, g->A, g->L, bps, g->nslots, g->dg, true).total;
-  g->smem_est = make_layout(N, g->A, g->L, bps, 1, 0, false).total;
+  g->smem_frame = make_layout(N, bps, g->nslots, g->dg, true).total;
+  g->smem_est = make_layout(N, bps, 1, 0, false).total;
   g->fft_slots = 2;
-  g->smem_fft = make_layout(N, g->A, g->L, bps, 2, 0, false).total;
+  g->smem_fft = make_layout(N, bps, 2, 0, false).total;
   return true;
 }
 
-void fill_w32(float2* w) {
-  for (int e = 0; e < 32; ++e) {
+// W_32^e = exp(-2j pi e / 32) as {Re, Im} and {-Im, Re}, e < 16.
+void fill_w32(float2* w, float2* wn) {
+  for (int e = 0; e < 16; ++e) {
     const double a = -2.0 * M_PI * e / 32.0;
-    w[e] = make_float2(static_cast<float>(std::cos(a)), static_cast<float>(std::sin(a)));
+    const float c = static_cast<float>(std::cos(a)), s = static_cast<float>(std::sin(a));
+    w[e] = make_float2(c, s);
+    wn[e] = make_float2(-s, c);
   }
+}
+
+// W_N^e = exp(-2j pi e / N), computed in double precision and rounded once.
+float2 tw2(long e, int N) {
+  const double a = -2.0 * M_PI * static_cast<double>(e % N) / N;
+  return make_float2(static_cast<float>(std::cos(a)), static_cast<float>(std::sin(a)));
+}
+
+// Twiddles of the FFT passes after the first, in the order the kernels read
+// them (see pass_tw_count in lsas_kernels.cuh).
+std::vector<float2> pass_twiddles(int N) {
+  std::vector<float2> t(pass_tw_count(N));
+  if (N <= 1024) {
+    const int R2 = N / 32;
+    for (int r = 0; r < R2; ++r)
+      for (int j = 0; j < 32; ++j) t[r * 32 + j] = tw2(static_cast<long>(j) * r, N);
+  } else {
+    for (int r = 0; r < 8; ++r)
+      for (int j = 0; j < 32; ++j) t[r * 32 + j] = tw2(8L * j * r, N);
+    for (int r = 0; r < 8; ++r)
+      for (int j = 0; j < 256; ++j) t[256 + r * 256 + j] = tw2(static_cast<long>(j) * r, N);
+  }
+  return t;
 }
 
 lsas_status upload_pilot(lsas_plan p, const double* re, const double* im) {
@@ -153,7 +174,7 @@ bool aligned16(const void* ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15u
 
 void base_params(lsas_plan p, KParams* k) {
   std::memset(k, 0, sizeof(*k));
-  k->twN = p->d_twN;
+  k->twP = p->d_twP;
   k->xinv = p->d_xinv;
   k->status = p->d_status;
   k->M = p->M;
@@ -171,7 +192,10 @@ void base_params(lsas_plan p, KParams* k) {
   k->nthr = p->nthr;
   k->inv_sqrtN = static_cast<float>(1.0 / std::sqrt(static_cast<double>(p->N)));
   for (int i = 0; i < kMaxThresholds; ++i) k->thr[i] = p->thr[i];
-  for (int i = 0; i < 32; ++i) k->w32[i] = p->w32[i];
+  for (int i = 0; i < 16; ++i) {
+    k->w32[i] = p->w32[i];
+    k->w32n[i] = p->w32n[i];
+  }
 }
 
 // Bulk copies need 16-byte aligned rows: every row start
@@ -291,7 +315,7 @@ lsas_status lsas_plan_create(int M, int N, int cp_len, int n_sym, int pilot_idx,
   p->nthr = L - 1;
   for (int b = 0; b < kMaxThresholds; ++b)
     p->thr[b] = b < L - 1 ? static_cast<float>((2.0 * (b + 1) - L) * A) : 0.f;
-  fill_w32(p->w32);
+  fill_w32(p->w32, p->w32n);
   p->launch = launcher_for(N);
   if (!plan_geometry(M, N, p->D, p->fmt, &p->geo)) {
     delete p;
@@ -301,20 +325,16 @@ lsas_status lsas_plan_create(int M, int N, int cp_len, int n_sym, int pilot_idx,
     delete p;
     return LSAS_ERR_CUDA;
   }
-  if (cudaMalloc(&p->d_twN, sizeof(float2) * N) != cudaSuccess ||
+  const std::vector<float2> tw = pass_twiddles(N);
+  if (cudaMalloc(&p->d_twP, sizeof(float2) * tw.size()) != cudaSuccess ||
       cudaMalloc(&p->d_xinv, sizeof(float2) * N) != cudaSuccess ||
       cudaMalloc(&p->d_status, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     lsas_plan_destroy(p);
     return LSAS_ERR_OOM;
   }
-  std::vector<float2> tw(N);
-  for (int i = 0; i < N; ++i) {
-    const double a = -2.0 * M_PI * static_cast<double>(i) / N;
-    tw[i] = make_float2(static_cast<float>(std::cos(a)), static_cast<float>(std::sin(a)));
-  }
   std::vector<double> one(N, 1.0), zero(N, 0.0);
-  if (cudaMemcpy(p->d_twN, tw.data(), sizeof(float2) * N, cudaMemcpyHostToDevice) !=
+  if (cudaMemcpy(p->d_twP, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice) !=
           cudaSuccess ||
       cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess ||
       upload_pilot(p, one.data(), zero.data()) != LSAS_OK) {
@@ -533,7 +553,7 @@ lsas_status lsas_plan_info(lsas_plan p, int out[8]) {
 lsas_status lsas_plan_destroy(lsas_plan p) {
   if (!p) return LSAS_ERR_INVALID_ARG;
   if (set_device(p) == LSAS_OK) cudaDeviceSynchronize();
-  cudaFree(p->d_twN);
+  cudaFree(p->d_twP);
   cudaFree(p->d_xinv);
   cudaFree(p->d_status);
   for (int i = 0; i < 2; ++i) {

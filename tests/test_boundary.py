@@ -17,7 +17,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 @pytest.fixture(scope="module")
 def L():
-    from paper_1901_07499_gb300 import build
+    from paper_1901_07499_gb300.build import build
     build()
     import paper_1901_07499_gb300.lsas as lsas
     return lsas
