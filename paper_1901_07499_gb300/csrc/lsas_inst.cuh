@@ -7,7 +7,6 @@ namespace lsas {
 
 template <int LOG2N, bool FC32>
 static cudaError_t launch_t(int kind, const KParams& p, int grid, int smem, cudaStream_t st) {
-  constexpr int T = Geo<LOG2N>::T;
   void (*fn)(const KParams) = nullptr;
   if (kind == kKindFrame) fn = frame_kernel<LOG2N, FC32>;
   else if (kind == kKindEstimate) fn = estimate_kernel<LOG2N, FC32>;
@@ -22,7 +21,8 @@ static cudaError_t launch_t(int kind, const KParams& p, int grid, int smem, cuda
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) limit[kind][dev] = smem;
   }
-  fn<<<grid, T, smem, st>>>(p);
+  const int threads = (kind == kKindFrame) ? Geo<LOG2N>::T : Geo<LOG2N>::TG;
+  fn<<<grid, threads, smem, st>>>(p);
   return cudaGetLastError();
 }
 

@@ -34,7 +34,7 @@ enum { kModeEstimate = 0, kModeDemod = 1, kModeRun = 2 };
 enum { kStOk = 0, kStTimeout = 6, kStDevice = 7 };
 
 constexpr int kMaxSlots = 4;
-constexpr int kSmemHeader = 128;     // mbarriers + flags
+constexpr int kSmemHeader = 256;     // mbarriers (2 groups x 4 slots) + flags
 constexpr int kMaxThresholds = 15;   // 256-QAM: 16 levels per axis
 
 struct KParams {
@@ -61,31 +61,24 @@ struct KParams {
 
 // ---------------------------------------------------------------- geometry
 //
-// Thread mapping of every kernel: a warp's lanes hold A antennas x F = 32/A
-// sub-lanes (antenna alpha = lane % A, sub-lane q = lane / A).  The FFT team
-// of antenna alpha is the set of threads with that alpha across the W warps
-// of the block, team index jt = warp * F + q, L = W * F = N / 32 threads per
-// team, 32 complex points per thread.  Because the A antennas of one bin sit
-// in lanes of one warp, the sum over antennas of MRC is a warp-shuffle
-// reduction, and lanes of different antennas share pass twiddles.
+// Thread mapping: a block holds G independent groups of W warps.  A warp's
+// lanes hold A antennas x F = 32/A sub-lanes (antenna alpha = lane % A,
+// sub-lane q = lane / A).  The FFT team of antenna alpha is the set of
+// threads of one group with that alpha, team index jt = (warp in group) * F
+// + q, L = W * F = N / 32 threads per team, 32 complex points per thread.
+// Because the A antennas of one subcarrier sit in lanes of one warp, the sum
+// over antennas of MRC is a warp-shuffle reduction, and lanes of different
+// antennas share pass-twiddle loads.  The groups of a block process disjoint
+// antenna chunks of the same frame with their own staging ring, exchange
+// buffer, barriers and partial sums, so they run out of phase with each
+// other; their partial sums are added in the demapping phase.
 
-template <int LOG2N>
-struct Geo {
-  static constexpr int N = 1 << LOG2N;
-  static constexpr int L = N / 32;                                  // threads per team
-  static constexpr int A = (N == 64) ? 16 : (N == 2048 ? 4 : 8);    // antennas per step
-  static constexpr int F = 32 / A;                                  // sub-lanes per warp
-  static constexpr int W = L / F;                                   // warps per block
-  static constexpr int T = 32 * W;                                  // threads per block
-  static constexpr int ALOG = (A == 16) ? 4 : (A == 8 ? 3 : 2);
-  // exchange stride (float2): N plus one pad per 32, then rounded so that
-  // antenna regions start 16/A float2 apart modulo the 16 bank pairs
-  static constexpr int XB = N + N / 32;
-  static constexpr int XS = XB + ((16 / A - XB % 16) + 16) % 16;
-};
-
-__host__ __device__ constexpr int geo_A(int N) { return (N == 64) ? 16 : (N == 2048 ? 4 : 8); }
-__host__ __device__ constexpr int geo_T(int N) { return 32 * ((N / 32) / (32 / geo_A(N))); }
+__host__ __device__ constexpr int geo_A(int N) { return N == 64 ? 16 : (N == 128 ? 8 : 4); }
+__host__ __device__ constexpr int geo_G(int N) { return (N >= 256 && N <= 1024) ? 2 : 1; }
+__host__ __device__ constexpr int geo_TG(int N) { return 32 * ((N / 32) / (32 / geo_A(N))); }
+__host__ __device__ constexpr int geo_T(int N) { return geo_G(N) * geo_TG(N); }
+// exchange stride (float2): N plus one pad per 32, then rounded so that
+// antenna regions start 16/A float2 apart modulo the 16 bank pairs
 __host__ __device__ constexpr int geo_XS(int N) {
   return (N + N / 32) + ((16 / geo_A(N) - (N + N / 32) % 16) + 16) % 16;
 }
@@ -96,33 +89,54 @@ __host__ __device__ constexpr int geo_spad(int N, int bps) {
                   : ((16 / geo_A(N)) < 2 ? 2 : 16 / geo_A(N));
 }
 
+template <int LOG2N>
+struct Geo {
+  static constexpr int N = 1 << LOG2N;
+  static constexpr int L = N / 32;          // threads per team
+  static constexpr int A = geo_A(N);        // antennas per group step
+  static constexpr int F = 32 / A;          // sub-lanes per warp
+  static constexpr int W = L / F;           // warps per group
+  static constexpr int TG = 32 * W;         // threads per group
+  static constexpr int G = geo_G(N);        // groups per block (frame kernel)
+  static constexpr int T = G * TG;          // threads per block (frame kernel)
+  static constexpr int XS = geo_XS(N);
+};
+
 __host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
 
+// Shared memory of a block: a header (mbarriers, flags), the pass twiddles,
+// then one region per group: staging slots, exchange buffer, and (frame
+// kernel) channel energy and partial sums, both in owner layout.
 struct Layout {
-  int team_stage;   // bytes per antenna per slot
-  int stage_off;    // slots
-  int ex_off;       // exchange buffer
   int tw_off;       // pass twiddles (float2[N], N <= 1024)
-  int e_off;        // channel energy (float[N], owner layout)
-  int p_off;        // combined sums (float2[dg][N], owner layout)
+  int group_off;    // first group region
+  int group_bytes;  // stride between group regions
+  int team_stage;   // bytes per antenna per staging slot
+  int stage_off;    // within a group region
+  int ex_off;
+  int e_off;
+  int p_off;
   int total;
 };
 
-__host__ __device__ inline Layout make_layout(int N, int bps, int nslots, int dg, bool frame) {
+__host__ __device__ inline Layout make_layout(int N, int bps, int nslots, int dg, int groups,
+                                              bool frame) {
   Layout l;
   const int A = geo_A(N);
+  l.tw_off = kSmemHeader;
+  l.group_off = align_up(l.tw_off + (N <= 1024 ? N * 8 : 0), 128);
   l.team_stage = (N + geo_spad(N, bps)) * bps;
-  l.stage_off = kSmemHeader;
-  l.ex_off = align_up(l.stage_off + nslots * A * l.team_stage, 128);
-  l.tw_off = l.ex_off + A * geo_XS(N) * 8;
-  l.e_off = l.tw_off + (N <= 1024 ? N * 8 : 0);
+  l.stage_off = 0;
+  l.ex_off = align_up(nslots * A * l.team_stage, 128);
+  l.e_off = l.ex_off + A * geo_XS(N) * 8;
   if (frame) {
     l.p_off = align_up(l.e_off + N * 4, 128);
-    l.total = l.p_off + dg * N * 8;
+    l.group_bytes = align_up(l.p_off + dg * N * 8, 128);
   } else {
     l.p_off = l.e_off;
-    l.total = l.e_off;
+    l.group_bytes = align_up(l.e_off, 128);
   }
+  l.total = l.group_off + groups * l.group_bytes;
   return l;
 }
 
@@ -281,12 +295,16 @@ __device__ __forceinline__ void dft(float2* v, const KParams& p) {
 // a compile-time offset.
 __device__ __forceinline__ int xpad(int n) { return n + (n >> 5); }
 
+// Synchronise one FFT team's group (gi): a warp, a named barrier, or the block.
 template <int LOG2N>
-__device__ __forceinline__ void team_sync() {
-  if constexpr (Geo<LOG2N>::W == 1) {
+__device__ __forceinline__ void team_sync(int gi) {
+  using G = Geo<LOG2N>;
+  if constexpr (G::W == 1) {
     __syncwarp();
-  } else {
+  } else if constexpr (G::G == 1) {
     __syncthreads();
+  } else {
+    named_sync(1 + gi, G::TG);
   }
 }
 
@@ -301,7 +319,7 @@ __device__ __forceinline__ int bin_of(int t, int e) {
   }
 }
 
-// Owner of bin k after the antenna reduction: the thread (tid) whose
+// Owner of bin k after the antenna reduction: the group thread (tid) whose
 // register e = alpha * (32/A) + c holds it, and the slot c.  Inverse of
 // bin_of with the thread mapping of Geo.
 template <int LOG2N>
@@ -322,6 +340,18 @@ __device__ __forceinline__ void owner_of(int k, int& tid, int& c) {
   tid = (jt / G::F) * 32 + (jt % G::F) * G::A + alpha;
 }
 
+// One interleaved int16 IQ word -> {I, Q} as floats, exactly, without the
+// conversion unit: flipping the sign bits gives offset-binary u = v + 32768,
+// 0x4B000000 | u is the float 2^23 + u, and one packed subtraction of
+// 2^23 + 32768 leaves v.
+__device__ __forceinline__ float2 sc16_to_float2(uint32_t w) {
+  const uint32_t u = w ^ 0x80008000u;
+  const uint32_t lo = (u & 0xffffu) | 0x4b000000u;
+  const uint32_t hi = __byte_perm(u, 0x4b000000u, 0x7632);
+  return __fadd2_rn(make_float2(__uint_as_float(lo), __uint_as_float(hi)),
+                    make_float2(-8421376.0f, -8421376.0f));
+}
+
 // Pass-1 inputs x[jt + r L], r < 32, of one antenna-symbol row (N samples).
 template <int LOG2N, bool FC32>
 __device__ __forceinline__ void load_row(float2 (&v)[32], const void* row, int jt,
@@ -334,11 +364,8 @@ __device__ __forceinline__ void load_row(float2 (&v)[32], const void* row, int j
   } else {
     const uint32_t* s = static_cast<const uint32_t*>(row);
 #pragma unroll
-    for (int r = 0; r < 32; ++r) {
-      const uint32_t w = from_global ? __ldg(s + jt + r * G::L) : s[jt + r * G::L];
-      v[r] = make_float2(static_cast<float>(static_cast<int16_t>(w & 0xffffu)),
-                         static_cast<float>(static_cast<int16_t>(w >> 16)));
-    }
+    for (int r = 0; r < 32; ++r)
+      v[r] = sc16_to_float2(from_global ? __ldg(s + jt + r * G::L) : s[jt + r * G::L]);
   }
 }
 
@@ -346,14 +373,16 @@ __device__ __forceinline__ void load_row(float2 (&v)[32], const void* row, int j
 // jt (Y1[jt*32 + r]); on return v[e] = Y[bin_of(jt, e)] (unscaled).  ex is
 // this antenna's exchange region; tw the pass twiddles (shared memory for
 // N <= 1024, global for N = 2048).  Every thread of the block calls this.
-template <int LOG2N>
-__device__ __forceinline__ void team_fft_rest(float2 (&v)[32], float2* ex, int jt,
-                                              const float2* tw, const KParams& p) {
+template <int LOG2N, typename AfterSync>
+__device__ __forceinline__ void team_fft_rest(float2 (&v)[32], float2* ex, int jt, int gi,
+                                              const float2* tw, const KParams& p,
+                                              AfterSync&& after_sync) {
   using G = Geo<LOG2N>;
   constexpr int L = G::L;
 #pragma unroll
   for (int r = 0; r < 32; ++r) ex[xpad(jt * 32 + r)] = v[r];
-  team_sync<LOG2N>();
+  team_sync<LOG2N>(gi);
+  after_sync();   // work placed where the team does not wait on it
   if constexpr (G::N <= 1024) {
 #pragma unroll
     for (int i = 0; i < 32 / L; ++i) {
@@ -384,7 +413,7 @@ __device__ __forceinline__ void team_fft_rest(float2 (&v)[32], float2* ex, int j
         }
       }
     }
-    team_sync<LOG2N>();   // all reads done before the second exchange
+    team_sync<LOG2N>(gi);   // all reads done before the second exchange
 #pragma unroll
     for (int i = 0; i < 4; ++i) dft<8>(v + i * 8, p);
 #pragma unroll
@@ -393,7 +422,7 @@ __device__ __forceinline__ void team_fft_rest(float2 (&v)[32], float2* ex, int j
 #pragma unroll
       for (int r = 0; r < 8; ++r) ex[xpad((j >> 5) * 256 + (j & 31) + 32 * r)] = v[i * 8 + r];
     }
-    team_sync<LOG2N>();
+    team_sync<LOG2N>(gi);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int j = jt + 64 * i;
@@ -444,7 +473,7 @@ __device__ __forceinline__ const float2* load_pass_twiddles(const KParams& p,
   using G = Geo<LOG2N>;
   if constexpr (G::N <= 1024) {
     float2* tws = reinterpret_cast<float2*>(smem + lay.tw_off);
-    for (int i = threadIdx.x; i < G::N; i += G::T) tws[i] = __ldg(p.twP + i);
+    for (int i = threadIdx.x; i < G::N; i += blockDim.x) tws[i] = __ldg(p.twP + i);
     return tws;
   } else {
     return p.twP;
@@ -453,42 +482,16 @@ __device__ __forceinline__ const float2* load_pass_twiddles(const KParams& p,
 
 // ------------------------------------------------------- staging pipeline
 
-struct StepInfo {
-  int g, c, s, d;   // group, antenna chunk, symbol, data index (-1 = pilot)
-};
-
-// Steps of a frame block: group-major, chunk, then items (pilot first in
-// group 0 of the fused mode, then the group's data symbols).
+// Items per antenna chunk in data-symbol group g: the pilot first (group 0 of
+// the fused mode), then the group's data symbols.
 __device__ __forceinline__ int group_items(const KParams& p, int g) {
   const int nd = min(p.dg, p.D - g * p.dg);
   return nd + ((p.mode == kModeRun && g == 0) ? 1 : 0);
 }
-__device__ inline StepInfo frame_step(const KParams& p, int i) {
-  StepInfo si;
-  int g = 0;
-  for (;;) {
-    const int n = p.chunks * group_items(p, g);
-    if (i < n) break;
-    i -= n;
-    ++g;
-  }
-  const int items = group_items(p, g);
-  si.g = g;
-  si.c = i / items;
-  int it = i % items;
-  if (p.mode == kModeRun && g == 0) {
-    if (it == 0) {
-      si.s = p.pilot_idx;
-      si.d = -1;
-      return si;
-    }
-    --it;
-  }
-  si.d = g * p.dg + it;
-  si.s = si.d < p.pilot_idx ? si.d : si.d + 1;
-  return si;
+// Antenna chunks handled by block group gi of G: c = gi, gi + G, ...
+__device__ __forceinline__ int chunks_of(const KParams& p, int gi, int G) {
+  return (p.chunks - gi + G - 1) / G;
 }
-
 template <int LOG2N, bool FC32>
 __device__ __forceinline__ const unsigned char* row_ptr(const KParams& p, int f, int m,
                                                         int s) {
@@ -499,19 +502,54 @@ __device__ __forceinline__ const unsigned char* row_ptr(const KParams& p, int f,
 }
 
 // Issue the bulk copies of one step (antennas of chunk c, symbol s) into a
-// slot; called by one thread.
+// slot.  Called by a whole warp: lane 0 registers the byte count on the
+// slot's mbarrier and lane a issues the copy of antenna row a.
 template <int LOG2N, bool FC32>
 __device__ __forceinline__ void issue_step(const KParams& p, int f, int c, int s,
                                            unsigned char* slot, int team_stage,
-                                           uint32_t bar, uint64_t pol) {
+                                           uint32_t bar, uint64_t pol, int lane) {
   using G = Geo<LOG2N>;
   constexpr uint32_t bytes = G::N * (FC32 ? 8 : 4);
   const int nvalid = min(G::A, p.M - c * G::A);
-  mbar_expect_tx(bar, bytes * nvalid);
-  for (int a = 0; a < nvalid; ++a)
-    bulk_load(smem_u32(slot + a * team_stage), row_ptr<LOG2N, FC32>(p, f, c * G::A + a, s),
+  if (lane == 0) mbar_expect_tx(bar, bytes * nvalid);
+  if (lane < nvalid)
+    bulk_load(smem_u32(slot + lane * team_stage), row_ptr<LOG2N, FC32>(p, f, c * G::A + lane, s),
               bytes, bar, pol);
 }
+
+// Walks the steps of one block group in order (data-symbol group, chunk,
+// item) with O(1) work per step.
+struct StepCursor {
+  int g, u, it, items, nc, G, gi;
+  __device__ void init(const KParams& p, int gi_, int G_) {
+    gi = gi_;
+    G = G_;
+    nc = chunks_of(p, gi, G);
+    g = 0;
+    u = 0;
+    it = 0;
+    items = group_items(p, 0);
+  }
+  // chunk and symbol of the current step
+  __device__ int chunk() const { return gi + G * u; }
+  __device__ int symbol(const KParams& p) const {
+    int i = it;
+    if (p.mode == kModeRun && g == 0) {
+      if (i == 0) return p.pilot_idx;
+      --i;
+    }
+    const int d = g * p.dg + i;
+    return d < p.pilot_idx ? d : d + 1;
+  }
+  __device__ void next(const KParams& p) {
+    if (++it < items) return;
+    it = 0;
+    if (++u < nc) return;
+    u = 0;
+    ++g;
+    items = group_items(p, g < p.groups ? g : 0);
+  }
+};
 
 __device__ __forceinline__ void latch(int* status, int code) {
   atomicCAS(status, 0, code);
@@ -542,44 +580,51 @@ __device__ __forceinline__ uint32_t gray(int l) { return static_cast<uint32_t>(l
 template <int LOG2N, bool FC32>
 __global__ void __launch_bounds__(Geo<LOG2N>::T, 1) frame_kernel(const KParams p) {
   using G = Geo<LOG2N>;
-  constexpr int N = G::N, A = G::A, T = G::T, F = G::F;
+  constexpr int N = G::N, A = G::A, T = G::T, TG = G::TG, F = G::F, NG = G::G;
   constexpr int OWN = 32 / A;  // bins per thread after the antenna reduction
   extern __shared__ __align__(128) unsigned char smem[];
   const int f = blockIdx.x;
   const int tid = threadIdx.x;
+  const int gi = tid / TG;             // group of this thread
+  const int ltid = tid % TG;           // thread index within the group
   const int lane = tid & 31;
   const int alpha = lane % A;
-  const int jt = (tid >> 5) * F + lane / A;
-  const Layout lay = make_layout(N, FC32 ? 8 : 4, p.nslots, p.dg, true);
+  const int jt = (ltid >> 5) * F + lane / A;
+  const Layout lay = make_layout(N, FC32 ? 8 : 4, p.nslots, p.dg, NG, true);
   const float2* tw = load_pass_twiddles<LOG2N>(p, smem, lay);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 64);
-  unsigned char* stage = smem + lay.stage_off;
-  float* E = reinterpret_cast<float*>(smem + lay.e_off);
-  float2* P = reinterpret_cast<float2*>(smem + lay.p_off);
-  float2* myex = reinterpret_cast<float2*>(smem + lay.ex_off) + alpha * G::XS;
   const int K = p.nslots;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem) + gi * kMaxSlots;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 192 + 4 * gi);
+  unsigned char* greg = smem + lay.group_off + gi * lay.group_bytes;
+  unsigned char* stage = greg + lay.stage_off;
+  float* E = reinterpret_cast<float*>(greg + lay.e_off);
+  float2* P = reinterpret_cast<float2*>(greg + lay.p_off);
+  float2* myex = reinterpret_cast<float2*>(greg + lay.ex_off) + alpha * G::XS;
   const int slot_bytes = A * lay.team_stage;
+  const int nc = chunks_of(p, gi, NG);
 
   int total = 0;
-  for (int g = 0; g < p.groups; ++g) total += p.chunks * group_items(p, g);
+  for (int g = 0; g < p.groups; ++g) total += nc * group_items(p, g);
 
   uint64_t pol = 0;
-  if (tid == 0) {
+  if (ltid == 0) {
     *abort_flag = 0;
     if (p.use_tma) {
-      pol = evict_first_policy();
       for (int s = 0; s < K; ++s) mbar_init(smem_u32(&bars[s]), 1);
       fence_mbar_init();
     }
   }
-  for (int k = tid; k < N; k += T) E[k] = 0.f;
+  for (int k = ltid; k < N; k += TG) E[k] = 0.f;
   __syncthreads();
-  if (tid == 0 && p.use_tma) {
+  StepCursor cur;   // next step to load (meaningful in warp 0 of the group)
+  cur.init(p, gi, NG);
+  if (ltid < 32 && p.use_tma) {
+    if (ltid == 0) pol = evict_first_policy();
+    pol = __shfl_sync(0xffffffffu, pol, 0);
     for (int i = 0; i < K && i < total; ++i) {
-      const StepInfo si = frame_step(p, i);
-      issue_step<LOG2N, FC32>(p, f, si.c, si.s, stage + i * slot_bytes, lay.team_stage,
-                              smem_u32(&bars[i]), pol);
+      issue_step<LOG2N, FC32>(p, f, cur.chunk(), cur.symbol(p), stage + i * slot_bytes,
+                              lay.team_stage, smem_u32(&bars[i]), pol, lane);
+      cur.next(p);
     }
   }
 
@@ -588,10 +633,11 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T, 1) frame_kernel(const KParams p
   for (int g = 0; g < p.groups; ++g) {
     const int nd = min(p.dg, p.D - g * p.dg);
     const int d0 = g * p.dg;
-    for (int i = tid; i < nd * N; i += T) P[i] = make_float2(0.f, 0.f);
-    __syncthreads();
+    for (int i = ltid; i < nd * N; i += TG) P[i] = make_float2(0.f, 0.f);
+    team_sync<LOG2N>(gi);
 
-    for (int c = 0; c < p.chunks; ++c) {
+    for (int u = 0; u < nc; ++u) {
+      const int c = gi + NG * u;
       const int m = c * A + alpha;
       const bool valid = m < p.M;
       const size_t hrow = (static_cast<size_t>(f) * p.M + m) * N;
@@ -609,7 +655,7 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T, 1) frame_kernel(const KParams p
           for (int e = 0; e < 32; ++e) e2[e] = make_float2(h[e].x * h[e].x + h[e].y * h[e].y, 0.f);
           reduce_scatter<A, 16>(e2, alpha);
 #pragma unroll
-          for (int cc = 0; cc < OWN; ++cc) E[cc * T + tid] += e2[cc].x;
+          for (int cc = 0; cc < OWN; ++cc) E[cc * TG + ltid] += e2[cc].x;
         }
       }
       const int items = group_items(p, g);
@@ -636,14 +682,17 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T, 1) frame_kernel(const KParams p
           }
         }
         dft<32>(v, p);
-        __syncthreads();  // staging slot consumed; exchange buffer free
-        if (tid == 0 && p.use_tma && step + K < total) {
-          const StepInfo si = frame_step(p, step + K);
-          fence_proxy_async();
-          issue_step<LOG2N, FC32>(p, f, si.c, si.s, stage + slot * slot_bytes, lay.team_stage,
-                                  smem_u32(&bars[slot]), pol);
-        }
-        team_fft_rest<LOG2N>(v, myex, jt, tw, p);
+        team_sync<LOG2N>(gi);  // staging slot consumed; exchange buffer free
+        // refill the consumed slot once the exchange barrier has passed, so
+        // the other warps of the group do not wait on the issuing warp
+        team_fft_rest<LOG2N>(v, myex, jt, gi, tw, p, [&] {
+          if (ltid < 32 && p.use_tma && step + K < total) {
+            fence_proxy_async();
+            issue_step<LOG2N, FC32>(p, f, cur.chunk(), cur.symbol(p), stage + slot * slot_bytes,
+                                    lay.team_stage, smem_u32(&bars[slot]), pol, lane);
+            cur.next(p);
+          }
+        });
         if (is_pilot) {
           // LS estimate H = Y conj(X) / |X|^2 (1/sqrt(N) folded into xinv)
 #pragma unroll
@@ -656,26 +705,32 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T, 1) frame_kernel(const KParams p
           }
           reduce_scatter<A, 16>(v, alpha);
 #pragma unroll
-          for (int cc = 0; cc < OWN; ++cc) E[cc * T + tid] += v[cc].x;
+          for (int cc = 0; cc < OWN; ++cc) E[cc * TG + ltid] += v[cc].x;
         } else {
           // MRC numerator: conj(H) Y summed over the antennas of the chunk
 #pragma unroll
           for (int e = 0; e < 32; ++e) v[e] = cmulc(h[e], v[e]);
           reduce_scatter<A, 16>(v, alpha);
-          float2* Pd = P + (d - d0) * N + tid;
+          float2* Pd = P + (d - d0) * N + ltid;
 #pragma unroll
-          for (int cc = 0; cc < OWN; ++cc) Pd[cc * T] = cadd(Pd[cc * T], v[cc]);
+          for (int cc = 0; cc < OWN; ++cc) Pd[cc * TG] = cadd(Pd[cc * TG], v[cc]);
         }
       }
     }
     __syncthreads();
+    float* E0 = reinterpret_cast<float*>(smem + lay.group_off + lay.e_off);
     if (g == 0) {
-      // E -> 1 / (sqrt(N) E); zero or non-finite energy flags the frame
-      for (int k = tid; k < N; k += T) {
-        const float e = E[k];
+      // E (summed over the groups) -> 1 / (sqrt(N) E); zero or non-finite
+      // energy flags the frame
+      for (int i = tid; i < N; i += T) {
+        float e = 0.f;
+#pragma unroll
+        for (int q = 0; q < NG; ++q)
+          e += reinterpret_cast<const float*>(smem + lay.group_off + q * lay.group_bytes +
+                                              lay.e_off)[i];
         const bool ok = (e > 0.f) && (e <= 3.4028234663852886e38f);
         if (!ok) latch(p.status, kStDevice);
-        E[k] = ok ? (1.0f / e) * p.inv_sqrtN : 0.f;
+        E0[i] = ok ? (1.0f / e) * p.inv_sqrtN : 0.f;
       }
       __syncthreads();
     }
@@ -692,8 +747,13 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T, 1) frame_kernel(const KParams p
         const int k = k0 + b;
         int otid, oc;
         owner_of<LOG2N>(k, otid, oc);
-        const float ie = E[oc * T + otid];
-        const float2 sum = P[dl * N + oc * T + otid];
+        const int i = oc * TG + otid;
+        const float ie = E0[i];
+        float2 sum = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < NG; ++q)
+          sum = cadd(sum, reinterpret_cast<const float2*>(smem + lay.group_off +
+                                                          q * lay.group_bytes + lay.p_off)[dl * N + i]);
         const float2 z = (ie != 0.f) ? make_float2(sum.x * ie, sum.y * ie) : make_float2(0.f, 0.f);
         if (p.eq) p.eq[(static_cast<size_t>(f) * p.D + d) * N + k] = z;
         uint32_t code = gray(axis_level(z.x, p));
@@ -705,7 +765,7 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T, 1) frame_kernel(const KParams p
     }
     __syncthreads();
   }
-  if (tid == 0 && p.use_tma && *abort_flag) {
+  if (ltid == 0 && p.use_tma && *abort_flag) {
     // a wait gave up: give any copy still in flight a bounded chance to land
     for (int s = 0; s < K && s < total; ++s) {
       const int last = total - 1 - ((total - 1 - s) % K);
@@ -716,8 +776,9 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T, 1) frame_kernel(const KParams p
 
 // ======================================================= estimate kernel
 
+// One group per block: antenna chunk c of frame f.
 template <int LOG2N, bool FC32>
-__global__ void __launch_bounds__(Geo<LOG2N>::T) estimate_kernel(const KParams p) {
+__global__ void __launch_bounds__(Geo<LOG2N>::TG) estimate_kernel(const KParams p) {
   using G = Geo<LOG2N>;
   constexpr int N = G::N, A = G::A, F = G::F;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -727,12 +788,12 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T) estimate_kernel(const KParams p
   const int lane = tid & 31;
   const int alpha = lane % A;
   const int jt = (tid >> 5) * F + lane / A;
-  const Layout lay = make_layout(N, FC32 ? 8 : 4, 1, 0, false);
+  const Layout lay = make_layout(N, FC32 ? 8 : 4, 1, 0, 1, false);
   const float2* tw = load_pass_twiddles<LOG2N>(p, smem, lay);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 64);
-  unsigned char* stage = smem + lay.stage_off;
-  float2* myex = reinterpret_cast<float2*>(smem + lay.ex_off) + alpha * G::XS;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 192);
+  unsigned char* stage = smem + lay.group_off + lay.stage_off;
+  float2* myex = reinterpret_cast<float2*>(smem + lay.group_off + lay.ex_off) + alpha * G::XS;
   const int m = c * A + alpha;
   const bool valid = m < p.M;
   if (tid == 0) {
@@ -740,11 +801,12 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T) estimate_kernel(const KParams p
     if (p.use_tma) {
       mbar_init(smem_u32(&bars[0]), 1);
       fence_mbar_init();
-      issue_step<LOG2N, FC32>(p, f, c, p.pilot_idx, stage, lay.team_stage, smem_u32(&bars[0]),
-                              evict_first_policy());
     }
   }
   __syncthreads();
+  if (tid < 32 && p.use_tma)
+    issue_step<LOG2N, FC32>(p, f, c, p.pilot_idx, stage, lay.team_stage, smem_u32(&bars[0]),
+                            evict_first_policy(), lane);
   float2 v[32];
   if (p.use_tma) wait_slot(smem_u32(&bars[0]), 0, abort_flag, p.status);
   if (valid) {
@@ -757,7 +819,7 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T) estimate_kernel(const KParams p
     for (int r = 0; r < 32; ++r) v[r] = make_float2(0.f, 0.f);
   }
   dft<32>(v, p);
-  team_fft_rest<LOG2N>(v, myex, jt, tw, p);
+  team_fft_rest<LOG2N>(v, myex, jt, 0, tw, p, [] {});
   if (valid) {
     const size_t hrow = (static_cast<size_t>(f) * p.M + m) * N;
 #pragma unroll
@@ -770,8 +832,9 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T) estimate_kernel(const KParams p
 
 // ======================================================= fft kernel
 
+// One group per block: antenna chunk c of frame f, every symbol.
 template <int LOG2N, bool FC32>
-__global__ void __launch_bounds__(Geo<LOG2N>::T) fft_kernel(const KParams p) {
+__global__ void __launch_bounds__(Geo<LOG2N>::TG) fft_kernel(const KParams p) {
   using G = Geo<LOG2N>;
   constexpr int N = G::N, A = G::A, F = G::F;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -781,12 +844,12 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T) fft_kernel(const KParams p) {
   const int lane = tid & 31;
   const int alpha = lane % A;
   const int jt = (tid >> 5) * F + lane / A;
-  const Layout lay = make_layout(N, FC32 ? 8 : 4, p.nslots, 0, false);
+  const Layout lay = make_layout(N, FC32 ? 8 : 4, p.nslots, 0, 1, false);
   const float2* tw = load_pass_twiddles<LOG2N>(p, smem, lay);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 64);
-  unsigned char* stage = smem + lay.stage_off;
-  float2* myex = reinterpret_cast<float2*>(smem + lay.ex_off) + alpha * G::XS;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 192);
+  unsigned char* stage = smem + lay.group_off + lay.stage_off;
+  float2* myex = reinterpret_cast<float2*>(smem + lay.group_off + lay.ex_off) + alpha * G::XS;
   const int m = c * A + alpha;
   const bool valid = m < p.M;
   const int K = p.nslots;
@@ -795,15 +858,17 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T) fft_kernel(const KParams p) {
   if (tid == 0) {
     *abort_flag = 0;
     if (p.use_tma) {
-      pol = evict_first_policy();
       for (int s = 0; s < K; ++s) mbar_init(smem_u32(&bars[s]), 1);
       fence_mbar_init();
-      for (int s = 0; s < K && s < p.S; ++s)
-        issue_step<LOG2N, FC32>(p, f, c, s, stage + s * slot_bytes, lay.team_stage,
-                                smem_u32(&bars[s]), pol);
     }
   }
   __syncthreads();
+  if (tid < 32 && p.use_tma) {
+    pol = evict_first_policy();
+    for (int s = 0; s < K && s < p.S; ++s)
+      issue_step<LOG2N, FC32>(p, f, c, s, stage + s * slot_bytes, lay.team_stage,
+                              smem_u32(&bars[s]), pol, lane);
+  }
   for (int s = 0; s < p.S; ++s) {
     const int slot = s % K;
     float2 v[32];
@@ -819,12 +884,13 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T) fft_kernel(const KParams p) {
     }
     dft<32>(v, p);
     __syncthreads();
-    if (tid == 0 && p.use_tma && s + K < p.S) {
-      fence_proxy_async();
-      issue_step<LOG2N, FC32>(p, f, c, s + K, stage + slot * slot_bytes, lay.team_stage,
-                              smem_u32(&bars[slot]), pol);
-    }
-    team_fft_rest<LOG2N>(v, myex, jt, tw, p);
+    team_fft_rest<LOG2N>(v, myex, jt, 0, tw, p, [&] {
+      if (tid < 32 && p.use_tma && s + K < p.S) {
+        fence_proxy_async();
+        issue_step<LOG2N, FC32>(p, f, c, s + K, stage + slot * slot_bytes, lay.team_stage,
+                                smem_u32(&bars[slot]), pol, lane);
+      }
+    });
     if (valid) {
       float2* out = p.Y_out + ((static_cast<size_t>(f) * p.M + m) * p.S + s) * N;
 #pragma unroll

@@ -100,13 +100,12 @@ bool plan_geometry(int M, int N, int D, lsas_input_fmt fmt, Geometry* g) {
   g->L = N / 32;
   g->T = geo_T(N);
   const int bps = fmt == LSAS_IN_SC16 ? 4 : 8;
+  const int G = geo_G(N);
   (void)M;
-  // fused frame kernel
   int best_dg = 0, slots = 2;
   for (slots = 2; slots >= 1; --slots) {
-    const Layout l0 = make_layout(N, bps, slots, 0, true);
-    const int room = kSmemLimit - l0.total;
-    best_dg = room / (N * 8);
+    for (best_dg = D; best_dg >= 1; --best_dg)
+      if (make_layout(N, bps, slots, best_dg, G, true).total <= kSmemLimit) break;
     if (best_dg >= 1) break;
   }
   if (best_dg < 1) return false;
@@ -114,12 +113,12 @@ bool plan_geometry(int M, int N, int D, lsas_input_fmt fmt, Geometry* g) {
   g->dg = (D + g->groups - 1) / g->groups;
   g->nslots = slots;
   while (g->nslots < kMaxSlots &&
-         make_layout(N, bps, g->nslots + 1, g->dg, true).total <= kSmemLimit)
+         make_layout(N, bps, g->nslots + 1, g->dg, G, true).total <= kSmemLimit)
     ++g->nslots;
-  g->smem_frame = make_layout(N, bps, g->nslots, g->dg, true).total;
-  g->smem_est = make_layout(N, bps, 1, 0, false).total;
+  g->smem_frame = make_layout(N, bps, g->nslots, g->dg, G, true).total;
+  g->smem_est = make_layout(N, bps, 1, 0, 1, false).total;
   g->fft_slots = 2;
-  g->smem_fft = make_layout(N, bps, 2, 0, false).total;
+  g->smem_fft = make_layout(N, bps, 2, 0, 1, false).total;
   return true;
 }
 
