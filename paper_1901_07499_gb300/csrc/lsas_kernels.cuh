@@ -52,6 +52,7 @@ struct KParams {
   int groups, dg;        // data-symbol groups per frame, symbols per group
   int mode;              // kModeDemod or kModeRun (frame_kernel)
   int use_tma, nslots;
+  int tmem_cols, tmem_cth;   // TMEM allocation (columns) and columns per thread
   int q, wbits, axes, nthr;
   float inv_sqrtN;
   float thr[kMaxThresholds];   // per-axis decision boundaries (float32)
@@ -104,19 +105,22 @@ struct Geo {
 
 __host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
 
-// Shared memory of a block: a header (mbarriers, flags), the pass twiddles,
-// then one region per group: staging slots, exchange buffer, and (frame
-// kernel) channel energy and partial sums, both in owner layout.
+// Shared memory of a block: a header (mbarriers, flags, TMEM address), the
+// pass twiddles, then one region per group: staging slots and exchange
+// buffer.  After the chunk loop of the fused kernel, group 0's staging slots
+// are reused for the partial-sum exchange between groups and for the
+// demapped codes.
 struct Layout {
   int tw_off;       // pass twiddles (float2[N], N <= 1024)
   int group_off;    // first group region
   int group_bytes;  // stride between group regions
   int team_stage;   // bytes per antenna per staging slot
   int stage_off;    // within a group region
-  int ex_off;
-  int e_off;
-  int p_off;
+  int ex_off;       // within a group region
+  int merge_off;    // fused kernel: float2[2][N] partial sums + float[N] energy
+  int codes_off;    // fused kernel: uint8[dg][N] demapped codes
   int total;
+  int reuse_end;    // end of the reused region (must stay inside group 0's slots)
 };
 
 __host__ __device__ inline Layout make_layout(int N, int bps, int nslots, int dg, int groups,
@@ -128,16 +132,30 @@ __host__ __device__ inline Layout make_layout(int N, int bps, int nslots, int dg
   l.team_stage = (N + geo_spad(N, bps)) * bps;
   l.stage_off = 0;
   l.ex_off = align_up(nslots * A * l.team_stage, 128);
-  l.e_off = l.ex_off + A * geo_XS(N) * 8;
-  if (frame) {
-    l.p_off = align_up(l.e_off + N * 4, 128);
-    l.group_bytes = align_up(l.p_off + dg * N * 8, 128);
-  } else {
-    l.p_off = l.e_off;
-    l.group_bytes = align_up(l.e_off, 128);
-  }
+  l.group_bytes = align_up(l.ex_off + A * geo_XS(N) * 8, 128);
   l.total = l.group_off + groups * l.group_bytes;
+  l.merge_off = l.group_off;
+  l.codes_off = align_up(l.merge_off + (groups > 1 ? 2 * N * 8 + N * 4 : 0), 128);
+  l.reuse_end = frame ? l.codes_off + dg * N : l.group_off;
   return l;
+}
+
+// Per-thread accumulators of the fused kernel live in tensor memory (TMEM):
+// OWN = 32/A subcarriers per thread after the antenna reduction, for dg data
+// symbols (complex) plus the channel energy.  Warps sharing a TMEM lane
+// quarter (warp % 4) split the columns by warp / 4.
+__host__ __device__ constexpr int geo_OWN(int N) { return 32 / geo_A(N); }
+__host__ __device__ inline int tmem_cols_thread(int N, int dg) {
+  return 2 * geo_OWN(N) * dg + geo_OWN(N);
+}
+__host__ __device__ inline int tmem_warps_per_quarter(int N) {
+  return geo_T(N) / 32 > 4 ? geo_T(N) / 128 : 1;
+}
+__host__ __device__ inline int tmem_alloc_cols(int N, int dg) {
+  const int need = tmem_cols_thread(N, dg) * tmem_warps_per_quarter(N);
+  int c = 32;
+  while (c < need) c *= 2;
+  return c;
 }
 
 // Number of pass twiddles in the host-built table (layout in pass_twiddles):
@@ -210,6 +228,92 @@ static __device__ __noinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t par
 __device__ __forceinline__ void named_sync(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
+
+// ------------------------------------------------------- tensor memory
+
+__device__ __forceinline__ void tmem_alloc(uint32_t smem_dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_dst),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// Load / store NC consecutive 32-bit columns of this thread's TMEM lane
+// (32x32b shape: thread i of the warp accesses lane base + i).
+template <int NC> struct Tmem;
+template <> struct Tmem<2> {
+  static __device__ __forceinline__ void ld(uint32_t t, float* v) {
+    uint32_t r[2];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];"
+                 : "=r"(r[0]), "=r"(r[1]) : "r"(t) : "memory");
+    for (int i = 0; i < 2; ++i) v[i] = __uint_as_float(r[i]);
+  }
+  static __device__ __forceinline__ void st(uint32_t t, const float* v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1,%2};" ::"r"(t),
+                 "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])) : "memory");
+  }
+};
+template <> struct Tmem<4> {
+  static __device__ __forceinline__ void ld(uint32_t t, float* v) {
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(t) : "memory");
+    for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+  }
+  static __device__ __forceinline__ void st(uint32_t t, const float* v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(t),
+                 "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+                 "r"(__float_as_uint(v[3])) : "memory");
+  }
+};
+template <> struct Tmem<8> {
+  static __device__ __forceinline__ void ld(uint32_t t, float* v) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                   "=r"(r[6]), "=r"(r[7]) : "r"(t) : "memory");
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+  }
+  static __device__ __forceinline__ void st(uint32_t t, const float* v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(t),
+                 "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+                 "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+                 "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])) : "memory");
+  }
+};
+template <> struct Tmem<16> {
+  static __device__ __forceinline__ void ld(uint32_t t, float* v) {
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                   "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                   "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]) : "r"(t) : "memory");
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+  }
+  static __device__ __forceinline__ void st(uint32_t t, const float* v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 "
+                 "[%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(t),
+                 "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+                 "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+                 "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+                 "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+                 "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+                 "r"(__float_as_uint(v[15])) : "memory");
+  }
+};
 
 // ------------------------------------------------------- complex helpers
 
@@ -581,10 +685,13 @@ template <int LOG2N, bool FC32>
 __global__ void __launch_bounds__(Geo<LOG2N>::T, 1) frame_kernel(const KParams p) {
   using G = Geo<LOG2N>;
   constexpr int N = G::N, A = G::A, T = G::T, TG = G::TG, F = G::F, NG = G::G;
-  constexpr int OWN = 32 / A;  // bins per thread after the antenna reduction
+  constexpr int OWN = 32 / A;  // subcarriers per thread after the antenna reduction
+  using TmP = Tmem<2 * OWN>;   // one data symbol of partial sums (complex)
+  using TmE = Tmem<OWN>;       // channel energy
   extern __shared__ __align__(128) unsigned char smem[];
   const int f = blockIdx.x;
   const int tid = threadIdx.x;
+  const int warp = tid >> 5;
   const int gi = tid / TG;             // group of this thread
   const int ltid = tid % TG;           // thread index within the group
   const int lane = tid & 31;
@@ -595,10 +702,9 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T, 1) frame_kernel(const KParams p
   const int K = p.nslots;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem) + gi * kMaxSlots;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 192 + 4 * gi);
+  uint32_t* tmem_base = reinterpret_cast<uint32_t*>(smem + 160);
   unsigned char* greg = smem + lay.group_off + gi * lay.group_bytes;
   unsigned char* stage = greg + lay.stage_off;
-  float* E = reinterpret_cast<float*>(greg + lay.e_off);
-  float2* P = reinterpret_cast<float2*>(greg + lay.p_off);
   float2* myex = reinterpret_cast<float2*>(greg + lay.ex_off) + alpha * G::XS;
   const int slot_bytes = A * lay.team_stage;
   const int nc = chunks_of(p, gi, NG);
@@ -614,27 +720,45 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T, 1) frame_kernel(const KParams p
       fence_mbar_init();
     }
   }
-  for (int k = ltid; k < N; k += TG) E[k] = 0.f;
+  if (warp == 0) tmem_alloc(smem_u32(tmem_base), p.tmem_cols);
+  tmem_fence_before();
   __syncthreads();
+  tmem_fence_after();
+  // this thread's TMEM lane and first column: P(dl) at 2*OWN*dl, E after the dg symbols
+  const uint32_t tacc = *tmem_base + (static_cast<uint32_t>(32 * (warp & 3)) << 16) +
+                        static_cast<uint32_t>((warp >> 2) * p.tmem_cth);
+  const uint32_t tE = tacc + 2 * OWN * p.dg;
+
   StepCursor cur;   // next step to load (meaningful in warp 0 of the group)
   cur.init(p, gi, NG);
   if (ltid < 32 && p.use_tma) {
     if (ltid == 0) pol = evict_first_policy();
     pol = __shfl_sync(0xffffffffu, pol, 0);
-    for (int i = 0; i < K && i < total; ++i) {
-      issue_step<LOG2N, FC32>(p, f, cur.chunk(), cur.symbol(p), stage + i * slot_bytes,
-                              lay.team_stage, smem_u32(&bars[i]), pol, lane);
-      cur.next(p);
-    }
   }
+
+  float zero[2 * OWN];
+#pragma unroll
+  for (int i = 0; i < 2 * OWN; ++i) zero[i] = 0.f;
+  TmE::st(tE, zero);
 
   float2 h[32];
   int step = 0;
+  int gend = 0;   // first step after the current data-symbol group
   for (int g = 0; g < p.groups; ++g) {
     const int nd = min(p.dg, p.D - g * p.dg);
     const int d0 = g * p.dg;
-    for (int i = ltid; i < nd * N; i += TG) P[i] = make_float2(0.f, 0.f);
-    team_sync<LOG2N>(gi);
+    for (int dl = 0; dl < nd; ++dl) TmP::st(tacc + 2 * OWN * dl, zero);
+    // loads never run ahead into the next data-symbol group: group 0's
+    // staging slots are reused by the demap phase at its end
+    gend += nc * group_items(p, g);
+    if (ltid < 32 && p.use_tma) {
+      fence_proxy_async();   // the demap phase wrote these slots through the generic proxy
+      for (int i = step; i < step + K && i < gend; ++i) {
+        issue_step<LOG2N, FC32>(p, f, cur.chunk(), cur.symbol(p), stage + (i % K) * slot_bytes,
+                                lay.team_stage, smem_u32(&bars[i % K]), pol, lane);
+        cur.next(p);
+      }
+    }
 
     for (int u = 0; u < nc; ++u) {
       const int c = gi + NG * u;
@@ -654,8 +778,13 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T, 1) frame_kernel(const KParams p
 #pragma unroll
           for (int e = 0; e < 32; ++e) e2[e] = make_float2(h[e].x * h[e].x + h[e].y * h[e].y, 0.f);
           reduce_scatter<A, 16>(e2, alpha);
+          float acc[OWN];
+          tmem_wait_st();
+          TmE::ld(tE, acc);
+          tmem_wait_ld();
 #pragma unroll
-          for (int cc = 0; cc < OWN; ++cc) E[cc * TG + ltid] += e2[cc].x;
+          for (int cc = 0; cc < OWN; ++cc) acc[cc] += e2[cc].x;
+          TmE::st(tE, acc);
         }
       }
       const int items = group_items(p, g);
@@ -686,7 +815,7 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T, 1) frame_kernel(const KParams p
         // refill the consumed slot once the exchange barrier has passed, so
         // the other warps of the group do not wait on the issuing warp
         team_fft_rest<LOG2N>(v, myex, jt, gi, tw, p, [&] {
-          if (ltid < 32 && p.use_tma && step + K < total) {
+          if (ltid < 32 && p.use_tma && step + K < gend) {
             fence_proxy_async();
             issue_step<LOG2N, FC32>(p, f, cur.chunk(), cur.symbol(p), stage + slot * slot_bytes,
                                     lay.team_stage, smem_u32(&bars[slot]), pol, lane);
@@ -704,66 +833,130 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T, 1) frame_kernel(const KParams p
             v[e] = make_float2(h[e].x * h[e].x + h[e].y * h[e].y, 0.f);
           }
           reduce_scatter<A, 16>(v, alpha);
+          float acc[OWN];
+          tmem_wait_st();
+          TmE::ld(tE, acc);
+          tmem_wait_ld();
 #pragma unroll
-          for (int cc = 0; cc < OWN; ++cc) E[cc * TG + ltid] += v[cc].x;
+          for (int cc = 0; cc < OWN; ++cc) acc[cc] += v[cc].x;
+          TmE::st(tE, acc);
         } else {
           // MRC numerator: conj(H) Y summed over the antennas of the chunk
 #pragma unroll
           for (int e = 0; e < 32; ++e) v[e] = cmulc(h[e], v[e]);
           reduce_scatter<A, 16>(v, alpha);
-          float2* Pd = P + (d - d0) * N + ltid;
+          float acc[2 * OWN];
+          const uint32_t tp = tacc + 2 * OWN * (d - d0);
+          tmem_wait_st();
+          TmP::ld(tp, acc);
+          tmem_wait_ld();
 #pragma unroll
-          for (int cc = 0; cc < OWN; ++cc) Pd[cc * TG] = cadd(Pd[cc * TG], v[cc]);
+          for (int cc = 0; cc < OWN; ++cc) {
+            acc[2 * cc] += v[cc].x;
+            acc[2 * cc + 1] += v[cc].y;
+          }
+          TmP::st(tp, acc);
         }
       }
     }
+    // ---- demap: owners read their sums from TMEM; with two groups the
+    // partner group's partial sums come through shared memory
+    tmem_wait_st();
+    tmem_fence_before();
     __syncthreads();
-    float* E0 = reinterpret_cast<float*>(smem + lay.group_off + lay.e_off);
+    tmem_fence_after();
+    float2* mP = reinterpret_cast<float2*>(smem + lay.merge_off);   // [2][N]
+    float* mE = reinterpret_cast<float*>(smem + lay.merge_off + 2 * N * 8);
+    uint8_t* codes = smem + lay.codes_off;
+    float ie[OWN];
     if (g == 0) {
-      // E (summed over the groups) -> 1 / (sqrt(N) E); zero or non-finite
-      // energy flags the frame
-      for (int i = tid; i < N; i += T) {
-        float e = 0.f;
+      float e[OWN];
+      TmE::ld(tE, e);
+      tmem_wait_ld();
+      if constexpr (NG > 1) {
+        if (gi == 1) {
 #pragma unroll
-        for (int q = 0; q < NG; ++q)
-          e += reinterpret_cast<const float*>(smem + lay.group_off + q * lay.group_bytes +
-                                              lay.e_off)[i];
-        const bool ok = (e > 0.f) && (e <= 3.4028234663852886e38f);
-        if (!ok) latch(p.status, kStDevice);
-        E0[i] = ok ? (1.0f / e) * p.inv_sqrtN : 0.f;
+          for (int cc = 0; cc < OWN; ++cc) mE[cc * TG + ltid] = e[cc];
+        }
+        __syncthreads();
+        if (gi == 0) {
+#pragma unroll
+          for (int cc = 0; cc < OWN; ++cc) {
+            e[cc] += mE[cc * TG + ltid];
+            mE[cc * TG + ltid] = e[cc];
+          }
+        }
+        __syncthreads();
+        if (gi == 1) {
+#pragma unroll
+          for (int cc = 0; cc < OWN; ++cc) e[cc] = mE[cc * TG + ltid];
+        }
       }
-      __syncthreads();
+      // E -> 1 / (sqrt(N) E); zero or non-finite energy flags the frame
+#pragma unroll
+      for (int cc = 0; cc < OWN; ++cc) {
+        const bool ok = (e[cc] > 0.f) && (e[cc] <= 3.4028234663852886e38f);
+        if (!ok) latch(p.status, kStDevice);
+        ie[cc] = ok ? (1.0f / e[cc]) * p.inv_sqrtN : 0.f;
+      }
+      // keep 1/E in the energy columns for the later data-symbol groups
+      TmE::st(tE, ie);
+    } else {
+      TmE::ld(tE, ie);
+      tmem_wait_ld();
     }
-    // demap + pack: 8 consecutive subcarriers -> q bytes
+    // symbols are demapped in pairs: group q takes the symbol of parity q
+    for (int dl0 = 0; dl0 < nd; dl0 += NG) {
+      const int dl = dl0 + gi;            // symbol this thread demaps
+      float acc[2 * OWN];
+      if constexpr (NG > 1) {
+        // hand the partner group the partial sums of its symbol
+        const int dp = dl0 + (1 - gi);
+        if (dp < nd) {
+          TmP::ld(tacc + 2 * OWN * dp, acc);
+          tmem_wait_ld();
+#pragma unroll
+          for (int cc = 0; cc < OWN; ++cc)
+            mP[(1 - gi) * N + cc * TG + ltid] = make_float2(acc[2 * cc], acc[2 * cc + 1]);
+        }
+        __syncthreads();
+      }
+      if (dl < nd) {
+        TmP::ld(tacc + 2 * OWN * dl, acc);
+        tmem_wait_ld();
+        const int d = d0 + dl;
+#pragma unroll
+        for (int cc = 0; cc < OWN; ++cc) {
+          float2 sum = make_float2(acc[2 * cc], acc[2 * cc + 1]);
+          if constexpr (NG > 1) sum = cadd(sum, mP[gi * N + cc * TG + ltid]);
+          const int k = bin_of<LOG2N>(jt, alpha * OWN + cc);
+          const float2 z = (ie[cc] != 0.f) ? make_float2(sum.x * ie[cc], sum.y * ie[cc])
+                                           : make_float2(0.f, 0.f);
+          if (p.eq) p.eq[(static_cast<size_t>(f) * p.D + d) * N + k] = z;
+          uint32_t code = gray(axis_level(z.x, p));
+          if (p.axes == 2) code = (code << p.wbits) | gray(axis_level(z.y, p));
+          codes[dl * N + k] = static_cast<uint8_t>(code);
+        }
+      }
+      if constexpr (NG > 1) __syncthreads();
+    }
+    __syncthreads();
+    // pack: 8 consecutive subcarriers -> q bytes
     const int items8 = nd * (N / 8);
     const size_t frame_bytes = static_cast<size_t>(p.D) * N * p.q / 8;
     for (int it = tid; it < items8; it += T) {
       const int dl = it / (N / 8);
       const int k0 = (it % (N / 8)) * 8;
-      const int d = d0 + dl;
       uint64_t acc = 0;
 #pragma unroll
-      for (int b = 0; b < 8; ++b) {
-        const int k = k0 + b;
-        int otid, oc;
-        owner_of<LOG2N>(k, otid, oc);
-        const int i = oc * TG + otid;
-        const float ie = E0[i];
-        float2 sum = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int q = 0; q < NG; ++q)
-          sum = cadd(sum, reinterpret_cast<const float2*>(smem + lay.group_off +
-                                                          q * lay.group_bytes + lay.p_off)[dl * N + i]);
-        const float2 z = (ie != 0.f) ? make_float2(sum.x * ie, sum.y * ie) : make_float2(0.f, 0.f);
-        if (p.eq) p.eq[(static_cast<size_t>(f) * p.D + d) * N + k] = z;
-        uint32_t code = gray(axis_level(z.x, p));
-        if (p.axes == 2) code = (code << p.wbits) | gray(axis_level(z.y, p));
-        acc = (acc << p.q) | code;
-      }
-      uint8_t* dst = p.bits + f * frame_bytes + (static_cast<size_t>(d) * N + k0) * p.q / 8;
+      for (int b = 0; b < 8; ++b) acc = (acc << p.q) | codes[dl * N + k0 + b];
+      uint8_t* dst = p.bits + f * frame_bytes + (static_cast<size_t>(d0 + dl) * N + k0) * p.q / 8;
       for (int j = 0; j < p.q; ++j) dst[j] = static_cast<uint8_t>(acc >> (8 * (p.q - 1 - j)));
     }
+    tmem_wait_st();
+    tmem_fence_before();
     __syncthreads();
+    tmem_fence_after();
   }
   if (ltid == 0 && p.use_tma && *abort_flag) {
     // a wait gave up: give any copy still in flight a bounded chance to land
@@ -772,6 +965,7 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T, 1) frame_kernel(const KParams p
       (void)mbar_wait_bounded(smem_u32(&bars[last % K]), (last / K) & 1);
     }
   }
+  if (warp == 0) tmem_dealloc(*tmem_base, p.tmem_cols);
 }
 
 // ======================================================= estimate kernel

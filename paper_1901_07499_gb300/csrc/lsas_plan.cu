@@ -37,6 +37,7 @@ struct Geometry {
   int A, L, T;
   int nslots, groups, dg, smem_frame;
   int smem_est, smem_fft, fft_slots;
+  int tmem_cols, tmem_cth;
 };
 
 }  // namespace
@@ -93,8 +94,10 @@ LaunchFn launcher_for(int N) {
   }
 }
 
-// Choose staging slots and data-symbol groups so that the fused kernel's
-// shared memory fits one block per SM.
+// Choose the staging depth (slots) and the data symbols per group so that the
+// fused kernel fits the shared memory of one SM and its accumulators fit
+// tensor memory: prefer one data-symbol group (no second pass over H), then
+// the deepest staging ring.
 bool plan_geometry(int M, int N, int D, lsas_input_fmt fmt, Geometry* g) {
   g->A = geo_A(N);
   g->L = N / 32;
@@ -102,20 +105,28 @@ bool plan_geometry(int M, int N, int D, lsas_input_fmt fmt, Geometry* g) {
   const int bps = fmt == LSAS_IN_SC16 ? 4 : 8;
   const int G = geo_G(N);
   (void)M;
-  int best_dg = 0, slots = 2;
-  for (slots = 2; slots >= 1; --slots) {
-    for (best_dg = D; best_dg >= 1; --best_dg)
-      if (make_layout(N, bps, slots, best_dg, G, true).total <= kSmemLimit) break;
-    if (best_dg >= 1) break;
+  const int own = geo_OWN(N);
+  const int cols_per_warp_slot = 512 / tmem_warps_per_quarter(N);
+  int dg_tmem = (cols_per_warp_slot - own) / (2 * own);
+  if (dg_tmem < 1) return false;
+  bool found = false;
+  for (int groups = (D + dg_tmem - 1) / dg_tmem; groups <= D && !found; ++groups) {
+    const int dg = (D + groups - 1) / groups;
+    for (int slots = kMaxSlots; slots >= 2; --slots) {
+      const Layout l = make_layout(N, bps, slots, dg, G, true);
+      const int slot_region = slots * geo_A(N) * l.team_stage;
+      if (l.total > kSmemLimit || l.reuse_end > l.group_off + slot_region) continue;
+      g->groups = groups;
+      g->dg = dg;
+      g->nslots = slots;
+      g->smem_frame = l.total;
+      found = true;
+      break;
+    }
   }
-  if (best_dg < 1) return false;
-  g->groups = (D + best_dg - 1) / best_dg;
-  g->dg = (D + g->groups - 1) / g->groups;
-  g->nslots = slots;
-  while (g->nslots < kMaxSlots &&
-         make_layout(N, bps, g->nslots + 1, g->dg, G, true).total <= kSmemLimit)
-    ++g->nslots;
-  g->smem_frame = make_layout(N, bps, g->nslots, g->dg, G, true).total;
+  if (!found) return false;
+  g->tmem_cols = tmem_alloc_cols(N, g->dg);
+  g->tmem_cth = tmem_cols_thread(N, g->dg);
   g->smem_est = make_layout(N, bps, 1, 0, 1, false).total;
   g->fft_slots = 2;
   g->smem_fft = make_layout(N, bps, 2, 0, 1, false).total;
@@ -185,6 +196,8 @@ void base_params(lsas_plan p, KParams* k) {
   k->groups = p->geo.groups;
   k->dg = p->geo.dg;
   k->nslots = p->geo.nslots;
+  k->tmem_cols = p->geo.tmem_cols;
+  k->tmem_cth = p->geo.tmem_cth;
   k->q = p->q;
   k->wbits = p->wbits;
   k->axes = p->axes;
