@@ -21,7 +21,7 @@ static cudaError_t launch_t(int kind, const KParams& p, int grid, int smem, cuda
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) limit[kind][dev] = smem;
   }
-  const int threads = (kind == kKindFrame) ? Geo<LOG2N>::T : Geo<LOG2N>::TG;
+  const int threads = (kind == kKindFrame) ? Geo<LOG2N>::T : Geo<LOG2N>::TW;
   fn<<<grid, threads, smem, st>>>(p);
   return cudaGetLastError();
 }

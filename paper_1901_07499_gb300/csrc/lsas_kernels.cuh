@@ -1,28 +1,32 @@
 // lsas_kernels.cuh -- device code of liblsas for sm_103a.
 //
-// Three kernels share one building block, the "team FFT": a team of
-// L = N/32 threads transforms one N-point OFDM symbol of one antenna, each
-// thread holding 32 complex points in registers.  A Stockham auto-sort FFT
-// (radix 32, then radix N/32; N = 2048 uses 32 x 8 x 8) runs its butterflies
-// in registers and exchanges data between passes through a swizzled
-// shared-memory buffer.  A block holds A teams = A antennas of one symbol.
+// One FFT team of L = N/32 threads transforms one N-point OFDM symbol of one
+// antenna, 32 complex points per thread in registers: a Stockham auto-sort
+// FFT, radix 32 then radix N/32 (N = 2048: 32 x 8 x 8), exchanging data
+// between passes through padded shared memory.  A warp's lanes hold A
+// antennas x F = 32/A sub-lanes, so a warp group of W warps holds the teams
+// of A antennas (A = 128/L, at most 32), and the sum over antennas of MRC is
+// a warp-shuffle reduction.
 //
 // Input samples are staged by bulk asynchronous copies (cp.async.bulk, the
 // TMA engine) into a ring of shared-memory slots, one contiguous CP-stripped
-// symbol row per antenna, completion tracked by mbarriers; this is the CP
-// removal of Sec. II-B done as addressing.  Every wait on an mbarrier is
-// bounded: after ~2 s it latches LSAS_ERR_TIMEOUT and the block runs on
-// without waiting again, so a missing completion can never hang the GPU.
+// symbol row per antenna, completion tracked by mbarriers: the CP removal of
+// Sec. II-B done as addressing.  Every wait on an mbarrier is bounded: after
+// ~2 s it latches LSAS_ERR_TIMEOUT and the block runs on without waiting
+// again, so a missing completion can never hang the GPU.
 //
-//   frame_kernel    one block per frame: pilot FFT -> LS estimate H (kept in
-//                   registers, written out) and the channel energy sum, then
-//                   every data symbol: FFT -> conj(H) Y -> sum over antennas
-//                   (shared-memory reduction) accumulated per subcarrier,
-//                   then z = sum / energy -> Gray slicer -> packed bits.
-//                   Sec. II-C (LS, MRC), Sec. III (conjugate and channel sum
-//                   formed once and reused for every data symbol).
-//   estimate_kernel one block per (frame, antenna chunk): pilot FFT -> H.
-//   fft_kernel      one block per (frame, antenna chunk): all symbols -> Y.
+//   frame_kernel    one block per frame, warp-specialised: a producer warp
+//                   group stages rows, converts them and runs the first FFT
+//                   pass(es); a consumer warp group runs the last pass, forms
+//                   the LS estimate from the pilot (Sec. II-C), multiplies
+//                   every data symbol by conj(H), sums over antennas with
+//                   shuffles and accumulates per subcarrier in tensor memory
+//                   (the conjugate and the channel-energy sum are formed once
+//                   per frame and reused, Sec. III), then z = sum / energy ->
+//                   Gray slicer -> packed bits.  The two groups hand the
+//                   pass boundary over through a double-buffered exchange.
+//   estimate_kernel one warp group per (frame, antenna chunk): pilot -> H.
+//   fft_kernel      one warp group per (frame, antenna chunk): symbols -> Y.
 #pragma once
 
 #include <cstdint>
@@ -33,8 +37,8 @@ namespace lsas {
 enum { kModeEstimate = 0, kModeDemod = 1, kModeRun = 2 };
 enum { kStOk = 0, kStTimeout = 6, kStDevice = 7 };
 
-constexpr int kMaxSlots = 4;
-constexpr int kSmemHeader = 256;     // mbarriers (2 groups x 4 slots) + flags
+constexpr int kMaxSlots = 6;
+constexpr int kSmemHeader = 256;     // mbarriers, TMEM address, flags
 constexpr int kMaxThresholds = 15;   // 256-QAM: 16 levels per axis
 
 struct KParams {
@@ -49,7 +53,7 @@ struct KParams {
   int* status;           // latched device status
   int M, S, cp, pilot_idx, D;
   int chunks;            // ceil(M / A)
-  int groups, dg;        // data-symbol groups per frame, symbols per group
+  int groups, dg;        // data-symbol groups per frame, data symbols per group
   int mode;              // kModeDemod or kModeRun (frame_kernel)
   int use_tma, nslots;
   int tmem_cols, tmem_cth;   // TMEM allocation (columns) and columns per thread
@@ -61,100 +65,77 @@ struct KParams {
 };
 
 // ---------------------------------------------------------------- geometry
-//
-// Thread mapping: a block holds G independent groups of W warps.  A warp's
-// lanes hold A antennas x F = 32/A sub-lanes (antenna alpha = lane % A,
-// sub-lane q = lane / A).  The FFT team of antenna alpha is the set of
-// threads of one group with that alpha, team index jt = (warp in group) * F
-// + q, L = W * F = N / 32 threads per team, 32 complex points per thread.
-// Because the A antennas of one subcarrier sit in lanes of one warp, the sum
-// over antennas of MRC is a warp-shuffle reduction, and lanes of different
-// antennas share pass-twiddle loads.  The groups of a block process disjoint
-// antenna chunks of the same frame with their own staging ring, exchange
-// buffer, barriers and partial sums, so they run out of phase with each
-// other; their partial sums are added in the demapping phase.
 
-__host__ __device__ constexpr int geo_A(int N) { return N == 64 ? 16 : (N == 128 ? 8 : 4); }
-__host__ __device__ constexpr int geo_G(int N) { return (N >= 256 && N <= 1024) ? 2 : 1; }
-__host__ __device__ constexpr int geo_TG(int N) { return 32 * ((N / 32) / (32 / geo_A(N))); }
-__host__ __device__ constexpr int geo_T(int N) { return geo_G(N) * geo_TG(N); }
-// exchange stride (float2): N plus one pad per 32, then rounded so that
-// antenna regions start 16/A float2 apart modulo the 16 bank pairs
+__host__ __device__ constexpr int geo_L(int N) { return N / 32; }
+__host__ __device__ constexpr int geo_A(int N) { return 128 / (N / 32) > 32 ? 32 : 128 / (N / 32); }
+__host__ __device__ constexpr int geo_F(int N) { return 32 / geo_A(N); }
+__host__ __device__ constexpr int geo_W(int N) { return geo_L(N) / geo_F(N); }
+__host__ __device__ constexpr int geo_TW(int N) { return 32 * geo_W(N); }
+__host__ __device__ constexpr int geo_T(int N) { return 2 * geo_TW(N); }
+__host__ __device__ constexpr int geo_OWN(int N) { return 32 / geo_A(N); }
+// exchange stride (float2): N plus one pad per 32, rounded so that antenna
+// regions start 16/A float2 apart modulo the 16 bank pairs (A <= 16)
 __host__ __device__ constexpr int geo_XS(int N) {
-  return (N + N / 32) + ((16 / geo_A(N) - (N + N / 32) % 16) + 16) % 16;
+  return geo_A(N) > 16 ? (N + N / 32)
+                       : (N + N / 32) + ((16 / geo_A(N) - (N + N / 32) % 16) + 16) % 16;
 }
 // staging stride pad (samples) per antenna: rows start F (sc16) or F/2
 // (fc32) words of banks apart, and stay 16-byte aligned for bulk copies
 __host__ __device__ constexpr int geo_spad(int N, int bps) {
-  return bps == 4 ? ((32 / geo_A(N)) < 4 ? 4 : 32 / geo_A(N))
-                  : ((16 / geo_A(N)) < 2 ? 2 : 16 / geo_A(N));
+  return bps == 4 ? (geo_F(N) < 4 ? 4 : geo_F(N)) : (geo_F(N) / 2 < 2 ? 2 : geo_F(N) / 2);
 }
 
 template <int LOG2N>
 struct Geo {
   static constexpr int N = 1 << LOG2N;
-  static constexpr int L = N / 32;          // threads per team
-  static constexpr int A = geo_A(N);        // antennas per group step
-  static constexpr int F = 32 / A;          // sub-lanes per warp
-  static constexpr int W = L / F;           // warps per group
-  static constexpr int TG = 32 * W;         // threads per group
-  static constexpr int G = geo_G(N);        // groups per block (frame kernel)
-  static constexpr int T = G * TG;          // threads per block (frame kernel)
+  static constexpr int L = geo_L(N);      // threads per FFT team
+  static constexpr int A = geo_A(N);      // antennas per step
+  static constexpr int F = geo_F(N);      // sub-lanes per warp
+  static constexpr int W = geo_W(N);      // warps per warp group
+  static constexpr int TW = geo_TW(N);    // threads per warp group
+  static constexpr int T = geo_T(N);      // threads of the fused kernel
+  static constexpr int OWN = geo_OWN(N);  // subcarriers per thread after the reduction
   static constexpr int XS = geo_XS(N);
 };
 
 __host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
 
-// Shared memory of a block: a header (mbarriers, flags, TMEM address), the
-// pass twiddles, then one region per group: staging slots and exchange
-// buffer.  After the chunk loop of the fused kernel, group 0's staging slots
-// are reused for the partial-sum exchange between groups and for the
-// demapped codes.
+// Shared memory: header, pass twiddles of the last pass (N <= 1024), the
+// staging ring, the final-pass exchange (two buffers in the fused kernel) and,
+// for N = 2048, the producer's middle-pass exchange.  After the chunk loop of
+// the fused kernel the staging ring holds the demapped codes.
 struct Layout {
-  int tw_off;       // pass twiddles (float2[N], N <= 1024)
-  int group_off;    // first group region
-  int group_bytes;  // stride between group regions
-  int team_stage;   // bytes per antenna per staging slot
-  int stage_off;    // within a group region
-  int ex_off;       // within a group region
-  int merge_off;    // fused kernel: float2[2][N] partial sums + float[N] energy
-  int codes_off;    // fused kernel: uint8[dg][N] demapped codes
+  int tw_off;
+  int stage_off;
+  int team_stage;   // bytes per antenna per slot
+  int ex_off;       // final-pass exchange buffer(s), A * XS float2 each
+  int ex1_off;      // N = 2048: middle-pass exchange
+  int codes_off;    // fused kernel, after the loop: uint8[dg][N]
   int total;
-  int reuse_end;    // end of the reused region (must stay inside group 0's slots)
 };
 
-__host__ __device__ inline Layout make_layout(int N, int bps, int nslots, int dg, int groups,
-                                              bool frame) {
+__host__ __device__ inline Layout make_layout(int N, int bps, int nslots, int nex) {
   Layout l;
   const int A = geo_A(N);
   l.tw_off = kSmemHeader;
-  l.group_off = align_up(l.tw_off + (N <= 1024 ? N * 8 : 0), 128);
+  l.stage_off = align_up(l.tw_off + (N <= 1024 ? N * 8 : 0), 128);
   l.team_stage = (N + geo_spad(N, bps)) * bps;
-  l.stage_off = 0;
-  l.ex_off = align_up(nslots * A * l.team_stage, 128);
-  l.group_bytes = align_up(l.ex_off + A * geo_XS(N) * 8, 128);
-  l.total = l.group_off + groups * l.group_bytes;
-  l.merge_off = l.group_off;
-  l.codes_off = align_up(l.merge_off + (groups > 1 ? 2 * N * 8 + N * 4 : 0), 128);
-  l.reuse_end = frame ? l.codes_off + dg * N : l.group_off;
+  l.ex_off = align_up(l.stage_off + nslots * A * l.team_stage, 128);
+  l.ex1_off = l.ex_off + nex * A * geo_XS(N) * 8;
+  l.total = align_up(l.ex1_off + (N > 1024 ? A * geo_XS(N) * 8 : 0), 128);
+  l.codes_off = l.stage_off;
   return l;
 }
 
-// Per-thread accumulators of the fused kernel live in tensor memory (TMEM):
-// OWN = 32/A subcarriers per thread after the antenna reduction, for dg data
-// symbols (complex) plus the channel energy.  Warps sharing a TMEM lane
-// quarter (warp % 4) split the columns by warp / 4.
-__host__ __device__ constexpr int geo_OWN(int N) { return 32 / geo_A(N); }
+// Tensor memory of the fused kernel: the consumer warps (one per TMEM lane
+// quarter) keep OWN subcarriers of partial sums for dg data symbols
+// (complex) plus the channel energy, per thread.
 __host__ __device__ inline int tmem_cols_thread(int N, int dg) {
   return 2 * geo_OWN(N) * dg + geo_OWN(N);
 }
-__host__ __device__ inline int tmem_warps_per_quarter(int N) {
-  return geo_T(N) / 32 > 4 ? geo_T(N) / 128 : 1;
-}
 __host__ __device__ inline int tmem_alloc_cols(int N, int dg) {
-  const int need = tmem_cols_thread(N, dg) * tmem_warps_per_quarter(N);
   int c = 32;
-  while (c < need) c *= 2;
+  while (c < tmem_cols_thread(N, dg)) c *= 2;
   return c;
 }
 
@@ -211,6 +192,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
 __device__ __forceinline__ uint64_t globaltimer() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -253,6 +245,17 @@ __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.
 // Load / store NC consecutive 32-bit columns of this thread's TMEM lane
 // (32x32b shape: thread i of the warp accesses lane base + i).
 template <int NC> struct Tmem;
+template <> struct Tmem<1> {
+  static __device__ __forceinline__ void ld(uint32_t t, float* v) {
+    uint32_t r;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(t) : "memory");
+    v[0] = __uint_as_float(r);
+  }
+  static __device__ __forceinline__ void st(uint32_t t, const float* v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(t),
+                 "r"(__float_as_uint(v[0])) : "memory");
+  }
+};
 template <> struct Tmem<2> {
   static __device__ __forceinline__ void ld(uint32_t t, float* v) {
     uint32_t r[2];
@@ -312,6 +315,18 @@ template <> struct Tmem<16> {
                  "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
                  "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
                  "r"(__float_as_uint(v[15])) : "memory");
+  }
+};
+
+// 32 columns as two 16-column halves
+template <> struct Tmem<32> {
+  static __device__ __forceinline__ void ld(uint32_t t, float* v) {
+    Tmem<16>::ld(t, v);
+    Tmem<16>::ld(t + 16, v + 16);
+  }
+  static __device__ __forceinline__ void st(uint32_t t, const float* v) {
+    Tmem<16>::st(t, v);
+    Tmem<16>::st(t + 16, v + 16);
   }
 };
 
@@ -393,23 +408,18 @@ __device__ __forceinline__ void dft(float2* v, const KParams& p) {
   for (int i = 0; i < R; ++i) v[i] = a[i];
 }
 
+
 // Padded exchange index: one float2 of padding after every 32 entries, so
 // that both the row writes (t*32 + r) and the column reads (j + 32 r) of a
 // transpose hit distinct banks, and every address is a per-thread base plus
 // a compile-time offset.
 __device__ __forceinline__ int xpad(int n) { return n + (n >> 5); }
 
-// Synchronise one FFT team's group (gi): a warp, a named barrier, or the block.
-template <int LOG2N>
-__device__ __forceinline__ void team_sync(int gi) {
-  using G = Geo<LOG2N>;
-  if constexpr (G::W == 1) {
-    __syncwarp();
-  } else if constexpr (G::G == 1) {
-    __syncthreads();
-  } else {
-    named_sync(1 + gi, G::TG);
-  }
+__device__ __forceinline__ void bar_sync(int id, int n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(int id, int n) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 
 // Bin k held in register e after the last FFT pass, for team thread t.
@@ -421,27 +431,6 @@ __device__ __forceinline__ int bin_of(int t, int e) {
   } else {
     return t + 64 * (e / 8) + 256 * (e % 8);
   }
-}
-
-// Owner of bin k after the antenna reduction: the group thread (tid) whose
-// register e = alpha * (32/A) + c holds it, and the slot c.  Inverse of
-// bin_of with the thread mapping of Geo.
-template <int LOG2N>
-__device__ __forceinline__ void owner_of(int k, int& tid, int& c) {
-  using G = Geo<LOG2N>;
-  constexpr int OWN = 32 / G::A;
-  int jt, e;
-  if constexpr (G::N <= 1024) {
-    const int kl = k & 31;
-    jt = kl % G::L;
-    e = (kl / G::L) * G::L + (k >> 5);
-  } else {
-    jt = k & 63;
-    e = 8 * ((k >> 6) & 3) + (k >> 8);
-  }
-  const int alpha = e / OWN;
-  c = e % OWN;
-  tid = (jt / G::F) * 32 + (jt % G::F) * G::A + alpha;
 }
 
 // One interleaved int16 IQ word -> {I, Q} as floats, exactly, without the
@@ -473,20 +462,86 @@ __device__ __forceinline__ void load_row(float2 (&v)[32], const void* row, int j
   }
 }
 
-// Remaining FFT passes: v holds the radix-32 pass-1 outputs of team thread
-// jt (Y1[jt*32 + r]); on return v[e] = Y[bin_of(jt, e)] (unscaled).  ex is
-// this antenna's exchange region; tw the pass twiddles (shared memory for
-// N <= 1024, global for N = 2048).  Every thread of the block calls this.
-template <int LOG2N, typename AfterSync>
-__device__ __forceinline__ void team_fft_rest(float2 (&v)[32], float2* ex, int jt, int gi,
-                                              const float2* tw, const KParams& p,
-                                              AfterSync&& after_sync) {
+// N = 2048 only: the middle radix-8 pass, producer side.  v holds pass-1
+// outputs (Y1[jt*32 + r]); ex1 is this antenna's middle exchange; sync()
+// synchronises the team.  On return v holds the pass-2 outputs of the
+// butterflies j = jt + 64 i, i < 4.
+template <int LOG2N, typename Sync>
+__device__ __forceinline__ void middle_pass(float2 (&v)[32], float2* ex1, int jt,
+                                            const float2* tw, const KParams& p, Sync&& sync) {
+  if constexpr (Geo<LOG2N>::N > 1024) {
+#pragma unroll
+    for (int r = 0; r < 32; ++r) ex1[xpad(jt * 32 + r)] = v[r];
+    sync();
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int j = jt + 64 * i;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const float2 u = ex1[xpad(j + 256 * r)];
+        v[i * 8 + r] = (r == 0) ? u : cmul(u, __ldg(tw + r * 32 + (j & 31)));
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) dft<8>(v + i * 8, p);
+  }
+}
+
+// Twiddles the producer applies before the last exchange (N <= 1024): the
+// factor W_N^(j r) of element Y1[j + 32 r] belongs to writer jt = r, output
+// k1 = j, i.e. W_N^(jt k1) for its register k1.  They depend only on jt.
+template <int LOG2N>
+__device__ __forceinline__ void writer_twiddles(float2 (&w)[32], int jt, const float2* tw) {
+  using G = Geo<LOG2N>;
+  static_assert(G::N <= 1024, "writer-side twiddles are for the two-pass FFT");
+#pragma unroll
+  for (int k1 = 0; k1 < 32; ++k1)
+    w[k1] = (jt == 0 || k1 == 0) ? make_float2(1.f, 0.f) : tw[jt * 32 + k1];
+}
+
+// Store the inputs of the last FFT pass into the exchange buffer ex.
+template <int LOG2N>
+__device__ __forceinline__ void final_exchange_write(const float2 (&v)[32], float2* ex, int jt) {
+  if constexpr (Geo<LOG2N>::N <= 1024) {
+#pragma unroll
+    for (int r = 0; r < 32; ++r) ex[xpad(jt * 32 + r)] = v[r];
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int j = jt + 64 * i;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) ex[xpad((j >> 5) * 256 + (j & 31) + 32 * r)] = v[i * 8 + r];
+    }
+  }
+}
+
+// Twiddles of the last FFT pass for team thread jt, in register order (they
+// depend only on jt, so a thread loads them once per kernel).
+template <int LOG2N>
+__device__ __forceinline__ void final_twiddles(float2 (&w)[32], int jt, const float2* tw) {
   using G = Geo<LOG2N>;
   constexpr int L = G::L;
+  if constexpr (G::N <= 1024) {
 #pragma unroll
-  for (int r = 0; r < 32; ++r) ex[xpad(jt * 32 + r)] = v[r];
-  team_sync<LOG2N>(gi);
-  after_sync();   // work placed where the team does not wait on it
+    for (int i = 0; i < 32 / L; ++i)
+#pragma unroll
+      for (int r = 0; r < L; ++r) w[i * L + r] = (r == 0) ? make_float2(1.f, 0.f) : tw[r * 32 + jt + i * L];
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+        w[i * 8 + r] = (r == 0) ? make_float2(1.f, 0.f) : __ldg(tw + 256 + r * 256 + jt + 64 * i);
+  }
+}
+
+// Load the inputs of the last FFT pass, times the register-held twiddles w,
+// for team thread jt; the pass itself runs in final_dft.
+template <int LOG2N>
+__device__ __forceinline__ void final_exchange_read_w(float2 (&v)[32], const float2* ex, int jt,
+                                                      const float2 (&w)[32]) {
+  using G = Geo<LOG2N>;
+  constexpr int L = G::L;
   if constexpr (G::N <= 1024) {
 #pragma unroll
     for (int i = 0; i < 32 / L; ++i) {
@@ -494,15 +549,9 @@ __device__ __forceinline__ void team_fft_rest(float2 (&v)[32], float2* ex, int j
 #pragma unroll
       for (int r = 0; r < L; ++r) {
         const float2 u = ex[xpad(j + 32 * r)];
-        if (r == 0) {
-          v[i * L + r] = u;
-        } else {
-          v[i * L + r] = cmul(u, tw[r * 32 + j]);
-        }
+        v[i * L + r] = (r == 0) ? u : cmul(u, w[i * L + r]);
       }
     }
-#pragma unroll
-    for (int i = 0; i < 32 / L; ++i) dft<L>(v + i * L, p);
   } else {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -510,38 +559,78 @@ __device__ __forceinline__ void team_fft_rest(float2 (&v)[32], float2* ex, int j
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
         const float2 u = ex[xpad(j + 256 * r)];
-        if (r == 0) {
-          v[i * 8 + r] = u;
-        } else {
-          v[i * 8 + r] = cmul(u, __ldg(tw + r * 32 + (j & 31)));
-        }
+        v[i * 8 + r] = (r == 0) ? u : cmul(u, w[i * 8 + r]);
       }
     }
-    team_sync<LOG2N>(gi);   // all reads done before the second exchange
+  }
+}
+
+// Load the already-twiddled inputs of the last FFT pass (N <= 1024).
+template <int LOG2N>
+__device__ __forceinline__ void final_exchange_read_plain(float2 (&v)[32], const float2* ex, int jt) {
+  using G = Geo<LOG2N>;
+  constexpr int L = G::L;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) dft<8>(v + i * 8, p);
+  for (int i = 0; i < 32 / L; ++i)
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int j = jt + 64 * i;
+    for (int r = 0; r < L; ++r) v[i * L + r] = ex[xpad(jt + i * L + 32 * r)];
+}
+
+// Load the inputs of the last FFT pass (with its twiddles) for team thread
+// jt; the pass itself runs in final_dft.
+template <int LOG2N>
+__device__ __forceinline__ void final_exchange_read(float2 (&v)[32], const float2* ex, int jt,
+                                                    const float2* tw) {
+  using G = Geo<LOG2N>;
+  constexpr int L = G::L;
+  if constexpr (G::N <= 1024) {
 #pragma unroll
-      for (int r = 0; r < 8; ++r) ex[xpad((j >> 5) * 256 + (j & 31) + 32 * r)] = v[i * 8 + r];
+    for (int i = 0; i < 32 / L; ++i) {
+      const int j = jt + i * L;
+#pragma unroll
+      for (int r = 0; r < L; ++r) {
+        const float2 u = ex[xpad(j + 32 * r)];
+        v[i * L + r] = (r == 0) ? u : cmul(u, tw[r * 32 + j]);
+      }
     }
-    team_sync<LOG2N>(gi);
+  } else {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int j = jt + 64 * i;
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
         const float2 u = ex[xpad(j + 256 * r)];
-        if (r == 0) {
-          v[i * 8 + r] = u;
-        } else {
-          v[i * 8 + r] = cmul(u, __ldg(tw + 256 + r * 256 + j));
-        }
+        v[i * 8 + r] = (r == 0) ? u : cmul(u, __ldg(tw + 256 + r * 256 + j));
       }
     }
+  }
+}
+
+// Last FFT pass; on return v[e] = Y[bin_of(jt, e)] (unscaled).
+template <int LOG2N>
+__device__ __forceinline__ void final_dft(float2 (&v)[32], const KParams& p) {
+  using G = Geo<LOG2N>;
+  if constexpr (G::N <= 1024) {
+#pragma unroll
+    for (int i = 0; i < 32 / G::L; ++i) dft<G::L>(v + i * G::L, p);
+  } else {
 #pragma unroll
     for (int i = 0; i < 4; ++i) dft<8>(v + i * 8, p);
+  }
+}
+
+// Pass twiddles of the last pass: copied to shared memory when N <= 1024.
+template <int LOG2N>
+__device__ __forceinline__ const float2* load_pass_twiddles(const KParams& p,
+                                                            unsigned char* smem,
+                                                            const Layout& lay) {
+  using G = Geo<LOG2N>;
+  if constexpr (G::N <= 1024) {
+    float2* tws = reinterpret_cast<float2*>(smem + lay.tw_off);
+    for (int i = threadIdx.x; i < G::N; i += blockDim.x) tws[i] = __ldg(p.twP + i);
+    return tws;
+  } else {
+    return p.twP;
   }
 }
 
@@ -569,21 +658,6 @@ __device__ __forceinline__ void reduce_scatter(float2* v, int alpha) {
   }
 }
 
-// Pass twiddles for the block: copied to shared memory when N <= 1024.
-template <int LOG2N>
-__device__ __forceinline__ const float2* load_pass_twiddles(const KParams& p,
-                                                            unsigned char* smem,
-                                                            const Layout& lay) {
-  using G = Geo<LOG2N>;
-  if constexpr (G::N <= 1024) {
-    float2* tws = reinterpret_cast<float2*>(smem + lay.tw_off);
-    for (int i = threadIdx.x; i < G::N; i += blockDim.x) tws[i] = __ldg(p.twP + i);
-    return tws;
-  } else {
-    return p.twP;
-  }
-}
-
 // ------------------------------------------------------- staging pipeline
 
 // Items per antenna chunk in data-symbol group g: the pilot first (group 0 of
@@ -592,10 +666,7 @@ __device__ __forceinline__ int group_items(const KParams& p, int g) {
   const int nd = min(p.dg, p.D - g * p.dg);
   return nd + ((p.mode == kModeRun && g == 0) ? 1 : 0);
 }
-// Antenna chunks handled by block group gi of G: c = gi, gi + G, ...
-__device__ __forceinline__ int chunks_of(const KParams& p, int gi, int G) {
-  return (p.chunks - gi + G - 1) / G;
-}
+
 template <int LOG2N, bool FC32>
 __device__ __forceinline__ const unsigned char* row_ptr(const KParams& p, int f, int m,
                                                         int s) {
@@ -607,7 +678,7 @@ __device__ __forceinline__ const unsigned char* row_ptr(const KParams& p, int f,
 
 // Issue the bulk copies of one step (antennas of chunk c, symbol s) into a
 // slot.  Called by a whole warp: lane 0 registers the byte count on the
-// slot's mbarrier and lane a issues the copy of antenna row a.
+// slot's mbarrier and lane a (and a + 32) issues the copy of antenna row a.
 template <int LOG2N, bool FC32>
 __device__ __forceinline__ void issue_step(const KParams& p, int f, int c, int s,
                                            unsigned char* slot, int team_stage,
@@ -616,26 +687,21 @@ __device__ __forceinline__ void issue_step(const KParams& p, int f, int c, int s
   constexpr uint32_t bytes = G::N * (FC32 ? 8 : 4);
   const int nvalid = min(G::A, p.M - c * G::A);
   if (lane == 0) mbar_expect_tx(bar, bytes * nvalid);
-  if (lane < nvalid)
-    bulk_load(smem_u32(slot + lane * team_stage), row_ptr<LOG2N, FC32>(p, f, c * G::A + lane, s),
+  for (int a = lane; a < nvalid; a += 32)
+    bulk_load(smem_u32(slot + a * team_stage), row_ptr<LOG2N, FC32>(p, f, c * G::A + a, s),
               bytes, bar, pol);
 }
 
-// Walks the steps of one block group in order (data-symbol group, chunk,
-// item) with O(1) work per step.
+// Walks the steps of the fused kernel in order (data-symbol group, antenna
+// chunk, item) with O(1) work per step.
 struct StepCursor {
-  int g, u, it, items, nc, G, gi;
-  __device__ void init(const KParams& p, int gi_, int G_) {
-    gi = gi_;
-    G = G_;
-    nc = chunks_of(p, gi, G);
+  int g, c, it, items;
+  __device__ void init(const KParams& p) {
     g = 0;
-    u = 0;
+    c = 0;
     it = 0;
     items = group_items(p, 0);
   }
-  // chunk and symbol of the current step
-  __device__ int chunk() const { return gi + G * u; }
   __device__ int symbol(const KParams& p) const {
     int i = it;
     if (p.mode == kModeRun && g == 0) {
@@ -648,8 +714,8 @@ struct StepCursor {
   __device__ void next(const KParams& p) {
     if (++it < items) return;
     it = 0;
-    if (++u < nc) return;
-    u = 0;
+    if (++c < p.chunks) return;
+    c = 0;
     ++g;
     items = group_items(p, g < p.groups ? g : 0);
   }
@@ -662,6 +728,7 @@ __device__ __forceinline__ void latch(int* status, int code) {
 // Wait for a slot; on timeout latch the status and stop waiting for good.
 __device__ __forceinline__ void wait_slot(uint32_t bar, uint32_t parity,
                                           volatile int* abort_flag, int* status) {
+  if (mbar_test_wait(bar, parity)) return;   // usually complete: no suspend
   if (*abort_flag) return;
   if (!mbar_wait_bounded(bar, parity)) {
     *abort_flag = 1;
@@ -681,117 +748,80 @@ __device__ __forceinline__ uint32_t gray(int l) { return static_cast<uint32_t>(l
 
 // ======================================================= frame kernel
 
+// Named barriers: 0 = whole block; FULL_b / EMPTY_b hand exchange buffer b
+// from producers to consumers and back; PROD synchronises the producers.
+enum { kBarFull0 = 1, kBarEmpty0 = 3, kBarProd = 5 };
+
 template <int LOG2N, bool FC32>
 __global__ void __launch_bounds__(Geo<LOG2N>::T, 1) frame_kernel(const KParams p) {
   using G = Geo<LOG2N>;
-  constexpr int N = G::N, A = G::A, T = G::T, TG = G::TG, F = G::F, NG = G::G;
-  constexpr int OWN = 32 / A;  // subcarriers per thread after the antenna reduction
+  constexpr int N = G::N, A = G::A, T = G::T, TW = G::TW, F = G::F, W = G::W;
+  constexpr int OWN = G::OWN;
   using TmP = Tmem<2 * OWN>;   // one data symbol of partial sums (complex)
   using TmE = Tmem<OWN>;       // channel energy
   extern __shared__ __align__(128) unsigned char smem[];
   const int f = blockIdx.x;
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
-  const int gi = tid / TG;             // group of this thread
-  const int ltid = tid % TG;           // thread index within the group
+  const bool producer = warp < W;
+  const int ltid = tid % TW;           // thread index within its warp group
   const int lane = tid & 31;
   const int alpha = lane % A;
   const int jt = (ltid >> 5) * F + lane / A;
-  const Layout lay = make_layout(N, FC32 ? 8 : 4, p.nslots, p.dg, NG, true);
+  const Layout lay = make_layout(N, FC32 ? 8 : 4, p.nslots, 2);
   const float2* tw = load_pass_twiddles<LOG2N>(p, smem, lay);
   const int K = p.nslots;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem) + gi * kMaxSlots;
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 192 + 4 * gi);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
   uint32_t* tmem_base = reinterpret_cast<uint32_t*>(smem + 160);
-  unsigned char* greg = smem + lay.group_off + gi * lay.group_bytes;
-  unsigned char* stage = greg + lay.stage_off;
-  float2* myex = reinterpret_cast<float2*>(greg + lay.ex_off) + alpha * G::XS;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 192);
+  unsigned char* stage = smem + lay.stage_off;
+  float2* ex0 = reinterpret_cast<float2*>(smem + lay.ex_off) + alpha * G::XS;
+  float2* ex1 = reinterpret_cast<float2*>(smem + lay.ex1_off) + alpha * G::XS;
   const int slot_bytes = A * lay.team_stage;
-  const int nc = chunks_of(p, gi, NG);
 
-  int total = 0;
-  for (int g = 0; g < p.groups; ++g) total += nc * group_items(p, g);
-
-  uint64_t pol = 0;
-  if (ltid == 0) {
+  if (tid == 0) {
     *abort_flag = 0;
     if (p.use_tma) {
       for (int s = 0; s < K; ++s) mbar_init(smem_u32(&bars[s]), 1);
       fence_mbar_init();
     }
   }
-  if (warp == 0) tmem_alloc(smem_u32(tmem_base), p.tmem_cols);
+  if (warp == W) tmem_alloc(smem_u32(tmem_base), p.tmem_cols);
   tmem_fence_before();
   __syncthreads();
   tmem_fence_after();
-  // this thread's TMEM lane and first column: P(dl) at 2*OWN*dl, E after the dg symbols
-  const uint32_t tacc = *tmem_base + (static_cast<uint32_t>(32 * (warp & 3)) << 16) +
-                        static_cast<uint32_t>((warp >> 2) * p.tmem_cth);
-  const uint32_t tE = tacc + 2 * OWN * p.dg;
 
-  StepCursor cur;   // next step to load (meaningful in warp 0 of the group)
-  cur.init(p, gi, NG);
-  if (ltid < 32 && p.use_tma) {
-    if (ltid == 0) pol = evict_first_policy();
-    pol = __shfl_sync(0xffffffffu, pol, 0);
-  }
-
-  float zero[2 * OWN];
-#pragma unroll
-  for (int i = 0; i < 2 * OWN; ++i) zero[i] = 0.f;
-  TmE::st(tE, zero);
-
-  float2 h[32];
-  int step = 0;
-  int gend = 0;   // first step after the current data-symbol group
-  for (int g = 0; g < p.groups; ++g) {
-    const int nd = min(p.dg, p.D - g * p.dg);
-    const int d0 = g * p.dg;
-    for (int dl = 0; dl < nd; ++dl) TmP::st(tacc + 2 * OWN * dl, zero);
-    // loads never run ahead into the next data-symbol group: group 0's
-    // staging slots are reused by the demap phase at its end
-    gend += nc * group_items(p, g);
-    if (ltid < 32 && p.use_tma) {
-      fence_proxy_async();   // the demap phase wrote these slots through the generic proxy
-      for (int i = step; i < step + K && i < gend; ++i) {
-        issue_step<LOG2N, FC32>(p, f, cur.chunk(), cur.symbol(p), stage + (i % K) * slot_bytes,
-                                lay.team_stage, smem_u32(&bars[i % K]), pol, lane);
-        cur.next(p);
-      }
+  int step = 0;     // global step counter (both groups walk the same steps)
+  int gend = 0;     // first step after the current data-symbol group
+  if (producer) {
+    // ================= producer: staging, conversion, first pass(es)
+    StepCursor cur;   // next step to load
+    cur.init(p);
+    uint64_t pol = 0;
+    if (warp == 0 && p.use_tma) {
+      if (lane == 0) pol = evict_first_policy();
+      pol = __shfl_sync(0xffffffffu, pol, 0);
     }
-
-    for (int u = 0; u < nc; ++u) {
-      const int c = gi + NG * u;
-      const int m = c * A + alpha;
-      const bool valid = m < p.M;
-      const size_t hrow = (static_cast<size_t>(f) * p.M + m) * N;
-      const bool need_fft_pilot = (p.mode == kModeRun && g == 0);
-      if (!need_fft_pilot) {
-        // channel from memory: given (demodulate) or written in group 0
-        const float2* Hs = (p.mode == kModeRun) ? p.H_out : p.H_in;
-#pragma unroll
-        for (int e = 0; e < 32; ++e)
-          h[e] = valid ? Hs[hrow + bin_of<LOG2N>(jt, e)] : make_float2(0.f, 0.f);
-        if (g == 0) {
-          // channel energy of this chunk: |H|^2 summed over its antennas
-          float2 e2[32];
-#pragma unroll
-          for (int e = 0; e < 32; ++e) e2[e] = make_float2(h[e].x * h[e].x + h[e].y * h[e].y, 0.f);
-          reduce_scatter<A, 16>(e2, alpha);
-          float acc[OWN];
-          tmem_wait_st();
-          TmE::ld(tE, acc);
-          tmem_wait_ld();
-#pragma unroll
-          for (int cc = 0; cc < OWN; ++cc) acc[cc] += e2[cc].x;
-          TmE::st(tE, acc);
+    float2 wpre[32];   // writer-side twiddles (N <= 1024)
+    if constexpr (N <= 1024) writer_twiddles<LOG2N>(wpre, jt, tw);
+    for (int g = 0; g < p.groups; ++g) {
+      gend += p.chunks * group_items(p, g);
+      // loads never run ahead into the next data-symbol group: its staging
+      // ring holds the demapped codes at the end of each group
+      if (warp == 0 && p.use_tma) {
+        fence_proxy_async();
+        for (int i = step; i < step + K && i < gend; ++i) {
+          issue_step<LOG2N, FC32>(p, f, cur.c, cur.symbol(p), stage + (i % K) * slot_bytes,
+                                  lay.team_stage, smem_u32(&bars[i % K]), pol, lane);
+          cur.next(p);
         }
       }
-      const int items = group_items(p, g);
-      for (int it = 0; it < items; ++it, ++step) {
-        const bool is_pilot = need_fft_pilot && it == 0;
-        const int d = d0 + it - (need_fft_pilot ? 1 : 0);
-        const int s = is_pilot ? p.pilot_idx : (d < p.pilot_idx ? d : d + 1);
+      StepCursor me;    // the step this thread processes
+      me.init(p);
+      for (int i = 0; i < step; ++i) me.next(p);
+      for (; step < gend; ++step, me.next(p)) {
+        const int m = me.c * A + alpha;
+        const bool valid = m < p.M;
         const int slot = step % K;
         float2 v[32];
         if (p.use_tma) {
@@ -804,133 +834,180 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T, 1) frame_kernel(const KParams p
           }
         } else {
           if (valid) {
-            load_row<LOG2N, FC32>(v, row_ptr<LOG2N, FC32>(p, f, m, s), jt, true);
+            load_row<LOG2N, FC32>(v, row_ptr<LOG2N, FC32>(p, f, m, me.symbol(p)), jt, true);
           } else {
 #pragma unroll
             for (int r = 0; r < 32; ++r) v[r] = make_float2(0.f, 0.f);
           }
         }
         dft<32>(v, p);
-        team_sync<LOG2N>(gi);  // staging slot consumed; exchange buffer free
-        // refill the consumed slot once the exchange barrier has passed, so
-        // the other warps of the group do not wait on the issuing warp
-        team_fft_rest<LOG2N>(v, myex, jt, gi, tw, p, [&] {
-          if (ltid < 32 && p.use_tma && step + K < gend) {
-            fence_proxy_async();
-            issue_step<LOG2N, FC32>(p, f, cur.chunk(), cur.symbol(p), stage + slot * slot_bytes,
-                                    lay.team_stage, smem_u32(&bars[slot]), pol, lane);
-            cur.next(p);
-          }
-        });
-        if (is_pilot) {
-          // LS estimate H = Y conj(X) / |X|^2 (1/sqrt(N) folded into xinv)
+        middle_pass<LOG2N>(v, ex1, jt, p.twP, p, [] { bar_sync(kBarProd, TW); });
+        if constexpr (N <= 1024) {
 #pragma unroll
-          for (int e = 0; e < 32; ++e) {
-            const int k = bin_of<LOG2N>(jt, e);
-            const float2 hv = cmul(v[e], __ldg(p.xinv + k));
-            h[e] = valid ? hv : make_float2(0.f, 0.f);
-            if (valid) p.H_out[hrow + k] = hv;
-            v[e] = make_float2(h[e].x * h[e].x + h[e].y * h[e].y, 0.f);
-          }
-          reduce_scatter<A, 16>(v, alpha);
-          float acc[OWN];
-          tmem_wait_st();
-          TmE::ld(tE, acc);
-          tmem_wait_ld();
-#pragma unroll
-          for (int cc = 0; cc < OWN; ++cc) acc[cc] += v[cc].x;
-          TmE::st(tE, acc);
-        } else {
-          // MRC numerator: conj(H) Y summed over the antennas of the chunk
-#pragma unroll
-          for (int e = 0; e < 32; ++e) v[e] = cmulc(h[e], v[e]);
-          reduce_scatter<A, 16>(v, alpha);
-          float acc[2 * OWN];
-          const uint32_t tp = tacc + 2 * OWN * (d - d0);
-          tmem_wait_st();
-          TmP::ld(tp, acc);
-          tmem_wait_ld();
-#pragma unroll
-          for (int cc = 0; cc < OWN; ++cc) {
-            acc[2 * cc] += v[cc].x;
-            acc[2 * cc + 1] += v[cc].y;
-          }
-          TmP::st(tp, acc);
+          for (int k1 = 1; k1 < 32; ++k1) v[k1] = cmul(v[k1], wpre[k1]);
         }
+        const int b = step & 1;
+        if (step >= 2) bar_sync(kBarEmpty0 + b, T);   // consumers released buffer b
+        final_exchange_write<LOG2N>(v, b ? ex0 + A * G::XS : ex0, jt);
+        bar_arrive(kBarFull0 + b, T);
+        bar_sync(kBarProd, TW);   // every producer is done with this staging slot
+        if (warp == 0 && p.use_tma && step + K < gend) {
+          fence_proxy_async();
+          issue_step<LOG2N, FC32>(p, f, cur.c, cur.symbol(p), stage + slot * slot_bytes,
+                                  lay.team_stage, smem_u32(&bars[slot]), pol, lane);
+          cur.next(p);
+        }
+      }
+      bar_sync(0, T);   // group's loop done (consumers finished too)
+      bar_sync(0, T);   // consumers wrote the codes
+      // pack: 8 consecutive subcarriers -> q bytes (producers and consumers)
+      const int nd = min(p.dg, p.D - g * p.dg);
+      const int items8 = nd * (N / 8);
+      const size_t frame_bytes = static_cast<size_t>(p.D) * N * p.q / 8;
+      const uint8_t* codes = smem + lay.codes_off;
+      for (int it = tid; it < items8; it += T) {
+        const int dl = it / (N / 8);
+        const int k0 = (it % (N / 8)) * 8;
+        uint64_t acc = 0;
+#pragma unroll
+        for (int bb = 0; bb < 8; ++bb) acc = (acc << p.q) | codes[dl * N + k0 + bb];
+        uint8_t* dst = p.bits + f * frame_bytes + (static_cast<size_t>(g * p.dg + dl) * N + k0) * p.q / 8;
+        for (int j = 0; j < p.q; ++j) dst[j] = static_cast<uint8_t>(acc >> (8 * (p.q - 1 - j)));
+      }
+      bar_sync(0, T);   // codes consumed before the ring is refilled
+    }
+    // balance the consumers' last two buffer releases
+    if (step >= 2) bar_sync(kBarEmpty0 + (step & 1), T);
+    if (step >= 1) bar_sync(kBarEmpty0 + ((step + 1) & 1), T);
+    if (tid == 0 && p.use_tma && *abort_flag) {
+      // a wait gave up: give any copy still in flight a bounded chance to land
+      for (int s = 0; s < K && s < step; ++s) {
+        const int last = step - 1 - ((step - 1 - s) % K);
+        (void)mbar_wait_bounded(smem_u32(&bars[last % K]), (last / K) & 1);
       }
     }
-    // ---- demap: owners read their sums from TMEM; with two groups the
-    // partner group's partial sums come through shared memory
-    tmem_wait_st();
-    tmem_fence_before();
-    __syncthreads();
-    tmem_fence_after();
-    float2* mP = reinterpret_cast<float2*>(smem + lay.merge_off);   // [2][N]
-    float* mE = reinterpret_cast<float*>(smem + lay.merge_off + 2 * N * 8);
-    uint8_t* codes = smem + lay.codes_off;
-    float ie[OWN];
-    if (g == 0) {
-      float e[OWN];
-      TmE::ld(tE, e);
-      tmem_wait_ld();
-      if constexpr (NG > 1) {
-        if (gi == 1) {
+  } else {
+    // ================= consumer: last pass, LS, MRC, accumulation, demap
+    const uint32_t tacc = *tmem_base + (static_cast<uint32_t>(32 * (warp & 3)) << 16);
+    const uint32_t tE = tacc + 2 * OWN * p.dg;
+    float zero[2 * OWN];
 #pragma unroll
-          for (int cc = 0; cc < OWN; ++cc) mE[cc * TG + ltid] = e[cc];
-        }
-        __syncthreads();
-        if (gi == 0) {
+    for (int i = 0; i < 2 * OWN; ++i) zero[i] = 0.f;
+    TmE::st(tE, zero);
+    float2 h[32];
+    float2 wlast[32];   // this thread's last-pass twiddles (N = 2048; the
+                        // producer applies them itself for N <= 1024)
+    if constexpr (N > 1024) final_twiddles<LOG2N>(wlast, jt, tw);
+    for (int g = 0; g < p.groups; ++g) {
+      const int nd = min(p.dg, p.D - g * p.dg);
+      const int d0 = g * p.dg;
+      for (int dl = 0; dl < nd; ++dl) TmP::st(tacc + 2 * OWN * dl, zero);
+      const bool need_fft_pilot = (p.mode == kModeRun && g == 0);
+      for (int c = 0; c < p.chunks; ++c) {
+        const int m = c * A + alpha;
+        const bool valid = m < p.M;
+        const size_t hrow = (static_cast<size_t>(f) * p.M + m) * N;
+        if (!need_fft_pilot) {
+          // channel from memory: given (demodulate) or written in group 0
+          const float2* Hs = (p.mode == kModeRun) ? p.H_out : p.H_in;
 #pragma unroll
-          for (int cc = 0; cc < OWN; ++cc) {
-            e[cc] += mE[cc * TG + ltid];
-            mE[cc * TG + ltid] = e[cc];
+          for (int e = 0; e < 32; ++e)
+            h[e] = valid ? Hs[hrow + bin_of<LOG2N>(jt, e)] : make_float2(0.f, 0.f);
+          if (g == 0) {
+            // channel energy of this chunk: |H|^2 summed over its antennas
+            float2 e2[32];
+#pragma unroll
+            for (int e = 0; e < 32; ++e) e2[e] = make_float2(h[e].x * h[e].x + h[e].y * h[e].y, 0.f);
+            reduce_scatter<A, 16>(e2, alpha);
+            float acc[OWN];
+            tmem_wait_st();
+            TmE::ld(tE, acc);
+            tmem_wait_ld();
+#pragma unroll
+            for (int cc = 0; cc < OWN; ++cc) acc[cc] += e2[cc].x;
+            TmE::st(tE, acc);
           }
         }
-        __syncthreads();
-        if (gi == 1) {
+        const int items = group_items(p, g);
+        for (int it = 0; it < items; ++it, ++step) {
+          const bool is_pilot = need_fft_pilot && it == 0;
+          const int d = d0 + it - (need_fft_pilot ? 1 : 0);
+          const int b = step & 1;
+          float2 v[32];
+          bar_sync(kBarFull0 + b, T);
+          if constexpr (N <= 1024) {
+            final_exchange_read_plain<LOG2N>(v, b ? ex0 + A * G::XS : ex0, jt);
+          } else {
+            final_exchange_read_w<LOG2N>(v, b ? ex0 + A * G::XS : ex0, jt, wlast);
+          }
+          bar_arrive(kBarEmpty0 + b, T);
+          final_dft<LOG2N>(v, p);
+          if (is_pilot) {
+            // LS estimate H = Y conj(X) / |X|^2 (1/sqrt(N) folded into xinv)
 #pragma unroll
-          for (int cc = 0; cc < OWN; ++cc) e[cc] = mE[cc * TG + ltid];
+            for (int e = 0; e < 32; ++e) {
+              const int k = bin_of<LOG2N>(jt, e);
+              const float2 hv = cmul(v[e], __ldg(p.xinv + k));
+              h[e] = valid ? hv : make_float2(0.f, 0.f);
+              if (valid) p.H_out[hrow + k] = hv;
+              v[e] = make_float2(h[e].x * h[e].x + h[e].y * h[e].y, 0.f);
+            }
+            reduce_scatter<A, 16>(v, alpha);
+            float acc[OWN];
+            tmem_wait_st();
+            TmE::ld(tE, acc);
+            tmem_wait_ld();
+#pragma unroll
+            for (int cc = 0; cc < OWN; ++cc) acc[cc] += v[cc].x;
+            TmE::st(tE, acc);
+          } else {
+            // MRC numerator: conj(H) Y summed over the antennas of the chunk
+#pragma unroll
+            for (int e = 0; e < 32; ++e) v[e] = cmulc(h[e], v[e]);
+            reduce_scatter<A, 16>(v, alpha);
+            float acc[2 * OWN];
+            const uint32_t tp = tacc + 2 * OWN * (d - d0);
+            tmem_wait_st();
+            TmP::ld(tp, acc);
+            tmem_wait_ld();
+#pragma unroll
+            for (int cc = 0; cc < OWN; ++cc) {
+              acc[2 * cc] += v[cc].x;
+              acc[2 * cc + 1] += v[cc].y;
+            }
+            TmP::st(tp, acc);
+          }
         }
       }
-      // E -> 1 / (sqrt(N) E); zero or non-finite energy flags the frame
+      tmem_wait_st();
+      bar_sync(0, T);   // the group's steps are done; the staging ring is free
+      float ie[OWN];
+      if (g == 0) {
+        float e[OWN];
+        TmE::ld(tE, e);
+        tmem_wait_ld();
+        // E -> 1 / (sqrt(N) E); zero or non-finite energy flags the frame
 #pragma unroll
-      for (int cc = 0; cc < OWN; ++cc) {
-        const bool ok = (e[cc] > 0.f) && (e[cc] <= 3.4028234663852886e38f);
-        if (!ok) latch(p.status, kStDevice);
-        ie[cc] = ok ? (1.0f / e[cc]) * p.inv_sqrtN : 0.f;
-      }
-      // keep 1/E in the energy columns for the later data-symbol groups
-      TmE::st(tE, ie);
-    } else {
-      TmE::ld(tE, ie);
-      tmem_wait_ld();
-    }
-    // symbols are demapped in pairs: group q takes the symbol of parity q
-    for (int dl0 = 0; dl0 < nd; dl0 += NG) {
-      const int dl = dl0 + gi;            // symbol this thread demaps
-      float acc[2 * OWN];
-      if constexpr (NG > 1) {
-        // hand the partner group the partial sums of its symbol
-        const int dp = dl0 + (1 - gi);
-        if (dp < nd) {
-          TmP::ld(tacc + 2 * OWN * dp, acc);
-          tmem_wait_ld();
-#pragma unroll
-          for (int cc = 0; cc < OWN; ++cc)
-            mP[(1 - gi) * N + cc * TG + ltid] = make_float2(acc[2 * cc], acc[2 * cc + 1]);
+        for (int cc = 0; cc < OWN; ++cc) {
+          const bool ok = (e[cc] > 0.f) && (e[cc] <= 3.4028234663852886e38f);
+          if (!ok) latch(p.status, kStDevice);
+          ie[cc] = ok ? (1.0f / e[cc]) * p.inv_sqrtN : 0.f;
         }
-        __syncthreads();
+        TmE::st(tE, ie);   // later data-symbol groups reuse 1/E
+      } else {
+        TmE::ld(tE, ie);
+        tmem_wait_ld();
       }
-      if (dl < nd) {
+      uint8_t* codes = smem + lay.codes_off;
+      for (int dl = 0; dl < nd; ++dl) {
+        float acc[2 * OWN];
         TmP::ld(tacc + 2 * OWN * dl, acc);
         tmem_wait_ld();
         const int d = d0 + dl;
 #pragma unroll
         for (int cc = 0; cc < OWN; ++cc) {
-          float2 sum = make_float2(acc[2 * cc], acc[2 * cc + 1]);
-          if constexpr (NG > 1) sum = cadd(sum, mP[gi * N + cc * TG + ltid]);
           const int k = bin_of<LOG2N>(jt, alpha * OWN + cc);
-          const float2 z = (ie[cc] != 0.f) ? make_float2(sum.x * ie[cc], sum.y * ie[cc])
+          const float2 z = (ie[cc] != 0.f) ? make_float2(acc[2 * cc] * ie[cc], acc[2 * cc + 1] * ie[cc])
                                            : make_float2(0.f, 0.f);
           if (p.eq) p.eq[(static_cast<size_t>(f) * p.D + d) * N + k] = z;
           uint32_t code = gray(axis_level(z.x, p));
@@ -938,41 +1015,34 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T, 1) frame_kernel(const KParams p
           codes[dl * N + k] = static_cast<uint8_t>(code);
         }
       }
-      if constexpr (NG > 1) __syncthreads();
-    }
-    __syncthreads();
-    // pack: 8 consecutive subcarriers -> q bytes
-    const int items8 = nd * (N / 8);
-    const size_t frame_bytes = static_cast<size_t>(p.D) * N * p.q / 8;
-    for (int it = tid; it < items8; it += T) {
-      const int dl = it / (N / 8);
-      const int k0 = (it % (N / 8)) * 8;
-      uint64_t acc = 0;
+      tmem_wait_st();
+      bar_sync(0, T);   // codes written
+      // pack (shared with the producers)
+      const int items8 = nd * (N / 8);
+      const size_t frame_bytes = static_cast<size_t>(p.D) * N * p.q / 8;
+      for (int it = tid; it < items8; it += T) {
+        const int dl = it / (N / 8);
+        const int k0 = (it % (N / 8)) * 8;
+        uint64_t acc = 0;
 #pragma unroll
-      for (int b = 0; b < 8; ++b) acc = (acc << p.q) | codes[dl * N + k0 + b];
-      uint8_t* dst = p.bits + f * frame_bytes + (static_cast<size_t>(d0 + dl) * N + k0) * p.q / 8;
-      for (int j = 0; j < p.q; ++j) dst[j] = static_cast<uint8_t>(acc >> (8 * (p.q - 1 - j)));
+        for (int bb = 0; bb < 8; ++bb) acc = (acc << p.q) | codes[dl * N + k0 + bb];
+        uint8_t* dst = p.bits + f * frame_bytes + (static_cast<size_t>(d0 + dl) * N + k0) * p.q / 8;
+        for (int j = 0; j < p.q; ++j) dst[j] = static_cast<uint8_t>(acc >> (8 * (p.q - 1 - j)));
+      }
+      bar_sync(0, T);
     }
-    tmem_wait_st();
     tmem_fence_before();
-    __syncthreads();
-    tmem_fence_after();
   }
-  if (ltid == 0 && p.use_tma && *abort_flag) {
-    // a wait gave up: give any copy still in flight a bounded chance to land
-    for (int s = 0; s < K && s < total; ++s) {
-      const int last = total - 1 - ((total - 1 - s) % K);
-      (void)mbar_wait_bounded(smem_u32(&bars[last % K]), (last / K) & 1);
-    }
-  }
-  if (warp == 0) tmem_dealloc(*tmem_base, p.tmem_cols);
+  __syncthreads();
+  tmem_fence_after();
+  if (warp == W) tmem_dealloc(*tmem_base, p.tmem_cols);
 }
 
 // ======================================================= estimate kernel
 
-// One group per block: antenna chunk c of frame f.
+// One warp group per block: antenna chunk c of frame f.
 template <int LOG2N, bool FC32>
-__global__ void __launch_bounds__(Geo<LOG2N>::TG) estimate_kernel(const KParams p) {
+__global__ void __launch_bounds__(Geo<LOG2N>::TW) estimate_kernel(const KParams p) {
   using G = Geo<LOG2N>;
   constexpr int N = G::N, A = G::A, F = G::F;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -982,12 +1052,13 @@ __global__ void __launch_bounds__(Geo<LOG2N>::TG) estimate_kernel(const KParams 
   const int lane = tid & 31;
   const int alpha = lane % A;
   const int jt = (tid >> 5) * F + lane / A;
-  const Layout lay = make_layout(N, FC32 ? 8 : 4, 1, 0, 1, false);
+  const Layout lay = make_layout(N, FC32 ? 8 : 4, 1, 1);
   const float2* tw = load_pass_twiddles<LOG2N>(p, smem, lay);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 192);
-  unsigned char* stage = smem + lay.group_off + lay.stage_off;
-  float2* myex = reinterpret_cast<float2*>(smem + lay.group_off + lay.ex_off) + alpha * G::XS;
+  unsigned char* stage = smem + lay.stage_off;
+  float2* ex = reinterpret_cast<float2*>(smem + lay.ex_off) + alpha * G::XS;
+  float2* ex1 = reinterpret_cast<float2*>(smem + lay.ex1_off) + alpha * G::XS;
   const int m = c * A + alpha;
   const bool valid = m < p.M;
   if (tid == 0) {
@@ -1013,7 +1084,11 @@ __global__ void __launch_bounds__(Geo<LOG2N>::TG) estimate_kernel(const KParams 
     for (int r = 0; r < 32; ++r) v[r] = make_float2(0.f, 0.f);
   }
   dft<32>(v, p);
-  team_fft_rest<LOG2N>(v, myex, jt, 0, tw, p, [] {});
+  middle_pass<LOG2N>(v, ex1, jt, p.twP, p, [] { __syncthreads(); });
+  final_exchange_write<LOG2N>(v, ex, jt);
+  __syncthreads();
+  final_exchange_read<LOG2N>(v, ex, jt, tw);
+  final_dft<LOG2N>(v, p);
   if (valid) {
     const size_t hrow = (static_cast<size_t>(f) * p.M + m) * N;
 #pragma unroll
@@ -1026,9 +1101,9 @@ __global__ void __launch_bounds__(Geo<LOG2N>::TG) estimate_kernel(const KParams 
 
 // ======================================================= fft kernel
 
-// One group per block: antenna chunk c of frame f, every symbol.
+// One warp group per block: antenna chunk c of frame f, every symbol.
 template <int LOG2N, bool FC32>
-__global__ void __launch_bounds__(Geo<LOG2N>::TG) fft_kernel(const KParams p) {
+__global__ void __launch_bounds__(Geo<LOG2N>::TW) fft_kernel(const KParams p) {
   using G = Geo<LOG2N>;
   constexpr int N = G::N, A = G::A, F = G::F;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -1038,12 +1113,13 @@ __global__ void __launch_bounds__(Geo<LOG2N>::TG) fft_kernel(const KParams p) {
   const int lane = tid & 31;
   const int alpha = lane % A;
   const int jt = (tid >> 5) * F + lane / A;
-  const Layout lay = make_layout(N, FC32 ? 8 : 4, p.nslots, 0, 1, false);
+  const Layout lay = make_layout(N, FC32 ? 8 : 4, p.nslots, 1);
   const float2* tw = load_pass_twiddles<LOG2N>(p, smem, lay);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 192);
-  unsigned char* stage = smem + lay.group_off + lay.stage_off;
-  float2* myex = reinterpret_cast<float2*>(smem + lay.group_off + lay.ex_off) + alpha * G::XS;
+  unsigned char* stage = smem + lay.stage_off;
+  float2* ex = reinterpret_cast<float2*>(smem + lay.ex_off) + alpha * G::XS;
+  float2* ex1 = reinterpret_cast<float2*>(smem + lay.ex1_off) + alpha * G::XS;
   const int m = c * A + alpha;
   const bool valid = m < p.M;
   const int K = p.nslots;
@@ -1077,14 +1153,17 @@ __global__ void __launch_bounds__(Geo<LOG2N>::TG) fft_kernel(const KParams p) {
       for (int r = 0; r < 32; ++r) v[r] = make_float2(0.f, 0.f);
     }
     dft<32>(v, p);
+    __syncthreads();   // staging slot consumed; exchange buffers free
+    if (tid < 32 && p.use_tma && s + K < p.S) {
+      fence_proxy_async();
+      issue_step<LOG2N, FC32>(p, f, c, s + K, stage + slot * slot_bytes, lay.team_stage,
+                              smem_u32(&bars[slot]), pol, lane);
+    }
+    middle_pass<LOG2N>(v, ex1, jt, p.twP, p, [] { __syncthreads(); });
+    final_exchange_write<LOG2N>(v, ex, jt);
     __syncthreads();
-    team_fft_rest<LOG2N>(v, myex, jt, 0, tw, p, [&] {
-      if (tid < 32 && p.use_tma && s + K < p.S) {
-        fence_proxy_async();
-        issue_step<LOG2N, FC32>(p, f, c, s + K, stage + slot * slot_bytes, lay.team_stage,
-                                smem_u32(&bars[slot]), pol, lane);
-      }
-    });
+    final_exchange_read<LOG2N>(v, ex, jt, tw);
+    final_dft<LOG2N>(v, p);
     if (valid) {
       float2* out = p.Y_out + ((static_cast<size_t>(f) * p.M + m) * p.S + s) * N;
 #pragma unroll

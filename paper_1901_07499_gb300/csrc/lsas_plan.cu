@@ -95,27 +95,23 @@ LaunchFn launcher_for(int N) {
 }
 
 // Choose the staging depth (slots) and the data symbols per group so that the
-// fused kernel fits the shared memory of one SM and its accumulators fit
-// tensor memory: prefer one data-symbol group (no second pass over H), then
-// the deepest staging ring.
+// fused kernel fits the shared memory of one SM, its accumulators fit tensor
+// memory, and the demapped codes fit the staging ring they reuse: prefer one
+// data-symbol group (no second pass over H), then the deepest ring.
 bool plan_geometry(int M, int N, int D, lsas_input_fmt fmt, Geometry* g) {
   g->A = geo_A(N);
   g->L = N / 32;
   g->T = geo_T(N);
   const int bps = fmt == LSAS_IN_SC16 ? 4 : 8;
-  const int G = geo_G(N);
   (void)M;
   const int own = geo_OWN(N);
-  const int cols_per_warp_slot = 512 / tmem_warps_per_quarter(N);
-  int dg_tmem = (cols_per_warp_slot - own) / (2 * own);
-  if (dg_tmem < 1) return false;
+  const int dg_tmem = (512 - own) / (2 * own);
   bool found = false;
   for (int groups = (D + dg_tmem - 1) / dg_tmem; groups <= D && !found; ++groups) {
     const int dg = (D + groups - 1) / groups;
     for (int slots = kMaxSlots; slots >= 2; --slots) {
-      const Layout l = make_layout(N, bps, slots, dg, G, true);
-      const int slot_region = slots * geo_A(N) * l.team_stage;
-      if (l.total > kSmemLimit || l.reuse_end > l.group_off + slot_region) continue;
+      const Layout l = make_layout(N, bps, slots, 2);
+      if (l.total > kSmemLimit || dg * N > slots * geo_A(N) * l.team_stage) continue;
       g->groups = groups;
       g->dg = dg;
       g->nslots = slots;
@@ -127,9 +123,9 @@ bool plan_geometry(int M, int N, int D, lsas_input_fmt fmt, Geometry* g) {
   if (!found) return false;
   g->tmem_cols = tmem_alloc_cols(N, g->dg);
   g->tmem_cth = tmem_cols_thread(N, g->dg);
-  g->smem_est = make_layout(N, bps, 1, 0, 1, false).total;
+  g->smem_est = make_layout(N, bps, 1, 1).total;
   g->fft_slots = 2;
-  g->smem_fft = make_layout(N, bps, 2, 0, 1, false).total;
+  g->smem_fft = make_layout(N, bps, 2, 1).total;
   return true;
 }
 
