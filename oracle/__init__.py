@@ -6,10 +6,11 @@ the CUDA library.
 """
 
 from .lsas_oracle import (Result, receive, strip_cp, dft, dft_matrix,
-                          ls_estimate, channel_energy, mrc, demap, slice_axis,
+                          ls_estimate, channel_energy, mrc, mrc_partial,
+                          mrc_combine, demap, slice_axis,
                           thresholds, qam_axis, gray_bits, pack_bits,
                           to_complex, data_symbols)
 
 __all__ = ["Result", "receive", "strip_cp", "dft", "dft_matrix", "ls_estimate",
-           "channel_energy", "mrc", "demap", "slice_axis", "thresholds",
+           "channel_energy", "mrc", "mrc_partial", "mrc_combine", "demap", "slice_axis", "thresholds",
            "qam_axis", "gray_bits", "pack_bits", "to_complex", "data_symbols"]

@@ -21,6 +21,10 @@ What it computes, step by step, for one received frame of M antennas
 5. Hard decision of each axis of ``z`` to the nearest Gray-QAM level and the
    level's Gray word (the demodulated output of Sec. II-B, in bits).
 
+The antenna split of step 4 (the distributed receiver Sec. IV proposes):
+each shard of antennas forms the two sums of step 4 over its own antennas;
+the shards' partial sums are added and divided afterwards.
+
 Readings taken where the paper is silent: unitary FFT scaling, natural
 subcarrier order (no fftshift), normalised MRC, the Gray labelling of the
 transmitter in ``synth`` and ties sent to the upper level.
@@ -111,6 +115,36 @@ def mrc(H: np.ndarray, Y_data: np.ndarray):
     ok = np.isfinite(E) & (E > 0)
     z = np.zeros_like(num)
     z[:, ok] = num[:, ok] / E[ok]
+    return z, E, bool(not np.all(ok))
+
+
+# --------------------------------------------------------------------------
+# 4'. Antenna-split MRC (the distributed receiver of Sec. IV)
+# --------------------------------------------------------------------------
+
+
+def mrc_partial(H: np.ndarray, Y_data: np.ndarray):
+    """Partial MRC sums of one shard of antennas (H [m][N], Y_data [m][D][N]).
+
+    P[d, k] = sum over the shard of conj(H[m, k]) Y[m, d, k] and
+    E[k] = sum over the shard of |H[m, k]|^2: the two sums of step 4 restricted
+    to the shard's antennas.  Adding the partials of a partition of the
+    antennas gives the sums of the whole array.
+    """
+    return np.einsum("mk,mdk->dk", np.conj(H), Y_data), channel_energy(H)
+
+
+def mrc_combine(P_parts, E_parts):
+    """z from shard partials (lists of P [D][N] and E [N]), added in list
+    order; zero or non-finite energy gives z = 0 and the flag, as in mrc()."""
+    P = np.zeros_like(np.asarray(P_parts[0], np.complex128))
+    E = np.zeros(np.asarray(E_parts[0]).shape, np.float64)
+    for Pg, Eg in zip(P_parts, E_parts):
+        P = P + Pg
+        E = E + Eg
+    ok = np.isfinite(E) & (E > 0)
+    z = np.zeros_like(P)
+    z[:, ok] = P[:, ok] / E[ok]
     return z, E, bool(not np.all(ok))
 
 

@@ -12,7 +12,10 @@ operand, a wrong Gray label or tie rule, bit order) fails at least one of them:
   frequency response; a complex (non +-1) pilot, where a missing conjugate
   shows; pilot at a symbol other than the first.
 * MRC: M = 1 equals per-subcarrier division; permutation and scale invariance;
-  identical antennas; noiseless recovery of the transmitted symbols.
+  identical antennas; noiseless recovery of the transmitted symbols.  The
+  antenna split: shard partials recover the symbols of a noiseless channel,
+  reduce to division for one antenna, match the whole array for any partition
+  and flag only bins with no energy in any shard.
 * Demap: brute-force nearest constellation point, Gray adjacency, golden Gray
   table, round trip through the transmitter's independent mapper, tie rule.
 * Statistics: LS error variance = sigma^2, and QPSK MRC bit-error rate against
@@ -210,6 +213,51 @@ def test_mrc_zero_energy_flag():
     Y = np.ones((2, 3, 8), complex)
     z, E, bad = oracle.mrc(H, Y)
     assert bad and np.all(z[:, 0] == 0) and np.allclose(z[:, 1:], 1.0)
+
+
+def _partition(M, rng):
+    cuts = sorted(rng.choice(np.arange(1, M), size=min(3, M - 1), replace=False))
+    return list(zip([0] + cuts, cuts + [M]))
+
+
+def test_mrc_antenna_split_recovers_symbols_and_divides():
+    rng = np.random.default_rng(14)
+    M, D, N = 7, 3, 16
+    H = rng.standard_normal((M, N)) + 1j * rng.standard_normal((M, N))
+    x = rng.standard_normal((D, N)) + 1j * rng.standard_normal((D, N))
+    Y = H[:, None, :] * x                        # noiseless: every antenna sees H x
+    for bounds in ([(m, m + 1) for m in range(M)], _partition(M, rng)):
+        parts = [oracle.mrc_partial(H[a:b], Y[a:b]) for a, b in bounds]
+        z, E, bad = oracle.mrc_combine([P for P, _ in parts], [e for _, e in parts])
+        assert not bad
+        assert np.allclose(z, x, rtol=1e-12)     # conj(H) weights undo the channel
+        assert np.allclose(E, np.sum(H.real ** 2 + H.imag ** 2, axis=0), rtol=1e-13)
+    # one antenna in one shard: the combiner is the per-subcarrier division
+    Yn = rng.standard_normal((1, D, N)) + 1j * rng.standard_normal((1, D, N))
+    P, e = oracle.mrc_partial(H[:1], Yn)
+    z1, _, _ = oracle.mrc_combine([P], [e])
+    assert np.allclose(z1, Yn[0] / H[0], rtol=1e-13)
+
+
+def test_mrc_antenna_split_matches_whole_array_and_flags():
+    rng = np.random.default_rng(15)
+    M, D, N = 9, 4, 32
+    H = rng.standard_normal((M, N)) + 1j * rng.standard_normal((M, N))
+    Y = rng.standard_normal((M, D, N)) + 1j * rng.standard_normal((M, D, N))
+    zf, Ef, _ = oracle.mrc(H, Y)
+    for _ in range(3):
+        parts = [oracle.mrc_partial(H[a:b], Y[a:b]) for a, b in _partition(M, rng)]
+        z, E, bad = oracle.mrc_combine([P for P, _ in parts], [e for _, e in parts])
+        assert not bad and np.allclose(z, zf, rtol=1e-12) and np.allclose(E, Ef, rtol=1e-13)
+    # a shard with no energy at a bin is fine while another shard has some
+    H0 = H.copy()
+    H0[:4, 5] = 0
+    H0[:, 7] = 0
+    parts = [oracle.mrc_partial(H0[a:b], Y[a:b]) for a, b in ((0, 4), (4, M))]
+    z, E, bad = oracle.mrc_combine([P for P, _ in parts], [e for _, e in parts])
+    assert bad and np.all(z[:, 7] == 0) and E[7] == 0
+    assert np.allclose(z[:, 5], np.sum(np.conj(H0[4:, 5])[:, None] * Y[4:, :, 5], axis=0)
+                       / np.sum(np.abs(H0[4:, 5]) ** 2), rtol=1e-12)
 
 
 # --------------------------------------------------------------- demap ----
