@@ -151,6 +151,39 @@ lsas_status lsas_run_frame(lsas_plan plan, const void* d_in, int n_frames,
                            void* stream);
 
 /*
+ * Antenna split, shard step (the distributed receiver of Sec. IV: MRC of
+ * Sec. II-C separates over antennas).  Runs the fused receiver for antennas
+ * [m_begin, m_begin + m_count) of the plan's M and stops at the MRC sums:
+ *   d_H  [F][M][N] complex: rows m_begin .. m_begin+m_count-1 are written
+ *        (the LS estimate, as lsas_run_frame writes them), others untouched;
+ *   d_P  [F][D][N] complex: P[d][k] = sum over the shard of
+ *        conj(H[m][k]) Y[m][s_d][k] (unitary Y);
+ *   d_E  [F][N] float: E[k] = sum over the shard of |H[m][k]|^2.
+ * d_in is the plan's [F][M][S*(N+CP)] input; only the shard's rows are read.
+ * A device that holds only its own antennas uses a plan with M = its count,
+ * m_begin = 0, m_count = M.  Errors: INVALID_ARG for a null pointer or a range
+ * outside [0, M); CAPACITY for n_frames > max_frames.  Asynchronous.
+ */
+lsas_status lsas_mrc_partial(lsas_plan plan, const void* d_in, int n_frames,
+                             int m_begin, int m_count, float* d_H, float* d_P,
+                             float* d_E, void* stream);
+
+/*
+ * Antenna split, combine step: adds the partials of n_shards shards in shard
+ * order 0 .. n_shards-1, then z = P / E, Gray slicing and packed bits exactly
+ * as lsas_run_frame.  d_P is [n_shards][F][D][N] complex and d_E
+ * [n_shards][F][N] float (shard g's lsas_mrc_partial outputs, stacked), both
+ * 16-byte aligned; d_bits [F][ceil(D*N*q/8)]; d_eq [F][D][N] complex or NULL.
+ * Only N, S, pilot position and QAM order of the plan matter here (not M).
+ * Zero or non-finite summed energy gives z = 0 and latches LSAS_ERR_DEVICE.
+ * Errors: INVALID_ARG for null/misaligned pointers or n_shards outside
+ * [1, 256]; CAPACITY for n_frames > max_frames.  Asynchronous.
+ */
+lsas_status lsas_mrc_combine(lsas_plan plan, const float* d_P, const float* d_E,
+                             int n_shards, int n_frames, uint8_t* d_bits,
+                             float* d_eq, void* stream);
+
+/*
  * lsas_run_frame on HOST buffers: copies the input to the device, runs the
  * receiver and copies H, bits and (if h_eq is not NULL) eq back, in chunks so
  * that transfers overlap the kernels.  Host buffers should be page-locked

@@ -34,7 +34,9 @@
 
 namespace lsas {
 
-enum { kModeEstimate = 0, kModeDemod = 1, kModeRun = 2 };
+// kModePartial: the fused path of one antenna shard, stopping at the MRC
+// partial sums (the antenna split of the distributed receiver, Sec. IV).
+enum { kModeEstimate = 0, kModeDemod = 1, kModeRun = 2, kModePartial = 3 };
 enum { kStOk = 0, kStTimeout = 6, kStDevice = 7 };
 
 constexpr int kMaxSlots = 6;
@@ -51,10 +53,17 @@ struct KParams {
   const float2* twP;     // pass twiddles W (layout: pass_tw_count)
   const float2* xinv;    // conj(X[k]) / |X[k]|^2 / sqrt(N)
   int* status;           // latched device status
-  int M, S, cp, pilot_idx, D;
+  float2* P_out;         // [F][D][N] shard partial sum conj(H) Y (partial)
+  float* E_out;          // [F][N]    shard partial sum |H|^2 (partial)
+  const float2* P_in;    // [G][F][D][N] partials to combine
+  const float* E_in;     // [G][F][N]
+  int M;                 // antennas this call processes
+  int m0, Mtot;          // first of them, antennas per frame in the arrays
+  int N, S, cp, pilot_idx, D;
+  int shards, nframes;   // combine: partials per frame, frames
   int chunks;            // ceil(M / A)
   int groups, dg;        // data-symbol groups per frame, data symbols per group
-  int mode;              // kModeDemod or kModeRun (frame_kernel)
+  int mode;              // kModeDemod, kModeRun or kModePartial (frame_kernel)
   int use_tma, nslots;
   int tmem_cols, tmem_cth;   // TMEM allocation (columns) and columns per thread
   int q, wbits, axes, nthr;
@@ -660,18 +669,24 @@ __device__ __forceinline__ void reduce_scatter(float2* v, int alpha) {
 
 // ------------------------------------------------------- staging pipeline
 
+// Whether the frame kernel transforms the pilot itself (LS estimate) rather
+// than reading a given channel.
+__device__ __forceinline__ bool fft_pilot(const KParams& p) {
+  return p.mode == kModeRun || p.mode == kModePartial;
+}
+
 // Items per antenna chunk in data-symbol group g: the pilot first (group 0 of
-// the fused mode), then the group's data symbols.
+// the fused modes), then the group's data symbols.
 __device__ __forceinline__ int group_items(const KParams& p, int g) {
   const int nd = min(p.dg, p.D - g * p.dg);
-  return nd + ((p.mode == kModeRun && g == 0) ? 1 : 0);
+  return nd + ((fft_pilot(p) && g == 0) ? 1 : 0);
 }
 
 template <int LOG2N, bool FC32>
 __device__ __forceinline__ const unsigned char* row_ptr(const KParams& p, int f, int m,
                                                         int s) {
   constexpr int bps = FC32 ? 8 : 4;
-  const size_t row = (static_cast<size_t>(f) * p.M + m) * p.S + s;
+  const size_t row = (static_cast<size_t>(f) * p.Mtot + p.m0 + m) * p.S + s;
   return static_cast<const unsigned char*>(p.in) +
          (row * (Geo<LOG2N>::N + p.cp) + p.cp) * bps;
 }
@@ -704,7 +719,7 @@ struct StepCursor {
   }
   __device__ int symbol(const KParams& p) const {
     int i = it;
-    if (p.mode == kModeRun && g == 0) {
+    if (fft_pilot(p) && g == 0) {
       if (i == 0) return p.pilot_idx;
       --i;
     }
@@ -862,7 +877,7 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T, 1) frame_kernel(const KParams p
       bar_sync(0, T);   // consumers wrote the codes
       // pack: 8 consecutive subcarriers -> q bytes (producers and consumers)
       const int nd = min(p.dg, p.D - g * p.dg);
-      const int items8 = nd * (N / 8);
+      const int items8 = (p.mode == kModePartial) ? 0 : nd * (N / 8);
       const size_t frame_bytes = static_cast<size_t>(p.D) * N * p.q / 8;
       const uint8_t* codes = smem + lay.codes_off;
       for (int it = tid; it < items8; it += T) {
@@ -902,14 +917,14 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T, 1) frame_kernel(const KParams p
       const int nd = min(p.dg, p.D - g * p.dg);
       const int d0 = g * p.dg;
       for (int dl = 0; dl < nd; ++dl) TmP::st(tacc + 2 * OWN * dl, zero);
-      const bool need_fft_pilot = (p.mode == kModeRun && g == 0);
+      const bool need_fft_pilot = fft_pilot(p) && g == 0;
       for (int c = 0; c < p.chunks; ++c) {
         const int m = c * A + alpha;
         const bool valid = m < p.M;
-        const size_t hrow = (static_cast<size_t>(f) * p.M + m) * N;
+        const size_t hrow = (static_cast<size_t>(f) * p.Mtot + p.m0 + m) * N;
         if (!need_fft_pilot) {
           // channel from memory: given (demodulate) or written in group 0
-          const float2* Hs = (p.mode == kModeRun) ? p.H_out : p.H_in;
+          const float2* Hs = fft_pilot(p) ? p.H_out : p.H_in;
 #pragma unroll
           for (int e = 0; e < 32; ++e)
             h[e] = valid ? Hs[hrow + bin_of<LOG2N>(jt, e)] : make_float2(0.f, 0.f);
@@ -981,6 +996,30 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T, 1) frame_kernel(const KParams p
       }
       tmem_wait_st();
       bar_sync(0, T);   // the group's steps are done; the staging ring is free
+      uint8_t* codes = smem + lay.codes_off;
+      if (p.mode == kModePartial) {
+        // the shard's partial sums leave the block; the combine kernel forms
+        // z over all shards (Y is the unscaled transform here: P gets the
+        // unitary 1/sqrt(N), E is already a sum of unitary |H|^2)
+        if (g == 0) {
+          float e[OWN];
+          TmE::ld(tE, e);
+          tmem_wait_ld();
+#pragma unroll
+          for (int cc = 0; cc < OWN; ++cc)
+            p.E_out[static_cast<size_t>(f) * N + bin_of<LOG2N>(jt, alpha * OWN + cc)] = e[cc];
+        }
+        for (int dl = 0; dl < nd; ++dl) {
+          float acc[2 * OWN];
+          TmP::ld(tacc + 2 * OWN * dl, acc);
+          tmem_wait_ld();
+          float2* dst = p.P_out + (static_cast<size_t>(f) * p.D + d0 + dl) * N;
+#pragma unroll
+          for (int cc = 0; cc < OWN; ++cc)
+            dst[bin_of<LOG2N>(jt, alpha * OWN + cc)] =
+                make_float2(acc[2 * cc] * p.inv_sqrtN, acc[2 * cc + 1] * p.inv_sqrtN);
+        }
+      } else {
       float ie[OWN];
       if (g == 0) {
         float e[OWN];
@@ -998,7 +1037,6 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T, 1) frame_kernel(const KParams p
         TmE::ld(tE, ie);
         tmem_wait_ld();
       }
-      uint8_t* codes = smem + lay.codes_off;
       for (int dl = 0; dl < nd; ++dl) {
         float acc[2 * OWN];
         TmP::ld(tacc + 2 * OWN * dl, acc);
@@ -1015,10 +1053,11 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T, 1) frame_kernel(const KParams p
           codes[dl * N + k] = static_cast<uint8_t>(code);
         }
       }
+      }
       tmem_wait_st();
       bar_sync(0, T);   // codes written
       // pack (shared with the producers)
-      const int items8 = nd * (N / 8);
+      const int items8 = (p.mode == kModePartial) ? 0 : nd * (N / 8);
       const size_t frame_bytes = static_cast<size_t>(p.D) * N * p.q / 8;
       for (int it = tid; it < items8; it += T) {
         const int dl = it / (N / 8);
@@ -1090,7 +1129,7 @@ __global__ void __launch_bounds__(Geo<LOG2N>::TW) estimate_kernel(const KParams 
   final_exchange_read<LOG2N>(v, ex, jt, tw);
   final_dft<LOG2N>(v, p);
   if (valid) {
-    const size_t hrow = (static_cast<size_t>(f) * p.M + m) * N;
+    const size_t hrow = (static_cast<size_t>(f) * p.Mtot + p.m0 + m) * N;
 #pragma unroll
     for (int e = 0; e < 32; ++e) {
       const int k = bin_of<LOG2N>(jt, e);
@@ -1165,7 +1204,7 @@ __global__ void __launch_bounds__(Geo<LOG2N>::TW) fft_kernel(const KParams p) {
     final_exchange_read<LOG2N>(v, ex, jt, tw);
     final_dft<LOG2N>(v, p);
     if (valid) {
-      float2* out = p.Y_out + ((static_cast<size_t>(f) * p.M + m) * p.S + s) * N;
+      float2* out = p.Y_out + ((static_cast<size_t>(f) * p.Mtot + p.m0 + m) * p.S + s) * N;
 #pragma unroll
       for (int e = 0; e < 32; ++e)
         out[bin_of<LOG2N>(jt, e)] = make_float2(v[e].x * p.inv_sqrtN, v[e].y * p.inv_sqrtN);

@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <cstdint>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -24,6 +25,7 @@ cudaError_t launch_n256(int, bool, const KParams&, int, int, cudaStream_t);
 cudaError_t launch_n512(int, bool, const KParams&, int, int, cudaStream_t);
 cudaError_t launch_n1024(int, bool, const KParams&, int, int, cudaStream_t);
 cudaError_t launch_n2048(int, bool, const KParams&, int, int, cudaStream_t);
+cudaError_t launch_combine(const KParams&, cudaStream_t);
 }  // namespace lsas
 
 using namespace lsas;
@@ -184,6 +186,9 @@ void base_params(lsas_plan p, KParams* k) {
   k->xinv = p->d_xinv;
   k->status = p->d_status;
   k->M = p->M;
+  k->m0 = 0;
+  k->Mtot = p->M;
+  k->N = p->N;
   k->S = p->S;
   k->cp = p->cp;
   k->pilot_idx = p->pilot_idx;
@@ -456,6 +461,57 @@ lsas_status lsas_run_frame(lsas_plan p, const void* d_in, int n_frames, float* d
   if (set_device(p) != LSAS_OK) return LSAS_ERR_CUDA;
   return launch_frame(p, d_in, n_frames, d_H, nullptr, d_bits, d_eq, kModeRun,
                       static_cast<cudaStream_t>(stream));
+}
+
+lsas_status lsas_mrc_partial(lsas_plan p, const void* d_in, int n_frames, int m_begin,
+                             int m_count, float* d_H, float* d_P, float* d_E, void* stream) {
+  if (!p) return LSAS_ERR_INVALID_ARG;
+  lsas_status s = check_frames(p, n_frames);
+  if (s != LSAS_OK) return s;
+  if (m_begin < 0 || m_count < 1 || m_begin > p->M - m_count) return LSAS_ERR_INVALID_ARG;
+  if (n_frames == 0) return LSAS_OK;
+  if (!d_in || !d_H || !d_P || !d_E) return LSAS_ERR_INVALID_ARG;
+  if (set_device(p) != LSAS_OK) return LSAS_ERR_CUDA;
+  KParams k;
+  base_params(p, &k);
+  k.in = d_in;
+  k.H_out = reinterpret_cast<float2*>(d_H);
+  k.P_out = reinterpret_cast<float2*>(d_P);
+  k.E_out = d_E;
+  k.M = m_count;
+  k.m0 = m_begin;
+  k.chunks = (m_count + p->geo.A - 1) / p->geo.A;
+  k.mode = kModePartial;
+  k.use_tma = tma_ok(p, d_in) ? 1 : 0;
+  if (p->launch(kKindFrame, p->fmt == LSAS_IN_FC32, k, n_frames, p->geo.smem_frame,
+                static_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return LSAS_ERR_CUDA;
+  return LSAS_OK;
+}
+
+lsas_status lsas_mrc_combine(lsas_plan p, const float* d_P, const float* d_E, int n_shards,
+                             int n_frames, uint8_t* d_bits, float* d_eq, void* stream) {
+  if (!p) return LSAS_ERR_INVALID_ARG;
+  lsas_status s = check_frames(p, n_frames);
+  if (s != LSAS_OK) return s;
+  if (n_shards < 1 || n_shards > 256) return LSAS_ERR_INVALID_ARG;
+  if (n_frames == 0) return LSAS_OK;
+  if (!d_P || !d_E || !d_bits) return LSAS_ERR_INVALID_ARG;
+  // the kernel reads partials and energies 16 bytes at a time
+  if ((reinterpret_cast<uintptr_t>(d_P) | reinterpret_cast<uintptr_t>(d_E)) % 16 != 0)
+    return LSAS_ERR_INVALID_ARG;
+  if (d_eq && reinterpret_cast<uintptr_t>(d_eq) % 8 != 0) return LSAS_ERR_INVALID_ARG;
+  if (set_device(p) != LSAS_OK) return LSAS_ERR_CUDA;
+  KParams k;
+  base_params(p, &k);
+  k.P_in = reinterpret_cast<const float2*>(d_P);
+  k.E_in = d_E;
+  k.shards = n_shards;
+  k.nframes = n_frames;
+  k.bits = d_bits;
+  k.eq = reinterpret_cast<float2*>(d_eq);
+  if (launch_combine(k, static_cast<cudaStream_t>(stream)) != cudaSuccess) return LSAS_ERR_CUDA;
+  return LSAS_OK;
 }
 
 lsas_status lsas_run_frame_host(lsas_plan p, const void* h_in, int n_frames, float* h_H,

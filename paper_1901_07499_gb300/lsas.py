@@ -57,6 +57,8 @@ lsas_estimate = _proto("lsas_estimate", [_vp, _vp, _i, _vp, _vp])
 lsas_demodulate = _proto("lsas_demodulate", [_vp, _vp, _vp, _i, _vp, _vp, _vp])
 lsas_run_frame = _proto("lsas_run_frame", [_vp, _vp, _i, _vp, _vp, _vp, _vp])
 lsas_run_frame_host = _proto("lsas_run_frame_host", [_vp, _vp, _i, _vp, _vp, _vp, _vp])
+lsas_mrc_partial = _proto("lsas_mrc_partial", [_vp, _vp, _i, _i, _i, _vp, _vp, _vp, _vp])
+lsas_mrc_combine = _proto("lsas_mrc_combine", [_vp, _vp, _vp, _i, _i, _vp, _vp, _vp])
 lsas_plan_sync = _proto("lsas_plan_sync", [_vp, _vp])
 lsas_plan_info = _proto("lsas_plan_info", [_vp, C.POINTER(_i)])
 lsas_plan_destroy = _proto("lsas_plan_destroy", [_vp])
@@ -64,7 +66,8 @@ lsas_plan_destroy = _proto("lsas_plan_destroy", [_vp])
 EXPORTED = ["lsas_status_str", "lsas_check_config", "lsas_frame_bytes",
             "lsas_plan_create", "lsas_plan_set", "lsas_plan_set_pilot",
             "lsas_fft", "lsas_estimate", "lsas_demodulate", "lsas_run_frame",
-            "lsas_run_frame_host", "lsas_plan_sync", "lsas_plan_info",
+            "lsas_run_frame_host", "lsas_mrc_partial", "lsas_mrc_combine",
+            "lsas_plan_sync", "lsas_plan_info",
             "lsas_plan_destroy"]
 
 
@@ -102,6 +105,24 @@ def _stream(stream) -> Optional[int]:
     if stream is None:
         stream = torch.cuda.current_stream()
     return stream.cuda_stream or None
+
+
+def gather_partials(P, E, group=None):
+    """Antenna split across processes (one shard of antennas per rank): every
+    rank passes its shard's partial sums P [F][D][N] complex64 and E [F][N]
+    float32 from Plan.mrc_partial and gets back all ranks' partials stacked in
+    rank order, [world][F][D][N] and [world][F][N], for Plan.mrc_combine, which
+    adds them in that fixed order.  Moves D*N complex + N real per frame and
+    rank, against M*S*(N+CP) input samples."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    Pr = torch.view_as_real(P.contiguous())
+    outP = [torch.empty_like(Pr) for _ in range(world)]
+    outE = [torch.empty_like(E) for _ in range(world)]
+    dist.all_gather(outP, Pr, group=group)
+    dist.all_gather(outE, E.contiguous(), group=group)
+    return torch.view_as_complex(torch.stack(outP)), torch.stack(outE)
 
 
 class Plan:
@@ -211,6 +232,36 @@ class Plan:
         check(lsas_run_frame_host(self._h, _ptr(x), F, _ptr(H), _ptr(bits), _ptr(eq),
                                   _stream(stream)), "lsas_run_frame_host")
         return H, bits, eq
+
+    # ---- antenna split (shard partial sums, then a fixed-order combine)
+    def empty_partials(self, F, shards=1, device="cuda"):
+        """Zeroed P [shards][F][D][N] complex64 and E [shards][F][N] float32."""
+        import torch
+        return (torch.zeros((shards, F, self.D, self.N), dtype=torch.complex64, device=device),
+                torch.zeros((shards, F, self.N), dtype=torch.float32, device=device))
+
+    def mrc_partial(self, x, m_begin, m_count, H, P, E, stream=None):
+        """Antennas [m_begin, m_begin + m_count): writes their rows of H and the
+        shard's partial sums P [F][D][N], E [F][N]."""
+        F = self._frames(x)
+        check(lsas_mrc_partial(self._h, _ptr(x), F, m_begin, m_count, _ptr(H), _ptr(P),
+                               _ptr(E), _stream(stream)), "lsas_mrc_partial")
+        return H, P, E
+
+    def mrc_combine(self, P, E, bits=None, eq=None, want_eq=False, stream=None):
+        """Adds the shards of P [G][F][D][N] and E [G][F][N] in order, then
+        slices and packs; returns (bits, eq)."""
+        G, F = int(P.shape[0]), int(P.shape[1])
+        if not (P.is_contiguous() and E.is_contiguous()):
+            raise ValueError("partials must be contiguous")
+        if tuple(E.shape) != (G, F, self.N) or tuple(P.shape[2:]) != (self.D, self.N):
+            raise ValueError("partials have the wrong shape")
+        bits = self.empty_bits(F, P.device) if bits is None else bits
+        if eq is None and want_eq:
+            eq = self.empty_eq(F, P.device)
+        check(lsas_mrc_combine(self._h, _ptr(P), _ptr(E), G, F, _ptr(bits), _ptr(eq),
+                               _stream(stream)), "lsas_mrc_combine")
+        return bits, eq
 
     def sync(self, stream=None) -> None:
         """Synchronise and raise if a device-side condition was latched."""
