@@ -184,6 +184,47 @@ lsas_status lsas_mrc_combine(lsas_plan plan, const float* d_P, const float* d_E,
                              float* d_eq, void* stream);
 
 /*
+ * Size of the library's fixed device scratch used by
+ * lsas_run_frame_split_static (16 MiB per device).
+ */
+#define LSAS_STATIC_SCRATCH_BYTES (16u << 20)
+
+/*
+ * The antenna-split receiver in one call that allocates no memory.  The
+ * paper has no counterpart: this is a library service, not a step of the
+ * method.  It computes what lsas_mrc_partial over n_shards even shards (shard
+ * g: M / n_shards antennas, one more for the first M % n_shards) followed by
+ * lsas_mrc_combine computes, with the shards' partial sums kept in a fixed
+ * device array of LSAS_STATIC_SCRATCH_BYTES inside the library instead of in
+ * caller buffers.  It is for callers that cannot allocate device memory at
+ * call time, for example a receive loop with a per-frame deadline, where
+ * cudaMalloc/cudaFree (or a framework allocator growing its pool) would
+ * synchronise the device and stall the other streams, or a process whose
+ * device memory is fully reserved up front.  It makes no cudaMalloc,
+ * cudaFree or other allocating call.
+ *   d_in, d_H, d_bits, d_eq: as lsas_run_frame (d_eq may be NULL).
+ *   Scratch needed: n_shards * n_frames * (D*N*8 + N*4) bytes; more than
+ *   LSAS_STATIC_SCRATCH_BYTES returns LSAS_ERR_CAPACITY before any launch
+ *   (for example at M = 64, N = 1024, 13 data symbols: n_shards * n_frames
+ *   <= 151).
+ * Nothing in the scratch needs to start at zero: the shard pass writes every
+ * partial sum that the combine pass of the same call reads.
+ * The first call on each device looks up the scratch address
+ * (cudaGetSymbolAddress) with that device current; a caller that captures
+ * its stream must make that first call before capture begins.
+ * The scratch is shared by all plans and streams of a device: calls whose
+ * execution overlaps on one device race on it and give wrong results, so
+ * serialise them (one stream, or synchronise between calls).
+ * Errors: INVALID_ARG for a null plan or pointer, n_shards outside [1, M] or
+ * n_frames < 0; CAPACITY as above or for n_frames > max_frames; CUDA if the
+ * scratch cannot be looked up or a launch fails.  Asynchronous.
+ */
+lsas_status lsas_run_frame_split_static(lsas_plan plan, const void* d_in,
+                                        int n_frames, int n_shards,
+                                        float* d_H, uint8_t* d_bits,
+                                        float* d_eq, void* stream);
+
+/*
  * lsas_run_frame on HOST buffers: copies the input to the device, runs the
  * receiver and copies H, bits and (if h_eq is not NULL) eq back, in chunks so
  * that transfers overlap the kernels.  Host buffers should be page-locked

@@ -12,6 +12,7 @@
 #include <cstdlib>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -247,6 +248,39 @@ lsas_status launch_frame(lsas_plan p, const void* d_in, int n_frames, float* d_H
       cudaSuccess)
     return LSAS_ERR_CUDA;
   return LSAS_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Fixed device scratch for lsas_run_frame_split_static: the antenna-split
+// partial sums of one call live here instead of in caller or library
+// allocations, so that the call allocates nothing.  One array per device
+// (a __device__ variable exists once in every context); its address is looked
+// up once per device with cudaGetSymbolAddress.  Calls that overlap in time on
+// one device share it and race.
+static __device__ __align__(256) unsigned char g_split_scratch[LSAS_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_split_scratch_mu;
+void* g_split_scratch_ptr[kMaxDevices] = {};
+
+// Address of this device's scratch (the device must be current); null on
+// failure.  Only the first call per device talks to the runtime.
+void* split_scratch_for(int dev) {
+  if (dev < 0 || dev >= kMaxDevices) return nullptr;
+  std::lock_guard<std::mutex> lock(g_split_scratch_mu);
+  if (!g_split_scratch_ptr[dev]) {
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_split_scratch) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    g_split_scratch_ptr[dev] = ptr;
+  }
+  return g_split_scratch_ptr[dev];
 }
 
 }  // namespace
@@ -635,6 +669,37 @@ lsas_status lsas_plan_destroy(lsas_plan p) {
   }
   delete p;
   return LSAS_OK;
+}
+
+lsas_status lsas_run_frame_split_static(lsas_plan p, const void* d_in, int n_frames,
+                                        int n_shards, float* d_H, uint8_t* d_bits,
+                                        float* d_eq, void* stream) {
+  if (!p) return LSAS_ERR_INVALID_ARG;
+  if (n_shards < 1 || n_shards > p->M || n_frames < 0) return LSAS_ERR_INVALID_ARG;
+  // partial sums of every shard and frame: P [G][F][D][N] complex, then E [G][F][N]
+  const size_t p_bytes = static_cast<size_t>(n_shards) * n_frames * p->D * p->N * 8;
+  const size_t e_bytes = static_cast<size_t>(n_shards) * n_frames * p->N * 4;
+  if (p_bytes + e_bytes > LSAS_STATIC_SCRATCH_BYTES) return LSAS_ERR_CAPACITY;
+  lsas_status s = check_frames(p, n_frames);
+  if (s != LSAS_OK) return s;
+  if (n_frames == 0) return LSAS_OK;
+  if (!d_in || !d_H || !d_bits) return LSAS_ERR_INVALID_ARG;
+  if (set_device(p) != LSAS_OK) return LSAS_ERR_CUDA;
+  unsigned char* scratch = static_cast<unsigned char*>(split_scratch_for(p->device));
+  if (!scratch) return LSAS_ERR_CUDA;
+  float* P = reinterpret_cast<float*>(scratch);
+  float* E = reinterpret_cast<float*>(scratch + p_bytes);   // p_bytes is a multiple of 512
+  // even split: shard g gets M / G antennas, plus one for the first M % G shards
+  int m0 = 0;
+  for (int g = 0; g < n_shards; ++g) {
+    const int mc = p->M / n_shards + (g < p->M % n_shards ? 1 : 0);
+    s = lsas_mrc_partial(p, d_in, n_frames, m0, mc, d_H,
+                         P + static_cast<size_t>(g) * n_frames * p->D * p->N * 2,
+                         E + static_cast<size_t>(g) * n_frames * p->N, stream);
+    if (s != LSAS_OK) return s;
+    m0 += mc;
+  }
+  return lsas_mrc_combine(p, P, E, n_shards, n_frames, d_bits, d_eq, stream);
 }
 
 }  // extern "C"

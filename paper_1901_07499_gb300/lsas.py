@@ -33,6 +33,7 @@ LSAS_ERR_CAPACITY = 4
 LSAS_ERR_CUDA = 5
 LSAS_ERR_TIMEOUT = 6
 LSAS_ERR_DEVICE = 7
+LSAS_STATIC_SCRATCH_BYTES = 16 << 20
 LSAS_IN_SC16 = 0
 LSAS_IN_FC32 = 1
 
@@ -59,6 +60,8 @@ lsas_run_frame = _proto("lsas_run_frame", [_vp, _vp, _i, _vp, _vp, _vp, _vp])
 lsas_run_frame_host = _proto("lsas_run_frame_host", [_vp, _vp, _i, _vp, _vp, _vp, _vp])
 lsas_mrc_partial = _proto("lsas_mrc_partial", [_vp, _vp, _i, _i, _i, _vp, _vp, _vp, _vp])
 lsas_mrc_combine = _proto("lsas_mrc_combine", [_vp, _vp, _vp, _i, _i, _vp, _vp, _vp])
+lsas_run_frame_split_static = _proto("lsas_run_frame_split_static",
+                                     [_vp, _vp, _i, _i, _vp, _vp, _vp, _vp])
 lsas_plan_sync = _proto("lsas_plan_sync", [_vp, _vp])
 lsas_plan_info = _proto("lsas_plan_info", [_vp, C.POINTER(_i)])
 lsas_plan_destroy = _proto("lsas_plan_destroy", [_vp])
@@ -67,6 +70,7 @@ EXPORTED = ["lsas_status_str", "lsas_check_config", "lsas_frame_bytes",
             "lsas_plan_create", "lsas_plan_set", "lsas_plan_set_pilot",
             "lsas_fft", "lsas_estimate", "lsas_demodulate", "lsas_run_frame",
             "lsas_run_frame_host", "lsas_mrc_partial", "lsas_mrc_combine",
+            "lsas_run_frame_split_static",
             "lsas_plan_sync", "lsas_plan_info",
             "lsas_plan_destroy"]
 
