@@ -37,8 +37,9 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_SRC = os.path.join(ROOT, "paper_1901_07499_gb300", "csrc", "lsas_kernels.cuh")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "frame_kernel_traffic.json")
+KERNEL_SRC = [os.path.join(ROOT, "paper_1901_07499_gb300", "csrc", n)
+              for n in ("lsas_kernels.cuh", "lsas_warp.cuh")]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fused_kernel_traffic.json")
 
 
 def parse():
@@ -93,8 +94,11 @@ def measured_peaks():
 
 
 def kernel_hash():
-    with open(KERNEL_SRC, "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for path in KERNEL_SRC:
+        with open(path, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def ncu_traffic(cfg, frames):
@@ -341,7 +345,7 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": peak_src,
-                         "kernel": "frame_kernel (fused CP strip+FFT+LS+MRC+demap)",
+                         "kernel": "warp_kernel (fused CP strip+FFT+LS+MRC+demap, per-warp pipelines)" if cfg.N <= 1024 else "frame_kernel (fused CP strip+FFT+LS+MRC+demap)",
                          "algorithmic_bytes_per_frame": in_b + h_b + bit_b},
             "e2e": {"value": samples / t_e2e, "unit": "samples/s",
                     "h2d_bytes_per_step": F * in_b, "d2h_bytes_per_step": F * (h_b + bit_b)},

@@ -2,15 +2,29 @@
 // includes it once so that the six lengths compile in parallel.
 #pragma once
 #include "lsas_kernels.cuh"
+#include "lsas_warp.cuh"
 
 namespace lsas {
 
 template <int LOG2N, bool FC32>
 static cudaError_t launch_t(int kind, const KParams& p, int grid, int smem, cudaStream_t st) {
   void (*fn)(const KParams) = nullptr;
-  if (kind == kKindFrame) fn = frame_kernel<LOG2N, FC32>;
-  else if (kind == kKindEstimate) fn = estimate_kernel<LOG2N, FC32>;
-  else fn = fft_kernel<LOG2N, FC32>;
+  int threads = Geo<LOG2N>::TW;
+  if (kind == kKindFrame) {
+    // fused receiver: per-warp pipelines up to N = 1024, the warp-specialised
+    // producer/consumer kernel for N = 2048
+    if constexpr (LOG2N <= 10) {
+      fn = warp_kernel<LOG2N, FC32>;
+      threads = kWThreads;
+    } else {
+      fn = frame_kernel<LOG2N, FC32>;
+      threads = Geo<LOG2N>::T;
+    }
+  } else if (kind == kKindEstimate) {
+    fn = estimate_kernel<LOG2N, FC32>;
+  } else {
+    fn = fft_kernel<LOG2N, FC32>;
+  }
   // raise the kernel's dynamic shared memory limit once per device
   static int limit[3][64] = {};
   int dev = 0;
@@ -21,7 +35,6 @@ static cudaError_t launch_t(int kind, const KParams& p, int grid, int smem, cuda
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) limit[kind][dev] = smem;
   }
-  const int threads = (kind == kKindFrame) ? Geo<LOG2N>::T : Geo<LOG2N>::TW;
   fn<<<grid, threads, smem, st>>>(p);
   return cudaGetLastError();
 }

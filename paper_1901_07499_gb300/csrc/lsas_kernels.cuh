@@ -154,6 +154,60 @@ __host__ __device__ inline int tmem_alloc_cols(int N, int dg) {
 //            [256 + r*256 + j] = W_2048^(j r), j < 256 (third pass).
 __host__ __device__ inline int pass_tw_count(int N) { return N <= 1024 ? N : 256 + 2048; }
 
+// ------------------------------------------------ warp kernel geometry
+//
+// The per-warp fused kernel (N <= 1024, lsas_warp.cuh): each of kWarps warps
+// transforms A = 32/L antenna rows per step on its own (the FFT team of one
+// antenna is L = N/32 lanes of one warp), with its own staging ring and
+// exchange region; the block synchronises only at data-symbol group ends.
+constexpr int kWarps = 8;
+constexpr int kWThreads = 32 * kWarps;
+constexpr int kWHeader = 512;      // mbarriers [kWarps][kMaxSlots], TMEM address, flags
+constexpr int kWTmemCols = 512;    // all of TMEM: two warps per lane quarter
+constexpr int kWTmemWarp = 256;    // columns per warp
+
+__host__ __device__ constexpr int wgeo_A(int N) { return 32 / (N / 32); }
+__host__ __device__ constexpr int wgeo_OWN(int N) { return N / 32; }
+// exchange stride (float2) per antenna: N plus one pad per 32, rounded so
+// that the antenna regions of a warp start 16/A float2 apart modulo 16
+__host__ __device__ constexpr int wgeo_XS(int N) {
+  return (N + N / 32) +
+         (((16 / wgeo_A(N)) % 16 - (N + N / 32) % 16) + 16) % 16;
+}
+// staging pad (samples) per antenna row: rows start L words of banks apart
+// (sc16) or L/2 bank pairs (fc32) and stay 16-byte aligned
+__host__ __device__ constexpr int wgeo_spad(int N, int bps) {
+  return bps == 4 ? (N / 32 >= 4 ? N / 32 : 4) : (N / 32 >= 4 ? N / 64 : 2);
+}
+
+// Shared memory of the warp kernel: header, last-pass twiddles, 1/E per
+// subcarrier, the demapped codes of one group, then one region per warp
+// (staging ring + exchange).  At group ends the per-warp regions together
+// hold the warps' partial sums for the cross-warp reduction.
+struct WLayout {
+  int tw_off, ie_off, codes_off, warp_off;
+  int team_stage;    // bytes per antenna row in a slot
+  int stage_bytes;   // one warp's ring
+  int warp_bytes;    // one warp's region
+  int total;
+};
+__host__ __device__ inline WLayout make_wlayout(int N, int bps, int nslots, int dg) {
+  WLayout l;
+  l.tw_off = kWHeader;
+  l.ie_off = l.tw_off + N * 8;
+  l.codes_off = l.ie_off + N * 4;
+  l.warp_off = align_up(l.codes_off + dg * N, 128);
+  l.team_stage = (N + wgeo_spad(N, bps)) * bps;
+  l.stage_bytes = nslots * wgeo_A(N) * l.team_stage;
+  l.warp_bytes = align_up(l.stage_bytes + wgeo_A(N) * wgeo_XS(N) * 8, 128);
+  l.total = l.warp_off + kWarps * l.warp_bytes;
+  return l;
+}
+// data symbols per group that the per-warp TMEM columns hold
+__host__ __device__ inline int wgeo_dg_max(int N) {
+  return (kWTmemWarp - wgeo_OWN(N)) / (2 * wgeo_OWN(N));
+}
+
 #ifdef __CUDACC__
 
 // ------------------------------------------------------- PTX primitives
@@ -336,6 +390,18 @@ template <> struct Tmem<32> {
   static __device__ __forceinline__ void st(uint32_t t, const float* v) {
     Tmem<16>::st(t, v);
     Tmem<16>::st(t + 16, v + 16);
+  }
+};
+
+// 64 columns as two 32-column halves
+template <> struct Tmem<64> {
+  static __device__ __forceinline__ void ld(uint32_t t, float* v) {
+    Tmem<32>::ld(t, v);
+    Tmem<32>::ld(t + 32, v + 32);
+  }
+  static __device__ __forceinline__ void st(uint32_t t, const float* v) {
+    Tmem<32>::st(t, v);
+    Tmem<32>::st(t + 32, v + 32);
   }
 };
 

@@ -38,6 +38,7 @@ constexpr int kHostChunk = 64;       // frames per transfer chunk (host path)
 
 struct Geometry {
   int A, L, T;
+  int Af;   // antennas per step of the fused kernel (frame launches)
   int nslots, groups, dg, smem_frame;
   int smem_est, smem_fft, fft_slots;
   int tmem_cols, tmem_cth;
@@ -103,6 +104,7 @@ LaunchFn launcher_for(int N) {
 // data-symbol group (no second pass over H), then the deepest ring.
 bool plan_geometry(int M, int N, int D, lsas_input_fmt fmt, Geometry* g) {
   g->A = geo_A(N);
+  g->Af = geo_A(N);
   g->L = N / 32;
   g->T = geo_T(N);
   const int bps = fmt == LSAS_IN_SC16 ? 4 : 8;
@@ -126,6 +128,31 @@ bool plan_geometry(int M, int N, int D, lsas_input_fmt fmt, Geometry* g) {
   if (!found) return false;
   g->tmem_cols = tmem_alloc_cols(N, g->dg);
   g->tmem_cth = tmem_cols_thread(N, g->dg);
+  if (N <= 1024) {
+    // per-warp kernel: TMEM bounds the data symbols per group; the deepest
+    // staging ring that fits, with room for one symbol of every warp's
+    // partial sums in the per-warp regions
+    found = false;
+    const int dgmax = wgeo_dg_max(N);
+    for (int groups = (D + dgmax - 1) / dgmax; groups <= D && !found; ++groups) {
+      const int dg = (D + groups - 1) / groups;
+      for (int slots = kMaxSlots; slots >= 2; --slots) {
+        const WLayout l = make_wlayout(N, bps, slots, dg);
+        if (l.total > kSmemLimit || l.warp_bytes < N * 8) continue;
+        g->groups = groups;
+        g->dg = dg;
+        g->nslots = slots;
+        g->smem_frame = l.total;
+        g->T = kWThreads;
+        g->Af = wgeo_A(N);
+        g->tmem_cols = kWTmemCols;
+        g->tmem_cth = kWTmemWarp;
+        found = true;
+        break;
+      }
+    }
+    if (!found) return false;
+  }
   g->smem_est = make_layout(N, bps, 1, 1).total;
   g->fft_slots = 2;
   g->smem_fft = make_layout(N, bps, 2, 1).total;
@@ -243,6 +270,7 @@ lsas_status launch_frame(lsas_plan p, const void* d_in, int n_frames, float* d_H
   k.bits = d_bits;
   k.eq = reinterpret_cast<float2*>(d_eq);
   k.mode = mode;
+  k.chunks = (p->M + p->geo.Af - 1) / p->geo.Af;
   k.use_tma = tma_ok(p, d_in) ? 1 : 0;
   if (p->launch(kKindFrame, p->fmt == LSAS_IN_FC32, k, n_frames, p->geo.smem_frame, st) !=
       cudaSuccess)
@@ -514,7 +542,7 @@ lsas_status lsas_mrc_partial(lsas_plan p, const void* d_in, int n_frames, int m_
   k.E_out = d_E;
   k.M = m_count;
   k.m0 = m_begin;
-  k.chunks = (m_count + p->geo.A - 1) / p->geo.A;
+  k.chunks = (m_count + p->geo.Af - 1) / p->geo.Af;
   k.mode = kModePartial;
   k.use_tma = tma_ok(p, d_in) ? 1 : 0;
   if (p->launch(kKindFrame, p->fmt == LSAS_IN_FC32, k, n_frames, p->geo.smem_frame,
@@ -636,7 +664,7 @@ lsas_status lsas_plan_sync(lsas_plan p, void* stream) {
 
 lsas_status lsas_plan_info(lsas_plan p, int out[8]) {
   if (!p || !out) return LSAS_ERR_INVALID_ARG;
-  out[0] = p->geo.A;
+  out[0] = p->geo.Af;
   out[1] = p->geo.T;
   out[2] = p->geo.smem_frame;
   out[3] = p->geo.groups;
