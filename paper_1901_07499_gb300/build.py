@@ -9,6 +9,7 @@ object file.
 from __future__ import annotations
 
 import concurrent.futures as cf
+import fcntl
 import glob
 import os
 import shutil
@@ -58,8 +59,20 @@ def _compile(src: str, obj: str, verbose: bool):
 
 
 def build(verbose: bool = False, jobs: int = 0) -> str:
-    """Compile every CUDA unit for sm_103a and link liblsas.so; returns its path."""
+    """Compile every CUDA unit for sm_103a and link liblsas.so; returns its path.
+
+    Concurrent callers (for example several test processes) are serialised
+    by a lock file next to the objects, so none sees a half-written object."""
     os.makedirs(OUT, exist_ok=True)
+    with open(os.path.join(OUT, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            return _build_locked(verbose, jobs)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(verbose: bool, jobs: int) -> str:
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     objs = [os.path.join(OUT, os.path.basename(s)[:-3] + ".o") for s in srcs]
     todo = [(s, o) for s, o in zip(srcs, objs) if _stale(s, o)]

@@ -15,7 +15,7 @@ static cudaError_t launch_t(int kind, const KParams& p, int grid, int smem, cuda
     // producer/consumer kernel for N = 2048
     if constexpr (LOG2N <= 10) {
       fn = warp_kernel<LOG2N, FC32>;
-      threads = kWThreads;
+      threads = 32 * wgeo_warps(FC32 ? 8 : 4);
     } else {
       fn = frame_kernel<LOG2N, FC32>;
       threads = Geo<LOG2N>::T;

@@ -156,15 +156,21 @@ __host__ __device__ inline int pass_tw_count(int N) { return N <= 1024 ? N : 256
 
 // ------------------------------------------------ warp kernel geometry
 //
-// The per-warp fused kernel (N <= 1024, lsas_warp.cuh): each of kWarps warps
+// The per-warp fused kernel (N <= 1024, lsas_warp.cuh): each of its warps
 // transforms A = 32/L antenna rows per step on its own (the FFT team of one
 // antenna is L = N/32 lanes of one warp), with its own staging ring and
 // exchange region; the block synchronises only at data-symbol group ends.
-constexpr int kWarps = 8;
-constexpr int kWThreads = 32 * kWarps;
-constexpr int kWHeader = 512;      // mbarriers [kWarps][kMaxSlots], TMEM address, flags
-constexpr int kWTmemCols = 512;    // all of TMEM: two warps per lane quarter
-constexpr int kWTmemWarp = 256;    // columns per warp
+// 8 warps (2 per scheduler): 12 would need <= 168 registers (the N = 1024
+// kernel then spills) and leave room for only a 2-slot staging ring, and
+// measured slower.
+__host__ __device__ constexpr int wgeo_warps(int /*bps*/) { return 8; }
+constexpr int kWMaxWarps = 12;
+constexpr int kWTmemAddr = kWMaxWarps * kMaxSlots * 8;   // after the mbarriers
+constexpr int kWAbort = kWTmemAddr + 16;
+constexpr int kWHeader = 640;      // mbarriers [warps][kMaxSlots], TMEM address, flags
+constexpr int kWTmemCols = 512;    // all of TMEM, split between the warps
+// TMEM columns per warp: warps w, w+4, ... share lane quarter w % 4
+__host__ __device__ constexpr int wgeo_tmem_warp(int warps) { return warps > 8 ? 160 : 256; }
 
 __host__ __device__ constexpr int wgeo_A(int N) { return 32 / (N / 32); }
 __host__ __device__ constexpr int wgeo_OWN(int N) { return N / 32; }
@@ -192,6 +198,7 @@ struct WLayout {
   int total;
 };
 __host__ __device__ inline WLayout make_wlayout(int N, int bps, int nslots, int dg) {
+  const int warps = wgeo_warps(bps);
   WLayout l;
   l.tw_off = kWHeader;
   l.ie_off = l.tw_off + N * 8;
@@ -200,12 +207,12 @@ __host__ __device__ inline WLayout make_wlayout(int N, int bps, int nslots, int 
   l.team_stage = (N + wgeo_spad(N, bps)) * bps;
   l.stage_bytes = nslots * wgeo_A(N) * l.team_stage;
   l.warp_bytes = align_up(l.stage_bytes + wgeo_A(N) * wgeo_XS(N) * 8, 128);
-  l.total = l.warp_off + kWarps * l.warp_bytes;
+  l.total = l.warp_off + warps * l.warp_bytes;
   return l;
 }
 // data symbols per group that the per-warp TMEM columns hold
-__host__ __device__ inline int wgeo_dg_max(int N) {
-  return (kWTmemWarp - wgeo_OWN(N)) / (2 * wgeo_OWN(N));
+__host__ __device__ inline int wgeo_dg_max(int N, int bps) {
+  return (wgeo_tmem_warp(wgeo_warps(bps)) - wgeo_OWN(N)) / (2 * wgeo_OWN(N));
 }
 
 #ifdef __CUDACC__

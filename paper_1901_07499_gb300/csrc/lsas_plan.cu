@@ -133,7 +133,7 @@ bool plan_geometry(int M, int N, int D, lsas_input_fmt fmt, Geometry* g) {
     // staging ring that fits, with room for one symbol of every warp's
     // partial sums in the per-warp regions
     found = false;
-    const int dgmax = wgeo_dg_max(N);
+    const int dgmax = wgeo_dg_max(N, bps);
     for (int groups = (D + dgmax - 1) / dgmax; groups <= D && !found; ++groups) {
       const int dg = (D + groups - 1) / groups;
       for (int slots = kMaxSlots; slots >= 2; --slots) {
@@ -143,10 +143,10 @@ bool plan_geometry(int M, int N, int D, lsas_input_fmt fmt, Geometry* g) {
         g->dg = dg;
         g->nslots = slots;
         g->smem_frame = l.total;
-        g->T = kWThreads;
+        g->T = 32 * wgeo_warps(bps);
         g->Af = wgeo_A(N);
         g->tmem_cols = kWTmemCols;
-        g->tmem_cth = kWTmemWarp;
+        g->tmem_cth = wgeo_tmem_warp(wgeo_warps(bps));
         found = true;
         break;
       }

@@ -1,7 +1,7 @@
 // lsas_warp.cuh -- per-warp fused receiver kernel for N <= 1024.
 //
-// One block per frame, kWarps warps, each an independent pipeline over whole
-// antenna-symbol rows.  Warp w takes antenna chunks w, w + kWarps, ... (A =
+// One block per frame, NW warps, each an independent pipeline over whole
+// antenna-symbol rows.  Warp w takes antenna chunks w, w + NW, ... (A =
 // 32/L antennas per chunk; L = N/32 lanes form one antenna's FFT team).  Per
 // step a warp
 //   * waits for its staging slot (bulk asynchronous copy of the CP-stripped
@@ -54,8 +54,11 @@ __device__ __forceinline__ int witem_symbol(const KParams& p, bool pilot_here, i
 }
 
 template <int LOG2N, bool FC32>
-__global__ void __launch_bounds__(kWThreads, 1) warp_kernel(const KParams p) {
+__global__ void __launch_bounds__(32 * wgeo_warps(FC32 ? 8 : 4), 1) warp_kernel(const KParams p) {
   constexpr int N = 1 << LOG2N;
+  constexpr int NW = wgeo_warps(FC32 ? 8 : 4);   // warps of the block
+  constexpr int NT = 32 * NW;
+  constexpr int TMW = wgeo_tmem_warp(NW);         // TMEM columns per warp
   constexpr int A = wgeo_A(N), OWN = wgeo_OWN(N), XS = wgeo_XS(N);
   static_assert(N <= 1024, "the per-warp kernel covers N <= 1024");
   using TmP = Tmem<2 * OWN>;   // one data symbol of partial sums (complex)
@@ -70,8 +73,8 @@ __global__ void __launch_bounds__(kWThreads, 1) warp_kernel(const KParams p) {
   const int K = p.nslots;
   const WLayout lay = make_wlayout(N, FC32 ? 8 : 4, K, p.dg);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem) + warp * kMaxSlots;
-  uint32_t* tmem_base = reinterpret_cast<uint32_t*>(smem + 384);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 400);
+  uint32_t* tmem_base = reinterpret_cast<uint32_t*>(smem + kWTmemAddr);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + kWAbort);
   float2* tws = reinterpret_cast<float2*>(smem + lay.tw_off);
   float* ie_s = reinterpret_cast<float*>(smem + lay.ie_off);
   uint8_t* codes = smem + lay.codes_off;
@@ -79,7 +82,7 @@ __global__ void __launch_bounds__(kWThreads, 1) warp_kernel(const KParams p) {
   float2* ex = reinterpret_cast<float2*>(stage + lay.stage_bytes) + alpha * XS;
   const int slot_bytes = A * lay.team_stage;
 
-  for (int i = tid; i < N; i += kWThreads) tws[i] = __ldg(p.twP + i);
+  for (int i = tid; i < N; i += NT) tws[i] = __ldg(p.twP + i);
   if (tid == 0) *abort_flag = 0;
   if (lane == 0 && p.use_tma) {
     for (int s = 0; s < K; ++s) mbar_init(smem_u32(&bars[s]), 1);
@@ -89,20 +92,25 @@ __global__ void __launch_bounds__(kWThreads, 1) warp_kernel(const KParams p) {
   tmem_fence_before();
   __syncthreads();
   tmem_fence_after();
-  // this warp's columns: its lane quarter, half of the 512 columns
+  // this warp's columns: TMW columns of its lane quarter
   const uint32_t tE = *tmem_base + (static_cast<uint32_t>(32 * (warp & 3)) << 16) +
-                      static_cast<uint32_t>((warp >> 2) * kWTmemWarp);
+                      static_cast<uint32_t>((warp >> 2) * TMW);
   const uint32_t tP = tE + OWN;   // data symbol dl at tP + 2 OWN dl
   uint64_t pol = 0;
   if (p.use_tma) {
     if (lane == 0) pol = evict_first_policy();
     pol = __shfl_sync(0xffffffffu, pol, 0);
   }
-  float zero[2 * OWN];
+  // zero-fill of accumulator columns, 16 (or fewer) at a time
+  constexpr int ZC = OWN < 16 ? OWN : 16;
+  float zero[ZC];
 #pragma unroll
-  for (int i = 0; i < 2 * OWN; ++i) zero[i] = 0.f;
+  for (int i = 0; i < ZC; ++i) zero[i] = 0.f;
 
-  const int nch = warp < p.chunks ? (p.chunks - 1 - warp) / kWarps + 1 : 0;
+  const int nch = warp < p.chunks ? (p.chunks - 1 - warp) / NW + 1 : 0;
+  // start the warps of the upper half a little later, so that the two warps
+  // sharing a scheduler tend to be in different phases of their steps
+  if (warp >= 4) __nanosleep(1400);
   int step = 0;   // this warp's step counter over the whole frame
   for (int g = 0; g < p.groups; ++g) {
     const int nd = min(p.dg, p.D - g * p.dg);
@@ -111,22 +119,28 @@ __global__ void __launch_bounds__(kWThreads, 1) warp_kernel(const KParams p) {
     const int items = group_items(p, g);
     const int gstart = step;
     const int gend = step + nch * items;
-    if (g == 0) TmE::st(tE, zero);
-    for (int dl = 0; dl < nd; ++dl) TmP::st(tP + 2 * OWN * dl, zero);
+    if (g == 0) {
+#pragma unroll
+      for (int q0 = 0; q0 < OWN; q0 += ZC) Tmem<ZC>::st(tE + q0, zero);
+    }
+    for (int dl = 0; dl < nd; ++dl) {
+#pragma unroll
+      for (int q0 = 0; q0 < 2 * OWN; q0 += ZC) Tmem<ZC>::st(tP + 2 * OWN * dl + q0, zero);
+    }
     if (p.use_tma) {
       // the ring held generic data (last group's reduction): order it before
       // the copies, then fill the first K slots of this group
       fence_proxy_async();
       for (int s = step; s < step + K && s < gend; ++s) {
         const int ls = s - gstart;
-        wissue<LOG2N, FC32>(p, f, warp + (ls / items) * kWarps,
+        wissue<LOG2N, FC32>(p, f, warp + (ls / items) * NW,
                             witem_symbol(p, pilot_here, d0, ls % items),
                             stage + (s % K) * slot_bytes, lay.team_stage,
                             smem_u32(&bars[s % K]), pol, lane);
       }
     }
     for (int lc = 0; lc < nch; ++lc) {
-      const int c = warp + lc * kWarps;
+      const int c = warp + lc * NW;
       const int m = c * A + alpha;
       const bool valid = m < p.M;
       const size_t hrow = (static_cast<size_t>(f) * p.Mtot + p.m0 + m) * N;
@@ -177,7 +191,7 @@ __global__ void __launch_bounds__(kWThreads, 1) warp_kernel(const KParams p) {
         if (p.use_tma && step + K < gend) {
           const int ls = step + K - gstart;
           fence_proxy_async();
-          wissue<LOG2N, FC32>(p, f, warp + (ls / items) * kWarps,
+          wissue<LOG2N, FC32>(p, f, warp + (ls / items) * NW,
                               witem_symbol(p, pilot_here, d0, ls % items),
                               stage + slot * slot_bytes, lay.team_stage, smem_u32(&bars[slot]),
                               pol, lane);
@@ -208,23 +222,43 @@ __global__ void __launch_bounds__(kWThreads, 1) warp_kernel(const KParams p) {
         } else {
           // MRC numerator: conj(H) Y summed over the chunk's antennas
           const int dl = it - (pilot_here ? 1 : 0);
-#pragma unroll
-          for (int e = 0; e < 32; ++e) v[e] = cmulc(h[e], v[e]);
-          reduce_scatter<A, 16>(v, alpha);
           const uint32_t tp = tP + 2 * OWN * dl;
-          tmem_wait_st();
+          if constexpr (A == 1) {
+            // one antenna per step: fuse the product into the accumulation,
+            // P += conj(H) Y as four FMAs per subcarrier
+            tmem_wait_st();
 #pragma unroll
-          for (int q0 = 0; q0 < 2 * OWN; q0 += (2 * OWN < 32 ? 2 * OWN : 32)) {
-            constexpr int QC = 2 * OWN < 32 ? 2 * OWN : 32;
-            float acc[QC];
-            Tmem<QC>::ld(tp + q0, acc);
-            tmem_wait_ld();
+            for (int q0 = 0; q0 < 64; q0 += 32) {
+              float acc[32];
+              Tmem<32>::ld(tp + q0, acc);
+              tmem_wait_ld();
 #pragma unroll
-            for (int i = 0; i < QC / 2; ++i) {
-              acc[2 * i] += v[q0 / 2 + i].x;
-              acc[2 * i + 1] += v[q0 / 2 + i].y;
+              for (int i = 0; i < 16; ++i) {
+                const float2 hh = h[q0 / 2 + i], y = v[q0 / 2 + i];
+                acc[2 * i] = fmaf(hh.x, y.x, fmaf(hh.y, y.y, acc[2 * i]));
+                acc[2 * i + 1] = fmaf(hh.x, y.y, fmaf(-hh.y, y.x, acc[2 * i + 1]));
+              }
+              Tmem<32>::st(tp + q0, acc);
             }
-            Tmem<QC>::st(tp + q0, acc);
+          } else {
+            // several antennas per step: sum them with shuffles first
+#pragma unroll
+            for (int e = 0; e < 32; ++e) v[e] = cmulc(h[e], v[e]);
+            reduce_scatter<A, 16>(v, alpha);
+            tmem_wait_st();
+#pragma unroll
+            for (int q0 = 0; q0 < 2 * OWN; q0 += (2 * OWN < 16 ? 2 * OWN : 16)) {
+              constexpr int QC = 2 * OWN < 16 ? 2 * OWN : 16;
+              float acc[QC];
+              Tmem<QC>::ld(tp + q0, acc);
+              tmem_wait_ld();
+#pragma unroll
+              for (int i = 0; i < QC / 2; ++i) {
+                acc[2 * i] += v[q0 / 2 + i].x;
+                acc[2 * i + 1] += v[q0 / 2 + i].y;
+              }
+              Tmem<QC>::st(tp + q0, acc);
+            }
           }
         }
       }
@@ -234,17 +268,17 @@ __global__ void __launch_bounds__(kWThreads, 1) warp_kernel(const KParams p) {
     // has landed; the per-warp regions are free for the reduction
     __syncthreads();
     if (g == 0) {
-      float* RE = reinterpret_cast<float*>(smem + lay.warp_off);   // [kWarps][N]
+      float* RE = reinterpret_cast<float*>(smem + lay.warp_off);   // [NW][N]
       float e[OWN];
       TmE::ld(tE, e);
       tmem_wait_ld();
 #pragma unroll
       for (int cc = 0; cc < OWN; ++cc) RE[warp * N + bin_of<LOG2N>(jt, alpha * OWN + cc)] = e[cc];
       __syncthreads();
-      for (int k = tid; k < N; k += kWThreads) {
+      for (int k = tid; k < N; k += NT) {
         float E = 0.f;
 #pragma unroll
-        for (int w = 0; w < kWarps; ++w) E += RE[w * N + k];
+        for (int w = 0; w < NW; ++w) E += RE[w * N + k];
         if (p.mode == kModePartial) {
           p.E_out[static_cast<size_t>(f) * N + k] = E;
         } else {
@@ -256,7 +290,7 @@ __global__ void __launch_bounds__(kWThreads, 1) warp_kernel(const KParams p) {
       }
       __syncthreads();
     }
-    float2* RP = reinterpret_cast<float2*>(smem + lay.warp_off);   // [kWarps][dlc][N]
+    float2* RP = reinterpret_cast<float2*>(smem + lay.warp_off);   // [NW][dlc][N]
     const int dlc = min(nd, lay.warp_bytes / (N * 8));
     for (int dl0 = 0; dl0 < nd; dl0 += dlc) {
       const int n = min(dlc, nd - dl0);
@@ -270,12 +304,12 @@ __global__ void __launch_bounds__(kWThreads, 1) warp_kernel(const KParams p) {
           dst[bin_of<LOG2N>(jt, alpha * OWN + cc)] = make_float2(acc[2 * cc], acc[2 * cc + 1]);
       }
       __syncthreads();
-      for (int idx = tid; idx < n * N; idx += kWThreads) {
+      for (int idx = tid; idx < n * N; idx += NT) {
         const int j = idx >> LOG2N;
         const int k = idx & (N - 1);
         float2 s = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int w = 0; w < kWarps; ++w) s = cadd(s, RP[static_cast<size_t>(w * dlc + j) * N + k]);
+        for (int w = 0; w < NW; ++w) s = cadd(s, RP[static_cast<size_t>(w * dlc + j) * N + k]);
         const int dl = dl0 + j;
         if (p.mode == kModePartial) {
           p.P_out[(static_cast<size_t>(f) * p.D + d0 + dl) * N + k] =
@@ -295,7 +329,7 @@ __global__ void __launch_bounds__(kWThreads, 1) warp_kernel(const KParams p) {
       // pack: 8 consecutive subcarriers -> q bytes
       const int items8 = nd * (N / 8);
       const size_t frame_bytes = static_cast<size_t>(p.D) * N * p.q / 8;
-      for (int it = tid; it < items8; it += kWThreads) {
+      for (int it = tid; it < items8; it += NT) {
         const int dl = it / (N / 8);
         const int k0 = (it % (N / 8)) * 8;
         uint64_t acc = 0;

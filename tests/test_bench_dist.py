@@ -64,8 +64,6 @@ def _split_worker(rank, world, port, out):
     import oracle
     import synth
     from synth.frames import sweep_config
-    from paper_1901_07499_gb300.build import build
-    build()
     from paper_1901_07499_gb300.lsas import gather_partials
     dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}",
                             rank=rank, world_size=world)
@@ -90,6 +88,8 @@ def _split_worker(rank, world, port, out):
 
 
 def test_two_rank_antenna_split_gathers_in_rank_order():
+    from paper_1901_07499_gb300.build import build
+    build()   # once, before the ranks import the binding
     world = 2
     port = _free_port()
     with mp.Manager() as m:
