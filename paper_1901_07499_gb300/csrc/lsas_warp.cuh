@@ -111,14 +111,14 @@ __global__ void __launch_bounds__(32 * wgeo_warps(FC32 ? 8 : 4), 1) warp_kernel(
   // start the warps of the upper half a little later, so that the two warps
   // sharing a scheduler tend to be in different phases of their steps
   if (warp >= 4) __nanosleep(1400);
-  int step = 0;   // this warp's step counter over the whole frame
+  int step = 0;    // this warp's step counter over the whole frame
+  int slot = 0;    // ring slot of the next step to consume (step % K) ...
+  int phase = 0;   // ... and its mbarrier phase ((step / K) & 1)
   for (int g = 0; g < p.groups; ++g) {
     const int nd = min(p.dg, p.D - g * p.dg);
     const int d0 = g * p.dg;
     const bool pilot_here = fft_pilot(p) && g == 0;
     const int items = group_items(p, g);
-    const int gstart = step;
-    const int gend = step + nch * items;
     if (g == 0) {
 #pragma unroll
       for (int q0 = 0; q0 < OWN; q0 += ZC) Tmem<ZC>::st(tE + q0, zero);
@@ -127,16 +127,24 @@ __global__ void __launch_bounds__(32 * wgeo_warps(FC32 ? 8 : 4), 1) warp_kernel(
 #pragma unroll
       for (int q0 = 0; q0 < 2 * OWN; q0 += ZC) Tmem<ZC>::st(tP + 2 * OWN * dl + q0, zero);
     }
+    // issue cursor: local chunk and item of the next step to stage, and how
+    // many steps of this group are still to be staged
+    int ic = 0, iit = 0;
+    int to_issue = nch * items;
     if (p.use_tma) {
       // the ring held generic data (last group's reduction): order it before
       // the copies, then fill the first K slots of this group
       fence_proxy_async();
-      for (int s = step; s < step + K && s < gend; ++s) {
-        const int ls = s - gstart;
-        wissue<LOG2N, FC32>(p, f, warp + (ls / items) * NW,
-                            witem_symbol(p, pilot_here, d0, ls % items),
-                            stage + (s % K) * slot_bytes, lay.team_stage,
-                            smem_u32(&bars[s % K]), pol, lane);
+      int is = slot;
+      for (int s = 0; s < K && to_issue > 0; ++s, --to_issue) {
+        wissue<LOG2N, FC32>(p, f, warp + ic * NW, witem_symbol(p, pilot_here, d0, iit),
+                            stage + is * slot_bytes, lay.team_stage, smem_u32(&bars[is]), pol,
+                            lane);
+        is = (is + 1 == K) ? 0 : is + 1;
+        if (++iit == items) {
+          iit = 0;
+          ++ic;
+        }
       }
     }
     for (int lc = 0; lc < nch; ++lc) {
@@ -166,10 +174,9 @@ __global__ void __launch_bounds__(32 * wgeo_warps(FC32 ? 8 : 4), 1) warp_kernel(
         }
       }
       for (int it = 0; it < items; ++it, ++step) {
-        const int slot = step % K;
         float2 v[32];
         if (p.use_tma) {
-          wait_slot(smem_u32(&bars[slot]), (step / K) & 1, abort_flag, p.status);
+          wait_slot(smem_u32(&bars[slot]), phase, abort_flag, p.status);
           if (valid) {
             load_row<LOG2N, FC32>(v, stage + slot * slot_bytes + alpha * lay.team_stage, jt, false);
           } else {
@@ -188,13 +195,20 @@ __global__ void __launch_bounds__(32 * wgeo_warps(FC32 ? 8 : 4), 1) warp_kernel(
         // every lane is done with the slot (and with the exchange of the
         // previous step): refill the slot K steps ahead
         __syncwarp();
-        if (p.use_tma && step + K < gend) {
-          const int ls = step + K - gstart;
+        if (p.use_tma && to_issue > 0) {
           fence_proxy_async();
-          wissue<LOG2N, FC32>(p, f, warp + (ls / items) * NW,
-                              witem_symbol(p, pilot_here, d0, ls % items),
+          wissue<LOG2N, FC32>(p, f, warp + ic * NW, witem_symbol(p, pilot_here, d0, iit),
                               stage + slot * slot_bytes, lay.team_stage, smem_u32(&bars[slot]),
                               pol, lane);
+          --to_issue;
+          if (++iit == items) {
+            iit = 0;
+            ++ic;
+          }
+        }
+        if (++slot == K) {
+          slot = 0;
+          phase ^= 1;
         }
         dft<32>(v, p);
         final_exchange_write<LOG2N>(v, ex, jt);
