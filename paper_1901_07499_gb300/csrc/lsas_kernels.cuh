@@ -517,11 +517,11 @@ __device__ __forceinline__ int bin_of(int t, int e) {
 
 // One interleaved int16 IQ word -> {I, Q} as floats, exactly, without the
 // conversion unit: flipping the sign bits gives offset-binary u = v + 32768,
-// 0x4B000000 | u is the float 2^23 + u, and one packed subtraction of
-// 2^23 + 32768 leaves v.
+// a byte permute places each half under the exponent bytes of 2^23 (the
+// float 2^23 + u), and one packed subtraction of 2^23 + 32768 leaves v.
 __device__ __forceinline__ float2 sc16_to_float2(uint32_t w) {
   const uint32_t u = w ^ 0x80008000u;
-  const uint32_t lo = (u & 0xffffu) | 0x4b000000u;
+  const uint32_t lo = __byte_perm(u, 0x4b000000u, 0x7610);
   const uint32_t hi = __byte_perm(u, 0x4b000000u, 0x7632);
   return __fadd2_rn(make_float2(__uint_as_float(lo), __uint_as_float(hi)),
                     make_float2(-8421376.0f, -8421376.0f));
