@@ -184,6 +184,31 @@ lsas_status lsas_mrc_combine(lsas_plan plan, const float* d_P, const float* d_E,
                              float* d_eq, void* stream);
 
 /*
+ * Steps a1-a2 (CP removal + FFT, Sec. II-B/II-C) on the tensor cores: the
+ * N-point DFT as two batched DFT-factor GEMMs (N = 32 x N/32, a twiddle
+ * between them) on tcgen05 with fp16 operands and fp32 accumulation in
+ * tensor memory.  terms = 3 splits every operand into fp16 hi + lo parts and
+ * sums three products (relative error ~1e-6); terms = 1 uses plain fp16
+ * operands (~1e-3).  Output as lsas_fft: d_Y [F][M][S][N] complex, unitary.
+ * A precision form of the FFT, next to the FP32 path lsas_fft.
+ * Supported: N in {512, 1024, 2048} and sc16 input, else LSAS_ERR_UNSUPPORTED;
+ * terms other than 1 or 3 give LSAS_ERR_INVALID_ARG.  Asynchronous.
+ */
+lsas_status lsas_fft_tc(lsas_plan plan, const void* d_in, int n_frames, int terms,
+                        float* d_Y, void* stream);
+
+/*
+ * Steps a3-a5 from transformed symbols (the staged form of the receiver):
+ * d_Y [F][M][S][N] complex (unitary FFT outputs, as lsas_fft or lsas_fft_tc
+ * write them) -> LS estimate d_H [F][M][N] (Sec. II-C), MRC over the
+ * antennas in antenna order and the Gray slicer, exactly the outputs of
+ * lsas_run_frame (d_bits, optional d_eq).  Zero channel energy latches
+ * LSAS_ERR_DEVICE.  Asynchronous.
+ */
+lsas_status lsas_receive_y(lsas_plan plan, const float* d_Y, int n_frames, float* d_H,
+                           uint8_t* d_bits, float* d_eq, void* stream);
+
+/*
  * Size of the library's fixed device scratch used by
  * lsas_run_frame_split_static (16 MiB per device).
  */

@@ -60,7 +60,11 @@ struct KParams {
   int M;                 // antennas this call processes
   int m0, Mtot;          // first of them, antennas per frame in the arrays
   int N, S, cp, pilot_idx, D;
-  int shards, nframes;   // combine: partials per frame, frames
+  int shards, nframes;   // combine: partials per frame, frames; tensor-core FFT: rows
+  const void* tc_w1;     // tensor-core FFT: 32-point DFT operand images (hi, lo)
+  const void* tc_w2;     //   N/32-point DFT operand images (hi, lo)
+  const float2* tc_tw;   //   inter-stage twiddles W_N^(n2 k1), [n2][k1]
+  int terms;             //   1: fp16 operands; 3: hi+lo split operands
   int chunks;            // ceil(M / A)
   int groups, dg;        // data-symbol groups per frame, data symbols per group
   int mode;              // kModeDemod, kModeRun or kModePartial (frame_kernel)

@@ -27,6 +27,11 @@ cudaError_t launch_n512(int, bool, const KParams&, int, int, cudaStream_t);
 cudaError_t launch_n1024(int, bool, const KParams&, int, int, cudaStream_t);
 cudaError_t launch_n2048(int, bool, const KParams&, int, int, cudaStream_t);
 cudaError_t launch_combine(const KParams&, cudaStream_t);
+cudaError_t launch_tcfft(const KParams&, int N, int grid, cudaStream_t);
+cudaError_t launch_yrx(const KParams&, int n_frames, cudaStream_t);
+int tc_smem_bytes(int N);
+bool tc_tables(int N, std::vector<uint16_t>& w1, std::vector<uint16_t>& w2,
+               std::vector<float2>& tw);
 }  // namespace lsas
 
 using namespace lsas;
@@ -57,6 +62,11 @@ struct lsas_plan_s {
   float2* d_xinv = nullptr;
   int* d_status = nullptr;
   float2 w32[16], w32n[16];
+  // tensor-core FFT tables (N = 512 .. 2048)
+  void* d_tc_w1 = nullptr;
+  void* d_tc_w2 = nullptr;
+  float2* d_tc_tw = nullptr;
+  int sms = 0;
   Geometry geo;
   LaunchFn launch = nullptr;
   // host-transfer staging (lsas_run_frame_host), allocated on first use
@@ -408,6 +418,28 @@ lsas_status lsas_plan_create(int M, int N, int cp_len, int n_sym, int pilot_idx,
     lsas_plan_destroy(p);
     return LSAS_ERR_OOM;
   }
+  std::vector<uint16_t> tcw1, tcw2;
+  std::vector<float2> tctw;
+  if (tc_tables(N, tcw1, tcw2, tctw)) {
+    if (cudaMalloc(&p->d_tc_w1, tcw1.size() * 2) != cudaSuccess ||
+        cudaMalloc(&p->d_tc_w2, tcw2.size() * 2) != cudaSuccess ||
+        cudaMalloc(&p->d_tc_tw, tctw.size() * sizeof(float2)) != cudaSuccess) {
+      cudaGetLastError();
+      lsas_plan_destroy(p);
+      return LSAS_ERR_OOM;
+    }
+    if (cudaMemcpy(p->d_tc_w1, tcw1.data(), tcw1.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p->d_tc_w2, tcw2.data(), tcw2.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p->d_tc_tw, tctw.data(), tctw.size() * sizeof(float2), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+      lsas_plan_destroy(p);
+      return LSAS_ERR_CUDA;
+    }
+  }
+  if (cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
+    lsas_plan_destroy(p);
+    return LSAS_ERR_CUDA;
+  }
   std::vector<double> one(N, 1.0), zero(N, 0.0);
   if (cudaMemcpy(p->d_twP, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice) !=
           cudaSuccess ||
@@ -576,6 +608,56 @@ lsas_status lsas_mrc_combine(lsas_plan p, const float* d_P, const float* d_E, in
   return LSAS_OK;
 }
 
+lsas_status lsas_fft_tc(lsas_plan p, const void* d_in, int n_frames, int terms, float* d_Y,
+                        void* stream) {
+  if (!p) return LSAS_ERR_INVALID_ARG;
+  if (terms != 1 && terms != 3) return LSAS_ERR_INVALID_ARG;
+  if (!p->d_tc_w1 || p->fmt != LSAS_IN_SC16) return LSAS_ERR_UNSUPPORTED;
+  lsas_status s = check_frames(p, n_frames);
+  if (s != LSAS_OK) return s;
+  if (n_frames == 0) return LSAS_OK;
+  if (!d_in || !d_Y) return LSAS_ERR_INVALID_ARG;
+  if (set_device(p) != LSAS_OK) return LSAS_ERR_CUDA;
+  KParams k;
+  base_params(p, &k);
+  k.in = d_in;
+  k.Y_out = reinterpret_cast<float2*>(d_Y);
+  k.nframes = n_frames;
+  k.terms = terms;
+  k.tc_w1 = p->d_tc_w1;
+  k.tc_w2 = p->d_tc_w2;
+  k.tc_tw = p->d_tc_tw;
+  // one persistent block per SM (two when the shared memory allows)
+  const size_t rows = static_cast<size_t>(n_frames) * p->M * p->S;
+  const int per_batch = (128 / (p->N / 32) > 4) ? 128 / (p->N / 32) : 4;
+  const size_t batches = (rows + per_batch - 1) / per_batch;
+  const int per_sm = tc_smem_bytes(p->N) * 2 <= kSmemLimit ? 2 : 1;
+  const size_t cap = static_cast<size_t>(p->sms) * per_sm;
+  const int grid = static_cast<int>(batches < cap ? batches : cap);
+  if (launch_tcfft(k, p->N, grid, static_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return LSAS_ERR_CUDA;
+  return LSAS_OK;
+}
+
+lsas_status lsas_receive_y(lsas_plan p, const float* d_Y, int n_frames, float* d_H,
+                           uint8_t* d_bits, float* d_eq, void* stream) {
+  if (!p) return LSAS_ERR_INVALID_ARG;
+  lsas_status s = check_frames(p, n_frames);
+  if (s != LSAS_OK) return s;
+  if (n_frames == 0) return LSAS_OK;
+  if (!d_Y || !d_H || !d_bits) return LSAS_ERR_INVALID_ARG;
+  if (set_device(p) != LSAS_OK) return LSAS_ERR_CUDA;
+  KParams k;
+  base_params(p, &k);
+  k.Y_out = reinterpret_cast<float2*>(const_cast<float*>(d_Y));
+  k.H_out = reinterpret_cast<float2*>(d_H);
+  k.bits = d_bits;
+  k.eq = reinterpret_cast<float2*>(d_eq);
+  if (launch_yrx(k, n_frames, static_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return LSAS_ERR_CUDA;
+  return LSAS_OK;
+}
+
 lsas_status lsas_run_frame_host(lsas_plan p, const void* h_in, int n_frames, float* h_H,
                                 uint8_t* h_bits, float* h_eq, void* stream) {
   if (!p) return LSAS_ERR_INVALID_ARG;
@@ -682,6 +764,9 @@ lsas_status lsas_plan_destroy(lsas_plan p) {
   cudaFree(p->d_twP);
   cudaFree(p->d_xinv);
   cudaFree(p->d_status);
+  cudaFree(p->d_tc_w1);
+  cudaFree(p->d_tc_w2);
+  cudaFree(p->d_tc_tw);
   for (int i = 0; i < 2; ++i) {
     cudaFree(p->d_in_stage[i]);
     cudaFree(p->d_H_stage[i]);

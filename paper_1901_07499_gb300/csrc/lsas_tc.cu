@@ -1,0 +1,413 @@
+// lsas_tc.cu -- the FFT of Sec. II-C as tensor-core DFT-factor GEMMs, and a
+// staged LS / MRC / demap pass that reads the transformed symbols from memory.
+//
+// Tensor-core FFT (N = 32 N2, N2 = N/32 in {16, 32, 64}).  With n = N2 n1 + n2
+// and k = k1 + 32 k2,
+//   stage 1   A1[n2][k1] = sum_n1 x[N2 n1 + n2] W_32^(n1 k1)        (GEMM, K = 32)
+//   twiddle   B1[n2][k1] = A1[n2][k1] W_N^(n2 k1)
+//   stage 2   X[k1 + 32 k2] = sum_n2 B1[n2][k1] W_N2^(n2 k2)       (GEMM, K = N2)
+// Each complex GEMM is a real one over [re | im] halves: a data row is
+// [x_re(0..K-1) | x_im(0..K-1)] and the DFT operand row of output (re, k) is
+// [cos | sin], of (im, k) [-sin | cos] (angle 2 pi n k / K).  Operands are
+// fp16, accumulators fp32 in tensor memory (tcgen05.mma kind::f16, M = 128).
+// With terms = 3 every operand is split into hi = fp16(v) and
+// lo = fp16(v - hi), and a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi (the lo*lo
+// term, ~2^-22 relative, is dropped); terms = 1 uses a_hi b_hi alone
+// (~2^-11 relative).  Stage-2 inputs are scaled by 2^-6 (exact) to stay in
+// fp16 range; the output is scaled back with the unitary 1/sqrt(N).
+//
+// Operand tiles use the canonical no-swizzle K-major layout: 8-row x 16-byte
+// core matrices, adjacent along K at 128 B, row groups at 128 * K / 8 B.
+#include <cfloat>
+#include <cmath>
+#include <vector>
+
+#include <cuda_fp16.h>
+
+#include "lsas_kernels.cuh"
+
+namespace lsas {
+
+constexpr int kTcThreads = 128;
+
+// byte offset of element (row, k) of a rows x K fp16 operand tile
+__host__ __device__ inline int tc_off(int row, int k, int K) {
+  return (row >> 3) * (16 * K) + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
+
+// Host: operand image (hi, lo) of the K-point DFT, 2K rows x 2K columns.
+static void dft_image(int K, std::vector<uint16_t>& img) {
+  const int R = 2 * K, C = 2 * K;
+  img.assign(2 * R * C, 0);
+  for (int r = 0; r < R; ++r) {
+    const int k = r % K;
+    for (int c = 0; c < C; ++c) {
+      const int n = c % K;
+      const double a = 2.0 * M_PI * static_cast<double>((static_cast<long>(n) * k) % K) / K;
+      // out re: x_re cos + x_im sin; out im: -x_re sin + x_im cos
+      const double w = (r < K) ? (c < K ? std::cos(a) : std::sin(a))
+                               : (c < K ? -std::sin(a) : std::cos(a));
+      const __half hi = __double2half(w);
+      const __half lo = __double2half(w - static_cast<double>(__half2float(hi)));
+      const int o = tc_off(r, c, C) / 2;
+      img[o] = __half_as_ushort(hi);
+      img[R * C + o] = __half_as_ushort(lo);
+    }
+  }
+}
+
+// Tables of the tensor-core FFT for one N (host side; the plan uploads them).
+bool tc_tables(int N, std::vector<uint16_t>& w1, std::vector<uint16_t>& w2,
+               std::vector<float2>& tw) {
+  const int N2 = N / 32;
+  if (N2 < 16 || N2 > 64) return false;
+  dft_image(32, w1);
+  dft_image(N2, w2);
+  tw.resize(static_cast<size_t>(N2) * 32);
+  for (int n2 = 0; n2 < N2; ++n2)
+    for (int k1 = 0; k1 < 32; ++k1) {
+      const double a = -2.0 * M_PI * static_cast<double>((n2 * k1) % N) / N;
+      tw[n2 * 32 + k1] = make_float2(static_cast<float>(std::cos(a)), static_cast<float>(std::sin(a)));
+    }
+  return true;
+}
+
+// ---------------------------------------------------------------- device
+
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, int K) {
+  uint64_t d = static_cast<uint64_t>((addr & 0x3FFFF) >> 4);
+  d |= static_cast<uint64_t>(128 >> 4) << 16;              // K-adjacent core matrices
+  d |= static_cast<uint64_t>((16 * K) >> 4) << 32;         // 8-row groups
+  d |= static_cast<uint64_t>(1) << 46;                     // descriptor version
+  return d;
+}
+// kind::f16 instruction descriptor: fp32 accumulator, fp16 A and B, both
+// K-major, M = 128, N columns
+__device__ __forceinline__ uint32_t tc_idesc(int n) {
+  return (1u << 4) | (static_cast<uint32_t>(n >> 3) << 17) | (static_cast<uint32_t>(128 >> 4) << 24);
+}
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                       uint32_t acc) {
+  asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+               "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+               :: "r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+               :: "r"(bar) : "memory");
+}
+
+// (a, b) -> packed fp16 hi = fp16(v) and lo = fp16(v - hi), as 32-bit words
+__device__ __forceinline__ void split16x2(float a, float b, uint32_t& hi, uint32_t& lo) {
+  const __half2 h = __floats2half2_rn(a, b);
+  const float2 hf = __half22float2(h);
+  const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+// Store one operand row of 2K values (re[0..K) then im[0..K)), hi and lo images.
+template <int K>
+__device__ __forceinline__ void store_row(unsigned char* hi_img, unsigned char* lo_img, int row,
+                                          const float* re, const float* im, bool want_lo) {
+#pragma unroll
+  for (int c = 0; c < 2 * K; c += 8) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int j = 0; j < 8; j += 2) {
+      const float a = c + j < K ? re[c + j] : im[c + j - K];
+      const float b = c + j + 1 < K ? re[c + j + 1] : im[c + j + 1 - K];
+      split16x2(a, b, h[j / 2], l[j / 2]);
+    }
+    const int o = tc_off(row, c, 2 * K);
+    *reinterpret_cast<uint4*>(hi_img + o) = make_uint4(h[0], h[1], h[2], h[3]);
+    if (want_lo) *reinterpret_cast<uint4*>(lo_img + o) = make_uint4(l[0], l[1], l[2], l[3]);
+  }
+}
+
+template <int LOG2N>
+struct TcGeo {
+  static constexpr int N = 1 << LOG2N;
+  static constexpr int N2 = N / 32;
+  static constexpr int R = (128 / N2 > 4) ? 128 / N2 : 4;   // antenna-symbols per batch
+  static constexpr int T1 = R * N2 / 128;                   // stage-1 tiles of 128 rows
+  static constexpr int T2 = R * 32 / 128;                   // stage-2 tiles
+  static constexpr int W1_BYTES = 64 * 64 * 2;              // one image
+  static constexpr int W2_BYTES = (2 * N2) * (2 * N2) * 2;
+  static constexpr int A1_BYTES = 128 * 64 * 2;             // one tile, one image
+  static constexpr int A2_BYTES = 128 * (2 * N2) * 2;
+  static constexpr int TS = N2 + 1;                         // transpose row stride (float2)
+  static constexpr int T_BYTES = R * 32 * TS * 8;
+  static constexpr int OFF_W1 = 0;
+  static constexpr int OFF_W2 = OFF_W1 + 2 * W1_BYTES;
+  static constexpr int OFF_A1 = OFF_W2 + 2 * W2_BYTES;      // A1 tiles, then (aliased) T
+  static constexpr int A1_REGION = (2 * T1 * A1_BYTES > T_BYTES) ? 2 * T1 * A1_BYTES : T_BYTES;
+  static constexpr int OFF_A2 = OFF_A1 + A1_REGION;
+  static constexpr int OFF_BAR = OFF_A2 + 2 * T2 * A2_BYTES;
+  static constexpr int SMEM = OFF_BAR + 64;
+};
+
+// Tensor-core FFT: p.nframes rows of N samples (antenna-symbols, CP dropped)
+// -> Y rows (unitary).  Persistent: block b takes batches b, b + grid, ...
+template <int LOG2N, bool FC32>
+__global__ void __launch_bounds__(kTcThreads, 1) tcfft_kernel(const KParams p) {
+  using G = TcGeo<LOG2N>;
+  constexpr int N = G::N, N2 = G::N2, R = G::R;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const bool split = p.terms == 3;
+  unsigned char* w1 = smem + G::OFF_W1;
+  unsigned char* w2 = smem + G::OFF_W2;
+  unsigned char* a1 = smem + G::OFF_A1;
+  float2* tbuf = reinterpret_cast<float2*>(smem + G::OFF_A1);
+  unsigned char* a2 = smem + G::OFF_A2;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + G::OFF_BAR);
+  uint32_t* tmem_base = reinterpret_cast<uint32_t*>(smem + G::OFF_BAR + 16);
+  // constant DFT operands into shared memory
+  {
+    const uint4* s1 = static_cast<const uint4*>(p.tc_w1);
+    const uint4* s2 = static_cast<const uint4*>(p.tc_w2);
+    for (int i = tid; i < 2 * G::W1_BYTES / 16; i += kTcThreads) reinterpret_cast<uint4*>(w1)[i] = s1[i];
+    for (int i = tid; i < 2 * G::W2_BYTES / 16; i += kTcThreads) reinterpret_cast<uint4*>(w2)[i] = s2[i];
+  }
+  if (tid == 0) {
+    mbar_init(smem_u32(bar), 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) tmem_alloc(smem_u32(tmem_base), 256);
+  fence_proxy_async();
+  tmem_fence_before();
+  __syncthreads();
+  tmem_fence_after();
+  const uint32_t tmem = *tmem_base;
+  const uint32_t lane_off = static_cast<uint32_t>(32 * warp) << 16;
+  const size_t total = static_cast<size_t>(p.nframes) * p.M * p.S;
+  const size_t nbatch = (total + R - 1) / R;
+  constexpr int bps = FC32 ? 8 : 4;
+  uint32_t phase = 0;
+  bool timed_out = false;
+  for (size_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
+    const size_t row0 = batch * R;
+    // ---- stage-1 operands: row (b, n2) = x[N2 n1 + n2], n1 < 32
+#pragma unroll
+    for (int t = 0; t < G::T1; ++t) {
+      const int lr = t * 128 + tid;
+      const int b = lr / N2, n2 = lr % N2;
+      float re[32], im[32];
+      if (row0 + b < total) {
+        const unsigned char* src = static_cast<const unsigned char*>(p.in) +
+                                   ((row0 + b) * (N + p.cp) + p.cp) * bps;
+#pragma unroll
+        for (int n1 = 0; n1 < 32; ++n1) {
+          float2 x;
+          if constexpr (FC32) x = __ldg(reinterpret_cast<const float2*>(src) + N2 * n1 + n2);
+          else x = sc16_to_float2(__ldg(reinterpret_cast<const uint32_t*>(src) + N2 * n1 + n2));
+          re[n1] = x.x;
+          im[n1] = x.y;
+        }
+      } else {
+#pragma unroll
+        for (int n1 = 0; n1 < 32; ++n1) re[n1] = im[n1] = 0.f;
+      }
+      store_row<32>(a1 + (2 * t) * G::A1_BYTES, a1 + (2 * t + 1) * G::A1_BYTES, tid, re, im, split);
+    }
+    fence_proxy_async();
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    if (tid == 0) {
+      for (int t = 0; t < G::T1; ++t)
+        for (int term = 0; term < p.terms; ++term) {
+          const uint32_t abase = smem_u32(a1 + (2 * t + (term == 2 ? 1 : 0)) * G::A1_BYTES);
+          const uint32_t bbase = smem_u32(w1 + (term == 1 ? 1 : 0) * G::W1_BYTES);
+          for (int kc = 0; kc < 4; ++kc)
+            tc_mma(tmem + t * 64, tc_desc(abase + kc * 256, 64), tc_desc(bbase + kc * 256, 64),
+                   tc_idesc(64), (term > 0 || kc > 0) ? 1u : 0u);
+        }
+      tc_commit(smem_u32(bar));
+    }
+    if (!timed_out && !mbar_wait_bounded(smem_u32(bar), phase)) {
+      timed_out = true;
+      latch(p.status, kStTimeout);
+    }
+    phase ^= 1;
+    tmem_fence_after();
+    // ---- twiddle, scale by 2^-6, transpose to T[b][k1][n2]
+#pragma unroll
+    for (int t = 0; t < G::T1; ++t) {
+      float d[64];
+      Tmem<64>::ld(tmem + lane_off + t * 64, d);
+      tmem_wait_ld();
+      const int lr = t * 128 + tid;
+      const int b = lr / N2, n2 = lr % N2;
+#pragma unroll
+      for (int k1 = 0; k1 < 32; ++k1) {
+        const float2 w = __ldg(p.tc_tw + n2 * 32 + k1);
+        const float2 c = cmul(make_float2(d[k1], d[32 + k1]), w);
+        tbuf[(b * 32 + k1) * G::TS + n2] = make_float2(c.x * 0.015625f, c.y * 0.015625f);
+      }
+    }
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    // ---- stage-2 operands: row (b, k1) = B1[n2][k1], n2 < N2
+#pragma unroll
+    for (int t = 0; t < G::T2; ++t) {
+      const int lr = t * 128 + tid;
+      const int b = lr / 32, k1 = lr % 32;
+      float re[N2], im[N2];
+#pragma unroll
+      for (int n2 = 0; n2 < N2; ++n2) {
+        const float2 c = tbuf[(b * 32 + k1) * G::TS + n2];
+        re[n2] = c.x;
+        im[n2] = c.y;
+      }
+      store_row<N2>(a2 + (2 * t) * G::A2_BYTES, a2 + (2 * t + 1) * G::A2_BYTES, tid, re, im, split);
+    }
+    fence_proxy_async();
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    if (tid == 0) {
+      for (int t = 0; t < G::T2; ++t)
+        for (int term = 0; term < p.terms; ++term) {
+          const uint32_t abase = smem_u32(a2 + (2 * t + (term == 2 ? 1 : 0)) * G::A2_BYTES);
+          const uint32_t bbase = smem_u32(w2 + (term == 1 ? 1 : 0) * G::W2_BYTES);
+          for (int kc = 0; kc < (2 * N2) / 16; ++kc)
+            tc_mma(tmem + 128 + t * (2 * N2), tc_desc(abase + kc * 256, 2 * N2),
+                   tc_desc(bbase + kc * 256, 2 * N2), tc_idesc(2 * N2), (term > 0 || kc > 0) ? 1u : 0u);
+        }
+      tc_commit(smem_u32(bar));
+    }
+    if (!timed_out && !mbar_wait_bounded(smem_u32(bar), phase)) {
+      timed_out = true;
+      latch(p.status, kStTimeout);
+    }
+    phase ^= 1;
+    tmem_fence_after();
+    // ---- output: row (b, k1) holds X[k1 + 32 k2], re at column k2, im at N2 + k2
+    const float so = p.inv_sqrtN * 64.f;
+#pragma unroll
+    for (int t = 0; t < G::T2; ++t) {
+      const int lr = t * 128 + tid;
+      const int b = lr / 32, k1 = lr % 32;
+      const bool ok = row0 + b < total;
+      float2* dst = p.Y_out + (row0 + b) * N + k1;
+#pragma unroll
+      for (int c0 = 0; c0 < N2; c0 += 16) {
+        float dr[16], di[16];
+        Tmem<16>::ld(tmem + lane_off + 128 + t * (2 * N2) + c0, dr);
+        Tmem<16>::ld(tmem + lane_off + 128 + t * (2 * N2) + N2 + c0, di);
+        tmem_wait_ld();
+        if (ok) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) dst[32 * (c0 + j)] = make_float2(dr[j] * so, di[j] * so);
+        }
+      }
+    }
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+  }
+  if (warp == 0) tmem_dealloc(tmem, 256);
+}
+
+template <int LOG2N, bool FC32>
+static cudaError_t launch_tc_t(const KParams& p, int grid, cudaStream_t st) {
+  using G = TcGeo<LOG2N>;
+  static int limit[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64 || limit[dev] < G::SMEM) {
+    e = cudaFuncSetAttribute(tcfft_kernel<LOG2N, FC32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             G::SMEM);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) limit[dev] = G::SMEM;
+  }
+  tcfft_kernel<LOG2N, FC32><<<grid, kTcThreads, G::SMEM, st>>>(p);
+  return cudaGetLastError();
+}
+
+int tc_smem_bytes(int N) {
+  switch (N) {
+    case 512: return TcGeo<9>::SMEM;
+    case 1024: return TcGeo<10>::SMEM;
+    case 2048: return TcGeo<11>::SMEM;
+  }
+  return 0;
+}
+
+cudaError_t launch_tcfft(const KParams& p, int N, int grid, cudaStream_t st) {
+  switch (N) {
+    case 512: return launch_tc_t<9, false>(p, grid, st);
+    case 1024: return launch_tc_t<10, false>(p, grid, st);
+    case 2048: return launch_tc_t<11, false>(p, grid, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------- staged receiver
+
+constexpr int kYrxMaxThreads = 128;
+constexpr int kYrxMaxD = 63;
+
+// LS, MRC and demap from transformed symbols Y [F][M][S][N] (unitary): one
+// thread per subcarrier k of one frame, the antenna loop in the thread (the
+// MRC sum over antennas in a fixed order), packed bits through shared memory.
+__global__ void __launch_bounds__(kYrxMaxThreads) yrx_kernel(const KParams p) {
+  __shared__ uint8_t codes[kYrxMaxD * kYrxMaxThreads];
+  const int N = p.N;
+  const int T = blockDim.x;   // min(N, 128) subcarriers per block
+  const int per = N / T;
+  const int f = blockIdx.x / per;
+  const int k0 = (blockIdx.x % per) * T;
+  const int k = k0 + threadIdx.x;
+  const float2 xs = p.xinv[k];                       // conj(X)/|X|^2/sqrt(N)
+  const float sq = 1.0f / p.inv_sqrtN;
+  const float2 xi = make_float2(xs.x * sq, xs.y * sq);   // conj(X)/|X|^2
+  float2 P[kYrxMaxD];
+  for (int d = 0; d < p.D; ++d) P[d] = make_float2(0.f, 0.f);
+  float E = 0.f;
+  for (int m = 0; m < p.M; ++m) {
+    const float2* Ym = p.Y_out + (static_cast<size_t>(f) * p.M + m) * p.S * N;
+    const float2 h = cmul(Ym[static_cast<size_t>(p.pilot_idx) * N + k], xi);
+    p.H_out[(static_cast<size_t>(f) * p.M + m) * N + k] = h;
+    E = fmaf(h.x, h.x, fmaf(h.y, h.y, E));
+    for (int d = 0; d < p.D; ++d) {
+      const int s = d < p.pilot_idx ? d : d + 1;
+      const float2 y = Ym[static_cast<size_t>(s) * N + k];
+      P[d].x = fmaf(h.x, y.x, fmaf(h.y, y.y, P[d].x));
+      P[d].y = fmaf(h.x, y.y, fmaf(-h.y, y.x, P[d].y));
+    }
+  }
+  const bool ok = (E > 0.f) && (E <= FLT_MAX);
+  if (!ok) latch(p.status, kStDevice);
+  const float ie = ok ? 1.0f / E : 0.f;
+  for (int d = 0; d < p.D; ++d) {
+    const float2 z = ok ? make_float2(P[d].x * ie, P[d].y * ie) : make_float2(0.f, 0.f);
+    if (p.eq) p.eq[(static_cast<size_t>(f) * p.D + d) * N + k] = z;
+    uint32_t code = gray(axis_level(z.x, p));
+    if (p.axes == 2) code = (code << p.wbits) | gray(axis_level(z.y, p));
+    codes[d * T + threadIdx.x] = static_cast<uint8_t>(code);
+  }
+  __syncthreads();
+  const size_t frame_bytes = static_cast<size_t>(p.D) * N * p.q / 8;
+  for (int it = threadIdx.x; it < p.D * (T / 8); it += T) {
+    const int d = it / (T / 8);
+    const int c8 = (it % (T / 8)) * 8;
+    uint64_t acc = 0;
+    for (int j = 0; j < 8; ++j) acc = (acc << p.q) | codes[d * T + c8 + j];
+    uint8_t* dst = p.bits + f * frame_bytes + (static_cast<size_t>(d) * N + k0 + c8) * p.q / 8;
+    for (int j = 0; j < p.q; ++j) dst[j] = static_cast<uint8_t>(acc >> (8 * (p.q - 1 - j)));
+  }
+}
+
+cudaError_t launch_yrx(const KParams& p, int n_frames, cudaStream_t st) {
+  const int T = p.N < kYrxMaxThreads ? p.N : kYrxMaxThreads;
+  yrx_kernel<<<n_frames * (p.N / T), T, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace lsas

@@ -62,6 +62,8 @@ lsas_mrc_partial = _proto("lsas_mrc_partial", [_vp, _vp, _i, _i, _i, _vp, _vp, _
 lsas_mrc_combine = _proto("lsas_mrc_combine", [_vp, _vp, _vp, _i, _i, _vp, _vp, _vp])
 lsas_run_frame_split_static = _proto("lsas_run_frame_split_static",
                                      [_vp, _vp, _i, _i, _vp, _vp, _vp, _vp])
+lsas_fft_tc = _proto("lsas_fft_tc", [_vp, _vp, _i, _i, _vp, _vp])
+lsas_receive_y = _proto("lsas_receive_y", [_vp, _vp, _i, _vp, _vp, _vp, _vp])
 lsas_plan_sync = _proto("lsas_plan_sync", [_vp, _vp])
 lsas_plan_info = _proto("lsas_plan_info", [_vp, C.POINTER(_i)])
 lsas_plan_destroy = _proto("lsas_plan_destroy", [_vp])
@@ -70,7 +72,7 @@ EXPORTED = ["lsas_status_str", "lsas_check_config", "lsas_frame_bytes",
             "lsas_plan_create", "lsas_plan_set", "lsas_plan_set_pilot",
             "lsas_fft", "lsas_estimate", "lsas_demodulate", "lsas_run_frame",
             "lsas_run_frame_host", "lsas_mrc_partial", "lsas_mrc_combine",
-            "lsas_run_frame_split_static",
+            "lsas_run_frame_split_static", "lsas_fft_tc", "lsas_receive_y",
             "lsas_plan_sync", "lsas_plan_info",
             "lsas_plan_destroy"]
 
@@ -204,6 +206,29 @@ class Plan:
             Y = torch.empty((F, self.M, self.S, self.N), dtype=torch.complex64, device=x.device)
         check(lsas_fft(self._h, _ptr(x), F, _ptr(Y), _stream(stream)), "lsas_fft")
         return Y
+
+    def fft_tc(self, x, terms=3, Y=None, stream=None):
+        """The FFT on the tensor cores (fp16 operands; terms=3 splits them
+        into hi + lo parts), Y [F][M][S][N] complex64."""
+        import torch
+        F = self._frames(x)
+        if Y is None:
+            Y = torch.empty((F, self.M, self.S, self.N), dtype=torch.complex64, device=x.device)
+        check(lsas_fft_tc(self._h, _ptr(x), F, terms, _ptr(Y), _stream(stream)), "lsas_fft_tc")
+        return Y
+
+    def receive_y(self, Y, H=None, bits=None, eq=None, want_eq=False, stream=None):
+        """LS, MRC and demap from transformed symbols Y [F][M][S][N]."""
+        F = int(Y.shape[0])
+        if not Y.is_contiguous() or tuple(Y.shape[1:]) != (self.M, self.S, self.N):
+            raise ValueError("Y must be a contiguous [F][M][S][N] complex64 tensor")
+        H = self.empty_H(F, Y.device) if H is None else H
+        bits = self.empty_bits(F, Y.device) if bits is None else bits
+        if eq is None and want_eq:
+            eq = self.empty_eq(F, Y.device)
+        check(lsas_receive_y(self._h, _ptr(Y), F, _ptr(H), _ptr(bits), _ptr(eq), _stream(stream)),
+              "lsas_receive_y")
+        return H, bits, eq
 
     def estimate(self, x, H=None, stream=None):
         F = self._frames(x)
