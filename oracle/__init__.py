@@ -9,8 +9,10 @@ from .lsas_oracle import (Result, receive, strip_cp, dft, dft_matrix,
                           ls_estimate, channel_energy, mrc, mrc_partial,
                           mrc_combine, demap, slice_axis,
                           thresholds, qam_axis, gray_bits, pack_bits,
-                          to_complex, data_symbols)
+                          to_complex, data_symbols, pn_metric, pn_sync,
+                          extract_frame, fftshift_rows)
 
 __all__ = ["Result", "receive", "strip_cp", "dft", "dft_matrix", "ls_estimate",
            "channel_energy", "mrc", "mrc_partial", "mrc_combine", "demap", "slice_axis", "thresholds",
-           "qam_axis", "gray_bits", "pack_bits", "to_complex", "data_symbols"]
+           "qam_axis", "gray_bits", "pack_bits", "to_complex", "data_symbols",
+           "pn_metric", "pn_sync", "extract_frame", "fftshift_rows"]

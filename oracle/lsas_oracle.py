@@ -25,9 +25,17 @@ The antenna split of step 4 (the distributed receiver Sec. IV proposes):
 each shard of antennas forms the two sums of step 4 over its own antennas;
 the shards' partial sums are added and divided afterwards.
 
+Upstream of step 1, packet detection (Sec. II-B): the received samples are
+correlated with the known PN sequence; the power of the correlation, summed
+over antennas, peaks where the preamble begins, and the frame follows it.
+Downstream, the paper's fftshift (Sec. II-C) reorders subcarriers so that the
+zero-frequency bin is in the middle.
+
 Readings taken where the paper is silent: unitary FFT scaling, natural
-subcarrier order (no fftshift), normalised MRC, the Gray labelling of the
-transmitter in ``synth`` and ties sent to the upper level.
+subcarrier order unless fftshift is asked for, normalised MRC, the Gray
+labelling of the transmitter in ``synth``, ties sent to the upper level, and
+the PN correlation combined over antennas by power with the earliest lag
+winning a tie.
 
 Pins: every function here is checked in ``tests/test_oracle_pins.py`` against
 closed forms, a library routine or brute force (see that file's docstring).
@@ -210,6 +218,43 @@ def pack_bits(bits: np.ndarray) -> np.ndarray:
     F = bits.shape[0]
     flat = bits.reshape(F, -1)
     return np.packbits(flat, axis=-1, bitorder="big")
+
+
+# --------------------------------------------------------------------------
+# 0. Packet detection and output order (Sec. II-B, Sec. II-C)
+# --------------------------------------------------------------------------
+
+
+def pn_metric(capture: np.ndarray, pn: np.ndarray, window: int) -> np.ndarray:
+    """Correlation of every antenna's samples with the known PN sequence,
+    combined over antennas by power (Sec. II-B: the received signal is
+    correlated with the PN sequence to find the start of the packet):
+    metric[tau] = sum_m |sum_n conj(pn[n]) y[m, tau + n]|^2, tau < window."""
+    y = np.asarray(capture, np.complex128)
+    p = np.conj(np.asarray(pn, np.complex128))
+    L = p.shape[0]
+    metric = np.zeros(window)
+    for tau in range(window):
+        c = y[:, tau:tau + L] @ p
+        metric[tau] = np.sum(np.abs(c) ** 2)
+    return metric
+
+
+def pn_sync(capture: np.ndarray, pn: np.ndarray, window: int):
+    """(offset of the preamble = first tau of the largest metric, metric)."""
+    metric = pn_metric(capture, pn, window)
+    return int(np.argmax(metric)), metric
+
+
+def extract_frame(capture: np.ndarray, start: int, T: int) -> np.ndarray:
+    """The T samples of each antenna row from ``start`` (interleaved IQ kept)."""
+    return np.asarray(capture)[:, start:start + T]
+
+
+def fftshift_rows(x: np.ndarray) -> np.ndarray:
+    """Subcarrier order of the paper's output (Sec. II-C, fftshift): the
+    zero-frequency bin moves to the middle of the last axis."""
+    return np.fft.fftshift(x, axes=-1)
 
 
 # --------------------------------------------------------------------------

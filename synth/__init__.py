@@ -8,12 +8,16 @@ white Gaussian noise and optionally quantises to interleaved int16 IQ (sc16).
 Its outputs feed both the CUDA library and the FP64 oracle as plain arrays.
 
 The frame layout follows Sec. II-B of the paper (one channel-estimation symbol,
-then QAM data symbols; CP + N samples per symbol, per antenna).  The PN preamble
-for packet detection is not generated: frames start at the first CP sample.
+then QAM data symbols; CP + N samples per symbol, per antenna).  ``generate``
+makes aligned frames that start at the first CP sample; ``generate_capture``
+(``synth.capture``) makes captures with the PN preamble for packet detection
+and a random delay before it.
 """
 
 from .frames import (FrameConfig, FrameBatch, generate, qam_map, gray_levels,
                      CONFIGS, config_by_name)
+from .capture import CaptureBatch, generate_capture, pn_sequence, PN_LEN
 
 __all__ = ["FrameConfig", "FrameBatch", "generate", "qam_map", "gray_levels",
-           "CONFIGS", "config_by_name"]
+           "CONFIGS", "config_by_name", "CaptureBatch", "generate_capture",
+           "pn_sequence", "PN_LEN"]

@@ -20,6 +20,11 @@ operand, a wrong Gray label or tie rule, bit order) fails at least one of them:
   table, round trip through the transmitter's independent mapper, tie rule.
 * Statistics: LS error variance = sigma^2, and QPSK MRC bit-error rate against
   the closed form for M-branch Rayleigh diversity.
+* Packet detection: the PN chips form an m-sequence (two-valued periodic
+  autocorrelation), the metric equals numpy's correlation, a noiseless
+  single-tap capture peaks at the true delay with the closed-form height, and
+  a multipath capture peaks on one of the channel's paths.  fftshift moves a
+  tone by half the band.
 """
 
 import cmath
@@ -258,6 +263,55 @@ def test_mrc_antenna_split_matches_whole_array_and_flags():
     assert bad and np.all(z[:, 7] == 0) and E[7] == 0
     assert np.allclose(z[:, 5], np.sum(np.conj(H0[4:, 5])[:, None] * Y[4:, :, 5], axis=0)
                        / np.sum(np.abs(H0[4:, 5]) ** 2), rtol=1e-12)
+
+
+# ------------------------------------------------- packet detection ----
+
+def test_pn_sequence_is_an_m_sequence():
+    p = synth.pn_sequence()
+    assert p.shape == (255,) and set(np.unique(p)) == {-1.0, 1.0}
+    assert p.sum() == -1.0                      # 128 ones and 127 zeros
+    ac = np.array([np.dot(p, np.roll(p, k)) for k in range(255)])
+    assert ac[0] == 255 and np.all(ac[1:] == -1)   # two-valued autocorrelation
+
+
+def test_pn_metric_matches_library_correlation():
+    rng = np.random.default_rng(21)
+    y = rng.standard_normal((3, 400)) + 1j * rng.standard_normal((3, 400))
+    pn = synth.pn_sequence()
+    W = 400 - 255 + 1
+    want = sum(np.abs(np.correlate(y[m], pn, "valid")) ** 2 for m in range(3))
+    assert np.allclose(oracle.pn_metric(y, pn, W), want, rtol=1e-12)
+
+
+def test_pn_sync_noiseless_single_tap_closed_form():
+    cfg = FrameConfig(M=4, N=64, cp=16, S=3, Q=4, taps=1, snr_db=None, fmt="fc32")
+    c = synth.generate_capture(cfg, frame_ids=range(3), max_delay=200)
+    pn = synth.pn_sequence()
+    for i in range(3):
+        y = oracle.to_complex(c.captures[i])
+        off, metric = oracle.pn_sync(y, pn, c.max_delay)
+        assert off == c.delay[i]
+        h = c.taps[i][:, 0].astype(np.complex64).astype(np.complex128)
+        assert np.isclose(metric[off], 255.0 ** 2 * np.sum(np.abs(h) ** 2), rtol=1e-5)
+
+
+def test_pn_sync_multipath_lands_on_a_path():
+    cfg = FrameConfig(M=8, N=256, cp=32, S=3, Q=16, taps=6, decay_db=2.0, snr_db=15.0, fmt="sc16")
+    c = synth.generate_capture(cfg, frame_ids=range(6), max_delay=300)
+    for i in range(6):
+        off, _ = oracle.pn_sync(oracle.to_complex(c.captures[i]), c.pn, c.max_delay)
+        assert c.delay[i] <= off < c.delay[i] + cfg.taps
+
+
+def test_fftshift_moves_a_tone_half_a_band():
+    N = 64
+    for k0 in (0, 5, 40):
+        x = np.exp(2j * np.pi * k0 * np.arange(N) / N)
+        Xs = oracle.fftshift_rows(oracle.dft(x))
+        assert np.argmax(np.abs(Xs)) == (k0 + N // 2) % N
+    r = np.arange(12).reshape(2, 6)
+    assert np.array_equal(oracle.fftshift_rows(r), np.roll(r, 3, axis=-1))
 
 
 # --------------------------------------------------------------- demap ----
