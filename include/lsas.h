@@ -209,6 +209,56 @@ lsas_status lsas_receive_y(lsas_plan plan, const float* d_Y, int n_frames, float
                            uint8_t* d_bits, float* d_eq, void* stream);
 
 /*
+ * Packet detection (Sec. II-B): the receiver correlates the received
+ * baseband with the maximum-length PN sequence that precedes every frame to
+ * find where the packet begins.  lsas_plan_set_pn stores the real PN chips
+ * (host array of len floats, 1 <= len <= 1024; the plan copies them).
+ */
+lsas_status lsas_plan_set_pn(lsas_plan plan, const float* host_pn, int len);
+
+/*
+ * For every frame f of d_capture [F][M][capture_len] (interleaved IQ in the
+ * plan's input format), the preamble start
+ *   d_offset[f] = argmax over tau < window of
+ *                 sum_m |sum_n pn[n] y[f][m][tau + n]|^2
+ * (the earliest tau on ties) and, if d_peak is not NULL, d_peak[f] = that
+ * maximum (float).  The frame begins at d_offset[f] + len.  Errors:
+ * INVALID_ARG if no PN sequence is set, for window < 1 or
+ * window + len - 1 > capture_len, or a null pointer; CAPACITY for
+ * n_frames > max_frames.  Asynchronous.
+ */
+lsas_status lsas_pn_sync(lsas_plan plan, const void* d_capture, int n_frames,
+                         int capture_len, int window, int* d_offset,
+                         float* d_peak, void* stream);
+
+/*
+ * Copy each frame out of its capture into the receiver's input layout:
+ * d_frames [F][M][S*(N+CP)] (plan format) takes the S*(N+CP) samples of each
+ * antenna row from d_offset[f] + len - backoff.  A backoff of a few samples
+ * starts the FFT windows early inside the cyclic prefix, which the LS
+ * estimate absorbs as a phase ramp; a late start would take samples of the
+ * next symbol.  A start outside the capture zero-fills that frame and
+ * latches LSAS_ERR_DEVICE.  Errors: INVALID_ARG for backoff < 0 or a null
+ * pointer; CAPACITY for n_frames > max_frames.  Asynchronous.
+ */
+lsas_status lsas_pn_extract(lsas_plan plan, const void* d_capture, int n_frames,
+                            int capture_len, const int* d_offset, int backoff,
+                            void* d_frames, void* stream);
+
+/*
+ * fftshift (Sec. II-C): reorder the subcarriers of an output buffer in place
+ * so that subcarrier k moves to (k + N/2) mod N (the zero-frequency bin to
+ * the middle).  what selects the buffer and its layout:
+ *   LSAS_SHIFT_H    d_buf [F][M][N] complex      LSAS_SHIFT_EQ  [F][D][N] complex
+ *   LSAS_SHIFT_Y    [F][M][S][N] complex         LSAS_SHIFT_BITS [F][D][N*q/8] bytes
+ * Applying it twice restores the natural order.  Errors: INVALID_ARG for an
+ * unknown what or a null pointer; CAPACITY for n_frames > max_frames.
+ */
+enum { LSAS_SHIFT_H = 0, LSAS_SHIFT_EQ = 1, LSAS_SHIFT_Y = 2, LSAS_SHIFT_BITS = 3 };
+lsas_status lsas_fftshift(lsas_plan plan, int what, void* d_buf, int n_frames,
+                          void* stream);
+
+/*
  * Size of the library's fixed device scratch used by
  * lsas_run_frame_split_static (16 MiB per device).
  */

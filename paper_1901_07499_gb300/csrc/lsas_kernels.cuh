@@ -65,6 +65,11 @@ struct KParams {
   const void* tc_w2;     //   N/32-point DFT operand images (hi, lo)
   const float2* tc_tw;   //   inter-stage twiddles W_N^(n2 k1), [n2][k1]
   int terms;             //   1: fp16 operands; 3: hi+lo split operands
+  const float* pn;       // packet detection: PN chips (real), pn_len of them
+  int pn_len, cap_len, window, backoff;
+  int* offsets;          //   per frame: detected preamble start (out)
+  float* peaks;          //   per frame: correlation power at it (out, nullable)
+  const int* offsets_in; //   per frame: preamble start (extraction)
   int chunks;            // ceil(M / A)
   int groups, dg;        // data-symbol groups per frame, data symbols per group
   int mode;              // kModeDemod, kModeRun or kModePartial (frame_kernel)

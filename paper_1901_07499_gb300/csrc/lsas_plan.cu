@@ -30,6 +30,11 @@ cudaError_t launch_combine(const KParams&, cudaStream_t);
 cudaError_t launch_tcfft(const KParams&, int N, int grid, cudaStream_t);
 cudaError_t launch_yrx(const KParams&, int n_frames, cudaStream_t);
 int tc_smem_bytes(int N);
+cudaError_t launch_pn(const KParams&, bool fc32, int n_frames, cudaStream_t);
+cudaError_t launch_extract(const KParams&, bool fc32, int n_frames, cudaStream_t);
+cudaError_t launch_shift(void* buf, int kind, size_t rows, int N, int rowbytes, int sms,
+                         cudaStream_t);
+int pn_smem_bytes(int pn_len);
 bool tc_tables(int N, std::vector<uint16_t>& w1, std::vector<uint16_t>& w2,
                std::vector<float2>& tw);
 }  // namespace lsas
@@ -40,6 +45,7 @@ namespace {
 
 constexpr int kSmemLimit = 232448;   // opt-in dynamic shared memory per block
 constexpr int kHostChunk = 64;       // frames per transfer chunk (host path)
+constexpr int kMaxPnLen = 1024;      // longest PN sequence lsas_plan_set_pn takes
 
 struct Geometry {
   int A, L, T;
@@ -67,6 +73,9 @@ struct lsas_plan_s {
   void* d_tc_w2 = nullptr;
   float2* d_tc_tw = nullptr;
   int sms = 0;
+  // packet detection: PN chips (lsas_plan_set_pn)
+  float* d_pn = nullptr;
+  int pn_len = 0;
   Geometry geo;
   LaunchFn launch = nullptr;
   // host-transfer staging (lsas_run_frame_host), allocated on first use
@@ -658,6 +667,90 @@ lsas_status lsas_receive_y(lsas_plan p, const float* d_Y, int n_frames, float* d
   return LSAS_OK;
 }
 
+lsas_status lsas_plan_set_pn(lsas_plan p, const float* host_pn, int len) {
+  if (!p || !host_pn || len < 1 || len > kMaxPnLen) return LSAS_ERR_INVALID_ARG;
+  if (set_device(p) != LSAS_OK) return LSAS_ERR_CUDA;
+  if (!p->d_pn && cudaMalloc(&p->d_pn, sizeof(float) * kMaxPnLen) != cudaSuccess) {
+    cudaGetLastError();
+    return LSAS_ERR_OOM;
+  }
+  if (cudaMemcpy(p->d_pn, host_pn, sizeof(float) * len, cudaMemcpyHostToDevice) != cudaSuccess)
+    return LSAS_ERR_CUDA;
+  p->pn_len = len;
+  return LSAS_OK;
+}
+
+lsas_status lsas_pn_sync(lsas_plan p, const void* d_capture, int n_frames, int capture_len,
+                         int window, int* d_offset, float* d_peak, void* stream) {
+  if (!p) return LSAS_ERR_INVALID_ARG;
+  if (p->pn_len < 1) return LSAS_ERR_INVALID_ARG;
+  lsas_status s = check_frames(p, n_frames);
+  if (s != LSAS_OK) return s;
+  if (window < 1 || capture_len < 1 || window > capture_len - p->pn_len + 1)
+    return LSAS_ERR_INVALID_ARG;
+  if (n_frames == 0) return LSAS_OK;
+  if (!d_capture || !d_offset) return LSAS_ERR_INVALID_ARG;
+  if (set_device(p) != LSAS_OK) return LSAS_ERR_CUDA;
+  KParams k;
+  base_params(p, &k);
+  k.in = d_capture;
+  k.pn = p->d_pn;
+  k.pn_len = p->pn_len;
+  k.cap_len = capture_len;
+  k.window = window;
+  k.offsets = d_offset;
+  k.peaks = d_peak;
+  if (launch_pn(k, p->fmt == LSAS_IN_FC32, n_frames, static_cast<cudaStream_t>(stream)) !=
+      cudaSuccess)
+    return LSAS_ERR_CUDA;
+  return LSAS_OK;
+}
+
+lsas_status lsas_pn_extract(lsas_plan p, const void* d_capture, int n_frames, int capture_len,
+                            const int* d_offset, int backoff, void* d_frames, void* stream) {
+  if (!p) return LSAS_ERR_INVALID_ARG;
+  lsas_status s = check_frames(p, n_frames);
+  if (s != LSAS_OK) return s;
+  if (capture_len < 1 || backoff < 0) return LSAS_ERR_INVALID_ARG;
+  if (n_frames == 0) return LSAS_OK;
+  if (!d_capture || !d_offset || !d_frames) return LSAS_ERR_INVALID_ARG;
+  if (set_device(p) != LSAS_OK) return LSAS_ERR_CUDA;
+  KParams k;
+  base_params(p, &k);
+  k.in = d_capture;
+  k.offsets_in = d_offset;
+  k.pn_len = p->pn_len;
+  k.backoff = backoff;
+  k.cap_len = capture_len;
+  k.Y_out = static_cast<float2*>(d_frames);
+  if (launch_extract(k, p->fmt == LSAS_IN_FC32, n_frames, static_cast<cudaStream_t>(stream)) !=
+      cudaSuccess)
+    return LSAS_ERR_CUDA;
+  return LSAS_OK;
+}
+
+lsas_status lsas_fftshift(lsas_plan p, int what, void* d_buf, int n_frames, void* stream) {
+  if (!p) return LSAS_ERR_INVALID_ARG;
+  lsas_status s = check_frames(p, n_frames);
+  if (s != LSAS_OK) return s;
+  size_t rows = 0;
+  switch (what) {
+    case LSAS_SHIFT_H: rows = static_cast<size_t>(n_frames) * p->M; break;
+    case LSAS_SHIFT_EQ: rows = static_cast<size_t>(n_frames) * p->D; break;
+    case LSAS_SHIFT_Y: rows = static_cast<size_t>(n_frames) * p->M * p->S; break;
+    case LSAS_SHIFT_BITS: rows = static_cast<size_t>(n_frames) * p->D; break;
+    default: return LSAS_ERR_INVALID_ARG;
+  }
+  if (n_frames == 0) return LSAS_OK;
+  if (!d_buf) return LSAS_ERR_INVALID_ARG;
+  if (set_device(p) != LSAS_OK) return LSAS_ERR_CUDA;
+  const int kind = what == LSAS_SHIFT_BITS ? 1 : 0;
+  if (launch_shift(d_buf, kind, rows, p->N, p->N * p->q / 8, p->sms,
+                   static_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return LSAS_ERR_CUDA;
+  return LSAS_OK;
+}
+
 lsas_status lsas_run_frame_host(lsas_plan p, const void* h_in, int n_frames, float* h_H,
                                 uint8_t* h_bits, float* h_eq, void* stream) {
   if (!p) return LSAS_ERR_INVALID_ARG;
@@ -767,6 +860,7 @@ lsas_status lsas_plan_destroy(lsas_plan p) {
   cudaFree(p->d_tc_w1);
   cudaFree(p->d_tc_w2);
   cudaFree(p->d_tc_tw);
+  cudaFree(p->d_pn);
   for (int i = 0; i < 2; ++i) {
     cudaFree(p->d_in_stage[i]);
     cudaFree(p->d_H_stage[i]);

@@ -34,6 +34,7 @@ LSAS_ERR_CUDA = 5
 LSAS_ERR_TIMEOUT = 6
 LSAS_ERR_DEVICE = 7
 LSAS_STATIC_SCRATCH_BYTES = 16 << 20
+LSAS_SHIFT_H, LSAS_SHIFT_EQ, LSAS_SHIFT_Y, LSAS_SHIFT_BITS = 0, 1, 2, 3
 LSAS_IN_SC16 = 0
 LSAS_IN_FC32 = 1
 
@@ -64,6 +65,10 @@ lsas_run_frame_split_static = _proto("lsas_run_frame_split_static",
                                      [_vp, _vp, _i, _i, _vp, _vp, _vp, _vp])
 lsas_fft_tc = _proto("lsas_fft_tc", [_vp, _vp, _i, _i, _vp, _vp])
 lsas_receive_y = _proto("lsas_receive_y", [_vp, _vp, _i, _vp, _vp, _vp, _vp])
+lsas_plan_set_pn = _proto("lsas_plan_set_pn", [_vp, C.POINTER(_f), _i])
+lsas_pn_sync = _proto("lsas_pn_sync", [_vp, _vp, _i, _i, _i, _vp, _vp, _vp])
+lsas_pn_extract = _proto("lsas_pn_extract", [_vp, _vp, _i, _i, _vp, _i, _vp, _vp])
+lsas_fftshift = _proto("lsas_fftshift", [_vp, _i, _vp, _i, _vp])
 lsas_plan_sync = _proto("lsas_plan_sync", [_vp, _vp])
 lsas_plan_info = _proto("lsas_plan_info", [_vp, C.POINTER(_i)])
 lsas_plan_destroy = _proto("lsas_plan_destroy", [_vp])
@@ -73,6 +78,7 @@ EXPORTED = ["lsas_status_str", "lsas_check_config", "lsas_frame_bytes",
             "lsas_fft", "lsas_estimate", "lsas_demodulate", "lsas_run_frame",
             "lsas_run_frame_host", "lsas_mrc_partial", "lsas_mrc_combine",
             "lsas_run_frame_split_static", "lsas_fft_tc", "lsas_receive_y",
+            "lsas_plan_set_pn", "lsas_pn_sync", "lsas_pn_extract", "lsas_fftshift",
             "lsas_plan_sync", "lsas_plan_info",
             "lsas_plan_destroy"]
 
@@ -229,6 +235,42 @@ class Plan:
         check(lsas_receive_y(self._h, _ptr(Y), F, _ptr(H), _ptr(bits), _ptr(eq), _stream(stream)),
               "lsas_receive_y")
         return H, bits, eq
+
+    # ---- packet detection and output order
+    def set_pn(self, pn) -> None:
+        chips = np.ascontiguousarray(np.asarray(pn, dtype=np.float32))
+        check(lsas_plan_set_pn(self._h, chips.ctypes.data_as(C.POINTER(_f)), int(chips.size)),
+              "lsas_plan_set_pn")
+        self.pn_len = int(chips.size)
+
+    def pn_sync(self, cap, window, offsets=None, peaks=None, stream=None):
+        """Preamble start per frame of captures cap [F][M][Lc][2]: (offsets, peaks)."""
+        import torch
+        if not cap.is_contiguous() or cap.dim() != 4 or cap.shape[1] != self.M:
+            raise ValueError("captures must be a contiguous [F][M][Lc][2] tensor")
+        F, Lc = int(cap.shape[0]), int(cap.shape[2])
+        offsets = torch.empty(F, dtype=torch.int32, device=cap.device) if offsets is None else offsets
+        peaks = torch.empty(F, dtype=torch.float32, device=cap.device) if peaks is None else peaks
+        check(lsas_pn_sync(self._h, _ptr(cap), F, Lc, window, _ptr(offsets), _ptr(peaks),
+                           _stream(stream)), "lsas_pn_sync")
+        return offsets, peaks
+
+    def pn_extract(self, cap, offsets, backoff=0, frames=None, stream=None):
+        """Frames [F][M][S(N+CP)][2] cut out of the captures after the preamble."""
+        import torch
+        F, Lc = int(cap.shape[0]), int(cap.shape[2])
+        if frames is None:
+            frames = torch.empty((F, self.M, self.S * (self.N + self.cp), 2), dtype=cap.dtype,
+                                 device=cap.device)
+        check(lsas_pn_extract(self._h, _ptr(cap), F, Lc, _ptr(offsets), backoff, _ptr(frames),
+                              _stream(stream)), "lsas_pn_extract")
+        return frames
+
+    def fftshift(self, what, buf, stream=None):
+        """In-place fftshift of an output buffer (what = LSAS_SHIFT_*)."""
+        check(lsas_fftshift(self._h, what, _ptr(buf), int(buf.shape[0]), _stream(stream)),
+              "lsas_fftshift")
+        return buf
 
     def estimate(self, x, H=None, stream=None):
         F = self._frames(x)
