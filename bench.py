@@ -55,6 +55,10 @@ def parse():
     ap.add_argument("--latency-calls", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving", action="store_true",
+                    help="serving-loop report: latency vs offered load (one JSON line per load)")
+    ap.add_argument("--serving-loads", default="1,5,10,20,40", help="offered loads, G samples/s")
+    ap.add_argument("--serving-seconds", type=float, default=2.0)
     return ap.parse_args()
 
 
@@ -243,9 +247,106 @@ def reference_arm(args, cfg):
     return 0
 
 
+def serving_report(args):
+    """Serving loop (lsas_server_*) under Poisson arrivals of frames of mixed
+    configurations: M in {16, 32, 64, 128}, N in {256, 512, 1024, 2048},
+    CP = N/8, 14 symbols, QAM in {4, 16, 64}, 8 taps, SNR U[5, 30] dB.  Six
+    seeded configurations are registered; each arrival picks one uniformly
+    and one of its 4 pooled frames (pinned host memory).  Per offered load
+    (antenna*subcarrier samples/s): achieved throughput and p50/p99 latency
+    from submit to results in host memory."""
+    import threading
+    import torch
+    import paper_1901_07499_gb300.lsas as lsas
+    rng = np.random.default_rng(0x5E5)
+    combos = []
+    while len(combos) < 6:
+        c = (int(rng.choice([16, 32, 64, 128])), int(rng.choice([256, 512, 1024, 2048])),
+             int(rng.choice([4, 16, 64])))
+        if c not in combos:
+            combos.append(c)
+    cfgs = [synth.frames.sweep_config(M, N).replace(Q=Q, taps=8, snr_db=(5.0, 30.0), F=4,
+                                              name=f"serve_M{M}_N{N}_Q{Q}") for M, N, Q in combos]
+    pools = [synth.generate(c, frame_ids=range(4)) for c in cfgs]
+    max_batch, max_wait = 16, 200.0
+    srv = lsas.Server(mem_budget=24 << 30, max_batch=max_batch, max_wait_us=max_wait)
+    ids = [srv.register(c.M, c.N, c.cp, c.S, c.pilot_idx, c.Q, fmt=c.fmt, pilot=b.pilot)
+           for c, b in zip(cfgs, pools)]
+    xs = [[torch.from_numpy(np.ascontiguousarray(b.frames[i])).pin_memory() for i in range(4)]
+          for b in pools]
+    ring = 512
+    outs = [[(torch.empty((c.M, c.N), dtype=torch.complex64).pin_memory(),
+              torch.empty(c.D * c.N * c.q // 8, dtype=torch.uint8).pin_memory())
+             for _ in range(ring)] for c in cfgs]
+    samples = [c.M * c.S * c.N for c in cfgs]
+    mean_samples = float(np.mean(samples))
+    for load in [float(v) for v in args.serving_loads.split(",")]:
+        rate = load * 1e9 / mean_samples          # frames per second
+        lat, done_samples = [], [0]
+        tickets = []
+        cv = threading.Condition()
+        finished = [False]
+
+        def waiter():
+            i = 0
+            while True:
+                with cv:
+                    while i >= len(tickets) and not finished[0]:
+                        cv.wait()
+                    if i >= len(tickets):
+                        return
+                    t, ci = tickets[i]
+                lat.append(srv.wait(t))
+                done_samples[0] += samples[ci]
+                i += 1
+
+        th = threading.Thread(target=waiter)
+        th.start()
+        st0 = srv.stats()
+        t0 = time.perf_counter()
+        t_next = t0
+        n = 0
+        while t_next - t0 < args.serving_seconds:
+            while time.perf_counter() < t_next:
+                pass
+            ci = int(rng.integers(len(cfgs)))
+            slot = n % ring
+            if n >= ring:   # the slot's previous result must be home before reuse
+                while len(lat) <= n - ring:
+                    time.sleep(0)
+            H, bits = outs[ci][slot]
+            t = srv.submit(ids[ci], xs[ci][n % 4], H, bits)
+            with cv:
+                tickets.append((t, ci))
+                cv.notify()
+            n += 1
+            t_next += rng.exponential(1.0 / rate)
+        with cv:
+            finished[0] = True
+            cv.notify()
+        th.join()
+        wall = time.perf_counter() - t0
+        st1 = srv.stats()
+        lat_us = np.array(lat)
+        print(json.dumps({
+            "mode": "serving", "offered_gsps": load, "achieved_gsps": done_samples[0] / wall / 1e9,
+            "frames": n, "launches": st1["launches"] - st0["launches"],
+            "latency_us": {"p50": float(np.percentile(lat_us, 50)),
+                           "p99": float(np.percentile(lat_us, 99)),
+                           "max": float(lat_us.max())},
+            "max_batch": max_batch, "max_wait_us": max_wait,
+            "configs": [c.name for c in cfgs], "data": "synthetic (seeded generator)"}))
+        sys.stdout.flush()
+    code = srv.close()
+    if code != lsas.LSAS_OK:
+        raise RuntimeError(f"server reported {lsas.lsas_status_str(code).decode()}")
+
+
 def main():
     args = parse()
     cfg = synth.config_by_name(args.config)
+    if args.serving:
+        return serving_report(args)
     if args.impl == "reference":
         return reference_arm(args, cfg)
 

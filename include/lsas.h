@@ -259,6 +259,51 @@ lsas_status lsas_fftshift(lsas_plan plan, int what, void* d_buf, int n_frames,
                           void* stream);
 
 /*
+ * Serving loop.  The paper processes frames as they arrive from the radios
+ * (Sec. II-B) and names frame-level batching as its next step (Sec. IV).  A
+ * server takes frames of several registered receiver configurations, one at
+ * a time, from host memory, batches them per configuration and runs the
+ * fused receiver (lsas_run_frame) on each batch.
+ *
+ * lsas_server_create: memory budget in bytes for everything registered
+ *   later; max_batch frames per launch (1..1024); max_wait_us, how long the
+ *   oldest waiting frame of a configuration may wait for more frames of it.
+ *   Starts one worker thread on the current device.  CUDA if there is no
+ *   device, INVALID_ARG for bad arguments.
+ * lsas_server_register: admit a configuration (as lsas_plan_create, plus the
+ *   input format and an optional host pilot of N interleaved re,im floats).
+ *   Its plan and staging for max_batch frames count against the budget:
+ *   LSAS_ERR_CAPACITY when they do not fit.  Returns its id.
+ * lsas_server_submit: queue one frame of a registered configuration:
+ *   h_in [M][S*(N+CP)] samples, results to h_H [M][N], h_bits [D*N*q/8],
+ *   h_eq [D][N] (nullable), all host memory that stays valid until the wait
+ *   returns (pinned memory for full copy speed).  Never blocks; gives a
+ *   ticket.
+ * lsas_server_wait: wait up to timeout_ms for a ticket's results;
+ *   LSAS_ERR_TIMEOUT if they are not ready (the ticket stays valid),
+ *   INVALID_ARG for an unknown ticket.  latency_us (nullable) receives the
+ *   time from submit to results in host memory.
+ * lsas_server_stats: out[0] launches, out[1] frames, out[2] bytes admitted,
+ *   out[3] configurations.
+ * lsas_server_destroy: finish queued frames, stop the worker, free all; it
+ *   returns a device-side condition latched by any configuration's plan
+ *   (LSAS_ERR_DEVICE, LSAS_ERR_TIMEOUT) or LSAS_OK.
+ * A frame's results do not depend on the other frames it is batched with.
+ */
+typedef struct lsas_server_s* lsas_server;
+lsas_status lsas_server_create(size_t mem_budget_bytes, int max_batch, double max_wait_us,
+                               lsas_server* out);
+lsas_status lsas_server_register(lsas_server server, int M, int N, int cp_len, int n_sym,
+                                 int pilot_idx, int qam_order, lsas_input_fmt fmt,
+                                 const float* host_pilot_iq, int* config_id);
+lsas_status lsas_server_submit(lsas_server server, int config_id, const void* h_in,
+                               float* h_H, uint8_t* h_bits, float* h_eq, uint64_t* ticket);
+lsas_status lsas_server_wait(lsas_server server, uint64_t ticket, double timeout_ms,
+                             double* latency_us);
+lsas_status lsas_server_stats(lsas_server server, uint64_t out[4]);
+lsas_status lsas_server_destroy(lsas_server server);
+
+/*
  * Size of the library's fixed device scratch used by
  * lsas_run_frame_split_static (16 MiB per device).
  */

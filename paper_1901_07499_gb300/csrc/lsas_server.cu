@@ -1,0 +1,344 @@
+// lsas_server.cu -- a serving loop around the fused receiver.
+//
+// Frames of several receiver configurations (antenna count, FFT length, QAM
+// order, ...) arrive one at a time in host memory.  A configuration is
+// registered once: that is where memory is admitted (its plan and its
+// staging buffers must fit the server's budget) and where its stream lives.
+// Submitted frames wait in a per-configuration queue; a worker thread takes
+// the configuration with the oldest waiting frame, gathers up to max_batch of
+// its frames (or fewer once the oldest has waited max_wait_us), uploads them
+// into the configuration's staging buffer, runs the fused receiver on the
+// batch and copies each frame's results back to its own host buffers.  A host
+// callback after the copies records the completion time and wakes waiters.
+// Each frame is processed exactly as it would be alone (frames are
+// independent in the kernel), so the results do not depend on the mix.
+// Device-side conditions (zero channel energy, a bounded wait that ran out)
+// latch in the configuration's plan and are returned by lsas_server_destroy.
+#include <chrono>
+#include <condition_variable>
+#include <cstdint>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "lsas.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+  uint64_t ticket;
+  int config;
+  const void* h_in;
+  float* h_H;
+  uint8_t* h_bits;
+  float* h_eq;
+  Clock::time_point submitted;
+};
+
+struct Done {
+  bool done = false;
+  lsas_status status = LSAS_OK;
+  double latency_us = 0.0;
+};
+
+struct Config {
+  lsas_plan plan = nullptr;
+  int M, N, cp, S, Q, D;
+  lsas_input_fmt fmt;
+  size_t in_b, h_b, bits_b, eq_b;   // bytes per frame
+  void* d_in = nullptr;
+  float* d_H = nullptr;
+  uint8_t* d_bits = nullptr;
+  float* d_eq = nullptr;
+  cudaStream_t stream = nullptr;
+  std::deque<Request> queue;
+  size_t bytes = 0;
+};
+
+struct Batch;
+
+}  // namespace
+
+struct lsas_server_s {
+  size_t budget = 0, used = 0;
+  int max_batch = 1;
+  double max_wait_us = 0;
+  int device = 0;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::vector<std::unique_ptr<Config>> configs;
+  std::map<uint64_t, Done> done;
+  uint64_t next_ticket = 1;
+  bool stop = false;
+  std::thread worker;
+  uint64_t launched = 0, frames = 0;
+};
+
+namespace {
+
+// Completion of one batch: a host callback after the batch's result copies.
+struct Batch {
+  lsas_server_s* s;
+  std::vector<std::pair<uint64_t, Clock::time_point>> items;
+  int config;
+};
+
+// Runs on a CUDA callback thread (no CUDA calls here): marks the batch's
+// frames done with their submit-to-results latency.
+void CUDART_CB batch_done(void* arg) {
+  Batch* b = static_cast<Batch*>(arg);
+  lsas_server_s* s = b->s;
+  const Clock::time_point now = Clock::now();
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    for (auto& it : b->items) {
+      Done& d = s->done[it.first];
+      d.done = true;
+      d.status = LSAS_OK;
+      d.latency_us = std::chrono::duration<double, std::micro>(now - it.second).count();
+    }
+  }
+  s->cv_done.notify_all();
+  delete b;
+}
+
+void fail_batch(lsas_server_s* s, const std::vector<Request>& reqs, lsas_status st) {
+  std::lock_guard<std::mutex> lock(s->mu);
+  for (const Request& r : reqs) {
+    Done& d = s->done[r.ticket];
+    d.done = true;
+    d.status = st;
+  }
+}
+
+void worker_loop(lsas_server_s* s) {
+  cudaSetDevice(s->device);
+  std::unique_lock<std::mutex> lock(s->mu);
+  for (;;) {
+    // the configuration whose oldest waiting frame is oldest
+    int pick = -1;
+    Clock::time_point oldest;
+    for (size_t c = 0; c < s->configs.size(); ++c) {
+      Config& cf = *s->configs[c];
+      if (cf.queue.empty()) continue;
+      if (pick < 0 || cf.queue.front().submitted < oldest) {
+        pick = static_cast<int>(c);
+        oldest = cf.queue.front().submitted;
+      }
+    }
+    if (pick < 0) {
+      if (s->stop) return;
+      s->cv_work.wait_for(lock, std::chrono::milliseconds(50));
+      continue;
+    }
+    Config& cf = *s->configs[pick];
+    const auto deadline = oldest + std::chrono::duration<double, std::micro>(s->max_wait_us);
+    if (static_cast<int>(cf.queue.size()) < s->max_batch && !s->stop && Clock::now() < deadline) {
+      s->cv_work.wait_until(lock, deadline);   // gather more of this configuration
+      continue;
+    }
+    std::vector<Request> reqs;
+    while (!cf.queue.empty() && static_cast<int>(reqs.size()) < s->max_batch) {
+      reqs.push_back(cf.queue.front());
+      cf.queue.pop_front();
+    }
+    lock.unlock();
+    // upload, run, download on the configuration's stream
+    lsas_status st = LSAS_OK;
+    const int F = static_cast<int>(reqs.size());
+    for (int i = 0; i < F && st == LSAS_OK; ++i)
+      if (cudaMemcpyAsync(static_cast<unsigned char*>(cf.d_in) + i * cf.in_b, reqs[i].h_in, cf.in_b,
+                          cudaMemcpyHostToDevice, cf.stream) != cudaSuccess)
+        st = LSAS_ERR_CUDA;
+    if (st == LSAS_OK) {
+      bool eq = false;   // z is computed when any frame of the batch asks for it
+      for (const Request& r : reqs) eq = eq || r.h_eq != nullptr;
+      st = lsas_run_frame(cf.plan, cf.d_in, F, cf.d_H, cf.d_bits, eq ? cf.d_eq : nullptr, cf.stream);
+    }
+    for (int i = 0; i < F && st == LSAS_OK; ++i) {
+      const Request& r = reqs[i];
+      if (cudaMemcpyAsync(r.h_H, reinterpret_cast<unsigned char*>(cf.d_H) + i * cf.h_b, cf.h_b,
+                          cudaMemcpyDeviceToHost, cf.stream) != cudaSuccess ||
+          cudaMemcpyAsync(r.h_bits, cf.d_bits + i * cf.bits_b, cf.bits_b, cudaMemcpyDeviceToHost,
+                          cf.stream) != cudaSuccess ||
+          (r.h_eq && cudaMemcpyAsync(r.h_eq, reinterpret_cast<unsigned char*>(cf.d_eq) + i * cf.eq_b,
+                                     cf.eq_b, cudaMemcpyDeviceToHost, cf.stream) != cudaSuccess))
+        st = LSAS_ERR_CUDA;
+    }
+    if (st == LSAS_OK) {
+      Batch* b = new Batch{s, {}, pick};
+      for (const Request& r : reqs) b->items.emplace_back(r.ticket, r.submitted);
+      if (cudaLaunchHostFunc(cf.stream, batch_done, b) != cudaSuccess) {
+        delete b;
+        st = LSAS_ERR_CUDA;
+      }
+    }
+    if (st != LSAS_OK) fail_batch(s, reqs, st);
+    lock.lock();
+    s->launched += 1;
+    s->frames += F;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+lsas_status lsas_server_create(size_t mem_budget_bytes, int max_batch, double max_wait_us,
+                               lsas_server* out) {
+  if (!out) return LSAS_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (max_batch < 1 || max_batch > 1024 || max_wait_us < 0) return LSAS_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return LSAS_ERR_CUDA;
+  }
+  lsas_server_s* s = new (std::nothrow) lsas_server_s();
+  if (!s) return LSAS_ERR_OOM;
+  s->budget = mem_budget_bytes;
+  s->max_batch = max_batch;
+  s->max_wait_us = max_wait_us;
+  s->device = dev;
+  s->worker = std::thread(worker_loop, s);
+  *out = s;
+  return LSAS_OK;
+}
+
+lsas_status lsas_server_register(lsas_server s, int M, int N, int cp_len, int n_sym,
+                                 int pilot_idx, int qam_order, lsas_input_fmt fmt,
+                                 const float* host_pilot_iq, int* config_id) {
+  if (!s || !config_id) return LSAS_ERR_INVALID_ARG;
+  lsas_status st = lsas_check_config(M, N, cp_len, n_sym, pilot_idx, qam_order);
+  if (st != LSAS_OK) return st;
+  size_t fb[4];
+  st = lsas_frame_bytes(M, N, cp_len, n_sym, qam_order, fmt, fb);
+  if (st != LSAS_OK) return st;
+  auto cf = std::make_unique<Config>();
+  cf->M = M;
+  cf->N = N;
+  cf->cp = cp_len;
+  cf->S = n_sym;
+  cf->Q = qam_order;
+  cf->D = n_sym - 1;
+  cf->fmt = fmt;
+  cf->in_b = fb[0];
+  cf->h_b = fb[1];
+  cf->bits_b = fb[2];
+  cf->eq_b = fb[3];
+  // admission: staging for max_batch frames plus the plan's own tables
+  const size_t plan_b = static_cast<size_t>(N) * 64 + (1u << 20);
+  cf->bytes = static_cast<size_t>(s->max_batch) * (fb[0] + fb[1] + fb[2] + fb[3]) + plan_b;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (s->used + cf->bytes > s->budget) return LSAS_ERR_CAPACITY;
+    s->used += cf->bytes;
+  }
+  auto undo = [&](lsas_status e) {
+    if (cf->plan) lsas_plan_destroy(cf->plan);
+    cudaFree(cf->d_in);
+    cudaFree(cf->d_H);
+    cudaFree(cf->d_bits);
+    cudaFree(cf->d_eq);
+    if (cf->stream) cudaStreamDestroy(cf->stream);
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->used -= cf->bytes;
+    return e;
+  };
+  if (cudaSetDevice(s->device) != cudaSuccess) return undo(LSAS_ERR_CUDA);
+  st = lsas_plan_create(M, N, cp_len, n_sym, pilot_idx, qam_order, &cf->plan);
+  if (st != LSAS_OK) return undo(st);
+  st = lsas_plan_set(cf->plan, fmt, s->max_batch);
+  if (st == LSAS_OK && host_pilot_iq) st = lsas_plan_set_pilot(cf->plan, host_pilot_iq);
+  if (st != LSAS_OK) return undo(st);
+  const size_t B = static_cast<size_t>(s->max_batch);
+  if (cudaMalloc(&cf->d_in, B * cf->in_b) != cudaSuccess ||
+      cudaMalloc(&cf->d_H, B * cf->h_b) != cudaSuccess ||
+      cudaMalloc(&cf->d_bits, B * cf->bits_b) != cudaSuccess ||
+      cudaMalloc(&cf->d_eq, B * cf->eq_b) != cudaSuccess) {
+    cudaGetLastError();
+    return undo(LSAS_ERR_OOM);
+  }
+  if (cudaStreamCreateWithFlags(&cf->stream, cudaStreamNonBlocking) != cudaSuccess)
+    return undo(LSAS_ERR_CUDA);
+  std::lock_guard<std::mutex> lock(s->mu);
+  s->configs.push_back(std::move(cf));
+  *config_id = static_cast<int>(s->configs.size()) - 1;
+  return LSAS_OK;
+}
+
+lsas_status lsas_server_submit(lsas_server s, int config_id, const void* h_in, float* h_H,
+                               uint8_t* h_bits, float* h_eq, uint64_t* ticket) {
+  if (!s || !h_in || !h_H || !h_bits || !ticket) return LSAS_ERR_INVALID_ARG;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (config_id < 0 || config_id >= static_cast<int>(s->configs.size())) return LSAS_ERR_INVALID_ARG;
+    if (s->stop) return LSAS_ERR_INVALID_ARG;
+    Config& cf = *s->configs[config_id];
+    const uint64_t t = s->next_ticket++;
+    cf.queue.push_back(Request{t, config_id, h_in, h_H, h_bits, h_eq, Clock::now()});
+    s->done[t] = Done{};
+    *ticket = t;
+  }
+  s->cv_work.notify_one();
+  return LSAS_OK;
+}
+
+lsas_status lsas_server_wait(lsas_server s, uint64_t ticket, double timeout_ms,
+                             double* latency_us) {
+  if (!s) return LSAS_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lock(s->mu);
+  auto it = s->done.find(ticket);
+  if (it == s->done.end()) return LSAS_ERR_INVALID_ARG;
+  const auto until = Clock::now() + std::chrono::duration<double, std::milli>(timeout_ms);
+  while (!s->done[ticket].done) {
+    if (s->cv_done.wait_until(lock, until) == std::cv_status::timeout && !s->done[ticket].done)
+      return LSAS_ERR_TIMEOUT;
+  }
+  Done d = s->done[ticket];
+  s->done.erase(ticket);
+  if (latency_us) *latency_us = d.latency_us;
+  return d.status;
+}
+
+lsas_status lsas_server_stats(lsas_server s, uint64_t out[4]) {
+  if (!s || !out) return LSAS_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(s->mu);
+  out[0] = s->launched;
+  out[1] = s->frames;
+  out[2] = s->used;
+  out[3] = s->configs.size();
+  return LSAS_OK;
+}
+
+lsas_status lsas_server_destroy(lsas_server s) {
+  if (!s) return LSAS_ERR_INVALID_ARG;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->stop = true;
+  }
+  s->cv_work.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  lsas_status st = LSAS_OK;
+  for (auto& cf : s->configs) {
+    if (cf->stream) cudaStreamSynchronize(cf->stream);
+    const lsas_status ps = lsas_plan_sync(cf->plan, cf->stream);
+    if (ps != LSAS_OK && st == LSAS_OK) st = ps;
+    lsas_plan_destroy(cf->plan);
+    cudaFree(cf->d_in);
+    cudaFree(cf->d_H);
+    cudaFree(cf->d_bits);
+    cudaFree(cf->d_eq);
+    if (cf->stream) cudaStreamDestroy(cf->stream);
+  }
+  delete s;
+  return st;
+}
+
+}  // extern "C"

@@ -69,6 +69,14 @@ lsas_plan_set_pn = _proto("lsas_plan_set_pn", [_vp, C.POINTER(_f), _i])
 lsas_pn_sync = _proto("lsas_pn_sync", [_vp, _vp, _i, _i, _i, _vp, _vp, _vp])
 lsas_pn_extract = _proto("lsas_pn_extract", [_vp, _vp, _i, _i, _vp, _i, _vp, _vp])
 lsas_fftshift = _proto("lsas_fftshift", [_vp, _i, _vp, _i, _vp])
+lsas_server_create = _proto("lsas_server_create", [C.c_size_t, _i, C.c_double, C.POINTER(_vp)])
+lsas_server_register = _proto("lsas_server_register",
+                              [_vp, _i, _i, _i, _i, _i, _i, _i, C.POINTER(_f), C.POINTER(_i)])
+lsas_server_submit = _proto("lsas_server_submit",
+                            [_vp, _i, _vp, _vp, _vp, _vp, C.POINTER(C.c_uint64)])
+lsas_server_wait = _proto("lsas_server_wait", [_vp, C.c_uint64, C.c_double, C.POINTER(C.c_double)])
+lsas_server_stats = _proto("lsas_server_stats", [_vp, C.POINTER(C.c_uint64)])
+lsas_server_destroy = _proto("lsas_server_destroy", [_vp])
 lsas_plan_sync = _proto("lsas_plan_sync", [_vp, _vp])
 lsas_plan_info = _proto("lsas_plan_info", [_vp, C.POINTER(_i)])
 lsas_plan_destroy = _proto("lsas_plan_destroy", [_vp])
@@ -79,6 +87,8 @@ EXPORTED = ["lsas_status_str", "lsas_check_config", "lsas_frame_bytes",
             "lsas_run_frame_host", "lsas_mrc_partial", "lsas_mrc_combine",
             "lsas_run_frame_split_static", "lsas_fft_tc", "lsas_receive_y",
             "lsas_plan_set_pn", "lsas_pn_sync", "lsas_pn_extract", "lsas_fftshift",
+            "lsas_server_create", "lsas_server_register", "lsas_server_submit",
+            "lsas_server_wait", "lsas_server_stats", "lsas_server_destroy",
             "lsas_plan_sync", "lsas_plan_info",
             "lsas_plan_destroy"]
 
@@ -345,6 +355,72 @@ class Plan:
         if getattr(self, "_h", None):
             lsas_plan_destroy(self._h)
             self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Serving loop: frames of registered configurations in host memory,
+    batched per configuration and run on the fused receiver.  Host tensors
+    passed to submit() are kept alive here until their wait() returns."""
+
+    def __init__(self, mem_budget: int, max_batch: int = 32, max_wait_us: float = 200.0):
+        h = _vp()
+        check(lsas_server_create(int(mem_budget), max_batch, float(max_wait_us), C.byref(h)),
+              "lsas_server_create")
+        self._h = h
+        self._live = {}
+        self.configs = {}
+
+    def register(self, M, N, cp, n_sym, pilot_idx=0, qam_order=4, fmt="sc16", pilot=None) -> int:
+        ptr = None
+        if pilot is not None:
+            x = np.asarray(pilot, dtype=np.complex128)
+            iq = np.ascontiguousarray(np.stack([x.real, x.imag], -1).astype(np.float32))
+            ptr = iq.ctypes.data_as(C.POINTER(_f))
+        cid = _i()
+        check(lsas_server_register(self._h, M, N, cp, n_sym, pilot_idx, qam_order, _fmt(fmt), ptr,
+                                   C.byref(cid)), "lsas_server_register")
+        q = int(round(np.log2(qam_order)))
+        self.configs[cid.value] = dict(M=M, N=N, cp=cp, S=n_sym, D=n_sym - 1, q=q)
+        return cid.value
+
+    def submit(self, cid, x, H, bits, eq=None) -> int:
+        t = C.c_uint64()
+        check(lsas_server_submit(self._h, cid, _ptr(x), _ptr(H), _ptr(bits), _ptr(eq), C.byref(t)),
+              "lsas_server_submit")
+        self._live[t.value] = (x, H, bits, eq)
+        return t.value
+
+    def wait(self, ticket, timeout_ms=30000.0) -> float:
+        lat = C.c_double()
+        code = lsas_server_wait(self._h, ticket, float(timeout_ms), C.byref(lat))
+        if code != LSAS_ERR_TIMEOUT:
+            self._live.pop(ticket, None)
+        check(code, "lsas_server_wait")
+        return lat.value
+
+    def stats(self) -> dict:
+        out = (C.c_uint64 * 4)()
+        check(lsas_server_stats(self._h, out), "lsas_server_stats")
+        return dict(launches=int(out[0]), frames=int(out[1]), admitted_bytes=int(out[2]),
+                    configs=int(out[3]))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self) -> int:
+        code = LSAS_OK
+        if getattr(self, "_h", None):
+            code = lsas_server_destroy(self._h)
+            self._h = None
+            self._live.clear()
+        return code
 
     def __del__(self):
         try:

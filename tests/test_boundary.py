@@ -92,3 +92,15 @@ def test_plan_create_without_gpu_fails_cleanly(L):
     assert h.value is None
     # invalid arguments are rejected before CUDA is touched
     assert L.lsas_plan_create(8, 63, 16, 4, 0, 4, C.byref(h)) == L.LSAS_ERR_INVALID_ARG
+
+
+def test_server_needs_a_gpu_and_valid_arguments(L):
+    import torch
+    h = C.c_void_p()
+    assert L.lsas_server_create(1 << 30, 0, 10.0, C.byref(h)) == L.LSAS_ERR_INVALID_ARG
+    assert L.lsas_server_create(1 << 30, 8, -1.0, C.byref(h)) == L.LSAS_ERR_INVALID_ARG
+    assert L.lsas_server_wait(None, 1, 1.0, None) == L.LSAS_ERR_INVALID_ARG
+    assert L.lsas_server_destroy(None) == L.LSAS_ERR_INVALID_ARG
+    if not torch.cuda.is_available():
+        assert L.lsas_server_create(1 << 30, 8, 10.0, C.byref(h)) == L.LSAS_ERR_CUDA
+        assert h.value is None
