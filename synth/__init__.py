@@ -17,7 +17,8 @@ and a random delay before it.
 from .frames import (FrameConfig, FrameBatch, generate, qam_map, gray_levels,
                      CONFIGS, config_by_name)
 from .capture import CaptureBatch, generate_capture, pn_sequence, PN_LEN
+from .lsdomain import ls_pairs
 
 __all__ = ["FrameConfig", "FrameBatch", "generate", "qam_map", "gray_levels",
            "CONFIGS", "config_by_name", "CaptureBatch", "generate_capture",
-           "pn_sequence", "PN_LEN"]
+           "pn_sequence", "PN_LEN", "ls_pairs"]

@@ -1,0 +1,77 @@
+"""Pins of the FP64 denoiser reference (oracle/denoiser.py).
+
+* conv equals numpy's correlation of the zero-padded row (the definition, by
+  an independent library routine), channel by channel.
+* With every weight zero the residual network is the identity.
+* The backward pass equals central finite differences of the forward pass
+  (sampled parameters, tiny rows), and the MSE gradient likewise.
+* Adam's first step from a zero state moves each parameter by
+  lr * g / (|g| + eps).
+* The LS-domain pairs have unit expected channel power and LS error
+  variance sigma^2.
+"""
+
+import numpy as np
+
+from oracle import denoiser as dn
+import synth
+
+
+def test_conv_is_padded_correlation():
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((2, 3, 17))
+    W = rng.standard_normal((4, 3, 5))
+    b = rng.standard_normal(4)
+    out = dn.conv(x, W, b)
+    for r in range(2):
+        for o in range(4):
+            want = b[o] + sum(np.correlate(np.pad(x[r, c], 2), W[o, c], "valid") for c in range(3))
+            assert np.allclose(out[r, o], want, rtol=1e-12, atol=1e-12)
+
+
+def test_zero_weights_are_identity():
+    rng = np.random.default_rng(2)
+    H = rng.standard_normal((3, 32)) + 1j * rng.standard_normal((3, 32))
+    assert np.allclose(dn.apply(np.zeros(dn.n_params()), H), H, rtol=1e-13)
+    assert dn.n_params() == 10978
+
+
+def test_backward_matches_finite_differences():
+    rng = np.random.default_rng(3)
+    params = dn.init_params(7) * 3.0
+    x0 = rng.standard_normal((2, 2, 12))
+    t = rng.standard_normal((2, 2, 12))
+
+    def loss(p):
+        y, _ = dn.forward(p, x0)
+        return dn.mse(y, t)[0]
+
+    y, cache = dn.forward(params, x0)
+    _, dy = dn.mse(y, t)
+    g = dn.backward(params, cache, dy)
+    idx = rng.choice(params.size, 300, replace=False)
+    h = 1e-6
+    for i in idx:
+        e = np.zeros_like(params)
+        e[i] = h
+        fd = (loss(params + e) - loss(params - e)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)) + 1e-9, (i, fd, g[i])
+
+
+def test_mse_gradient_and_adam_first_step():
+    rng = np.random.default_rng(4)
+    y, t = rng.standard_normal(50), rng.standard_normal(50)
+    L, d = dn.mse(y, t)
+    e = np.zeros(50)
+    e[7] = 1e-7
+    assert np.isclose((dn.mse(y + e, t)[0] - dn.mse(y - e, t)[0]) / 2e-7, d[7], rtol=1e-6)
+    p, g = rng.standard_normal(20), rng.standard_normal(20)
+    p1, m, v = dn.adam(p, g, np.zeros(20), np.zeros(20), 1, lr=0.01, eps=1e-8)
+    assert np.allclose(p1, p - 0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12)
+
+
+def test_ls_pairs_statistics():
+    H, Hls, snr = synth.ls_pairs(400, 256, snr_db_range=(10.0, 10.0), seed=5)
+    assert abs(np.mean(np.abs(H) ** 2) - 1.0) < 0.1
+    err = np.mean(np.abs(Hls - H) ** 2)
+    assert abs(err - 0.1) < 0.005          # sigma^2 = 10^-1
