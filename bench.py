@@ -59,6 +59,10 @@ def parse():
                     help="serving-loop report: latency vs offered load (one JSON line per load)")
     ap.add_argument("--serving-loads", default="1,5,10,20,40", help="offered loads, G samples/s")
     ap.add_argument("--serving-seconds", type=float, default=2.0)
+    ap.add_argument("--denoiser", action="store_true",
+                    help="learned LS refinement: train, then MSE/BER against plain LS per SNR")
+    ap.add_argument("--denoiser-rows", type=int, default=200_000)
+    ap.add_argument("--denoiser-ckpt", default="")
     return ap.parse_args()
 
 
@@ -342,11 +346,68 @@ def serving_report(args):
         raise RuntimeError(f"server reported {lsas.lsas_status_str(code).decode()}")
 
 
+def denoiser_report(args):
+    """Train the LS refinement on LS-domain rows (N = 1024, 4..16 taps,
+    1..3 dB/tap, SNR U[0, 30] dB), then per SNR in {0, 5, 10, 20, 30} dB run
+    16 frames of 64 antennas, N = 1024, 16-QAM (8 taps, 2 dB/tap, sc16)
+    through lsas_run_frame (plain LS) and through lsas_estimate -> refinement
+    (bf16 weights) -> lsas_demodulate; report channel MSE against the true
+    channel, bit error rate against the transmitted bits, and device time of
+    the refinement per frame."""
+    import torch
+    import paper_1901_07499_gb300.lsas as lsas
+    import paper_1901_07499_gb300.denoiser as dnm
+    t0 = time.perf_counter()
+    losses = []
+    dn = dnm.train(rows=args.denoiser_rows, N=1024, batch=256, epochs=1, lr=1e-3, seed=1,
+                   log=lambda ep, rows, loss: losses.append(loss))
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "denoiser-train", "rows": dn.rows_seen, "steps": dn.step,
+                      "final_loss": losses[-1], "first_chunk_loss": losses[0],
+                      "seconds": time.perf_counter() - t0, "params": lsas.LSAS_DN_PARAMS,
+                      "data": "synthetic LS-domain pairs (synth.ls_pairs)"}))
+    sys.stdout.flush()
+    if args.denoiser_ckpt:
+        dn.save(args.denoiser_ckpt)
+    pb = dn.bf16_params()
+    F = 16
+    for snr in (0.0, 5.0, 10.0, 20.0, 30.0):
+        cfg = synth.frames.sweep_config(64, 1024).replace(Q=16, taps=8, decay_db=2.0, snr_db=snr, F=F,
+                                                           name=f"denoiser_eval_{int(snr)}dB")
+        b = synth.generate(cfg, frame_ids=range(F))
+        plan = lsas.Plan(cfg.M, cfg.N, cfg.cp, cfg.S, cfg.pilot_idx, cfg.Q, fmt=cfg.fmt,
+                         max_frames=F, pilot=b.pilot)
+        x = torch.from_numpy(np.ascontiguousarray(b.frames)).cuda()
+        H_ls, bits_ls, _ = plan.run_frame(x)
+        H_dn = dn.apply(H_ls, params_bf16=pb)
+        bits_dn, _ = plan.demodulate(x, H_dn)
+        plan.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(5):
+            dn.apply(H_ls, out=H_dn, params_bf16=pb)
+        e1.record()
+        torch.cuda.synchronize()
+        Htrue = np.fft.fft(b.taps, cfg.N, axis=-1) * b.gain[:, None, None]
+        def mse(Hg):
+            return float(np.mean(np.abs(Hg.cpu().numpy() - Htrue) ** 2) / np.mean(np.abs(Htrue) ** 2))
+        def ber(bits):
+            got = np.unpackbits(bits.cpu().numpy(), axis=-1, bitorder="big")[:, :cfg.D * cfg.N * cfg.q]
+            return float(np.mean(got != b.bits.reshape(F, -1)))
+        print(json.dumps({"mode": "denoiser-eval", "snr_db": snr, "frames": F, "M": cfg.M, "N": cfg.N,
+                          "qam": cfg.Q, "nmse_ls": mse(H_ls), "nmse_dn": mse(H_dn),
+                          "ber_ls": ber(bits_ls), "ber_dn": ber(bits_dn),
+                          "refine_us_per_frame": 1e3 * e0.elapsed_time(e1) / 5 / F}))
+        sys.stdout.flush()
+
+
 def main():
     args = parse()
     cfg = synth.config_by_name(args.config)
     if args.serving:
         return serving_report(args)
+    if args.denoiser:
+        return denoiser_report(args)
     if args.impl == "reference":
         return reference_arm(args, cfg)
 

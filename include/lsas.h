@@ -304,6 +304,36 @@ lsas_status lsas_server_stats(lsas_server server, uint64_t out[4]);
 lsas_status lsas_server_destroy(lsas_server server);
 
 /*
+ * Learned refinement of the LS channel estimate (Sec. II-C's LS estimate is
+ * its input and remains the fallback).  Rows are antenna rows of N
+ * subcarriers (R = F*M for a [F][M][N] H); N a multiple of 128 in
+ * [128, 2048].  Per row: normalise by the RMS of the row, a residual 1-D
+ * convolutional network over subcarriers (2 -> 32 -> 32 -> 32 -> 2
+ * channels, kernel 5, ReLU), denormalise.  Parameters: one float vector of
+ * LSAS_DN_PARAMS values, W1[32][2][5] b1[32] W2[32][32][5] b2[32]
+ * W3[32][32][5] b3[32] W4[2][32][5] b4[2]; the bf16 form has the same order.
+ * d_work: caller-owned device scratch of lsas_dn_work_size floats.
+ *   lsas_dn_apply  d_H [R][N] complex -> d_Hout [R][N] complex (may not
+ *                  alias d_H); bf16 != 0 reads bf16 parameters; fp32 sums.
+ *   lsas_dn_grad   mean squared error between the network output and the
+ *                  true rows d_Htrue normalised by the same RMS -> d_loss[0]
+ *                  and the gradient d_grad [LSAS_DN_PARAMS].
+ *   lsas_dn_adam   one Adam step (beta1 0.9, beta2 0.999, eps 1e-8; step
+ *                  counted from 1) on parameters, first and second moments.
+ *   lsas_dn_to_bf16  round the parameters to bf16 (nearest even).
+ * Errors: INVALID_ARG for bad sizes or null pointers.  Asynchronous.
+ */
+#define LSAS_DN_PARAMS 10978
+lsas_status lsas_dn_work_size(int R, int N, size_t* floats);
+lsas_status lsas_dn_apply(const void* d_params, int bf16, const float* d_H, int R, int N,
+                          float* d_work, float* d_Hout, void* stream);
+lsas_status lsas_dn_grad(const float* d_params, const float* d_Hls, const float* d_Htrue, int R,
+                         int N, float* d_work, float* d_grad, float* d_loss, void* stream);
+lsas_status lsas_dn_adam(float* d_params, const float* d_grad, float* d_m, float* d_v, int step,
+                         float lr, void* stream);
+lsas_status lsas_dn_to_bf16(const float* d_params, uint16_t* d_params_bf16, void* stream);
+
+/*
  * Size of the library's fixed device scratch used by
  * lsas_run_frame_split_static (16 MiB per device).
  */

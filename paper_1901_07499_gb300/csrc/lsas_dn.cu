@@ -1,0 +1,370 @@
+// lsas_dn.cu -- learned refinement of the LS channel estimate (Sec. II-C's
+// LS is the input, the fallback and the yardstick).
+//
+// Per antenna row of N subcarriers: normalise H_LS by its RMS, run a residual
+// 1-D convolutional network over subcarriers (2 -> 32 -> 32 -> 32 -> 2
+// channels, kernel 5, ReLU, output added to the input), denormalise.  The
+// same kernels train it: forward with cached pre-activations, mean squared
+// error against the normalised true channel, backward (data gradients as
+// forward convolutions with transposed, flipped weights and ReLU masks;
+// weight gradients as fixed-order block reductions) and Adam.  Inference can
+// read bf16 weights; every sum is fp32.
+//
+// Layouts: activations [R][C][N] float; parameters one float vector
+// W1[32][2][5] b1[32] W2[32][32][5] b2[32] W3[32][32][5] b3[32] W4[2][32][5]
+// b4[2] (10978 values).
+#include <cuda_bf16.h>
+
+#include "lsas.h"
+#include "lsas_kernels.cuh"
+
+namespace lsas {
+
+constexpr int kDnK = 5;
+constexpr int kDnPos = 128;   // subcarriers per block of the conv kernels
+constexpr int kDnParams = 10978;
+constexpr int kOffW1 = 0, kOffB1 = 320, kOffW2 = 352, kOffB2 = 5472, kOffW3 = 5504,
+              kOffB3 = 10624, kOffW4 = 10656, kOffB4 = 10976;
+
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// out[r][o][p] = mask? (pre[r][o][p] > 0) * (b[o] + sum_c sum_k W[o][c][k] in'[r][c][p+k-2]) + res
+// with in' = relu(in) when relu_in.  grid (R, N / kDnPos), kDnPos threads.
+template <int CIN, int COUT, typename WT>
+__global__ void __launch_bounds__(kDnPos) dn_conv_kernel(const float* __restrict__ in,
+                                                         const WT* __restrict__ W,
+                                                         const WT* __restrict__ b, int relu_in,
+                                                         const float* __restrict__ pre,
+                                                         const float* __restrict__ res,
+                                                         float* __restrict__ out, int N) {
+  __shared__ float ws[COUT * CIN * kDnK];
+  __shared__ float xs[CIN][kDnPos + kDnK - 1];
+  const int r = blockIdx.x;
+  const int p0 = blockIdx.y * kDnPos;
+  const int t = threadIdx.x;
+  for (int i = t; i < COUT * CIN * kDnK; i += kDnPos) ws[i] = to_f(W[i]);
+  const float* inr = in + static_cast<size_t>(r) * CIN * N;
+  for (int i = t; i < CIN * (kDnPos + kDnK - 1); i += kDnPos) {
+    const int c = i / (kDnPos + kDnK - 1), j = i % (kDnPos + kDnK - 1);
+    const int p = p0 + j - 2;
+    float v = (p >= 0 && p < N) ? inr[static_cast<size_t>(c) * N + p] : 0.f;
+    if (relu_in) v = fmaxf(v, 0.f);
+    xs[c][j] = v;
+  }
+  __syncthreads();
+  float acc[COUT];
+#pragma unroll
+  for (int o = 0; o < COUT; ++o) acc[o] = b ? to_f(b[o]) : 0.f;
+#pragma unroll 4
+  for (int c = 0; c < CIN; ++c) {
+#pragma unroll
+    for (int k = 0; k < kDnK; ++k) {
+      const float x = xs[c][t + k];
+#pragma unroll
+      for (int o = 0; o < COUT; ++o) acc[o] = fmaf(ws[(o * CIN + c) * kDnK + k], x, acc[o]);
+    }
+  }
+  const size_t base = static_cast<size_t>(r) * COUT * N + p0 + t;
+#pragma unroll
+  for (int o = 0; o < COUT; ++o) {
+    float v = acc[o];
+    if (pre) v = pre[base + static_cast<size_t>(o) * N] > 0.f ? v : 0.f;
+    if (res) v += res[base + static_cast<size_t>(o) * N];
+    out[base + static_cast<size_t>(o) * N] = v;
+  }
+}
+
+// W'[c][o][k] = W[o][c][4 - k]: data gradient of a conv as a forward conv.
+__global__ void dn_wt_kernel(const float* W, float* Wt, int cin, int cout) {
+  const int n = cin * cout * kDnK;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int k = i % kDnK, o = (i / kDnK) % cout, c = i / (kDnK * cout);
+    Wt[i] = W[(o * cin + c) * kDnK + (kDnK - 1 - k)];
+  }
+}
+
+// dW[o][c][k] = sum_r sum_p dout[r][o][p] in'[r][c][p + k - 2] and, for
+// c = 0, db[o] = sum dout[r][o][p].  One block per (o, c), fixed-order tree.
+constexpr int kDnGradThreads = 256;
+__global__ void __launch_bounds__(kDnGradThreads) dn_wgrad_kernel(
+    const float* __restrict__ dout, const float* __restrict__ in, int relu_in, int cin, int cout,
+    int R, int N, float* __restrict__ dW, float* __restrict__ db) {
+  __shared__ float red[kDnK + 1][kDnGradThreads];
+  const int o = blockIdx.x, c = blockIdx.y, t = threadIdx.x;
+  float acc[kDnK + 1] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  const size_t total = static_cast<size_t>(R) * N;
+  for (size_t i = t; i < total; i += kDnGradThreads) {
+    const int r = static_cast<int>(i / N), p = static_cast<int>(i % N);
+    const float g = dout[(static_cast<size_t>(r) * cout + o) * N + p];
+    const float* x = in + (static_cast<size_t>(r) * cin + c) * N;
+#pragma unroll
+    for (int k = 0; k < kDnK; ++k) {
+      const int q = p + k - 2;
+      float v = (q >= 0 && q < N) ? x[q] : 0.f;
+      if (relu_in) v = fmaxf(v, 0.f);
+      acc[k] = fmaf(g, v, acc[k]);
+    }
+    acc[kDnK] += g;
+  }
+#pragma unroll
+  for (int k = 0; k <= kDnK; ++k) red[k][t] = acc[k];
+  __syncthreads();
+  for (int s = kDnGradThreads / 2; s > 0; s >>= 1) {
+    if (t < s) {
+#pragma unroll
+      for (int k = 0; k <= kDnK; ++k) red[k][t] += red[k][t + s];
+    }
+    __syncthreads();
+  }
+  if (t < kDnK) dW[(o * cin + c) * kDnK + t] = red[t][0];
+  if (t == 0 && c == 0) db[o] = red[kDnK][0];
+}
+
+// x0 = [Re H, Im H] / rms and, when Ht is given, t = [Re Ht, Im Ht] / rms;
+// rms over the row of H.  One block per row.
+__global__ void dn_prepare_kernel(const float2* H, const float2* Ht, int N, float* x0, float* tt,
+                                  float* rms) {
+  __shared__ float red[256];
+  const int r = blockIdx.x, t = threadIdx.x;
+  const float2* h = H + static_cast<size_t>(r) * N;
+  float s = 0.f;
+  for (int k = t; k < N; k += 256) s = fmaf(h[k].x, h[k].x, fmaf(h[k].y, h[k].y, s));
+  red[t] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (t < w) red[t] += red[t + w];
+    __syncthreads();
+  }
+  const float rr = sqrtf(red[0] / N);
+  const float inv = rr > 0.f ? 1.0f / rr : 0.f;
+  if (t == 0) rms[r] = rr;
+  float* x = x0 + static_cast<size_t>(r) * 2 * N;
+  for (int k = t; k < N; k += 256) {
+    x[k] = h[k].x * inv;
+    x[N + k] = h[k].y * inv;
+  }
+  if (Ht) {
+    const float2* g = Ht + static_cast<size_t>(r) * N;
+    float* y = tt + static_cast<size_t>(r) * 2 * N;
+    for (int k = t; k < N; k += 256) {
+      y[k] = g[k].x * inv;
+      y[N + k] = g[k].y * inv;
+    }
+  }
+}
+
+// H = (y[0] + j y[1]) rms
+__global__ void dn_finish_kernel(const float* y, const float* rms, int R, int N, float2* H) {
+  const size_t n = static_cast<size_t>(R) * N;
+  for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int r = static_cast<int>(i / N), k = static_cast<int>(i % N);
+    const float* yr = y + static_cast<size_t>(r) * 2 * N;
+    H[i] = make_float2(yr[k] * rms[r], yr[N + k] * rms[r]);
+  }
+}
+
+// dy = 2 (y - t) / n, per-block partial sums of (y - t)^2
+constexpr int kDnLossBlocks = 256;
+__global__ void dn_loss_kernel(const float* y, const float* tt, size_t n, float* dy, float* part) {
+  __shared__ float red[256];
+  const int t = threadIdx.x;
+  float s = 0.f;
+  const float sc = 2.0f / static_cast<float>(n);
+  for (size_t i = blockIdx.x * static_cast<size_t>(256) + t; i < n; i += static_cast<size_t>(gridDim.x) * 256) {
+    const float d = y[i] - tt[i];
+    dy[i] = sc * d;
+    s = fmaf(d, d, s);
+  }
+  red[t] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (t < w) red[t] += red[t + w];
+    __syncthreads();
+  }
+  if (t == 0) part[blockIdx.x] = red[0];
+}
+__global__ void dn_loss_final_kernel(const float* part, int nb, size_t n, float* loss) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    float s = 0.f;
+    for (int i = 0; i < nb; ++i) s += part[i];
+    *loss = s / static_cast<float>(n);
+  }
+}
+
+__global__ void dn_adam_kernel(float* p, const float* g, float* m, float* v, int n, float lr,
+                               float b1, float b2, float eps, float c1, float c2) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+__global__ void dn_bf16_kernel(const float* p, __nv_bfloat16* q, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    q[i] = __float2bfloat16_rn(p[i]);
+}
+
+// ------------------------------------------------------------- host side
+
+// Work buffer (floats): x0, t, y, dy [R][2][N]; a1, a2, a3, g1, g2 [R][32][N];
+// rms [R]; transposed weights [5120]; loss partials.
+struct DnWork {
+  float *x0, *tt, *y, *dy, *a1, *a2, *a3, *g1, *g2, *rms, *wt, *part;
+};
+size_t dn_work_floats(int R, int N) {
+  return static_cast<size_t>(R) * N * (4 * 2 + 5 * 32) + R + 5120 + kDnLossBlocks;
+}
+static DnWork dn_work(float* w, int R, int N) {
+  DnWork d;
+  const size_t s2 = static_cast<size_t>(R) * 2 * N, s32 = static_cast<size_t>(R) * 32 * N;
+  d.x0 = w; d.tt = d.x0 + s2; d.y = d.tt + s2; d.dy = d.y + s2;
+  d.a1 = d.dy + s2; d.a2 = d.a1 + s32; d.a3 = d.a2 + s32; d.g1 = d.a3 + s32; d.g2 = d.g1 + s32;
+  d.rms = d.g2 + s32; d.wt = d.rms + R; d.part = d.wt + 5120;
+  return d;
+}
+
+template <int CIN, int COUT, typename WT>
+static void conv(const float* in, const WT* W, const WT* b, int relu_in, const float* pre,
+                 const float* res, float* out, int R, int N, cudaStream_t st) {
+  dn_conv_kernel<CIN, COUT, WT><<<dim3(R, N / kDnPos), kDnPos, 0, st>>>(in, W, b, relu_in, pre, res,
+                                                                       out, N);
+}
+
+template <typename WT>
+static void forward(const WT* P, const DnWork& d, int R, int N, cudaStream_t st) {
+  conv<2, 32, WT>(d.x0, P + kOffW1, P + kOffB1, 0, nullptr, nullptr, d.a1, R, N, st);
+  conv<32, 32, WT>(d.a1, P + kOffW2, P + kOffB2, 1, nullptr, nullptr, d.a2, R, N, st);
+  conv<32, 32, WT>(d.a2, P + kOffW3, P + kOffB3, 1, nullptr, nullptr, d.a3, R, N, st);
+  conv<32, 2, WT>(d.a3, P + kOffW4, P + kOffB4, 1, nullptr, d.x0, d.y, R, N, st);
+}
+
+cudaError_t dn_apply(const void* params, bool bf16, const float2* H, int R, int N, float* work,
+                     float2* Hout, int sms, cudaStream_t st) {
+  const DnWork d = dn_work(work, R, N);
+  dn_prepare_kernel<<<R, 256, 0, st>>>(H, nullptr, N, d.x0, nullptr, d.rms);
+  if (bf16) forward(static_cast<const __nv_bfloat16*>(params), d, R, N, st);
+  else forward(static_cast<const float*>(params), d, R, N, st);
+  const size_t n = static_cast<size_t>(R) * N;
+  const int fg = static_cast<int>((n + 255) / 256 < static_cast<size_t>(sms) * 8 ? (n + 255) / 256 : sms * 8);
+  dn_finish_kernel<<<fg, 256, 0, st>>>(d.y, d.rms, R, N, Hout);
+  return cudaGetLastError();
+}
+
+cudaError_t dn_grad(const float* P, const float2* Hls, const float2* Ht, int R, int N, float* work,
+                    float* grad, float* loss, cudaStream_t st) {
+  const DnWork d = dn_work(work, R, N);
+  dn_prepare_kernel<<<R, 256, 0, st>>>(Hls, Ht, N, d.x0, d.tt, d.rms);
+  forward(P, d, R, N, st);
+  const size_t n = static_cast<size_t>(R) * 2 * N;
+  dn_loss_kernel<<<kDnLossBlocks, 256, 0, st>>>(d.y, d.tt, n, d.dy, d.part);
+  dn_loss_final_kernel<<<1, 32, 0, st>>>(d.part, kDnLossBlocks, n, loss);
+  // layer 4: input relu(a3); dy -> g1 = d a3 (masked by a3 > 0)
+  dn_wgrad_kernel<<<dim3(2, 32), kDnGradThreads, 0, st>>>(d.dy, d.a3, 1, 32, 2, R, N, grad + kOffW4,
+                                                          grad + kOffB4);
+  dn_wt_kernel<<<8, 256, 0, st>>>(P + kOffW4, d.wt, 32, 2);
+  conv<2, 32, float>(d.dy, d.wt, nullptr, 0, d.a3, nullptr, d.g1, R, N, st);
+  // layer 3: input relu(a2); g1 -> g2 = d a2
+  dn_wgrad_kernel<<<dim3(32, 32), kDnGradThreads, 0, st>>>(d.g1, d.a2, 1, 32, 32, R, N,
+                                                           grad + kOffW3, grad + kOffB3);
+  dn_wt_kernel<<<20, 256, 0, st>>>(P + kOffW3, d.wt, 32, 32);
+  conv<32, 32, float>(d.g1, d.wt, nullptr, 0, d.a2, nullptr, d.g2, R, N, st);
+  // layer 2: input relu(a1); g2 -> g1 = d a1
+  dn_wgrad_kernel<<<dim3(32, 32), kDnGradThreads, 0, st>>>(d.g2, d.a1, 1, 32, 32, R, N,
+                                                           grad + kOffW2, grad + kOffB2);
+  dn_wt_kernel<<<20, 256, 0, st>>>(P + kOffW2, d.wt, 32, 32);
+  conv<32, 32, float>(d.g2, d.wt, nullptr, 0, d.a1, nullptr, d.g1, R, N, st);
+  // layer 1: input x0
+  dn_wgrad_kernel<<<dim3(32, 2), kDnGradThreads, 0, st>>>(d.g1, d.x0, 0, 2, 32, R, N,
+                                                          grad + kOffW1, grad + kOffB1);
+  return cudaGetLastError();
+}
+
+cudaError_t dn_adam(float* p, const float* g, float* m, float* v, int step, float lr, float b1,
+                    float b2, float eps, cudaStream_t st) {
+  const float c1 = 1.f - powf(b1, static_cast<float>(step));
+  const float c2 = 1.f - powf(b2, static_cast<float>(step));
+  dn_adam_kernel<<<44, 256, 0, st>>>(p, g, m, v, kDnParams, lr, b1, b2, eps, c1, c2);
+  return cudaGetLastError();
+}
+
+cudaError_t dn_to_bf16(const float* p, void* q, cudaStream_t st) {
+  dn_bf16_kernel<<<44, 256, 0, st>>>(p, static_cast<__nv_bfloat16*>(q), kDnParams);
+  return cudaGetLastError();
+}
+
+}  // namespace lsas
+
+namespace {
+lsas_status dn_check(int R, int N) {
+  if (R < 1 || N < 128 || N > 2048 || N % 128 != 0) return LSAS_ERR_INVALID_ARG;
+  return LSAS_OK;
+}
+int dn_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = 1;
+  }
+  return sms;
+}
+}  // namespace
+
+extern "C" {
+
+lsas_status lsas_dn_work_size(int R, int N, size_t* floats) {
+  if (!floats) return LSAS_ERR_INVALID_ARG;
+  const lsas_status s = dn_check(R, N);
+  if (s != LSAS_OK) return s;
+  *floats = lsas::dn_work_floats(R, N);
+  return LSAS_OK;
+}
+
+lsas_status lsas_dn_apply(const void* d_params, int bf16, const float* d_H, int R, int N,
+                          float* d_work, float* d_Hout, void* stream) {
+  const lsas_status s = dn_check(R, N);
+  if (s != LSAS_OK) return s;
+  if (!d_params || !d_H || !d_work || !d_Hout) return LSAS_ERR_INVALID_ARG;
+  if (lsas::dn_apply(d_params, bf16 != 0, reinterpret_cast<const float2*>(d_H), R, N, d_work,
+                     reinterpret_cast<float2*>(d_Hout), dn_sms(),
+                     static_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return LSAS_ERR_CUDA;
+  return LSAS_OK;
+}
+
+lsas_status lsas_dn_grad(const float* d_params, const float* d_Hls, const float* d_Htrue, int R,
+                         int N, float* d_work, float* d_grad, float* d_loss, void* stream) {
+  const lsas_status s = dn_check(R, N);
+  if (s != LSAS_OK) return s;
+  if (!d_params || !d_Hls || !d_Htrue || !d_work || !d_grad || !d_loss) return LSAS_ERR_INVALID_ARG;
+  if (lsas::dn_grad(d_params, reinterpret_cast<const float2*>(d_Hls),
+                    reinterpret_cast<const float2*>(d_Htrue), R, N, d_work, d_grad, d_loss,
+                    static_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return LSAS_ERR_CUDA;
+  return LSAS_OK;
+}
+
+lsas_status lsas_dn_adam(float* d_params, const float* d_grad, float* d_m, float* d_v, int step,
+                         float lr, void* stream) {
+  if (!d_params || !d_grad || !d_m || !d_v || step < 1 || !(lr > 0.f)) return LSAS_ERR_INVALID_ARG;
+  if (lsas::dn_adam(d_params, d_grad, d_m, d_v, step, lr, 0.9f, 0.999f, 1e-8f,
+                    static_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return LSAS_ERR_CUDA;
+  return LSAS_OK;
+}
+
+lsas_status lsas_dn_to_bf16(const float* d_params, uint16_t* d_params_bf16, void* stream) {
+  if (!d_params || !d_params_bf16) return LSAS_ERR_INVALID_ARG;
+  if (lsas::dn_to_bf16(d_params, d_params_bf16, static_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return LSAS_ERR_CUDA;
+  return LSAS_OK;
+}
+
+}  // extern "C"

@@ -35,6 +35,7 @@ LSAS_ERR_TIMEOUT = 6
 LSAS_ERR_DEVICE = 7
 LSAS_STATIC_SCRATCH_BYTES = 16 << 20
 LSAS_SHIFT_H, LSAS_SHIFT_EQ, LSAS_SHIFT_Y, LSAS_SHIFT_BITS = 0, 1, 2, 3
+LSAS_DN_PARAMS = 10978
 LSAS_IN_SC16 = 0
 LSAS_IN_FC32 = 1
 
@@ -77,6 +78,11 @@ lsas_server_submit = _proto("lsas_server_submit",
 lsas_server_wait = _proto("lsas_server_wait", [_vp, C.c_uint64, C.c_double, C.POINTER(C.c_double)])
 lsas_server_stats = _proto("lsas_server_stats", [_vp, C.POINTER(C.c_uint64)])
 lsas_server_destroy = _proto("lsas_server_destroy", [_vp])
+lsas_dn_work_size = _proto("lsas_dn_work_size", [_i, _i, C.POINTER(C.c_size_t)])
+lsas_dn_apply = _proto("lsas_dn_apply", [_vp, _i, _vp, _i, _i, _vp, _vp, _vp])
+lsas_dn_grad = _proto("lsas_dn_grad", [_vp, _vp, _vp, _i, _i, _vp, _vp, _vp, _vp])
+lsas_dn_adam = _proto("lsas_dn_adam", [_vp, _vp, _vp, _vp, _i, C.c_float, _vp])
+lsas_dn_to_bf16 = _proto("lsas_dn_to_bf16", [_vp, _vp, _vp])
 lsas_plan_sync = _proto("lsas_plan_sync", [_vp, _vp])
 lsas_plan_info = _proto("lsas_plan_info", [_vp, C.POINTER(_i)])
 lsas_plan_destroy = _proto("lsas_plan_destroy", [_vp])
@@ -89,6 +95,8 @@ EXPORTED = ["lsas_status_str", "lsas_check_config", "lsas_frame_bytes",
             "lsas_plan_set_pn", "lsas_pn_sync", "lsas_pn_extract", "lsas_fftshift",
             "lsas_server_create", "lsas_server_register", "lsas_server_submit",
             "lsas_server_wait", "lsas_server_stats", "lsas_server_destroy",
+            "lsas_dn_work_size", "lsas_dn_apply", "lsas_dn_grad", "lsas_dn_adam",
+            "lsas_dn_to_bf16",
             "lsas_plan_sync", "lsas_plan_info",
             "lsas_plan_destroy"]
 

@@ -27,7 +27,7 @@ def declared_functions():
     with open(os.path.join(ROOT, "include", "lsas.h")) as fh:
         text = fh.read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(lsas_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(lsas_[a-z_0-9]+)\s*\(", text)))
 
 
 def test_library_exports_every_declared_function(L):
