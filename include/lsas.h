@@ -19,7 +19,8 @@
  *
  * Conventions fixed by this library where the paper leaves them open:
  *   - forward FFT kernel exp(-2j pi k n / N), unitary scale 1/sqrt(N);
- *     subcarriers in natural order k = 0 .. N-1 (no fftshift);
+ *     subcarriers in natural order k = 0 .. N-1 (lsas_fftshift reorders
+ *     outputs the way the paper does);
  *   - LS for a general pilot: H = Y conj(X) / |X|^2;
  *   - normalised MRC: z[d,k] = sum_m conj(H[m,k]) Y[m,d,k] / sum_m |H[m,k]|^2;
  *   - square Gray QAM of unit average energy: per axis L = sqrt(Q) levels at
@@ -332,6 +333,18 @@ lsas_status lsas_dn_grad(const float* d_params, const float* d_Hls, const float*
 lsas_status lsas_dn_adam(float* d_params, const float* d_grad, float* d_m, float* d_v, int step,
                          float lr, void* stream);
 lsas_status lsas_dn_to_bf16(const float* d_params, uint16_t* d_params_bf16, void* stream);
+
+/*
+ * Test hook of failure detection (no counterpart in the paper).  Every wait
+ * of the fused kernel on a staging copy is bounded (~2 s, %globaltimer):
+ * when it runs out the block latches LSAS_ERR_TIMEOUT, stops issuing
+ * copies, skips its remaining waits and finishes.  kind = 1 makes that
+ * happen without any fault: block 0's first staging phase also waits for 16
+ * bytes that no copy delivers.  kind = 0 (the default) turns it off.
+ * Applies to the per-warp fused kernel (N <= 1024).  INVALID_ARG for other
+ * kinds.
+ */
+lsas_status lsas_plan_set_fault(lsas_plan plan, int kind);
 
 /*
  * Size of the library's fixed device scratch used by

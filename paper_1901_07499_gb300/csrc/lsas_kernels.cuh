@@ -70,6 +70,7 @@ struct KParams {
   int* offsets;          //   per frame: detected preamble start (out)
   float* peaks;          //   per frame: correlation power at it (out, nullable)
   const int* offsets_in; //   per frame: preamble start (extraction)
+  int fault;             // test hook: 1 = block 0 waits for 16 bytes that never come
   int chunks;            // ceil(M / A)
   int groups, dg;        // data-symbol groups per frame, data symbols per group
   int mode;              // kModeDemod, kModeRun or kModePartial (frame_kernel)
@@ -245,6 +246,10 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
                "r"(bytes)
                : "memory");
+}
+// Raise the byte count a phase waits for, without arriving.
+__device__ __forceinline__ void mbar_expect_tx_only(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src,
                                           uint32_t bytes, uint32_t bar,

@@ -76,6 +76,7 @@ struct lsas_plan_s {
   // packet detection: PN chips (lsas_plan_set_pn)
   float* d_pn = nullptr;
   int pn_len = 0;
+  int fault = 0;   // test hook of the bounded waits (lsas_plan_set_fault)
   Geometry geo;
   LaunchFn launch = nullptr;
   // host-transfer staging (lsas_run_frame_host), allocated on first use
@@ -232,6 +233,7 @@ void base_params(lsas_plan p, KParams* k) {
   k->twP = p->d_twP;
   k->xinv = p->d_xinv;
   k->status = p->d_status;
+  k->fault = p->fault;
   k->M = p->M;
   k->m0 = 0;
   k->Mtot = p->M;
@@ -748,6 +750,12 @@ lsas_status lsas_fftshift(lsas_plan p, int what, void* d_buf, int n_frames, void
   if (launch_shift(d_buf, kind, rows, p->N, p->N * p->q / 8, p->sms,
                    static_cast<cudaStream_t>(stream)) != cudaSuccess)
     return LSAS_ERR_CUDA;
+  return LSAS_OK;
+}
+
+lsas_status lsas_plan_set_fault(lsas_plan p, int kind) {
+  if (!p || kind < 0 || kind > 1) return LSAS_ERR_INVALID_ARG;
+  p->fault = kind;
   return LSAS_OK;
 }
 

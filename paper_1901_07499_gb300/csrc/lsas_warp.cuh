@@ -112,6 +112,7 @@ __global__ void __launch_bounds__(32 * wgeo_warps(FC32 ? 8 : 4), 1) warp_kernel(
   // sharing a scheduler tend to be in different phases of their steps
   if (warp >= 4) __nanosleep(1400);
   int step = 0;    // this warp's step counter over the whole frame
+  int issued = 0;  // steps whose copies this warp has issued
   int slot = 0;    // ring slot of the next step to consume (step % K) ...
   int phase = 0;   // ... and its mbarrier phase ((step / K) & 1)
   for (int g = 0; g < p.groups; ++g) {
@@ -131,7 +132,7 @@ __global__ void __launch_bounds__(32 * wgeo_warps(FC32 ? 8 : 4), 1) warp_kernel(
     // many steps of this group are still to be staged
     int ic = 0, iit = 0;
     int to_issue = nch * items;
-    if (p.use_tma) {
+    if (p.use_tma && !*abort_flag) {
       // the ring held generic data (last group's reduction): order it before
       // the copies, then fill the first K slots of this group
       fence_proxy_async();
@@ -140,6 +141,11 @@ __global__ void __launch_bounds__(32 * wgeo_warps(FC32 ? 8 : 4), 1) warp_kernel(
         wissue<LOG2N, FC32>(p, f, warp + ic * NW, witem_symbol(p, pilot_here, d0, iit),
                             stage + is * slot_bytes, lay.team_stage, smem_u32(&bars[is]), pol,
                             lane);
+        // test hook: the first staging phase of block 0 also waits for 16
+        // bytes that no copy delivers, so its bounded wait runs out
+        if (p.fault == 1 && blockIdx.x == 0 && warp == 0 && g == 0 && s == 0 && lane == 0)
+          mbar_expect_tx_only(smem_u32(&bars[is]), 16);
+        ++issued;
         is = (is + 1 == K) ? 0 : is + 1;
         if (++iit == items) {
           iit = 0;
@@ -195,7 +201,8 @@ __global__ void __launch_bounds__(32 * wgeo_warps(FC32 ? 8 : 4), 1) warp_kernel(
         // every lane is done with the slot (and with the exchange of the
         // previous step): refill the slot K steps ahead
         __syncwarp();
-        if (p.use_tma && to_issue > 0) {
+        if (p.use_tma && to_issue > 0 && !*abort_flag) {
+          ++issued;
           fence_proxy_async();
           wissue<LOG2N, FC32>(p, f, warp + ic * NW, witem_symbol(p, pilot_here, d0, iit),
                               stage + slot * slot_bytes, lay.team_stage, smem_u32(&bars[slot]),
@@ -357,9 +364,10 @@ __global__ void __launch_bounds__(32 * wgeo_warps(FC32 ? 8 : 4), 1) warp_kernel(
   }
   if (lane == 0 && p.use_tma && *abort_flag) {
     // a wait gave up: give any copy of this warp still in flight a bounded
-    // chance to land before the block's shared memory is released
-    for (int s = 0; s < K && s < step; ++s) {
-      const int last = step - 1 - ((step - 1 - s) % K);
+    // chance to land before the block's shared memory is released (copies
+    // stop being issued after the abort: only the issued steps count)
+    for (int s = 0; s < K && s < issued; ++s) {
+      const int last = issued - 1 - ((issued - 1 - s) % K);
       (void)mbar_wait_bounded(smem_u32(&bars[last % K]), (last / K) & 1);
     }
   }
