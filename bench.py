@@ -351,9 +351,9 @@ def denoiser_report(args):
     1..3 dB/tap, SNR U[0, 30] dB), then per SNR in {0, 5, 10, 20, 30} dB run
     16 frames of 64 antennas, N = 1024, 16-QAM (8 taps, 2 dB/tap, sc16)
     through lsas_run_frame (plain LS) and through lsas_estimate -> refinement
-    (bf16 weights) -> lsas_demodulate; report channel MSE against the true
-    channel, bit error rate against the transmitted bits, and device time of
-    the refinement per frame."""
+    (bf16 weights; CUDA-core and tensor-core forms) -> lsas_demodulate; report
+    channel MSE against the true channel, bit error rate against the
+    transmitted bits, and device time of each refinement per frame."""
     import torch
     import paper_1901_07499_gb300.lsas as lsas
     import paper_1901_07499_gb300.denoiser as dnm
@@ -363,7 +363,8 @@ def denoiser_report(args):
                    log=lambda ep, rows, loss: losses.append(loss))
     torch.cuda.synchronize()
     print(json.dumps({"mode": "denoiser-train", "rows": dn.rows_seen, "steps": dn.step,
-                      "final_loss": losses[-1], "first_chunk_loss": losses[0],
+                      "final_loss": losses[-1] if losses else None,
+                      "first_chunk_loss": losses[0] if losses else None,
                       "seconds": time.perf_counter() - t0, "params": lsas.LSAS_DN_PARAMS,
                       "data": "synthetic LS-domain pairs (synth.ls_pairs)"}))
     sys.stdout.flush()
@@ -381,13 +382,21 @@ def denoiser_report(args):
         H_ls, bits_ls, _ = plan.run_frame(x)
         H_dn = dn.apply(H_ls, params_bf16=pb)
         bits_dn, _ = plan.demodulate(x, H_dn)
+        H_tc = dn.apply(H_ls, params_bf16=pb, tensor_cores=True)
+        bits_tc, _ = plan.demodulate(x, H_tc)
         plan.sync()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record()
         for _ in range(5):
             dn.apply(H_ls, out=H_dn, params_bf16=pb)
-        e1.record()
+        ev[1].record()
+        ev[2].record()
+        for _ in range(5):
+            dn.apply(H_ls, out=H_tc, params_bf16=pb, tensor_cores=True)
+        ev[3].record()
         torch.cuda.synchronize()
+        if int(dn.status().item()) != 0:
+            raise RuntimeError("tensor-core refinement reported a timeout")
         Htrue = np.fft.fft(b.taps, cfg.N, axis=-1) * b.gain[:, None, None]
         def mse(Hg):
             return float(np.mean(np.abs(Hg.cpu().numpy() - Htrue) ** 2) / np.mean(np.abs(Htrue) ** 2))
@@ -396,8 +405,10 @@ def denoiser_report(args):
             return float(np.mean(got != b.bits.reshape(F, -1)))
         print(json.dumps({"mode": "denoiser-eval", "snr_db": snr, "frames": F, "M": cfg.M, "N": cfg.N,
                           "qam": cfg.Q, "nmse_ls": mse(H_ls), "nmse_dn": mse(H_dn),
-                          "ber_ls": ber(bits_ls), "ber_dn": ber(bits_dn),
-                          "refine_us_per_frame": 1e3 * e0.elapsed_time(e1) / 5 / F}))
+                          "nmse_dn_tc": mse(H_tc), "ber_ls": ber(bits_ls), "ber_dn": ber(bits_dn),
+                          "ber_dn_tc": ber(bits_tc),
+                          "refine_us_per_frame": 1e3 * ev[0].elapsed_time(ev[1]) / 5 / F,
+                          "refine_tc_us_per_frame": 1e3 * ev[2].elapsed_time(ev[3]) / 5 / F}))
         sys.stdout.flush()
 
 

@@ -313,7 +313,8 @@ lsas_status lsas_server_destroy(lsas_server server);
  * channels, kernel 5, ReLU), denormalise.  Parameters: one float vector of
  * LSAS_DN_PARAMS values, W1[32][2][5] b1[32] W2[32][32][5] b2[32]
  * W3[32][32][5] b3[32] W4[2][32][5] b4[2]; the bf16 form has the same order.
- * d_work: caller-owned device scratch of lsas_dn_work_size floats.
+ * d_work: caller-owned device scratch of lsas_dn_work_size floats, 16-byte
+ *   aligned (INVALID_ARG otherwise).
  *   lsas_dn_apply  d_H [R][N] complex -> d_Hout [R][N] complex (may not
  *                  alias d_H); bf16 != 0 reads bf16 parameters; fp32 sums.
  *   lsas_dn_grad   mean squared error between the network output and the
@@ -322,6 +323,13 @@ lsas_status lsas_server_destroy(lsas_server server);
  *   lsas_dn_adam   one Adam step (beta1 0.9, beta2 0.999, eps 1e-8; step
  *                  counted from 1) on parameters, first and second moments.
  *   lsas_dn_to_bf16  round the parameters to bf16 (nearest even).
+ *   lsas_dn_apply_tc  as lsas_dn_apply with bf16 parameters, the two
+ *                  32 -> 32 layers on the tensor cores: bf16 operands, fp32
+ *                  sums, each ReLU output rounded to bf16 (nearest even)
+ *                  before the next layer.  d_status: caller-owned device
+ *                  int, latched to LSAS_ERR_TIMEOUT (6) if a tensor-core
+ *                  completion wait gives up after ~2 s (the rows are then
+ *                  invalid); never cleared by the library.
  * Errors: INVALID_ARG for bad sizes or null pointers.  Asynchronous.
  */
 #define LSAS_DN_PARAMS 10978
@@ -333,6 +341,8 @@ lsas_status lsas_dn_grad(const float* d_params, const float* d_Hls, const float*
 lsas_status lsas_dn_adam(float* d_params, const float* d_grad, float* d_m, float* d_v, int step,
                          float lr, void* stream);
 lsas_status lsas_dn_to_bf16(const float* d_params, uint16_t* d_params_bf16, void* stream);
+lsas_status lsas_dn_apply_tc(const uint16_t* d_params_bf16, const float* d_H, int R, int N,
+                             float* d_work, float* d_Hout, int* d_status, void* stream);
 
 /*
  * Test hook of failure detection (no counterpart in the paper).  Every wait

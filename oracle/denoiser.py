@@ -76,12 +76,26 @@ def prepare(H: np.ndarray):
     return x0, rms
 
 
-def forward(params: np.ndarray, x0: np.ndarray):
+def bf16_round(x: np.ndarray) -> np.ndarray:
+    """Round to the nearest bfloat16 (8 significant bits, ties to even) by way
+    of float32, as a kernel rounds its float32 sums: the float32 bit pattern
+    plus 0x7FFF plus the lowest kept bit, truncated to the upper 16 bits."""
+    b = np.asarray(x, np.float64).astype(np.float32).view(np.uint32).astype(np.uint64)
+    r = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward(params: np.ndarray, x0: np.ndarray, act=None):
+    """Network output y and the pre-activations.  ``act`` (optional) is
+    applied to every ReLU output before the next layer reads it: the
+    tensor-core inference path stores its activations as bfloat16, which
+    ``act=bf16_round`` reproduces."""
     W1, b1, W2, b2, W3, b3, W4, b4 = unpack(params)
+    f = (lambda v: v) if act is None else act
     a1 = conv(x0, W1, b1)
-    a2 = conv(np.maximum(a1, 0), W2, b2)
-    a3 = conv(np.maximum(a2, 0), W3, b3)
-    a4 = conv(np.maximum(a3, 0), W4, b4)
+    a2 = conv(f(np.maximum(a1, 0)), W2, b2)
+    a3 = conv(f(np.maximum(a2, 0)), W3, b3)
+    a4 = conv(f(np.maximum(a3, 0)), W4, b4)
     return x0 + a4, (x0, a1, a2, a3)
 
 
@@ -128,8 +142,8 @@ def adam(params, grad, m, v, step, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
     return params - lr * mh / (np.sqrt(vh) + eps), m, v
 
 
-def apply(params: np.ndarray, H: np.ndarray) -> np.ndarray:
-    """Denoised channel rows H [R][N] complex."""
+def apply(params: np.ndarray, H: np.ndarray, act=None) -> np.ndarray:
+    """Denoised channel rows H [R][N] complex (``act`` as in forward)."""
     x0, rms = prepare(H)
-    y, _ = forward(params, x0)
+    y, _ = forward(params, x0, act)
     return (y[:, 0] + 1j * y[:, 1]) * rms[:, None]

@@ -210,20 +210,274 @@ __global__ void dn_bf16_kernel(const float* p, __nv_bfloat16* q, int n) {
     q[i] = __float2bfloat16_rn(p[i]);
 }
 
+// ------------------------------------------------------ tensor-core inference
+//
+// All four layers on tcgen05 (kind::f16, bf16 operands, fp32 accumulators in
+// TMEM); the CUDA cores only split the input, apply ReLU, round to bf16
+// and write the output.  Each block of 512 threads runs four tile
+// slots of 128 threads that share one weight image; a slot walks tiles of
+// (row, 116 output subcarriers).  Layers 2 and 3 work in place on the slot's
+// one activation buffer: the epilogue writes only after the MMAs that read
+// the buffer have completed.
+//
+// Every layer reads activation rows m .. m + 4 for MMA row m and writes row
+// m + 2, with position rows at a uniform 16-byte stride, so the operand of
+// tap k is the same buffer shifted by k rows (no im2col):
+//  * layer 1 (2 -> 32): the input row holds x0 split into three bf16 terms
+//    (hi, mid, lo of the real and imaginary parts; fp32-exact products) in
+//    one 8-element K chunk; with the K-chunk stride set to one row, one
+//    K = 16 MMA covers two taps: 3 MMAs (the sixth tap's weights are zero);
+//  * layers 2, 3 (32 -> 32): activations as [channel chunk of 8][row][8];
+//    5 taps x 2 K-halves, N = 32: 10 MMAs each;
+//  * layer 4 (32 -> 2): the same operands, N = 16 with 14 zero outputs.
+// Biases enter each layer as one more K = 16 MMA of a constant operand (a
+// one in the first K slot of every row) against a B holding the bias in its
+// first K slot, so the epilogue is a TMEM load and one relu-and-round
+// conversion per channel pair.  Buffer rows 0, 1, 130, 131 are zero halos,
+// so each layer's output is exact on two fewer MMA rows per side: 116 valid
+// outputs of 128.  Activations at positions outside [0, N) are zero, as
+// every layer's zero padding asks.
+constexpr int kTcValid = 116;                    // final outputs per tile
+constexpr int kTcFirst = 6;                      // first valid MMA row
+constexpr int kTcRows = 132;                     // buffer rows (2-row halos)
+constexpr int kTcLbo = kTcRows * 16;             // bytes between channel chunks
+constexpr int kTcActBytes = 4 * kTcLbo;          // one activation buffer (32 ch)
+constexpr int kTcXBytes = (kTcRows + 1) * 16;    // split input rows (+1 zero row)
+// weight image: B operands of layer 1 (3 x 1 KB), layers 2 and 3 (5 taps x
+// 2 KB each), layer 4 (5 taps x 1 KB), the four bias operands (1 KB each),
+// then the constant A operand of the bias MMAs (129 rows of [1, 0 x 7])
+constexpr int kTcL1 = 0, kTcL2 = 3072, kTcL3 = kTcL2 + 10240, kTcL4 = kTcL3 + 10240;
+constexpr int kTcBias = kTcL4 + 5120;
+constexpr int kTcOnes = kTcBias + 4 * 1024;
+constexpr int kTcImgBytes = kTcOnes + 129 * 16;
+constexpr int kTcImgFloats = kTcImgBytes / 4;
+constexpr int kTcSlots = 4;                      // tiles in flight per block
+constexpr int kTcSlotBytes = kTcXBytes + kTcActBytes;
+constexpr int kTcSmem = kTcImgBytes + kTcSlots * kTcSlotBytes + kTcSlots * 8 + 16;
+static_assert(kTcImgBytes % 16 == 0 && kTcSlotBytes % 16 == 0, "16-byte operand alignment");
+
+__global__ void dn_tc_image_kernel(const __nv_bfloat16* __restrict__ P, float* __restrict__ img) {
+  unsigned char* b = reinterpret_cast<unsigned char*>(img);
+  const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < kTcImgBytes / 2; e += gridDim.x * blockDim.x) {
+    if (e < 1536) {                                   // layer 1: MMA j covers taps 2j, 2j + 1
+      const int j = e / 512, o = (e / 16) % 32, kk = e % 16;
+      const int tap = 2 * j + (kk >> 3), term = kk & 7;   // term: hi re, hi im, mid re, ...
+      const __nv_bfloat16 w = (tap <= 4 && term < 6) ? P[kOffW1 + (o * 2 + (term & 1)) * 5 + tap] : zero;
+      *reinterpret_cast<__nv_bfloat16*>(b + kTcL1 + j * 1024 + (o >> 3) * 256 + (kk >> 3) * 128 +
+                                        (o & 7) * 16 + (kk & 7) * 2) = w;
+    } else if (e < 1536 + 10240) {                    // layers 2, 3: tap k, element (o, c)
+      const int f = e - 1536;
+      const int l = f / 5120, k = (f / 1024) % 5, o = (f / 32) % 32, c = f % 32;
+      const __nv_bfloat16 w = P[(l == 0 ? kOffW2 : kOffW3) + (o * 32 + c) * 5 + k];
+      *reinterpret_cast<__nv_bfloat16*>(b + kTcL2 + l * 10240 + k * 2048 + (o >> 3) * 512 +
+                                        (c >> 3) * 128 + (o & 7) * 16 + (c & 7) * 2) = w;
+    } else if (e < kTcBias / 2) {                     // layer 4: tap k, element (o < 16, c)
+      const int f = e - 1536 - 10240;
+      const int k = f / 512, o = (f / 32) % 16, c = f % 32;
+      const __nv_bfloat16 w = o < 2 ? P[kOffW4 + (o * 32 + c) * 5 + k] : zero;
+      *reinterpret_cast<__nv_bfloat16*>(b + kTcL4 + k * 1024 + (o >> 3) * 512 + (c >> 3) * 128 +
+                                        (o & 7) * 16 + (c & 7) * 2) = w;
+    } else if (e < kTcBias / 2 + 2048) {              // bias operand of layer l: (o, k = 0)
+      const int f = e - kTcBias / 2;
+      const int l = f / 512, o = (f / 16) % 32, k = f % 16;
+      const int src = l == 0 ? kOffB1 : l == 1 ? kOffB2 : l == 2 ? kOffB3 : kOffB4;
+      const __nv_bfloat16 w = (k == 0 && (l < 3 || o < 2)) ? P[src + o] : zero;
+      *reinterpret_cast<__nv_bfloat16*>(b + kTcBias + l * 1024 + (o >> 3) * 256 + (k >> 3) * 128 +
+                                        (o & 7) * 16 + (k & 7) * 2) = w;
+    } else {                                          // the constant operand: rows [1, 0 x 7]
+      const int f = e - kTcBias / 2 - 2048;
+      *reinterpret_cast<__nv_bfloat16*>(b + kTcOnes + 2 * f) = __float2bfloat16_rn((f & 7) == 0 ? 1.f : 0.f);
+    }
+  }
+}
+
+// ReLU and round to bf16 (nearest even) a pair of channels: o in the low half
+__device__ __forceinline__ uint32_t relu_bf16x2(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+// layer output of MMA row m (bias included) -> buffer row m + 2; zero outside [0, N)
+__device__ __forceinline__ void tc_epilogue(const float* d, bool inside, unsigned char* out, int m) {
+  if (inside) {
+#pragma unroll
+    for (int kc = 0; kc < 4; ++kc)
+      *reinterpret_cast<uint4*>(out + kc * kTcLbo + (m + 2) * 16) =
+          make_uint4(relu_bf16x2(d[8 * kc], d[8 * kc + 1]), relu_bf16x2(d[8 * kc + 2], d[8 * kc + 3]),
+                     relu_bf16x2(d[8 * kc + 4], d[8 * kc + 5]), relu_bf16x2(d[8 * kc + 6], d[8 * kc + 7]));
+  } else {
+#pragma unroll
+    for (int kc = 0; kc < 4; ++kc)
+      *reinterpret_cast<uint4*>(out + kc * kTcLbo + (m + 2) * 16) = make_uint4(0u, 0u, 0u, 0u);
+  }
+}
+
+// x -> three bf16 terms whose sum is x to float32 precision
+__device__ __forceinline__ void split3(float x, __nv_bfloat16& hi, __nv_bfloat16& mid, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(hi);
+  mid = __float2bfloat16_rn(r1);
+  lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
+}
+__device__ __forceinline__ uint4 x_row(float re, float im) {
+  __nv_bfloat16 h[8];
+  split3(re, h[0], h[2], h[4]);
+  split3(im, h[1], h[3], h[5]);
+  h[6] = h[7] = __float2bfloat16_rn(0.f);
+  return *reinterpret_cast<const uint4*>(h);
+}
+
+__global__ void __launch_bounds__(128 * kTcSlots, 2) dn_tc_kernel(const float* __restrict__ img_g,
+                                                       const float* __restrict__ x0,
+                                                       const float* __restrict__ rms, int R, int N,
+                                                       float2* __restrict__ Hout, int* status) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned char* wimg = smem;
+  const int t = threadIdx.x;
+  const int slot = t >> 7, u = t & 127, warp = t >> 5;
+  unsigned char* xb = smem + kTcImgBytes + slot * kTcSlotBytes;           // split input rows
+  unsigned char* act = xb + kTcXBytes;                                     // layers 1-3 out
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kTcImgBytes + kTcSlots * kTcSlotBytes);
+  uint32_t* tbase = reinterpret_cast<uint32_t*>(bars + kTcSlots);
+  uint64_t* bar = &bars[slot];
+  if (t == 0) {
+    for (int g = 0; g < kTcSlots; ++g) mbar_init(smem_u32(&bars[g]), 1);
+    fence_mbar_init();
+    mbar_expect_tx(smem_u32(&bars[0]), kTcImgBytes);        // phase 0 of slot 0's barrier
+    bulk_load(smem_u32(wimg), img_g, kTcImgBytes, smem_u32(&bars[0]), evict_last_policy());
+  }
+  __syncwarp();
+  if (warp == 0) tmem_alloc(smem_u32(tbase), 32 * kTcSlots);
+  // halo rows of both activation buffers stay zero
+  if (u < 16) {                                     // 4 chunks x rows 0, 1, 130, 131
+    const int kc = u >> 2, row = (u & 3) < 2 ? (u & 3) : kTcRows - 4 + (u & 3);
+    *reinterpret_cast<uint4*>(act + kc * kTcLbo + row * 16) = make_uint4(0u, 0u, 0u, 0u);
+  }
+  const int tiles_row = (N + kTcValid - 1) / kTcValid;
+  const int tiles = R * tiles_row;
+  const int stride = gridDim.x * kTcSlots;
+  // x0 of a tile for this thread: rows u and 128 + u (u < 4) of the split
+  // input, and the residual at MMA row u; fetched one tile ahead
+  float xa0 = 0.f, xa1 = 0.f, xb0 = 0.f, xb1 = 0.f, xr0 = 0.f, xr1 = 0.f;
+  auto fetch = [&](int tile) {
+    xa0 = xa1 = xb0 = xb1 = xr0 = xr1 = 0.f;
+    if (tile >= tiles) return;
+    const int r = tile / tiles_row, s0 = (tile % tiles_row) * kTcValid - kTcFirst;
+    const float* re = x0 + static_cast<size_t>(r) * 2 * N;
+    const float* im = re + N;
+    const int qa = s0 - 2 + u, qb = s0 + 126 + u, qr = s0 + u;
+    if (qa >= 0 && qa < N) { xa0 = re[qa]; xa1 = im[qa]; }
+    if (u < 4 && qb >= 0 && qb < N) { xb0 = re[qb]; xb1 = im[qb]; }
+    if (qr >= 0 && qr < N) { xr0 = re[qr]; xr1 = im[qr]; }
+  };
+  int tile = blockIdx.x * kTcSlots + slot;
+  fetch(tile);
+  tmem_fence_before();
+  __syncthreads();
+  tmem_fence_after();
+  const uint32_t tm = *tbase + 32 * slot + (static_cast<uint32_t>(32 * (warp & 3)) << 16);
+  const uint32_t tm_mma = *tbase + 32 * slot;
+  const uint32_t id32 = umma_idesc(32, true), id16 = umma_idesc(16, true);
+  // descriptors at offset 0; an offset o (bytes, 16-aligned) adds o >> 4
+  const uint64_t dx = umma_desc(smem_u32(xb), 16, 128);
+  const uint64_t da = umma_desc(smem_u32(act), kTcLbo, 128);
+  const uint64_t dw1 = umma_desc(smem_u32(wimg), 128, 256);
+  const uint64_t dw = umma_desc(smem_u32(wimg), 128, 512);
+  const uint64_t dones = umma_desc(smem_u32(wimg + kTcOnes), 16, 128);
+  // every thread waits for the image (phase 0 of slot 0's barrier)
+  bool ok = mbar_wait_bounded(smem_u32(&bars[0]), 0);
+  if (!ok) latch(status, kStTimeout);
+  uint32_t phase = slot == 0 ? 1u : 0u;
+  auto issue_wait = [&](int layer) {
+    fence_proxy_async();
+    tmem_fence_before();
+    named_sync(1 + slot, 128);
+    tmem_fence_after();
+    if (u == 0) {
+      umma_f16(tm_mma, dones, dw1 + ((kTcBias + 1024 * (layer - 1)) >> 4), layer == 4 ? id16 : id32, 0u);
+      if (layer == 1) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+          umma_f16(tm_mma, dx + 2 * j, dw1 + ((kTcL1 + 1024 * j) >> 4), id32, 1u);
+      } else {
+        const int boff = layer == 2 ? kTcL2 : layer == 3 ? kTcL3 : kTcL4;
+        const int tapb = layer == 4 ? 1024 : 2048;
+        const uint32_t idesc = layer == 4 ? id16 : id32;
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+#pragma unroll
+          for (int kh = 0; kh < 2; ++kh)
+            umma_f16(tm_mma, da + ((k * 16 + kh * 2 * kTcLbo) >> 4),
+                     dw + ((boff + k * tapb + kh * 256) >> 4), idesc, 1u);
+      }
+      umma_commit(smem_u32(bar));
+      // the issuing thread alone waits; the others sleep in the barrier
+      if (ok && !mbar_wait_bounded(smem_u32(bar), phase)) {
+        ok = false;
+        latch(status, kStTimeout);
+      }
+    }
+    phase ^= 1;
+    tmem_fence_before();
+    named_sync(1 + slot, 128);
+    tmem_fence_after();
+  };
+  for (; tile < tiles; tile += stride) {
+    const int r = tile / tiles_row;
+    const int s0 = (tile % tiles_row) * kTcValid - kTcFirst;   // position of MMA row 0
+    const float xres0 = xr0, xres1 = xr1;
+    // split input: row b <-> position s0 - 2 + b; row 132 stays zero
+    *reinterpret_cast<uint4*>(xb + u * 16) = x_row(xa0, xa1);
+    if (u < 4) *reinterpret_cast<uint4*>(xb + (128 + u) * 16) = x_row(xb0, xb1);
+    if (u == 4) *reinterpret_cast<uint4*>(xb + kTcRows * 16) = make_uint4(0u, 0u, 0u, 0u);
+    fetch(tile + stride);                                     // next tile's x0, in flight
+    const int q = s0 + u;                                     // position of MMA row u
+    const bool inside = q >= 0 && q < N;
+    float d[32];
+    issue_wait(1);
+    Tmem<32>::ld(tm, d);
+    tmem_wait_ld();
+    tc_epilogue(d, inside, act, u);
+    issue_wait(2);
+    Tmem<32>::ld(tm, d);
+    tmem_wait_ld();
+    tc_epilogue(d, inside, act, u);
+    issue_wait(3);
+    Tmem<32>::ld(tm, d);
+    tmem_wait_ld();
+    tc_epilogue(d, inside, act, u);
+    issue_wait(4);
+    float y[2];
+    Tmem<2>::ld(tm, y);
+    tmem_wait_ld();
+    if (u >= kTcFirst && u < kTcFirst + kTcValid && q < N) {
+      const float rr = rms[r];
+      Hout[static_cast<size_t>(r) * N + q] =
+          make_float2((xres0 + y[0]) * rr, (xres1 + y[1]) * rr);
+    }
+  }
+  tmem_fence_before();
+  __syncthreads();
+  tmem_fence_after();
+  if (warp == 0) tmem_dealloc(*tbase, 32 * kTcSlots);
+}
+
 // ------------------------------------------------------------- host side
 
-// Work buffer (floats): x0, t, y, dy [R][2][N]; a1, a2, a3, g1, g2 [R][32][N];
-// rms [R]; transposed weights [5120]; loss partials.
+// Work buffer (floats): the tensor-core weight image [kTcImgFloats] (first,
+// so that it keeps the buffer's alignment); x0, t, y, dy [R][2][N]; a1, a2,
+// a3, g1, g2 [R][32][N]; rms [R]; transposed weights [5120]; loss partials.
 struct DnWork {
-  float *x0, *tt, *y, *dy, *a1, *a2, *a3, *g1, *g2, *rms, *wt, *part;
+  float *img, *x0, *tt, *y, *dy, *a1, *a2, *a3, *g1, *g2, *rms, *wt, *part;
 };
 size_t dn_work_floats(int R, int N) {
-  return static_cast<size_t>(R) * N * (4 * 2 + 5 * 32) + R + 5120 + kDnLossBlocks;
+  return kTcImgFloats + static_cast<size_t>(R) * N * (4 * 2 + 5 * 32) + R + 5120 + kDnLossBlocks;
 }
 static DnWork dn_work(float* w, int R, int N) {
   DnWork d;
   const size_t s2 = static_cast<size_t>(R) * 2 * N, s32 = static_cast<size_t>(R) * 32 * N;
-  d.x0 = w; d.tt = d.x0 + s2; d.y = d.tt + s2; d.dy = d.y + s2;
+  d.img = w; d.x0 = w + kTcImgFloats; d.tt = d.x0 + s2; d.y = d.tt + s2; d.dy = d.y + s2;
   d.a1 = d.dy + s2; d.a2 = d.a1 + s32; d.a3 = d.a2 + s32; d.g1 = d.a3 + s32; d.g2 = d.g1 + s32;
   d.rms = d.g2 + s32; d.wt = d.rms + R; d.part = d.wt + 5120;
   return d;
@@ -253,6 +507,27 @@ cudaError_t dn_apply(const void* params, bool bf16, const float2* H, int R, int 
   const size_t n = static_cast<size_t>(R) * N;
   const int fg = static_cast<int>((n + 255) / 256 < static_cast<size_t>(sms) * 8 ? (n + 255) / 256 : sms * 8);
   dn_finish_kernel<<<fg, 256, 0, st>>>(d.y, d.rms, R, N, Hout);
+  return cudaGetLastError();
+}
+
+cudaError_t dn_apply_tc(const void* params_bf16, const float2* H, int R, int N, float* work,
+                        float2* Hout, int* status, int sms, cudaStream_t st) {
+  const DnWork d = dn_work(work, R, N);
+  static bool attr = false;
+  if (!attr) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(dn_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const auto* P = static_cast<const __nv_bfloat16*>(params_bf16);
+  dn_tc_image_kernel<<<(kTcImgBytes / 2 + 255) / 256, 256, 0, st>>>(P, d.img);
+  dn_prepare_kernel<<<R, 256, 0, st>>>(H, nullptr, N, d.x0, nullptr, d.rms);
+  // two blocks fit per SM (shared memory and the launch bounds' register cap)
+  const int tiles = R * ((N + kTcValid - 1) / kTcValid);
+  const int want = (tiles + kTcSlots - 1) / kTcSlots;
+  const int grid = want < sms * 2 ? want : sms * 2;
+  dn_tc_kernel<<<grid, 128 * kTcSlots, kTcSmem, st>>>(d.img, d.x0, d.rms, R, N, Hout, status);
   return cudaGetLastError();
 }
 
@@ -356,6 +631,19 @@ lsas_status lsas_dn_adam(float* d_params, const float* d_grad, float* d_m, float
   if (!d_params || !d_grad || !d_m || !d_v || step < 1 || !(lr > 0.f)) return LSAS_ERR_INVALID_ARG;
   if (lsas::dn_adam(d_params, d_grad, d_m, d_v, step, lr, 0.9f, 0.999f, 1e-8f,
                     static_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return LSAS_ERR_CUDA;
+  return LSAS_OK;
+}
+
+lsas_status lsas_dn_apply_tc(const uint16_t* d_params_bf16, const float* d_H, int R, int N,
+                             float* d_work, float* d_Hout, int* d_status, void* stream) {
+  const lsas_status s = dn_check(R, N);
+  if (s != LSAS_OK) return s;
+  if (!d_params_bf16 || !d_H || !d_work || !d_Hout || !d_status) return LSAS_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(d_work) % 16 != 0) return LSAS_ERR_INVALID_ARG;
+  if (lsas::dn_apply_tc(d_params_bf16, reinterpret_cast<const float2*>(d_H), R, N, d_work,
+                        reinterpret_cast<float2*>(d_Hout), d_status, dn_sms(),
+                        static_cast<cudaStream_t>(stream)) != cudaSuccess)
     return LSAS_ERR_CUDA;
   return LSAS_OK;
 }

@@ -260,6 +260,11 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src,
       "l"(src), "r"(bytes), "r"(bar), "l"(policy)
       : "memory");
 }
+__device__ __forceinline__ uint64_t evict_last_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
 __device__ __forceinline__ uint64_t evict_first_policy() {
   uint64_t pol;
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
@@ -413,6 +418,35 @@ template <> struct Tmem<32> {
     Tmem<16>::st(t + 16, v + 16);
   }
 };
+
+// ------------------------------------------------------- tcgen05 MMA
+
+// Shared-memory operand descriptor, no swizzle: start address, byte offset
+// between core matrices adjacent along K (lbo) and between 8-row groups (sbo).
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = static_cast<uint64_t>((addr & 0x3FFFF) >> 4);
+  d |= static_cast<uint64_t>((lbo >> 4) & 0x3FFF) << 16;
+  d |= static_cast<uint64_t>((sbo >> 4) & 0x3FFF) << 32;
+  d |= static_cast<uint64_t>(1) << 46;   // descriptor version
+  return d;
+}
+// kind::f16 instruction descriptor: fp32 accumulator, A and B both fp16 or
+// both bf16, K-major, M = 128, n columns.
+__device__ __forceinline__ uint32_t umma_idesc(int n, bool bf16) {
+  const uint32_t ab = bf16 ? 1u : 0u;
+  return (1u << 4) | (ab << 7) | (ab << 10) | (static_cast<uint32_t>(n >> 3) << 17) |
+         (static_cast<uint32_t>(128 >> 4) << 24);
+}
+__device__ __forceinline__ void umma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t acc) {
+  asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+               "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+               :: "r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+               :: "r"(bar) : "memory");
+}
 
 // 64 columns as two 32-column halves
 template <> struct Tmem<64> {

@@ -55,6 +55,7 @@ class Denoiser:
         self.rows_seen = 0
         self._work = None
         self._work_key = None
+        self._status = None
 
     def work(self, R: int, N: int):
         import torch
@@ -87,13 +88,32 @@ class Denoiser:
         L.check(L.lsas_dn_to_bf16(L._ptr(self.params), L._ptr(q), L._stream(None)), "lsas_dn_to_bf16")
         return q
 
-    def apply(self, H, out=None, bf16: bool = True, params_bf16=None):
-        """Refined rows of H [..., N] complex64 (device; rows = all leading axes)."""
+    def status(self):
+        """Device status word of the tensor-core path (0, or 6 after a wait
+        that gave up); created on first use."""
+        import torch
+        if self._status is None:
+            self._status = torch.zeros(1, dtype=torch.int32, device=self.device)
+        return self._status
+
+    def apply(self, H, out=None, bf16: bool = True, params_bf16=None, tensor_cores: bool = False):
+        """Refined rows of H [..., N] complex64 (device; rows = all leading axes).
+
+        ``tensor_cores``: the 32 -> 32 layers on tcgen05 with bf16 activations
+        (bf16 parameters only)."""
         import torch
         N = int(H.shape[-1])
         R = int(H.numel() // N)
         if out is None:
             out = torch.empty_like(H)
+        if tensor_cores:
+            if not bf16:
+                raise ValueError("the tensor-core path reads bf16 parameters")
+            pb = params_bf16 if params_bf16 is not None else self.bf16_params()
+            L.check(L.lsas_dn_apply_tc(L._ptr(pb), L._ptr(H), R, N, L._ptr(self.work(R, N)),
+                                       L._ptr(out), L._ptr(self.status()), L._stream(None)),
+                    "lsas_dn_apply_tc")
+            return out
         p = (params_bf16 if params_bf16 is not None else self.bf16_params()) if bf16 else self.params
         L.check(L.lsas_dn_apply(L._ptr(p), 1 if bf16 else 0, L._ptr(H), R, N,
                                 L._ptr(self.work(R, N)), L._ptr(out), L._stream(None)),

@@ -83,6 +83,7 @@ lsas_dn_apply = _proto("lsas_dn_apply", [_vp, _i, _vp, _i, _i, _vp, _vp, _vp])
 lsas_dn_grad = _proto("lsas_dn_grad", [_vp, _vp, _vp, _i, _i, _vp, _vp, _vp, _vp])
 lsas_dn_adam = _proto("lsas_dn_adam", [_vp, _vp, _vp, _vp, _i, C.c_float, _vp])
 lsas_dn_to_bf16 = _proto("lsas_dn_to_bf16", [_vp, _vp, _vp])
+lsas_dn_apply_tc = _proto("lsas_dn_apply_tc", [_vp, _vp, _i, _i, _vp, _vp, _vp, _vp])
 lsas_plan_set_fault = _proto("lsas_plan_set_fault", [_vp, _i])
 lsas_plan_sync = _proto("lsas_plan_sync", [_vp, _vp])
 lsas_plan_info = _proto("lsas_plan_info", [_vp, C.POINTER(_i)])
@@ -97,7 +98,7 @@ EXPORTED = ["lsas_status_str", "lsas_check_config", "lsas_frame_bytes",
             "lsas_server_create", "lsas_server_register", "lsas_server_submit",
             "lsas_server_wait", "lsas_server_stats", "lsas_server_destroy",
             "lsas_dn_work_size", "lsas_dn_apply", "lsas_dn_grad", "lsas_dn_adam",
-            "lsas_dn_to_bf16", "lsas_plan_set_fault",
+            "lsas_dn_to_bf16", "lsas_dn_apply_tc", "lsas_plan_set_fault",
             "lsas_plan_sync", "lsas_plan_info",
             "lsas_plan_destroy"]
 

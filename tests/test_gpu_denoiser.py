@@ -10,6 +10,21 @@ reference in oracle/denoiser.py, on LS-domain rows from synth.ls_pairs.
 * Training: 120 steps lower the MSE on held-out rows below that of plain LS
   (the untrained network's identity), deterministically, and a checkpoint
   round-trips exactly.
+* Tensor-core inference (bf16 operands and activations, fp32 sums) against
+  the reference with the same bf16 parameters and every ReLU output rounded
+  to bf16.  The two sides round sums that differ in their last float32 bits
+  (fp32 against fp64 accumulation of 10 to 160 products), so an activation
+  that close to a bf16 rounding boundary lands one bf16 step (2^-7 relative)
+  apart, and the flip spreads through the later layers' receptive field (up
+  to 13 outputs).  Perturbing the reference's own sums by 1e-6 relative
+  noise (fp32-sized) before rounding moves its outputs by up to 1.1e-2 of
+  the row RMS, 4e-4 RMS, with 4-7 % of outputs beyond 1e-4 on these inputs
+  and parameters.  The bar: max error <= 3e-2, RMS error <= 1e-3 (of the
+  row RMS), at most 10 % of outputs beyond 1e-4, and the median within 1e-6
+  (outputs away from a flip agree to fp32 rounding).  A wrong tap, bias,
+  halo or tile offset moves outputs by O(1) and fails the max.
+  Sizes: N = 128, 1024, 2048 (each ends in a partial 116-subcarrier tile), and
+  the evaluation batch (1024 rows of 1024) with 24 sampled rows.
 """
 
 import numpy as np
@@ -104,3 +119,45 @@ def test_training_beats_plain_ls_and_checkpoints(D, tmp_path):
     dn.save(path)
     back = D.Denoiser.load(path)
     assert back.step == dn.step and torch.equal(back.params, dn.params) and torch.equal(back.v, dn.v)
+
+
+def _check_tc(got, want, rms):
+    e = np.abs(got - want) / rms
+    assert np.max(e) <= 3e-2, np.max(e)
+    assert np.sqrt(np.mean(e ** 2)) <= 1e-3, np.sqrt(np.mean(e ** 2))
+    assert np.mean(e > 1e-4) <= 0.10, np.mean(e > 1e-4)
+    assert np.median(e) <= 1e-6, np.median(e)
+
+
+@pytest.mark.parametrize("R,N", [(6, 128), (8, 1024), (5, 2048)])
+def test_tensor_core_forward_matches_reference(D, R, N):
+    H, Hls, _ = synth.ls_pairs(R, N, seed=21 + N)
+    p = D.init_params(3) * np.float32(4.0)
+    dn = D.Denoiser(p)
+    pb = dn.bf16_params()
+    x = _t(Hls.astype(np.complex64))
+    got = dn.apply(x, params_bf16=pb, tensor_cores=True).cpu().numpy()
+    assert int(dn.status().item()) == 0
+    pr = _bf16_round(p)
+    want = odn.apply(pr, Hls.astype(np.complex64), act=odn.bf16_round)
+    rms = np.sqrt(np.mean(np.abs(want) ** 2))
+    _check_tc(got, want, rms)
+    # the CUDA-core path on the same bf16 parameters differs only by the
+    # activation rounding (bounded by the bf16 step, 2^-8 relative per value)
+    cc = dn.apply(x, params_bf16=pb).cpu().numpy()
+    assert np.sqrt(np.mean(np.abs(got - cc) ** 2)) <= 1e-2 * rms
+
+
+def test_tensor_core_forward_evaluation_batch(D):
+    """16 frames x 64 antennas x 1024 subcarriers, as timed; 24 sampled rows
+    against the reference."""
+    R, N = 1024, 1024
+    H, Hls, _ = synth.ls_pairs(R, N, seed=31)
+    p = D.init_params(6) * np.float32(4.0)
+    dn = D.Denoiser(p)
+    got = dn.apply(_t(Hls.astype(np.complex64)), tensor_cores=True).cpu().numpy()
+    assert int(dn.status().item()) == 0
+    rows = np.random.default_rng(32).choice(R, 24, replace=False)
+    want = odn.apply(_bf16_round(p), Hls[rows].astype(np.complex64), act=odn.bf16_round)
+    rms = np.sqrt(np.mean(np.abs(want) ** 2))
+    _check_tc(got[rows], want, rms)

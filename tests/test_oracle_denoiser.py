@@ -9,6 +9,10 @@
   lr * g / (|g| + eps).
 * The LS-domain pairs have unit expected channel power and LS error
   variance sigma^2.
+* bf16_round: exact bfloat16 values stay, ties go to the even significand,
+  and the relative error never exceeds 2^-8; the activation hook is applied
+  exactly once to each of the three ReLU outputs (with zero biases, doubling
+  every activation scales the network's residual by 2^3).
 """
 
 import numpy as np
@@ -75,3 +79,27 @@ def test_ls_pairs_statistics():
     assert abs(np.mean(np.abs(H) ** 2) - 1.0) < 0.1
     err = np.mean(np.abs(Hls - H) ** 2)
     assert abs(err - 0.1) < 0.005          # sigma^2 = 10^-1
+
+
+def test_bf16_round_values_and_bound():
+    u = 2.0 ** -7                     # bf16 spacing in [1, 2)
+    got = dn.bf16_round(np.array([1.0, 1 + u / 2, 1 + 1.5 * u, 1 + 0.49 * u, -3.0, 0.0, 2.0 ** -130]))
+    assert list(got[:6]) == [1.0, 1.0, 1 + 2 * u, 1.0, -3.0, 0.0]
+    assert got[6] == 2.0 ** -130      # a bfloat16 subnormal: kept, not flushed
+    x = np.random.default_rng(9).standard_normal(100_000) * 10.0 ** np.random.default_rng(10).uniform(-3, 3, 100_000)
+    r = dn.bf16_round(x)
+    assert np.max(np.abs(r - x) / np.abs(x)) <= 2.0 ** -8 * (1 + 1e-6)   # half the spacing 2^-7
+    assert np.array_equal(dn.bf16_round(r), r)
+
+
+def test_activation_hook_applied_once_per_relu():
+    rng = np.random.default_rng(11)
+    p = dn.init_params(5) * 3.0
+    W1, b1, W2, b2, W3, b3, W4, b4 = dn.unpack(p)
+    assert not b1.any() and not b4.any()          # init has zero biases
+    x0 = rng.standard_normal((2, 2, 40))
+    y, _ = dn.forward(p, x0)
+    y2, _ = dn.forward(p, x0, act=lambda v: 2.0 * v)
+    assert np.allclose(y2 - x0, 8.0 * (y - x0), rtol=1e-12, atol=1e-12)
+    yb, _ = dn.forward(p, x0, act=dn.bf16_round)
+    assert 0 < np.max(np.abs(yb - y)) < 0.05 * np.max(np.abs(y - x0))
