@@ -521,7 +521,8 @@ def main():
                          "kernel": "warp_kernel (fused CP strip+FFT+LS+MRC+demap, per-warp pipelines)" if cfg.N <= 1024 else "frame_kernel (fused CP strip+FFT+LS+MRC+demap)",
                          "algorithmic_bytes_per_frame": in_b + h_b + bit_b},
             "e2e": {"value": samples / t_e2e, "unit": "samples/s",
-                    "h2d_bytes_per_step": F * in_b, "d2h_bytes_per_step": F * (h_b + bit_b)},
+                    "h2d_bytes_per_step": F * plan.host_input_bytes_per_frame(),
+                    "d2h_bytes_per_step": F * (h_b + bit_b)},
             "latency_ms": {"frames_per_call": 1, "p50": lat[len(lat) // 2],
                            "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
             "gpu_launches": args.steps,

@@ -403,7 +403,10 @@ lsas_status lsas_run_frame_split_static(lsas_plan plan, const void* d_in,
  * that transfers overlap the kernels.  Host buffers should be page-locked
  * (cudaHostAlloc / pinned) for full speed.  The first call on a plan
  * allocates the plan's device staging buffers.  Returns after the results
- * are in host memory (it synchronises stream).
+ * are in host memory (it synchronises stream).  When CP > 0 and a row of N
+ * samples spans at least 1 KB, only the N samples after each cyclic prefix
+ * cross the host link (the receiver never reads the prefixes): M*S*N*bps
+ * bytes per frame instead of M*S*(N+CP)*bps, bps = 4 (SC16) or 8 (FC32).
  */
 lsas_status lsas_run_frame_host(lsas_plan plan, const void* h_in,
                                 int n_frames, float* h_H, uint8_t* h_bits,

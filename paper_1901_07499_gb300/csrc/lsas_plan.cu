@@ -102,6 +102,11 @@ int ilog2i(int x) {
 size_t in_bytes_per_frame(int M, int N, int cp, int S, lsas_input_fmt fmt) {
   return static_cast<size_t>(M) * S * (N + cp) * (fmt == LSAS_IN_SC16 ? 4 : 8);
 }
+// Whether lsas_run_frame_host copies only the samples after each cyclic
+// prefix (rows of at least 1 KB kept).
+bool host_strips_cp(int N, int cp, lsas_input_fmt fmt) {
+  return cp > 0 && static_cast<size_t>(N) * (fmt == LSAS_IN_SC16 ? 4 : 8) >= 1024;
+}
 size_t bits_bytes_per_frame(int N, int S, int Q) {
   return static_cast<size_t>(S - 1) * N * ilog2i(Q) / 8;
 }
@@ -772,6 +777,14 @@ lsas_status lsas_run_frame_host(lsas_plan p, const void* h_in, int n_frames, flo
   const size_t hb = static_cast<size_t>(p->M) * p->N * 8;
   const size_t bb = bits_bytes_per_frame(p->N, p->S, p->Q);
   const size_t eb = static_cast<size_t>(p->D) * p->N * 8;
+  // The receiver never reads the cyclic prefixes (step 1 drops them), so a
+  // pitched copy moves only the N samples after each prefix once rows are
+  // long enough for pitched copies to run at full speed; the staging buffer
+  // keeps the [M][S*(N+CP)] layout.
+  const size_t bps = p->fmt == LSAS_IN_SC16 ? 4 : 8;
+  const size_t pitch = static_cast<size_t>(p->N + p->cp) * bps;
+  const size_t keep = static_cast<size_t>(p->N) * bps, skip = static_cast<size_t>(p->cp) * bps;
+  const bool strip = host_strips_cp(p->N, p->cp, p->fmt);
   if (!p->d_in_stage[0]) {
     for (int i = 0; i < 2; ++i) {
       if (cudaMalloc(&p->d_in_stage[i], inb * chunk) != cudaSuccess ||
@@ -804,9 +817,14 @@ lsas_status lsas_run_frame_host(lsas_plan p, const void* h_in, int n_frames, flo
     const int nf = (n_frames - f0) < chunk ? (n_frames - f0) : chunk;
     if (c >= 2 && cudaStreamWaitEvent(p->up_stream, p->ev_down[b], 0) != cudaSuccess)
       return LSAS_ERR_CUDA;
-    if (cudaMemcpyAsync(p->d_in_stage[b], static_cast<const unsigned char*>(h_in) + inb * f0,
-                        inb * nf, cudaMemcpyHostToDevice, p->up_stream) != cudaSuccess ||
-        cudaEventRecord(p->ev_up[b], p->up_stream) != cudaSuccess ||
+    const unsigned char* src = static_cast<const unsigned char*>(h_in) + inb * f0;
+    unsigned char* dst = static_cast<unsigned char*>(p->d_in_stage[b]);
+    const cudaError_t up =
+        strip ? cudaMemcpy2DAsync(dst + skip, pitch, src + skip, pitch, keep,
+                                  static_cast<size_t>(p->M) * p->S * nf, cudaMemcpyHostToDevice,
+                                  p->up_stream)
+              : cudaMemcpyAsync(dst, src, inb * nf, cudaMemcpyHostToDevice, p->up_stream);
+    if (up != cudaSuccess || cudaEventRecord(p->ev_up[b], p->up_stream) != cudaSuccess ||
         cudaStreamWaitEvent(st, p->ev_up[b], 0) != cudaSuccess)
       return LSAS_ERR_CUDA;
     lsas_status r = launch_frame(p, p->d_in_stage[b], nf, reinterpret_cast<float*>(p->d_H_stage[b]),

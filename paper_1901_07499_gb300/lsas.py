@@ -317,6 +317,14 @@ class Plan:
                              _stream(stream)), "lsas_run_frame")
         return H, bits, eq
 
+    def host_input_bytes_per_frame(self) -> int:
+        """Input bytes per frame that lsas_run_frame_host moves over the host
+        link: the samples after each cyclic prefix once a row of N samples
+        spans at least 1 KB, else whole rows."""
+        bps = 4 if self.fmt == "sc16" else 8
+        strip = self.cp > 0 and self.N * bps >= 1024
+        return self.M * self.S * (self.N if strip else self.N + self.cp) * bps
+
     def run_frame_host(self, x, H, bits, eq=None, stream=None):
         """Host (pinned) tensors in and out; copies happen inside the call."""
         F = self._frames(x)

@@ -203,9 +203,12 @@ def test_argument_errors(L):
     assert plan.sync_status() == L.LSAS_OK
 
 
-def test_host_entry_point_matches_device_path(L):
+@pytest.mark.parametrize("M,N", [(32, 512), (16, 128)])
+def test_host_entry_point_matches_device_path(L, M, N):
+    """The host-buffer path (N = 512: prefixes stripped in the transfer;
+    N = 128: whole rows) gives the device path's bytes exactly."""
     import torch
-    cfg = sweep_config(32, 512)
+    cfg = sweep_config(M, N)
     b = synth.generate(cfg, frame_ids=range(150))   # > 2 transfer chunks
     plan = make_plan(L, cfg)
     xd = to_torch_frames(b)
@@ -218,6 +221,7 @@ def test_host_entry_point_matches_device_path(L):
     plan.run_frame_host(xh, Hh, bh, eh)
     plan.sync()
     assert torch.equal(Hh, H.cpu()) and torch.equal(bh, bits.cpu()) and torch.equal(eh, eq.cpu())
+    assert plan.host_input_bytes_per_frame() == cfg.M * cfg.S * (cfg.N if N >= 256 else cfg.N + cfg.cp) * 4
 
 
 def test_deterministic(L):
