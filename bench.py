@@ -488,6 +488,20 @@ def main():
         if i >= 10:
             lat.append(a.elapsed_time(c))
     lat.sort()
+    # the same single frame with its antennas split into equal shards that
+    # run side by side (8 antennas per shard keeps every warp of a block busy)
+    shards = max([g for g in range(1, cfg.M + 1) if cfg.M % g == 0 and cfg.M // g >= 8] or [1])
+    lat_s = []
+    if cfg.N <= 1024 and shards > 1:
+        for i in range(args.latency_calls + 10):
+            a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            plan.run_frame_split(x1, shards, H1, b1)
+            c.record(stream)
+            c.synchronize()
+            if i >= 10:
+                lat_s.append(a.elapsed_time(c))
+        lat_s.sort()
 
     # end to end through the host-buffer entry point
     xh = x[:F].cpu().pin_memory()
@@ -524,7 +538,10 @@ def main():
                     "h2d_bytes_per_step": F * plan.host_input_bytes_per_frame(),
                     "d2h_bytes_per_step": F * (h_b + bit_b)},
             "latency_ms": {"frames_per_call": 1, "p50": lat[len(lat) // 2],
-                           "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
+                           "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                           "antenna_split": ({"shards": shards, "p50": lat_s[len(lat_s) // 2],
+                                              "p99": lat_s[min(len(lat_s) - 1, int(0.99 * len(lat_s)))]}
+                                             if lat_s else None)},
             "gpu_launches": args.steps,
             "clocks": clocks,
             "cpu_baseline": cpu,

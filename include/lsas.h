@@ -382,6 +382,12 @@ lsas_status lsas_plan_set_fault(lsas_plan plan, int kind);
  *   <= 151).
  * Nothing in the scratch needs to start at zero: the shard pass writes every
  * partial sum that the combine pass of the same call reads.
+ * Launches: when n_shards divides M and N <= 1024, the shard pass is one
+ * launch whose grid row g processes shard g of every frame, so a frame's
+ * shards run on different SMs at the same time (the latency of a single
+ * frame falls roughly by the number of shards while each shard keeps at
+ * least 8 antennas); otherwise one launch per shard.  Both give the same
+ * partial sums, hence the same results.
  * The first call on each device looks up the scratch address
  * (cudaGetSymbolAddress) with that device current; a caller that captures
  * its stream must make that first call before capture begins.

@@ -71,6 +71,10 @@ struct KParams {
   float* peaks;          //   per frame: correlation power at it (out, nullable)
   const int* offsets_in; //   per frame: preamble start (extraction)
   int fault;             // test hook: 1 = block 0 waits for 16 bytes that never come
+  int shard_y;           // partial mode, one launch for all shards: antennas per grid row
+                         // blockIdx.y (its first antenna is m0 + blockIdx.y * shard_y, its
+                         // partials start at shard blockIdx.y of [G][F][...]); 0 otherwise
+  int grid_y;            // grid rows (shards) of the launch; 0 or 1 for a 1-D grid
   int chunks;            // ceil(M / A)
   int groups, dg;        // data-symbol groups per frame, data symbols per group
   int mode;              // kModeDemod, kModeRun or kModePartial (frame_kernel)
@@ -807,7 +811,7 @@ template <int LOG2N, bool FC32>
 __device__ __forceinline__ const unsigned char* row_ptr(const KParams& p, int f, int m,
                                                         int s) {
   constexpr int bps = FC32 ? 8 : 4;
-  const size_t row = (static_cast<size_t>(f) * p.Mtot + p.m0 + m) * p.S + s;
+  const size_t row = (static_cast<size_t>(f) * p.Mtot + p.m0 + blockIdx.y * p.shard_y + m) * p.S + s;
   return static_cast<const unsigned char*>(p.in) +
          (row * (Geo<LOG2N>::N + p.cp) + p.cp) * bps;
 }

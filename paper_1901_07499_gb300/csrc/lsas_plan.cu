@@ -922,6 +922,27 @@ lsas_status lsas_run_frame_split_static(lsas_plan p, const void* d_in, int n_fra
   if (!scratch) return LSAS_ERR_CUDA;
   float* P = reinterpret_cast<float*>(scratch);
   float* E = reinterpret_cast<float*>(scratch + p_bytes);   // p_bytes is a multiple of 512
+  if (p->N <= 1024 && p->M % n_shards == 0 && n_shards > 1) {
+    // equal shards on the per-warp kernel: one launch, grid row g = shard g,
+    // so the shards of a frame run side by side (the same partial sums as
+    // one launch per shard)
+    KParams k;
+    base_params(p, &k);
+    k.in = d_in;
+    k.H_out = reinterpret_cast<float2*>(d_H);
+    k.P_out = reinterpret_cast<float2*>(P);
+    k.E_out = E;
+    k.M = p->M / n_shards;
+    k.shard_y = k.M;
+    k.grid_y = n_shards;
+    k.chunks = (k.M + p->geo.Af - 1) / p->geo.Af;
+    k.mode = kModePartial;
+    k.use_tma = tma_ok(p, d_in) ? 1 : 0;
+    if (p->launch(kKindFrame, p->fmt == LSAS_IN_FC32, k, n_frames, p->geo.smem_frame,
+                  static_cast<cudaStream_t>(stream)) != cudaSuccess)
+      return LSAS_ERR_CUDA;
+    return lsas_mrc_combine(p, P, E, n_shards, n_frames, d_bits, d_eq, stream);
+  }
   // even split: shard g gets M / G antennas, plus one for the first M % G shards
   int m0 = 0;
   for (int g = 0; g < n_shards; ++g) {

@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(32 * wgeo_warps(FC32 ? 8 : 4), 1) warp_kernel(
       const int c = warp + lc * NW;
       const int m = c * A + alpha;
       const bool valid = m < p.M;
-      const size_t hrow = (static_cast<size_t>(f) * p.Mtot + p.m0 + m) * N;
+      const size_t hrow = (static_cast<size_t>(f) * p.Mtot + p.m0 + blockIdx.y * p.shard_y + m) * N;
       float2 h[32];
       if (!pilot_here) {
         // channel from memory: given (demodulate) or written in group 0
@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(32 * wgeo_warps(FC32 ? 8 : 4), 1) warp_kernel(
 #pragma unroll
         for (int w = 0; w < NW; ++w) E += RE[w * N + k];
         if (p.mode == kModePartial) {
-          p.E_out[static_cast<size_t>(f) * N + k] = E;
+          p.E_out[(static_cast<size_t>(blockIdx.y) * gridDim.x + f) * N + k] = E;
         } else {
           // zero or non-finite energy flags the frame; z = 0 there
           const bool ok = (E > 0.f) && (E <= 3.4028234663852886e38f);
@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(32 * wgeo_warps(FC32 ? 8 : 4), 1) warp_kernel(
         for (int w = 0; w < NW; ++w) s = cadd(s, RP[static_cast<size_t>(w * dlc + j) * N + k]);
         const int dl = dl0 + j;
         if (p.mode == kModePartial) {
-          p.P_out[(static_cast<size_t>(f) * p.D + d0 + dl) * N + k] =
+          p.P_out[((static_cast<size_t>(blockIdx.y) * gridDim.x + f) * p.D + d0 + dl) * N + k] =
               make_float2(s.x * p.inv_sqrtN, s.y * p.inv_sqrtN);
         } else {
           const float ie = ie_s[k];

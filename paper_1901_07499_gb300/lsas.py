@@ -332,6 +332,20 @@ class Plan:
                                   _stream(stream)), "lsas_run_frame_host")
         return H, bits, eq
 
+    def run_frame_split(self, x, n_shards, H=None, bits=None, eq=None, want_eq=False, stream=None):
+        """lsas_run_frame_split_static: the antenna-split receiver with its
+        partial sums in the library's fixed scratch.  With equal shards (M a
+        multiple of n_shards, N <= 1024) one launch runs every shard of a
+        frame side by side, which cuts the latency of small batches."""
+        F = self._frames(x)
+        H = self.empty_H(F, x.device) if H is None else H
+        bits = self.empty_bits(F, x.device) if bits is None else bits
+        if eq is None and want_eq:
+            eq = self.empty_eq(F, x.device)
+        check(lsas_run_frame_split_static(self._h, _ptr(x), F, int(n_shards), _ptr(H), _ptr(bits),
+                                          _ptr(eq), _stream(stream)), "lsas_run_frame_split_static")
+        return H, bits, eq
+
     # ---- antenna split (shard partial sums, then a fixed-order combine)
     def empty_partials(self, F, shards=1, device="cuda"):
         """Zeroed P [shards][F][D][N] complex64 and E [shards][F][N] float32."""
