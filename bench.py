@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--frames", type=int, default=0, help="frames per step (default: config)")
     ap.add_argument("--pool", type=int, default=32, help="distinct seeded frames tiled")
     ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--latency-calls", type=int, default=200)
+    ap.add_argument("--latency-calls", type=int, default=1000)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving", action="store_true",
@@ -196,6 +196,56 @@ def time_oracle(cfg, seconds, min_frames=1):
     return rate, frames, blas_threads(), t_used
 
 
+ORACLE_ONE_CORE = r"""
+import json, sys, time
+sys.path.insert(0, sys.argv[1])
+import oracle, synth
+cfg = synth.config_by_name(sys.argv[2])
+seconds = float(sys.argv[3])
+frames, used, fid = 0, 0.0, 0
+while used < seconds or frames < 1:
+    b = synth.generate(cfg, frame_ids=[fid])
+    t0 = time.perf_counter()
+    oracle.receive(b.frames, cfg.N, cfg.cp, cfg.S, cfg.pilot_idx, cfg.Q, b.pilot, keep_Y=False)
+    used += time.perf_counter() - t0
+    frames += 1
+    fid += 1
+print(json.dumps({"rate": frames * cfg.M * cfg.S * cfg.N / used, "frames": frames, "seconds": used}))
+"""
+
+
+def time_oracle_one_core(cfg, seconds):
+    """The oracle on one core: a fresh interpreter with its BLAS held to one
+    thread (set before numpy loads).  Returns the parsed JSON or None."""
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               BLIS_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, "-c", ORACLE_ONE_CORE, ROOT, cfg.name, str(seconds)],
+                             env=env, capture_output=True, text=True, timeout=120 + 4 * seconds)
+        return json.loads(out.stdout.strip().splitlines()[-1]) if out.returncode == 0 else None
+    except Exception:
+        return None
+
+
+def cpu_model():
+    """CPU model name from lscpu (or /proc/cpuinfo), for the baseline's record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return os.uname().machine
+
+
 def blas_threads():
     try:
         from threadpoolctl import threadpool_info
@@ -208,6 +258,22 @@ def blas_threads():
         if os.environ.get(var):
             return int(os.environ[var])
     return os.cpu_count() or 1
+
+
+def fp32_roofline(cfg, F, ms_step, clocks):
+    """The FFT's FP32 rate against the CUDA cores' FP32 peak: nominal
+    5 N log2 N flop per FFT (every symbol of every antenna), peak = SMs x 128
+    FP32 lanes x 2 flop (FMA) x the maximum SM clock."""
+    import math
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak = sms * 128 * 2 * mhz * 1e6 / 1e12
+    flops = F * cfg.M * cfg.S * 5.0 * cfg.N * math.log2(cfg.N)
+    achieved = flops / (ms_step * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "flop_per_frame": flops / F,
+            "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz"}
 
 
 def workload_config(cfg, F, pool):
@@ -520,7 +586,13 @@ def main():
         rate, nfr, threads, used = time_oracle(cfg, args.cpu_seconds)
         cpu = {"value": rate, "unit": "samples/s", "cores": threads, "kind": "oracle",
                "sample": f"{nfr} frames of the same workload ({used:.1f} s), "
-                         "generation excluded"}
+                         "generation excluded",
+               "cpu_model": cpu_model()}
+        one = time_oracle_one_core(cfg, args.cpu_seconds / 2)
+        if one is not None:
+            cpu["one_core"] = {"value": one["rate"], "unit": "samples/s",
+                               "sample": f"{one['frames']} frames ({one['seconds']:.1f} s), "
+                                         "BLAS held to one thread"}
 
     if rank == 0:
         line = {
@@ -534,6 +606,7 @@ def main():
                          "peak_source": peak_src,
                          "kernel": "warp_kernel (fused CP strip+FFT+LS+MRC+demap, per-warp pipelines)" if cfg.N <= 1024 else "frame_kernel (fused CP strip+FFT+LS+MRC+demap)",
                          "algorithmic_bytes_per_frame": in_b + h_b + bit_b},
+            "roofline_fp32": fp32_roofline(cfg, F, ms_step, clocks),
             "e2e": {"value": samples / t_e2e, "unit": "samples/s",
                     "h2d_bytes_per_step": F * plan.host_input_bytes_per_frame(),
                     "d2h_bytes_per_step": F * (h_b + bit_b)},
