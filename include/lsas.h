@@ -264,7 +264,10 @@ lsas_status lsas_fftshift(lsas_plan plan, int what, void* d_buf, int n_frames,
  * (Sec. II-B) and names frame-level batching as its next step (Sec. IV).  A
  * server takes frames of several registered receiver configurations, one at
  * a time, from host memory, batches them per configuration and runs the
- * fused receiver (lsas_run_frame) on each batch.
+ * fused receiver (lsas_run_frame) on each batch.  Each configuration has two
+ * lanes (a stream with staging for max_batch frames) and at most one batch
+ * per lane in flight.  While both are busy its frames wait and the next
+ * batch takes up to max_batch of them.
  *
  * lsas_server_create: memory budget in bytes for everything registered
  *   later; max_batch frames per launch (1..1024); max_wait_us, how long the
@@ -273,8 +276,9 @@ lsas_status lsas_fftshift(lsas_plan plan, int what, void* d_buf, int n_frames,
  *   device, INVALID_ARG for bad arguments.
  * lsas_server_register: admit a configuration (as lsas_plan_create, plus the
  *   input format and an optional host pilot of N interleaved re,im floats).
- *   Its plan and staging for max_batch frames count against the budget:
- *   LSAS_ERR_CAPACITY when they do not fit.  Returns its id.
+ *   Its plan and the staging of both lanes (2 * max_batch frames) count
+ *   against the budget: LSAS_ERR_CAPACITY when they do not fit.  Returns
+ *   its id.
  * lsas_server_submit: queue one frame of a registered configuration:
  *   h_in [M][S*(N+CP)] samples, results to h_H [M][N], h_bits [D*N*q/8],
  *   h_eq [D][N] (nullable), all host memory that stays valid until the wait

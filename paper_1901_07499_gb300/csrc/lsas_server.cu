@@ -4,12 +4,19 @@
 // order, ...) arrive one at a time in host memory.  A configuration is
 // registered once: that is where memory is admitted (its plan and its
 // staging buffers must fit the server's budget) and where its stream lives.
-// Submitted frames wait in a per-configuration queue; a worker thread takes
-// the configuration with the oldest waiting frame, gathers up to max_batch of
-// its frames (or fewer once the oldest has waited max_wait_us), uploads them
-// into the configuration's staging buffer, runs the fused receiver on the
-// batch and copies each frame's results back to its own host buffers.  A host
-// callback after the copies records the completion time and wakes waiters.
+// Submitted frames wait in a per-configuration queue.  Each configuration
+// has two lanes (a stream with its own staging buffers), and a lane holds one
+// batch from dispatch until its results are home.  A worker thread takes the
+// configuration with the oldest waiting frame among those with a free lane,
+// gathers up to max_batch of its frames (or fewer once the oldest has waited
+// max_wait_us), uploads them into the lane's staging buffers, runs the fused
+// receiver on the batch and copies each frame's results back to its own host
+// buffers.  A host callback after the copies records the completion time,
+// frees the lane and wakes waiters.  While both lanes of a configuration are
+// busy its frames accumulate, so under load the batches grow to max_batch
+// instead of queueing many small launches (a launch of one frame costs about
+// as much device time as one of a full wave); the two lanes let one batch's
+// upload overlap the other's kernel.
 // Each frame is processed exactly as it would be alone (frames are
 // independent in the kernel), so the results do not depend on the mix.
 // Device-side conditions (zero channel energy, a bounded wait that ran out)
@@ -47,18 +54,30 @@ struct Done {
   double latency_us = 0.0;
 };
 
-struct Config {
-  lsas_plan plan = nullptr;
-  int M, N, cp, S, Q, D;
-  lsas_input_fmt fmt;
-  size_t in_b, h_b, bits_b, eq_b;   // bytes per frame
+// One stream with staging for max_batch frames; busy while a batch is on it.
+struct Lane {
   void* d_in = nullptr;
   float* d_H = nullptr;
   uint8_t* d_bits = nullptr;
   float* d_eq = nullptr;
   cudaStream_t stream = nullptr;
+  bool busy = false;
+};
+constexpr int kLanes = 2;
+
+struct Config {
+  lsas_plan plan = nullptr;   // shared by the lanes (read-only tables, latched status)
+  int M, N, cp, S, Q, D;
+  lsas_input_fmt fmt;
+  size_t in_b, h_b, bits_b, eq_b;   // bytes per frame
+  Lane lanes[kLanes];
   std::deque<Request> queue;
   size_t bytes = 0;
+  int free_lane() const {
+    for (int l = 0; l < kLanes; ++l)
+      if (!lanes[l].busy) return l;
+    return -1;
+  }
 };
 
 struct Batch;
@@ -86,11 +105,11 @@ namespace {
 struct Batch {
   lsas_server_s* s;
   std::vector<std::pair<uint64_t, Clock::time_point>> items;
-  int config;
+  int config, lane;
 };
 
 // Runs on a CUDA callback thread (no CUDA calls here): marks the batch's
-// frames done with their submit-to-results latency.
+// frames done with their submit-to-results latency and frees its lane.
 void CUDART_CB batch_done(void* arg) {
   Batch* b = static_cast<Batch*>(arg);
   lsas_server_s* s = b->s;
@@ -103,8 +122,10 @@ void CUDART_CB batch_done(void* arg) {
       d.status = LSAS_OK;
       d.latency_us = std::chrono::duration<double, std::micro>(now - it.second).count();
     }
+    s->configs[b->config]->lanes[b->lane].busy = false;
   }
   s->cv_done.notify_all();
+  s->cv_work.notify_one();
   delete b;
 }
 
@@ -121,19 +142,23 @@ void worker_loop(lsas_server_s* s) {
   cudaSetDevice(s->device);
   std::unique_lock<std::mutex> lock(s->mu);
   for (;;) {
-    // the configuration whose oldest waiting frame is oldest
+    // the configuration with a free lane whose oldest waiting frame is oldest
     int pick = -1;
     Clock::time_point oldest;
     for (size_t c = 0; c < s->configs.size(); ++c) {
       Config& cf = *s->configs[c];
-      if (cf.queue.empty()) continue;
+      if (cf.queue.empty() || cf.free_lane() < 0) continue;
       if (pick < 0 || cf.queue.front().submitted < oldest) {
         pick = static_cast<int>(c);
         oldest = cf.queue.front().submitted;
       }
     }
     if (pick < 0) {
-      if (s->stop) return;
+      // nothing to dispatch: every queue is empty or waits for a busy lane
+      // (a lane frees when its batch's callback runs, which notifies us)
+      bool pending = false;
+      for (const auto& c : s->configs) pending = pending || !c->queue.empty();
+      if (s->stop && !pending) return;
       s->cv_work.wait_for(lock, std::chrono::milliseconds(50));
       continue;
     }
@@ -148,39 +173,59 @@ void worker_loop(lsas_server_s* s) {
       reqs.push_back(cf.queue.front());
       cf.queue.pop_front();
     }
+    const int li = cf.free_lane();
+    Lane& ln = cf.lanes[li];
+    ln.busy = true;
     lock.unlock();
-    // upload, run, download on the configuration's stream
+    // upload, run, download on the lane's stream; as in lsas_run_frame_host,
+    // only the samples after each cyclic prefix cross the host link once rows
+    // of N samples span at least 1 KB (the receiver never reads the prefixes)
     lsas_status st = LSAS_OK;
     const int F = static_cast<int>(reqs.size());
-    for (int i = 0; i < F && st == LSAS_OK; ++i)
-      if (cudaMemcpyAsync(static_cast<unsigned char*>(cf.d_in) + i * cf.in_b, reqs[i].h_in, cf.in_b,
-                          cudaMemcpyHostToDevice, cf.stream) != cudaSuccess)
-        st = LSAS_ERR_CUDA;
+    const size_t bps = cf.fmt == LSAS_IN_SC16 ? 4 : 8;
+    const size_t pitch = static_cast<size_t>(cf.N + cf.cp) * bps;
+    const size_t keep = static_cast<size_t>(cf.N) * bps, skip = static_cast<size_t>(cf.cp) * bps;
+    const bool strip = cf.cp > 0 && keep >= 1024;
+    for (int i = 0; i < F && st == LSAS_OK; ++i) {
+      unsigned char* dst = static_cast<unsigned char*>(ln.d_in) + i * cf.in_b;
+      const unsigned char* src = static_cast<const unsigned char*>(reqs[i].h_in);
+      const cudaError_t e =
+          strip ? cudaMemcpy2DAsync(dst + skip, pitch, src + skip, pitch, keep,
+                                    static_cast<size_t>(cf.M) * cf.S, cudaMemcpyHostToDevice, ln.stream)
+                : cudaMemcpyAsync(dst, src, cf.in_b, cudaMemcpyHostToDevice, ln.stream);
+      if (e != cudaSuccess) st = LSAS_ERR_CUDA;
+    }
     if (st == LSAS_OK) {
       bool eq = false;   // z is computed when any frame of the batch asks for it
       for (const Request& r : reqs) eq = eq || r.h_eq != nullptr;
-      st = lsas_run_frame(cf.plan, cf.d_in, F, cf.d_H, cf.d_bits, eq ? cf.d_eq : nullptr, cf.stream);
+      st = lsas_run_frame(cf.plan, ln.d_in, F, ln.d_H, ln.d_bits, eq ? ln.d_eq : nullptr, ln.stream);
     }
     for (int i = 0; i < F && st == LSAS_OK; ++i) {
       const Request& r = reqs[i];
-      if (cudaMemcpyAsync(r.h_H, reinterpret_cast<unsigned char*>(cf.d_H) + i * cf.h_b, cf.h_b,
-                          cudaMemcpyDeviceToHost, cf.stream) != cudaSuccess ||
-          cudaMemcpyAsync(r.h_bits, cf.d_bits + i * cf.bits_b, cf.bits_b, cudaMemcpyDeviceToHost,
-                          cf.stream) != cudaSuccess ||
-          (r.h_eq && cudaMemcpyAsync(r.h_eq, reinterpret_cast<unsigned char*>(cf.d_eq) + i * cf.eq_b,
-                                     cf.eq_b, cudaMemcpyDeviceToHost, cf.stream) != cudaSuccess))
+      if (cudaMemcpyAsync(r.h_H, reinterpret_cast<unsigned char*>(ln.d_H) + i * cf.h_b, cf.h_b,
+                          cudaMemcpyDeviceToHost, ln.stream) != cudaSuccess ||
+          cudaMemcpyAsync(r.h_bits, ln.d_bits + i * cf.bits_b, cf.bits_b, cudaMemcpyDeviceToHost,
+                          ln.stream) != cudaSuccess ||
+          (r.h_eq && cudaMemcpyAsync(r.h_eq, reinterpret_cast<unsigned char*>(ln.d_eq) + i * cf.eq_b,
+                                     cf.eq_b, cudaMemcpyDeviceToHost, ln.stream) != cudaSuccess))
         st = LSAS_ERR_CUDA;
     }
     if (st == LSAS_OK) {
-      Batch* b = new Batch{s, {}, pick};
+      Batch* b = new Batch{s, {}, pick, li};
       for (const Request& r : reqs) b->items.emplace_back(r.ticket, r.submitted);
-      if (cudaLaunchHostFunc(cf.stream, batch_done, b) != cudaSuccess) {
+      if (cudaLaunchHostFunc(ln.stream, batch_done, b) != cudaSuccess) {
         delete b;
         st = LSAS_ERR_CUDA;
       }
     }
-    if (st != LSAS_OK) fail_batch(s, reqs, st);
+    if (st != LSAS_OK) {
+      // nothing will call back for this batch: wait for what was queued on
+      // the lane, then free it
+      cudaStreamSynchronize(ln.stream);
+      fail_batch(s, reqs, st);
+    }
     lock.lock();
+    if (st != LSAS_OK) ln.busy = false;
     s->launched += 1;
     s->frames += F;
   }
@@ -232,9 +277,9 @@ lsas_status lsas_server_register(lsas_server s, int M, int N, int cp_len, int n_
   cf->h_b = fb[1];
   cf->bits_b = fb[2];
   cf->eq_b = fb[3];
-  // admission: staging for max_batch frames plus the plan's own tables
+  // admission: staging for max_batch frames on each lane plus the plan's own tables
   const size_t plan_b = static_cast<size_t>(N) * 64 + (1u << 20);
-  cf->bytes = static_cast<size_t>(s->max_batch) * (fb[0] + fb[1] + fb[2] + fb[3]) + plan_b;
+  cf->bytes = kLanes * static_cast<size_t>(s->max_batch) * (fb[0] + fb[1] + fb[2] + fb[3]) + plan_b;
   {
     std::lock_guard<std::mutex> lock(s->mu);
     if (s->used + cf->bytes > s->budget) return LSAS_ERR_CAPACITY;
@@ -242,11 +287,13 @@ lsas_status lsas_server_register(lsas_server s, int M, int N, int cp_len, int n_
   }
   auto undo = [&](lsas_status e) {
     if (cf->plan) lsas_plan_destroy(cf->plan);
-    cudaFree(cf->d_in);
-    cudaFree(cf->d_H);
-    cudaFree(cf->d_bits);
-    cudaFree(cf->d_eq);
-    if (cf->stream) cudaStreamDestroy(cf->stream);
+    for (Lane& ln : cf->lanes) {
+      cudaFree(ln.d_in);
+      cudaFree(ln.d_H);
+      cudaFree(ln.d_bits);
+      cudaFree(ln.d_eq);
+      if (ln.stream) cudaStreamDestroy(ln.stream);
+    }
     std::lock_guard<std::mutex> lock(s->mu);
     s->used -= cf->bytes;
     return e;
@@ -258,15 +305,17 @@ lsas_status lsas_server_register(lsas_server s, int M, int N, int cp_len, int n_
   if (st == LSAS_OK && host_pilot_iq) st = lsas_plan_set_pilot(cf->plan, host_pilot_iq);
   if (st != LSAS_OK) return undo(st);
   const size_t B = static_cast<size_t>(s->max_batch);
-  if (cudaMalloc(&cf->d_in, B * cf->in_b) != cudaSuccess ||
-      cudaMalloc(&cf->d_H, B * cf->h_b) != cudaSuccess ||
-      cudaMalloc(&cf->d_bits, B * cf->bits_b) != cudaSuccess ||
-      cudaMalloc(&cf->d_eq, B * cf->eq_b) != cudaSuccess) {
-    cudaGetLastError();
-    return undo(LSAS_ERR_OOM);
+  for (Lane& ln : cf->lanes) {
+    if (cudaMalloc(&ln.d_in, B * cf->in_b) != cudaSuccess ||
+        cudaMalloc(&ln.d_H, B * cf->h_b) != cudaSuccess ||
+        cudaMalloc(&ln.d_bits, B * cf->bits_b) != cudaSuccess ||
+        cudaMalloc(&ln.d_eq, B * cf->eq_b) != cudaSuccess) {
+      cudaGetLastError();
+      return undo(LSAS_ERR_OOM);
+    }
+    if (cudaStreamCreateWithFlags(&ln.stream, cudaStreamNonBlocking) != cudaSuccess)
+      return undo(LSAS_ERR_CUDA);
   }
-  if (cudaStreamCreateWithFlags(&cf->stream, cudaStreamNonBlocking) != cudaSuccess)
-    return undo(LSAS_ERR_CUDA);
   std::lock_guard<std::mutex> lock(s->mu);
   s->configs.push_back(std::move(cf));
   *config_id = static_cast<int>(s->configs.size()) - 1;
@@ -327,15 +376,18 @@ lsas_status lsas_server_destroy(lsas_server s) {
   if (s->worker.joinable()) s->worker.join();
   lsas_status st = LSAS_OK;
   for (auto& cf : s->configs) {
-    if (cf->stream) cudaStreamSynchronize(cf->stream);
-    const lsas_status ps = lsas_plan_sync(cf->plan, cf->stream);
+    for (Lane& ln : cf->lanes)
+      if (ln.stream) cudaStreamSynchronize(ln.stream);
+    const lsas_status ps = lsas_plan_sync(cf->plan, cf->lanes[0].stream);
     if (ps != LSAS_OK && st == LSAS_OK) st = ps;
     lsas_plan_destroy(cf->plan);
-    cudaFree(cf->d_in);
-    cudaFree(cf->d_H);
-    cudaFree(cf->d_bits);
-    cudaFree(cf->d_eq);
-    if (cf->stream) cudaStreamDestroy(cf->stream);
+    for (Lane& ln : cf->lanes) {
+      cudaFree(ln.d_in);
+      cudaFree(ln.d_H);
+      cudaFree(ln.d_bits);
+      cudaFree(ln.d_eq);
+      if (ln.stream) cudaStreamDestroy(ln.stream);
+    }
   }
   delete s;
   return st;

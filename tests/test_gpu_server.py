@@ -9,6 +9,10 @@ submitted interleaved in random order from pinned host memory.
   with LSAS_ERR_CAPACITY; an unknown ticket is refused; a wait with no time
   left on a frame still queued behind a long batch window times out and the
   ticket stays valid.
+* Batching under load: with no batch window at all (max_wait_us = 0), a burst
+  of 64 frames of one configuration still runs in a handful of full batches,
+  because a configuration has at most two batches (lanes) in flight and its
+  frames accumulate meanwhile; every frame equals its run alone.
 """
 
 import numpy as np
@@ -98,3 +102,29 @@ def test_admission_tickets_and_timeouts(L):
     assert L.lsas_server_wait(srv.handle, t, 1.0, None) == L.LSAS_ERR_TIMEOUT
     assert srv.wait(t) > 0            # still valid; the batch window closes
     assert srv.close() == L.LSAS_OK
+
+
+def test_burst_fills_batches_while_lanes_are_busy(L):
+    import torch
+    c = sweep_config(64, 1024)
+    F, B = 64, 8
+    b = synth.generate(c, frame_ids=range(4))
+    srv = L.Server(mem_budget=2 << 30, max_batch=B, max_wait_us=0.0)
+    cid = srv.register(c.M, c.N, c.cp, c.S, c.pilot_idx, c.Q, fmt=c.fmt, pilot=b.pilot)
+    xs = [_pinned(b.frames[i]) for i in range(4)]
+    outs = [(torch.empty((c.M, c.N), dtype=torch.complex64).pin_memory(),
+             torch.empty(c.D * c.N * c.q // 8, dtype=torch.uint8).pin_memory()) for _ in range(F)]
+    tickets = [srv.submit(cid, xs[f % 4], *outs[f]) for f in range(F)]   # one burst
+    for t in tickets:
+        srv.wait(t)
+    st = srv.stats()
+    assert st["frames"] == F
+    assert st["launches"] <= 24, st          # one launch per frame without the lanes
+    assert srv.close() == L.LSAS_OK
+    plan = L.Plan(c.M, c.N, c.cp, c.S, c.pilot_idx, c.Q, fmt=c.fmt, max_frames=4, pilot=b.pilot)
+    Ha, ba, _ = plan.run_frame(torch.from_numpy(np.ascontiguousarray(b.frames)).cuda())
+    plan.sync()
+    Ha, ba = Ha.cpu().numpy(), ba.cpu().numpy()
+    for f, (H, bits) in enumerate(outs):
+        assert np.array_equal(H.numpy().view(np.uint32), Ha[f % 4].view(np.uint32))
+        assert np.array_equal(bits.numpy(), ba[f % 4])
