@@ -74,28 +74,9 @@ bool tc_tables(int N, std::vector<uint16_t>& w1, std::vector<uint16_t>& w2,
 
 // ---------------------------------------------------------------- device
 
-__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, int K) {
-  uint64_t d = static_cast<uint64_t>((addr & 0x3FFFF) >> 4);
-  d |= static_cast<uint64_t>(128 >> 4) << 16;              // K-adjacent core matrices
-  d |= static_cast<uint64_t>((16 * K) >> 4) << 32;         // 8-row groups
-  d |= static_cast<uint64_t>(1) << 46;                     // descriptor version
-  return d;
-}
-// kind::f16 instruction descriptor: fp32 accumulator, fp16 A and B, both
-// K-major, M = 128, N columns
-__device__ __forceinline__ uint32_t tc_idesc(int n) {
-  return (1u << 4) | (static_cast<uint32_t>(n >> 3) << 17) | (static_cast<uint32_t>(128 >> 4) << 24);
-}
-__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
-                                       uint32_t acc) {
-  asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
-               "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-               :: "r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
-}
-__device__ __forceinline__ void tc_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-               :: "r"(bar) : "memory");
-}
+// Operand images are K-major rows of K halves: core matrices adjacent along K
+// are 128 bytes apart, 8-row groups 16 K bytes apart.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, int K) { return umma_desc(addr, 128, 16 * K); }
 
 // (a, b) -> packed fp16 hi = fp16(v) and lo = fp16(v - hi), as 32-bit words
 __device__ __forceinline__ void split16x2(float a, float b, uint32_t& hi, uint32_t& lo) {
@@ -153,7 +134,7 @@ template <int LOG2N, bool FC32>
 __global__ void __launch_bounds__(kTcThreads, 1) tcfft_kernel(const KParams p) {
   using G = TcGeo<LOG2N>;
   constexpr int N = G::N, N2 = G::N2, R = G::R;
-  extern __shared__ __align__(1024) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
   const bool split = p.terms == 3;
@@ -222,10 +203,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) tcfft_kernel(const KParams p) {
           const uint32_t abase = smem_u32(a1 + (2 * t + (term == 2 ? 1 : 0)) * G::A1_BYTES);
           const uint32_t bbase = smem_u32(w1 + (term == 1 ? 1 : 0) * G::W1_BYTES);
           for (int kc = 0; kc < 4; ++kc)
-            tc_mma(tmem + t * 64, tc_desc(abase + kc * 256, 64), tc_desc(bbase + kc * 256, 64),
-                   tc_idesc(64), (term > 0 || kc > 0) ? 1u : 0u);
+            umma_f16(tmem + t * 64, tc_desc(abase + kc * 256, 64), tc_desc(bbase + kc * 256, 64),
+                     umma_idesc(64, false), (term > 0 || kc > 0) ? 1u : 0u);
         }
-      tc_commit(smem_u32(bar));
+      umma_commit(smem_u32(bar));
     }
     if (!timed_out && !mbar_wait_bounded(smem_u32(bar), phase)) {
       timed_out = true;
@@ -275,10 +256,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) tcfft_kernel(const KParams p) {
           const uint32_t abase = smem_u32(a2 + (2 * t + (term == 2 ? 1 : 0)) * G::A2_BYTES);
           const uint32_t bbase = smem_u32(w2 + (term == 1 ? 1 : 0) * G::W2_BYTES);
           for (int kc = 0; kc < (2 * N2) / 16; ++kc)
-            tc_mma(tmem + 128 + t * (2 * N2), tc_desc(abase + kc * 256, 2 * N2),
-                   tc_desc(bbase + kc * 256, 2 * N2), tc_idesc(2 * N2), (term > 0 || kc > 0) ? 1u : 0u);
+            umma_f16(tmem + 128 + t * (2 * N2), tc_desc(abase + kc * 256, 2 * N2),
+                     tc_desc(bbase + kc * 256, 2 * N2), umma_idesc(2 * N2, false),
+                     (term > 0 || kc > 0) ? 1u : 0u);
         }
-      tc_commit(smem_u32(bar));
+      umma_commit(smem_u32(bar));
     }
     if (!timed_out && !mbar_wait_bounded(smem_u32(bar), phase)) {
       timed_out = true;
