@@ -423,6 +423,26 @@ lsas_status lsas_run_frame_host(lsas_plan plan, const void* h_in,
                                 float* h_eq, void* stream);
 
 /*
+ * Call timing (the paper times each receiver function and averages it;
+ * Sec. III).  While a plan's profiling is on, every call of a device entry
+ * point on that plan records a CUDA event before and after what it enqueues
+ * on its stream; lsas_run_frame_host, which synchronises, is timed on the
+ * host clock.  A call that calls another entry point (the per-shard form of
+ * lsas_run_frame_split_static) records both.  Profiling is on from creation
+ * when the environment variable LSAS_PROFILE is "1", and otherwise follows
+ * lsas_plan_set_profile.
+ * lsas_plan_profile: waits for the recorded calls to finish, adds them to
+ *   per-function totals and writes them as one JSON object,
+ *   {"lsas_run_frame": {"calls": 3, "ms": 5.71}, ...}, NUL-terminated, into
+ *   buf (len bytes).  needed (nullable) receives the bytes required.  With
+ *   buf NULL only the size is reported and nothing is cleared; a successful
+ *   write clears the totals.  CAPACITY if len is too small (the totals are
+ *   kept), INVALID_ARG for a null plan or both buf and needed null.
+ */
+lsas_status lsas_plan_set_profile(lsas_plan plan, int on);
+lsas_status lsas_plan_profile(lsas_plan plan, char* buf, size_t len, size_t* needed);
+
+/*
  * Synchronise stream, then return and clear the plan's latched device status
  * (LSAS_OK, LSAS_ERR_TIMEOUT or LSAS_ERR_DEVICE), or LSAS_ERR_CUDA.
  */

@@ -7,13 +7,16 @@
 // conj(X)/|X|^2/sqrt(N) (Sec. II-C: LS is a division by the pilot), and a
 // status word the kernels latch device-side conditions into.  Every argument
 // is checked here before anything is enqueued.
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstdint>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "lsas.h"
@@ -88,7 +91,88 @@ struct lsas_plan_s {
   cudaEvent_t ev_up[2] = {nullptr, nullptr};
   cudaEvent_t ev_k[2] = {nullptr, nullptr};
   cudaEvent_t ev_down[2] = {nullptr, nullptr};
+  // call timing (LSAS_PROFILE=1 at creation, or lsas_plan_set_profile)
+  struct ProfRec {
+    const char* name;
+    cudaEvent_t a, b;   // null for a call timed on the host clock
+    double host_ms;
+  };
+  bool prof = false;
+  std::mutex prof_mu;
+  std::vector<ProfRec> prof_recs;
+  std::vector<cudaEvent_t> prof_pool;
+  std::map<std::string, std::pair<uint64_t, double>> prof_acc;
 };
+
+namespace {
+
+cudaEvent_t prof_event(lsas_plan p) {   // caller holds prof_mu
+  if (!p->prof_pool.empty()) {
+    cudaEvent_t e = p->prof_pool.back();
+    p->prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+// Times one library call while the plan's profiling is on: events on the
+// call's stream around what it enqueues, or the host clock for a call that
+// synchronises before it returns.  Records are folded by lsas_plan_profile.
+class ProfScope {
+ public:
+  ProfScope(lsas_plan p, const char* name, void* stream, bool host = false)
+      : p_(p && p->prof ? p : nullptr), name_(name), st_(static_cast<cudaStream_t>(stream)),
+        host_(host) {
+    if (!p_) return;
+    if (host_) {
+      t0_ = std::chrono::steady_clock::now();
+      return;
+    }
+    std::lock_guard<std::mutex> lock(p_->prof_mu);
+    a_ = prof_event(p_);
+    if (a_ && cudaEventRecord(a_, st_) != cudaSuccess) {
+      cudaGetLastError();
+      p_->prof_pool.push_back(a_);
+      a_ = nullptr;
+    }
+  }
+  ~ProfScope() {
+    if (!p_) return;
+    std::lock_guard<std::mutex> lock(p_->prof_mu);
+    if (host_) {
+      const double ms =
+          std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0_).count();
+      p_->prof_recs.push_back({name_, nullptr, nullptr, ms});
+      return;
+    }
+    if (!a_) return;
+    cudaEvent_t b = prof_event(p_);
+    if (b && cudaEventRecord(b, st_) == cudaSuccess) {
+      p_->prof_recs.push_back({name_, a_, b, 0.0});
+    } else {
+      cudaGetLastError();
+      p_->prof_pool.push_back(a_);
+      if (b) p_->prof_pool.push_back(b);
+    }
+  }
+  ProfScope(const ProfScope&) = delete;
+  ProfScope& operator=(const ProfScope&) = delete;
+
+ private:
+  lsas_plan p_;
+  const char* name_;
+  cudaStream_t st_;
+  bool host_;
+  cudaEvent_t a_ = nullptr;
+  std::chrono::steady_clock::time_point t0_;
+};
+
+}  // namespace
 
 namespace {
 
@@ -418,6 +502,10 @@ lsas_status lsas_plan_create(int M, int N, int cp_len, int n_sym, int pilot_idx,
     p->thr[b] = b < L - 1 ? static_cast<float>((2.0 * (b + 1) - L) * A) : 0.f;
   fill_w32(p->w32, p->w32n);
   p->launch = launcher_for(N);
+  {
+    const char* e = std::getenv("LSAS_PROFILE");
+    p->prof = e && e[0] == '1';
+  }
   if (!plan_geometry(M, N, p->D, p->fmt, &p->geo)) {
     delete p;
     return LSAS_ERR_UNSUPPORTED;
@@ -522,6 +610,7 @@ lsas_status lsas_fft(lsas_plan p, const void* d_in, int n_frames, float* d_Y, vo
   k.nslots = p->geo.fft_slots;
   k.use_tma = tma_ok(p, d_in) ? 1 : 0;
   const int grid = n_frames * k.chunks;
+  ProfScope prof(p, "lsas_fft", stream);
   if (p->launch(kKindFft, p->fmt == LSAS_IN_FC32, k, grid, p->geo.smem_fft,
                 static_cast<cudaStream_t>(stream)) != cudaSuccess)
     return LSAS_ERR_CUDA;
@@ -543,6 +632,7 @@ lsas_status lsas_estimate(lsas_plan p, const void* d_in, int n_frames, float* d_
   k.mode = kModeEstimate;
   k.use_tma = tma_ok(p, d_in) ? 1 : 0;
   const int grid = n_frames * k.chunks;
+  ProfScope prof(p, "lsas_estimate", stream);
   if (p->launch(kKindEstimate, p->fmt == LSAS_IN_FC32, k, grid, p->geo.smem_est,
                 static_cast<cudaStream_t>(stream)) != cudaSuccess)
     return LSAS_ERR_CUDA;
@@ -557,6 +647,7 @@ lsas_status lsas_demodulate(lsas_plan p, const void* d_in, const float* d_H, int
   if (n_frames == 0) return LSAS_OK;
   if (!d_in || !d_H || !d_bits) return LSAS_ERR_INVALID_ARG;
   if (set_device(p) != LSAS_OK) return LSAS_ERR_CUDA;
+  ProfScope prof(p, "lsas_demodulate", stream);
   return launch_frame(p, d_in, n_frames, nullptr, d_H, d_bits, d_eq, kModeDemod,
                       static_cast<cudaStream_t>(stream));
 }
@@ -569,6 +660,7 @@ lsas_status lsas_run_frame(lsas_plan p, const void* d_in, int n_frames, float* d
   if (n_frames == 0) return LSAS_OK;
   if (!d_in || !d_H || !d_bits) return LSAS_ERR_INVALID_ARG;
   if (set_device(p) != LSAS_OK) return LSAS_ERR_CUDA;
+  ProfScope prof(p, "lsas_run_frame", stream);
   return launch_frame(p, d_in, n_frames, d_H, nullptr, d_bits, d_eq, kModeRun,
                       static_cast<cudaStream_t>(stream));
 }
@@ -591,6 +683,7 @@ lsas_status lsas_mrc_partial(lsas_plan p, const void* d_in, int n_frames, int m_
   k.M = m_count;
   k.m0 = m_begin;
   k.chunks = (m_count + p->geo.Af - 1) / p->geo.Af;
+  ProfScope prof(p, "lsas_mrc_partial", stream);
   k.mode = kModePartial;
   k.use_tma = tma_ok(p, d_in) ? 1 : 0;
   if (p->launch(kKindFrame, p->fmt == LSAS_IN_FC32, k, n_frames, p->geo.smem_frame,
@@ -620,6 +713,7 @@ lsas_status lsas_mrc_combine(lsas_plan p, const float* d_P, const float* d_E, in
   k.nframes = n_frames;
   k.bits = d_bits;
   k.eq = reinterpret_cast<float2*>(d_eq);
+  ProfScope prof(p, "lsas_mrc_combine", stream);
   if (launch_combine(k, static_cast<cudaStream_t>(stream)) != cudaSuccess) return LSAS_ERR_CUDA;
   return LSAS_OK;
 }
@@ -650,6 +744,7 @@ lsas_status lsas_fft_tc(lsas_plan p, const void* d_in, int n_frames, int terms, 
   const int per_sm = tc_smem_bytes(p->N) * 2 <= kSmemLimit ? 2 : 1;
   const size_t cap = static_cast<size_t>(p->sms) * per_sm;
   const int grid = static_cast<int>(batches < cap ? batches : cap);
+  ProfScope prof(p, "lsas_fft_tc", stream);
   if (launch_tcfft(k, p->N, grid, static_cast<cudaStream_t>(stream)) != cudaSuccess)
     return LSAS_ERR_CUDA;
   return LSAS_OK;
@@ -669,6 +764,7 @@ lsas_status lsas_receive_y(lsas_plan p, const float* d_Y, int n_frames, float* d
   k.H_out = reinterpret_cast<float2*>(d_H);
   k.bits = d_bits;
   k.eq = reinterpret_cast<float2*>(d_eq);
+  ProfScope prof(p, "lsas_receive_y", stream);
   if (launch_yrx(k, n_frames, static_cast<cudaStream_t>(stream)) != cudaSuccess)
     return LSAS_ERR_CUDA;
   return LSAS_OK;
@@ -707,6 +803,7 @@ lsas_status lsas_pn_sync(lsas_plan p, const void* d_capture, int n_frames, int c
   k.window = window;
   k.offsets = d_offset;
   k.peaks = d_peak;
+  ProfScope prof(p, "lsas_pn_sync", stream);
   if (launch_pn(k, p->fmt == LSAS_IN_FC32, n_frames, static_cast<cudaStream_t>(stream)) !=
       cudaSuccess)
     return LSAS_ERR_CUDA;
@@ -730,6 +827,7 @@ lsas_status lsas_pn_extract(lsas_plan p, const void* d_capture, int n_frames, in
   k.backoff = backoff;
   k.cap_len = capture_len;
   k.Y_out = static_cast<float2*>(d_frames);
+  ProfScope prof(p, "lsas_pn_extract", stream);
   if (launch_extract(k, p->fmt == LSAS_IN_FC32, n_frames, static_cast<cudaStream_t>(stream)) !=
       cudaSuccess)
     return LSAS_ERR_CUDA;
@@ -752,6 +850,7 @@ lsas_status lsas_fftshift(lsas_plan p, int what, void* d_buf, int n_frames, void
   if (!d_buf) return LSAS_ERR_INVALID_ARG;
   if (set_device(p) != LSAS_OK) return LSAS_ERR_CUDA;
   const int kind = what == LSAS_SHIFT_BITS ? 1 : 0;
+  ProfScope prof(p, "lsas_fftshift", stream);
   if (launch_shift(d_buf, kind, rows, p->N, p->N * p->q / 8, p->sms,
                    static_cast<cudaStream_t>(stream)) != cudaSuccess)
     return LSAS_ERR_CUDA;
@@ -804,6 +903,7 @@ lsas_status lsas_run_frame_host(lsas_plan p, const void* h_in, int n_frames, flo
           cudaEventCreateWithFlags(&p->ev_down[i], cudaEventDisableTiming) != cudaSuccess)
         return LSAS_ERR_CUDA;
   }
+  ProfScope prof(p, "lsas_run_frame_host", stream, /*host=*/true);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   // Chunk c uses staging buffer c % 2.  Uploads run on up_stream, kernels on
   // the caller's stream, downloads on down_stream, so the upload of chunk
@@ -877,6 +977,55 @@ lsas_status lsas_plan_info(lsas_plan p, int out[8]) {
   return LSAS_OK;
 }
 
+lsas_status lsas_plan_set_profile(lsas_plan p, int on) {
+  if (!p) return LSAS_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(p->prof_mu);
+  p->prof = on != 0;
+  return LSAS_OK;
+}
+
+lsas_status lsas_plan_profile(lsas_plan p, char* buf, size_t len, size_t* needed) {
+  if (!p || (!buf && !needed)) return LSAS_ERR_INVALID_ARG;
+  if (set_device(p) != LSAS_OK) return LSAS_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(p->prof_mu);
+  // fold the finished records (waits for the calls' stop events)
+  lsas_status st = LSAS_OK;
+  for (const auto& r : p->prof_recs) {
+    double ms = r.host_ms;
+    if (r.a) {
+      float f = 0.f;
+      if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&f, r.a, r.b) != cudaSuccess) {
+        cudaGetLastError();
+        st = LSAS_ERR_CUDA;
+      }
+      ms = f;
+      p->prof_pool.push_back(r.a);
+      p->prof_pool.push_back(r.b);
+    }
+    auto& acc = p->prof_acc[r.name];
+    acc.first += 1;
+    acc.second += ms;
+  }
+  p->prof_recs.clear();
+  if (st != LSAS_OK) return st;
+  std::string js = "{";
+  char item[192];
+  bool first = true;
+  for (const auto& kv : p->prof_acc) {
+    std::snprintf(item, sizeof(item), "%s\"%s\": {\"calls\": %llu, \"ms\": %.6f}", first ? "" : ", ",
+                  kv.first.c_str(), static_cast<unsigned long long>(kv.second.first), kv.second.second);
+    js += item;
+    first = false;
+  }
+  js += "}";
+  if (needed) *needed = js.size() + 1;
+  if (!buf) return LSAS_OK;
+  if (len < js.size() + 1) return LSAS_ERR_CAPACITY;
+  std::memcpy(buf, js.c_str(), js.size() + 1);
+  p->prof_acc.clear();
+  return LSAS_OK;
+}
+
 lsas_status lsas_plan_destroy(lsas_plan p) {
   if (!p) return LSAS_ERR_INVALID_ARG;
   if (set_device(p) == LSAS_OK) cudaDeviceSynchronize();
@@ -900,6 +1049,11 @@ lsas_status lsas_plan_destroy(lsas_plan p) {
     if (p->ev_k[i]) cudaEventDestroy(p->ev_k[i]);
     if (p->ev_down[i]) cudaEventDestroy(p->ev_down[i]);
   }
+  for (const auto& r : p->prof_recs) {
+    if (r.a) cudaEventDestroy(r.a);
+    if (r.b) cudaEventDestroy(r.b);
+  }
+  for (cudaEvent_t e : p->prof_pool) cudaEventDestroy(e);
   delete p;
   return LSAS_OK;
 }
@@ -918,6 +1072,7 @@ lsas_status lsas_run_frame_split_static(lsas_plan p, const void* d_in, int n_fra
   if (n_frames == 0) return LSAS_OK;
   if (!d_in || !d_H || !d_bits) return LSAS_ERR_INVALID_ARG;
   if (set_device(p) != LSAS_OK) return LSAS_ERR_CUDA;
+  ProfScope prof(p, "lsas_run_frame_split_static", stream);
   unsigned char* scratch = static_cast<unsigned char*>(split_scratch_for(p->device));
   if (!scratch) return LSAS_ERR_CUDA;
   float* P = reinterpret_cast<float*>(scratch);

@@ -85,6 +85,8 @@ lsas_dn_adam = _proto("lsas_dn_adam", [_vp, _vp, _vp, _vp, _i, C.c_float, _vp])
 lsas_dn_to_bf16 = _proto("lsas_dn_to_bf16", [_vp, _vp, _vp])
 lsas_dn_apply_tc = _proto("lsas_dn_apply_tc", [_vp, _vp, _i, _i, _vp, _vp, _vp, _vp])
 lsas_plan_set_fault = _proto("lsas_plan_set_fault", [_vp, _i])
+lsas_plan_set_profile = _proto("lsas_plan_set_profile", [_vp, _i])
+lsas_plan_profile = _proto("lsas_plan_profile", [_vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)])
 lsas_plan_sync = _proto("lsas_plan_sync", [_vp, _vp])
 lsas_plan_info = _proto("lsas_plan_info", [_vp, C.POINTER(_i)])
 lsas_plan_destroy = _proto("lsas_plan_destroy", [_vp])
@@ -99,6 +101,7 @@ EXPORTED = ["lsas_status_str", "lsas_check_config", "lsas_frame_bytes",
             "lsas_server_wait", "lsas_server_stats", "lsas_server_destroy",
             "lsas_dn_work_size", "lsas_dn_apply", "lsas_dn_grad", "lsas_dn_adam",
             "lsas_dn_to_bf16", "lsas_dn_apply_tc", "lsas_plan_set_fault",
+            "lsas_plan_set_profile", "lsas_plan_profile",
             "lsas_plan_sync", "lsas_plan_info",
             "lsas_plan_destroy"]
 
@@ -375,6 +378,20 @@ class Plan:
         check(lsas_mrc_combine(self._h, _ptr(P), _ptr(E), G, F, _ptr(bits), _ptr(eq),
                                _stream(stream)), "lsas_mrc_combine")
         return bits, eq
+
+    def set_profile(self, on: bool = True) -> None:
+        """Time every library call on this plan (CUDA events on its stream)."""
+        check(lsas_plan_set_profile(self._h, 1 if on else 0), "lsas_plan_set_profile")
+
+    def profile(self) -> dict:
+        """Per-function call counts and device milliseconds since the last
+        read: {"lsas_run_frame": {"calls": n, "ms": t}, ...}; clears them."""
+        import json
+        need = C.c_size_t()
+        check(lsas_plan_profile(self._h, None, 0, C.byref(need)), "lsas_plan_profile")
+        buf = C.create_string_buffer(need.value + 256)
+        check(lsas_plan_profile(self._h, buf, len(buf), C.byref(need)), "lsas_plan_profile")
+        return json.loads(buf.value.decode())
 
     def sync(self, stream=None) -> None:
         """Synchronise and raise if a device-side condition was latched."""

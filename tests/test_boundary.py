@@ -81,6 +81,8 @@ def test_null_plan_is_rejected(L):
     assert L.lsas_plan_sync(None, None) == L.LSAS_ERR_INVALID_ARG
     assert L.lsas_plan_destroy(None) == L.LSAS_ERR_INVALID_ARG
     assert L.lsas_plan_create(8, 64, 16, 4, 0, 4, None) == L.LSAS_ERR_INVALID_ARG
+    assert L.lsas_plan_set_profile(None, 1) == L.LSAS_ERR_INVALID_ARG
+    assert L.lsas_plan_profile(None, None, 0, None) == L.LSAS_ERR_INVALID_ARG
 
 
 def test_plan_create_without_gpu_fails_cleanly(L):
