@@ -388,9 +388,10 @@ lsas_status lsas_plan_set_fault(lsas_plan plan, int kind);
  * partial sum that the combine pass of the same call reads.
  * Launches: when n_shards divides M and N <= 1024, the shard pass is one
  * launch whose grid row g processes shard g of every frame, so a frame's
- * shards run on different SMs at the same time (the latency of a single
- * frame falls roughly by the number of shards while each shard keeps at
- * least 8 antennas); otherwise one launch per shard.  Both give the same
+ * shards run on different SMs at the same time; for small batches
+ * (2 * n_frames * n_shards <= SMs) its grid layers also split the data
+ * symbols into their groups, each block repeating the pilot transform.
+ * Otherwise there is one launch per shard.  Every form gives the same
  * partial sums, hence the same results.
  * The first call on each device looks up the scratch address
  * (cudaGetSymbolAddress) with that device current; a caller that captures

@@ -35,7 +35,7 @@ static cudaError_t launch_t(int kind, const KParams& p, int grid, int smem, cuda
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) limit[kind][dev] = smem;
   }
-  fn<<<dim3(grid, p.grid_y > 1 ? p.grid_y : 1), threads, smem, st>>>(p);
+  fn<<<dim3(grid, p.grid_y > 1 ? p.grid_y : 1, p.group_z ? p.groups : 1), threads, smem, st>>>(p);
   return cudaGetLastError();
 }
 

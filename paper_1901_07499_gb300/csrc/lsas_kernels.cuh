@@ -75,6 +75,8 @@ struct KParams {
                          // blockIdx.y (its first antenna is m0 + blockIdx.y * shard_y, its
                          // partials start at shard blockIdx.y of [G][F][...]); 0 otherwise
   int grid_y;            // grid rows (shards) of the launch; 0 or 1 for a 1-D grid
+  int group_z;           // partial mode of the per-warp kernel: 1 = grid z index g runs
+                         // data-symbol group g alone (groups grid layers); 0 otherwise
   int chunks;            // ceil(M / A)
   int groups, dg;        // data-symbol groups per frame, data symbols per group
   int mode;              // kModeDemod, kModeRun or kModePartial (frame_kernel)

@@ -1090,6 +1090,9 @@ lsas_status lsas_run_frame_split_static(lsas_plan p, const void* d_in, int n_fra
     k.M = p->M / n_shards;
     k.shard_y = k.M;
     k.grid_y = n_shards;
+    // small batches: one block per data-symbol group as well (each repeats
+    // the pilot transform), so a frame's groups also run side by side
+    k.group_z = (p->geo.groups > 1 && n_frames * n_shards * 2 <= p->sms) ? 1 : 0;
     k.chunks = (k.M + p->geo.Af - 1) / p->geo.Af;
     k.mode = kModePartial;
     k.use_tma = tma_ok(p, d_in) ? 1 : 0;

@@ -115,12 +115,17 @@ __global__ void __launch_bounds__(32 * wgeo_warps(FC32 ? 8 : 4), 1) warp_kernel(
   int issued = 0;  // steps whose copies this warp has issued
   int slot = 0;    // ring slot of the next step to consume (step % K) ...
   int phase = 0;   // ... and its mbarrier phase ((step / K) & 1)
-  for (int g = 0; g < p.groups; ++g) {
+  // one data-symbol group per grid z index (partial mode, small batches):
+  // every group's block transforms the pilot itself; group 0 alone writes H
+  // and the channel energy
+  const int g_lo = p.group_z ? static_cast<int>(blockIdx.z) : 0;
+  const int g_hi = p.group_z ? g_lo + 1 : p.groups;
+  for (int g = g_lo; g < g_hi; ++g) {
     const int nd = min(p.dg, p.D - g * p.dg);
     const int d0 = g * p.dg;
-    const bool pilot_here = fft_pilot(p) && g == 0;
-    const int items = group_items(p, g);
-    if (g == 0) {
+    const bool pilot_here = fft_pilot(p) && (g == 0 || p.group_z);
+    const int items = nd + (pilot_here ? 1 : 0);
+    if (g == g_lo) {
 #pragma unroll
       for (int q0 = 0; q0 < OWN; q0 += ZC) Tmem<ZC>::st(tE + q0, zero);
     }
@@ -229,7 +234,7 @@ __global__ void __launch_bounds__(32 * wgeo_warps(FC32 ? 8 : 4), 1) warp_kernel(
             const int k = bin_of<LOG2N>(jt, e);
             const float2 hv = cmul(v[e], __ldg(p.xinv + k));
             h[e] = valid ? hv : make_float2(0.f, 0.f);
-            if (valid) p.H_out[hrow + k] = hv;
+            if (valid && g == 0) p.H_out[hrow + k] = hv;
             v[e] = make_float2(h[e].x * h[e].x + h[e].y * h[e].y, 0.f);
           }
           reduce_scatter<A, 16>(v, alpha);
