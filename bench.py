@@ -361,6 +361,7 @@ def serving_report(args):
         finished = [False]
 
         def waiter():
+            # collects results in groups of up to 64 tickets (one call each)
             i = 0
             while True:
                 with cv:
@@ -368,10 +369,11 @@ def serving_report(args):
                         cv.wait()
                     if i >= len(tickets):
                         return
-                    t, ci = tickets[i]
-                lat.append(srv.wait(t))
-                done_samples[0] += samples[ci]
-                i += 1
+                    chunk = tickets[i:i + 64]
+                got = srv.wait_many([t for t, _ in chunk])
+                done_samples[0] += sum(samples[ci] for _, ci in chunk)
+                lat.extend(got)
+                i += len(chunk)
 
         th = threading.Thread(target=waiter)
         th.start()
@@ -382,18 +384,24 @@ def serving_report(args):
         while t_next - t0 < args.serving_seconds:
             while time.perf_counter() < t_next:
                 pass
-            ci = int(rng.integers(len(cfgs)))
-            slot = n % ring
-            if n >= ring:   # the slot's previous result must be home before reuse
-                while len(lat) <= n - ring:
-                    time.sleep(0)
-            H, bits = outs[ci][slot]
-            t = srv.submit(ids[ci], xs[ci][n % 4], H, bits)
+            # every arrival that is due goes to the server in one call
+            now = time.perf_counter()
+            batch, cis = [], []
+            while t_next <= now and t_next - t0 < args.serving_seconds and len(batch) < 64:
+                ci = int(rng.integers(len(cfgs)))
+                slot = n % ring
+                if n >= ring:   # the slot's previous result must be home before reuse
+                    while len(lat) <= n - ring:
+                        time.sleep(0)
+                H, bits = outs[ci][slot]
+                batch.append((ids[ci], xs[ci][n % 4], H, bits))
+                cis.append(ci)
+                n += 1
+                t_next += rng.exponential(1.0 / rate)
+            ts = srv.submit_many(batch)
             with cv:
-                tickets.append((t, ci))
+                tickets.extend(zip(ts, cis))
                 cv.notify()
-            n += 1
-            t_next += rng.exponential(1.0 / rate)
         with cv:
             finished[0] = True
             cv.notify()

@@ -288,6 +288,16 @@ lsas_status lsas_fftshift(lsas_plan plan, int what, void* d_buf, int n_frames,
  *   LSAS_ERR_TIMEOUT if they are not ready (the ticket stays valid),
  *   INVALID_ARG for an unknown ticket.  latency_us (nullable) receives the
  *   time from submit to results in host memory.
+ * lsas_server_submit_many: lsas_server_submit for n frames in one call
+ *   (arrays of n entries; h_eq may be NULL, or an array whose entries may be
+ *   NULL).  Either every frame is queued (tickets[i] for frame i) or, on
+ *   INVALID_ARG for any entry, none is.
+ * lsas_server_wait_many: waits up to timeout_ms in total for all n tickets.
+ *   On LSAS_ERR_TIMEOUT every ticket stays valid.  Otherwise all n are
+ *   consumed; latency_us[i] and status[i] (both nullable arrays) receive each
+ *   frame's latency and status, and the call returns the first frame status
+ *   that is not LSAS_OK (or LSAS_OK).  INVALID_ARG for an unknown ticket
+ *   (nothing consumed).
  * lsas_server_stats: out[0] launches, out[1] frames, out[2] bytes admitted,
  *   out[3] configurations.
  * lsas_server_destroy: finish queued frames, stop the worker, free all; it
@@ -305,6 +315,12 @@ lsas_status lsas_server_submit(lsas_server server, int config_id, const void* h_
                                float* h_H, uint8_t* h_bits, float* h_eq, uint64_t* ticket);
 lsas_status lsas_server_wait(lsas_server server, uint64_t ticket, double timeout_ms,
                              double* latency_us);
+lsas_status lsas_server_submit_many(lsas_server server, int n, const int* config_ids,
+                                    const void* const* h_in, float* const* h_H,
+                                    uint8_t* const* h_bits, float* const* h_eq,
+                                    uint64_t* tickets);
+lsas_status lsas_server_wait_many(lsas_server server, int n, const uint64_t* tickets,
+                                  double timeout_ms, double* latency_us, lsas_status* status);
 lsas_status lsas_server_stats(lsas_server server, uint64_t out[4]);
 lsas_status lsas_server_destroy(lsas_server server);
 

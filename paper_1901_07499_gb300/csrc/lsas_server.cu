@@ -339,6 +339,57 @@ lsas_status lsas_server_submit(lsas_server s, int config_id, const void* h_in, f
   return LSAS_OK;
 }
 
+lsas_status lsas_server_submit_many(lsas_server s, int n, const int* config_ids,
+                                    const void* const* h_in, float* const* h_H,
+                                    uint8_t* const* h_bits, float* const* h_eq,
+                                    uint64_t* tickets) {
+  if (!s || n < 0 || (n > 0 && (!config_ids || !h_in || !h_H || !h_bits || !tickets)))
+    return LSAS_ERR_INVALID_ARG;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (s->stop) return LSAS_ERR_INVALID_ARG;
+    // validate everything first: either all frames are queued or none
+    for (int i = 0; i < n; ++i)
+      if (config_ids[i] < 0 || config_ids[i] >= static_cast<int>(s->configs.size()) || !h_in[i] ||
+          !h_H[i] || !h_bits[i])
+        return LSAS_ERR_INVALID_ARG;
+    const Clock::time_point now = Clock::now();
+    for (int i = 0; i < n; ++i) {
+      const uint64_t t = s->next_ticket++;
+      s->configs[config_ids[i]]->queue.push_back(
+          Request{t, config_ids[i], h_in[i], h_H[i], h_bits[i], h_eq ? h_eq[i] : nullptr, now});
+      s->done[t] = Done{};
+      tickets[i] = t;
+    }
+  }
+  if (n > 0) s->cv_work.notify_one();
+  return LSAS_OK;
+}
+
+lsas_status lsas_server_wait_many(lsas_server s, int n, const uint64_t* tickets,
+                                  double timeout_ms, double* latency_us, lsas_status* status) {
+  if (!s || n < 0 || (n > 0 && !tickets)) return LSAS_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lock(s->mu);
+  for (int i = 0; i < n; ++i)
+    if (s->done.find(tickets[i]) == s->done.end()) return LSAS_ERR_INVALID_ARG;
+  const auto until = Clock::now() + std::chrono::duration<double, std::milli>(timeout_ms);
+  for (int i = 0; i < n; ++i) {
+    while (!s->done[tickets[i]].done) {
+      if (s->cv_done.wait_until(lock, until) == std::cv_status::timeout && !s->done[tickets[i]].done)
+        return LSAS_ERR_TIMEOUT;   // every ticket stays valid
+    }
+  }
+  lsas_status first = LSAS_OK;
+  for (int i = 0; i < n; ++i) {
+    const Done d = s->done[tickets[i]];
+    s->done.erase(tickets[i]);
+    if (latency_us) latency_us[i] = d.latency_us;
+    if (status) status[i] = d.status;
+    if (d.status != LSAS_OK && first == LSAS_OK) first = d.status;
+  }
+  return first;
+}
+
 lsas_status lsas_server_wait(lsas_server s, uint64_t ticket, double timeout_ms,
                              double* latency_us) {
   if (!s) return LSAS_ERR_INVALID_ARG;

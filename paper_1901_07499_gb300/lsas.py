@@ -77,6 +77,12 @@ lsas_server_submit = _proto("lsas_server_submit",
                             [_vp, _i, _vp, _vp, _vp, _vp, C.POINTER(C.c_uint64)])
 lsas_server_wait = _proto("lsas_server_wait", [_vp, C.c_uint64, C.c_double, C.POINTER(C.c_double)])
 lsas_server_stats = _proto("lsas_server_stats", [_vp, C.POINTER(C.c_uint64)])
+lsas_server_submit_many = _proto("lsas_server_submit_many",
+                                 [_vp, _i, C.POINTER(_i), C.POINTER(_vp), C.POINTER(_vp),
+                                  C.POINTER(_vp), C.POINTER(_vp), C.POINTER(C.c_uint64)])
+lsas_server_wait_many = _proto("lsas_server_wait_many",
+                               [_vp, _i, C.POINTER(C.c_uint64), C.c_double, C.POINTER(C.c_double),
+                                C.POINTER(_i)])
 lsas_server_destroy = _proto("lsas_server_destroy", [_vp])
 lsas_dn_work_size = _proto("lsas_dn_work_size", [_i, _i, C.POINTER(C.c_size_t)])
 lsas_dn_apply = _proto("lsas_dn_apply", [_vp, _i, _vp, _i, _i, _vp, _vp, _vp])
@@ -99,6 +105,7 @@ EXPORTED = ["lsas_status_str", "lsas_check_config", "lsas_frame_bytes",
             "lsas_plan_set_pn", "lsas_pn_sync", "lsas_pn_extract", "lsas_fftshift",
             "lsas_server_create", "lsas_server_register", "lsas_server_submit",
             "lsas_server_wait", "lsas_server_stats", "lsas_server_destroy",
+            "lsas_server_submit_many", "lsas_server_wait_many",
             "lsas_dn_work_size", "lsas_dn_apply", "lsas_dn_grad", "lsas_dn_adam",
             "lsas_dn_to_bf16", "lsas_dn_apply_tc", "lsas_plan_set_fault",
             "lsas_plan_set_profile", "lsas_plan_profile",
@@ -452,6 +459,38 @@ class Server:
             self._live.pop(ticket, None)
         check(code, "lsas_server_wait")
         return lat.value
+
+    def submit_many(self, frames) -> list:
+        """frames: sequence of (config_id, x, H, bits[, eq]); one call queues
+        them all (or none) and returns their tickets in order."""
+        n = len(frames)
+        if n == 0:
+            return []
+        cids = (_i * n)(*[int(f[0]) for f in frames])
+        xs = (_vp * n)(*[_ptr(f[1]) for f in frames])
+        Hs = (_vp * n)(*[_ptr(f[2]) for f in frames])
+        bs = (_vp * n)(*[_ptr(f[3]) for f in frames])
+        eqs = [f[4] if len(f) > 4 else None for f in frames]
+        es = (_vp * n)(*[_ptr(e) for e in eqs]) if any(e is not None for e in eqs) else None
+        t = (C.c_uint64 * n)()
+        check(lsas_server_submit_many(self._h, n, cids, xs, Hs, bs, es, t), "lsas_server_submit_many")
+        for i, f in enumerate(frames):
+            self._live[t[i]] = (f[1], f[2], f[3], eqs[i])
+        return list(t)
+
+    def wait_many(self, tickets, timeout_ms=30000.0) -> list:
+        """Wait for all tickets; their submit-to-results latencies (us)."""
+        n = len(tickets)
+        if n == 0:
+            return []
+        t = (C.c_uint64 * n)(*tickets)
+        lat = (C.c_double * n)()
+        code = lsas_server_wait_many(self._h, n, t, float(timeout_ms), lat, None)
+        if code != LSAS_ERR_TIMEOUT and code != LSAS_ERR_INVALID_ARG:
+            for k in tickets:
+                self._live.pop(k, None)
+        check(code, "lsas_server_wait_many")
+        return list(lat)
 
     def stats(self) -> dict:
         out = (C.c_uint64 * 4)()

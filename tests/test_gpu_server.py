@@ -13,6 +13,9 @@ submitted interleaved in random order from pinned host memory.
   of 64 frames of one configuration still runs in a handful of full batches,
   because a configuration has at most two batches (lanes) in flight and its
   frames accumulate meanwhile; every frame equals its run alone.
+* Batch submission: lsas_server_submit_many queues all frames or none (one
+  bad entry refuses the call), lsas_server_wait_many returns every frame's
+  latency, and the results equal those of single submissions.
 """
 
 import numpy as np
@@ -128,3 +131,37 @@ def test_burst_fills_batches_while_lanes_are_busy(L):
     for f, (H, bits) in enumerate(outs):
         assert np.array_equal(H.numpy().view(np.uint32), Ha[f % 4].view(np.uint32))
         assert np.array_equal(bits.numpy(), ba[f % 4])
+
+
+def test_submit_many_and_wait_many(L):
+    import ctypes as C
+    import torch
+    c = sweep_config(16, 512)
+    F = 12
+    b = synth.generate(c, frame_ids=range(F))
+    srv = L.Server(mem_budget=1 << 30, max_batch=8, max_wait_us=100.0)
+    cid = srv.register(c.M, c.N, c.cp, c.S, c.pilot_idx, c.Q, fmt=c.fmt, pilot=b.pilot)
+    xs = [_pinned(b.frames[f]) for f in range(F)]
+    outs = [(torch.empty((c.M, c.N), dtype=torch.complex64).pin_memory(),
+             torch.empty(c.D * c.N * c.q // 8, dtype=torch.uint8).pin_memory()) for _ in range(F)]
+    # one bad entry (unknown configuration): nothing is queued
+    n = 2
+    cids = (C.c_int * n)(cid, cid + 7)
+    ptr = lambda t: t.data_ptr()
+    arr = lambda vals: (C.c_void_p * n)(*vals)
+    tk = (C.c_uint64 * n)()
+    assert L.lsas_server_submit_many(srv.handle, n, cids, arr([ptr(xs[0])] * 2), arr([ptr(outs[0][0])] * 2),
+                                     arr([ptr(outs[0][1])] * 2), None, tk) == L.LSAS_ERR_INVALID_ARG
+    assert srv.stats()["frames"] == 0
+    tickets = srv.submit_many([(cid, xs[f], *outs[f]) for f in range(F)])
+    assert len(tickets) == F and len(set(tickets)) == F
+    lat = srv.wait_many(tickets)
+    assert len(lat) == F and min(lat) > 0
+    assert srv.stats()["frames"] == F
+    assert srv.close() == L.LSAS_OK
+    plan = L.Plan(c.M, c.N, c.cp, c.S, c.pilot_idx, c.Q, fmt=c.fmt, max_frames=F, pilot=b.pilot)
+    Ha, ba, _ = plan.run_frame(torch.from_numpy(np.ascontiguousarray(b.frames)).cuda())
+    plan.sync()
+    for f in range(F):
+        assert np.array_equal(outs[f][0].numpy().view(np.uint32), Ha[f].cpu().numpy().view(np.uint32))
+        assert np.array_equal(outs[f][1].numpy(), ba[f].cpu().numpy())
