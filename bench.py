@@ -569,7 +569,7 @@ def main():
     # run side by side (8 antennas per shard keeps every warp of a block busy)
     shards = max([g for g in range(1, cfg.M + 1) if cfg.M % g == 0 and cfg.M // g >= 8] or [1])
     lat_s = []
-    if cfg.N <= 1024 and shards > 1:
+    if shards > 1:
         for i in range(args.latency_calls + 10):
             a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)

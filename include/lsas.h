@@ -402,9 +402,9 @@ lsas_status lsas_plan_set_fault(lsas_plan plan, int kind);
  *   <= 151).
  * Nothing in the scratch needs to start at zero: the shard pass writes every
  * partial sum that the combine pass of the same call reads.
- * Launches: when n_shards divides M and N <= 1024, the shard pass is one
- * launch whose grid row g processes shard g of every frame, so a frame's
- * shards run on different SMs at the same time; for small batches
+ * Launches: when n_shards divides M, the shard pass is one launch whose
+ * grid row g processes shard g of every frame, so a frame's shards run on
+ * different SMs at the same time; for N <= 1024 and small batches
  * (2 * n_frames * n_shards <= SMs) its grid layers also split the data
  * symbols into their groups, each block repeating the pilot transform.
  * Otherwise there is one launch per shard.  Every form gives the same

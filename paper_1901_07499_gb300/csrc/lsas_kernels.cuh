@@ -1048,7 +1048,7 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T, 1) frame_kernel(const KParams p
       for (int c = 0; c < p.chunks; ++c) {
         const int m = c * A + alpha;
         const bool valid = m < p.M;
-        const size_t hrow = (static_cast<size_t>(f) * p.Mtot + p.m0 + m) * N;
+        const size_t hrow = (static_cast<size_t>(f) * p.Mtot + p.m0 + blockIdx.y * p.shard_y + m) * N;
         if (!need_fft_pilot) {
           // channel from memory: given (demodulate) or written in group 0
           const float2* Hs = fft_pilot(p) ? p.H_out : p.H_in;
@@ -1134,13 +1134,14 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T, 1) frame_kernel(const KParams p
           tmem_wait_ld();
 #pragma unroll
           for (int cc = 0; cc < OWN; ++cc)
-            p.E_out[static_cast<size_t>(f) * N + bin_of<LOG2N>(jt, alpha * OWN + cc)] = e[cc];
+            p.E_out[(static_cast<size_t>(blockIdx.y) * gridDim.x + f) * N +
+                    bin_of<LOG2N>(jt, alpha * OWN + cc)] = e[cc];
         }
         for (int dl = 0; dl < nd; ++dl) {
           float acc[2 * OWN];
           TmP::ld(tacc + 2 * OWN * dl, acc);
           tmem_wait_ld();
-          float2* dst = p.P_out + (static_cast<size_t>(f) * p.D + d0 + dl) * N;
+          float2* dst = p.P_out + ((static_cast<size_t>(blockIdx.y) * gridDim.x + f) * p.D + d0 + dl) * N;
 #pragma unroll
           for (int cc = 0; cc < OWN; ++cc)
             dst[bin_of<LOG2N>(jt, alpha * OWN + cc)] =

@@ -1077,10 +1077,9 @@ lsas_status lsas_run_frame_split_static(lsas_plan p, const void* d_in, int n_fra
   if (!scratch) return LSAS_ERR_CUDA;
   float* P = reinterpret_cast<float*>(scratch);
   float* E = reinterpret_cast<float*>(scratch + p_bytes);   // p_bytes is a multiple of 512
-  if (p->N <= 1024 && p->M % n_shards == 0 && n_shards > 1) {
-    // equal shards on the per-warp kernel: one launch, grid row g = shard g,
-    // so the shards of a frame run side by side (the same partial sums as
-    // one launch per shard)
+  if (p->M % n_shards == 0 && n_shards > 1) {
+    // equal shards: one launch, grid row g = shard g, so the shards of a
+    // frame run side by side (the same partial sums as one launch per shard)
     KParams k;
     base_params(p, &k);
     k.in = d_in;
@@ -1092,7 +1091,7 @@ lsas_status lsas_run_frame_split_static(lsas_plan p, const void* d_in, int n_fra
     k.grid_y = n_shards;
     // small batches: one block per data-symbol group as well (each repeats
     // the pilot transform), so a frame's groups also run side by side
-    k.group_z = (p->geo.groups > 1 && n_frames * n_shards * 2 <= p->sms) ? 1 : 0;
+    k.group_z = (p->N <= 1024 && p->geo.groups > 1 && n_frames * n_shards * 2 <= p->sms) ? 1 : 0;
     k.chunks = (k.M + p->geo.Af - 1) / p->geo.Af;
     k.mode = kModePartial;
     k.use_tma = tma_ok(p, d_in) ? 1 : 0;

@@ -4,8 +4,8 @@ sums in the library's fixed device scratch (no allocation in the call).
 Called through the C ABI and compared with the allocating entry points on
 the same frames: lsas_mrc_partial + lsas_mrc_combine over caller-allocated
 partials (same shards, same order: identical bits, eq within 1e-6 of its
-rms) and lsas_run_frame.  Equal shards on N <= 1024 run as one launch with a
-grid row per shard; the other cases launch once per shard.  Two calls in a row must both match, and the
+rms) and lsas_run_frame.  Equal shards run as one launch with a grid row per
+shard (N = 2048 included); the other cases launch once per shard.  Two calls in a row must both match, and the
 second must leave the device's free memory unchanged.  Sizes beyond the
 scratch are refused with LSAS_ERR_CAPACITY.  The file name keeps it last in collection;
 it also passes alone in a fresh process.
@@ -51,7 +51,8 @@ def _split_allocating(L, plan, x, G):
 
 
 @pytest.mark.parametrize("M,N,G,F", [(8, 64, 2, 4), (13, 1024, 3, 3), (64, 1024, 4, 2),
-                                     (64, 1024, 8, 1), (16, 256, 16, 2)])
+                                     (64, 1024, 8, 1), (16, 256, 16, 2), (32, 2048, 4, 1),
+                                     (12, 2048, 5, 2)])
 def test_static_split_matches_allocating_path(L, M, N, G, F):
     import torch
     cfg = sweep_config(M, N).replace(M=M)
