@@ -13,7 +13,8 @@
 
 namespace lsas {
 
-constexpr int kCombineThreads = 256;
+// small blocks: a single frame's 13 x 1024 / 8 threads spread over ~26 SMs
+constexpr int kCombineThreads = 64;
 
 // One thread per 8 consecutive points (data symbol d, subcarriers k0..k0+7)
 // of one frame: it reads 64 B of partial sums and 32 B of energies per shard
@@ -34,6 +35,9 @@ __global__ void __launch_bounds__(kCombineThreads) combine_kernel(const KParams 
     P[j] = make_float2(0.f, 0.f);
     E[j] = 0.f;
   }
+  // unrolled so that several shards' loads are in flight at once (the sums
+  // still run in shard order)
+#pragma unroll 4
   for (int g = 0; g < p.shards; ++g) {
     const size_t gf = static_cast<size_t>(g) * p.nframes + f;
     const float4* Pg = reinterpret_cast<const float4*>(p.P_in + gf * dn + r * 8);
