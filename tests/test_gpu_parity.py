@@ -4,7 +4,8 @@ on the same seeded synthetic frames.
 Covers the whole path (lsas_run_frame), each step alone (lsas_fft = CP
 removal + FFT, lsas_estimate = LS, lsas_demodulate = MRC + demap with the
 oracle's channel), the antenna-count x FFT-length grid, odd shapes (M not a
-multiple of the antennas per block, M = 1, pilot not first, the paper's
+multiple of the antennas per block, M = 1, M = 256, one data symbol,
+CP = N - 1, pilot not first, the paper's
 CP 72, a CP that defeats the bulk-copy alignment, BPSK and 256-QAM, float32
 input), full-scale amplitudes, the zero-energy status, argument errors,
 the host-buffer entry point, determinism, and the 1000-frame 64-antenna
@@ -79,6 +80,25 @@ def test_odd_antenna_counts(L, M, N):
 @pytest.mark.parametrize("M,N", [(16, 64), (16, 1024), (5, 1024)])
 def test_paper_shapes(L, M, N):
     run_and_check(L, paper_config(M, N, F=2))
+
+
+@pytest.mark.parametrize("M,N,F", [(256, 256, 2), (256, 1024, 1), (256, 2048, 1)])
+def test_maximum_antenna_count(L, M, N, F):
+    """M = 256, the largest the interface takes, on both fused kernels."""
+    run_and_check(L, sweep_config(M, N).replace(M=M), F=F)
+
+
+@pytest.mark.parametrize("N,S", [(256, 2), (1024, 2), (2048, 3)])
+def test_fewest_symbols(L, N, S):
+    """One pilot and one (or two) data symbols: a single data-symbol group."""
+    run_and_check(L, sweep_config(16, N).replace(S=S), F=3)
+
+
+@pytest.mark.parametrize("N", [64, 1024])
+def test_longest_cyclic_prefix(L, N):
+    """CP = N - 1, the largest the interface takes (rows no longer 16-byte
+    aligned: the plain-load path)."""
+    run_and_check(L, sweep_config(8, N).replace(cp=N - 1), F=2)
 
 
 @pytest.mark.parametrize("pilot_idx", [1, 6, 13])
