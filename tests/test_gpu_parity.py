@@ -9,7 +9,8 @@ CP = N - 1, pilot not first, the paper's
 CP 72, a CP that defeats the bulk-copy alignment, BPSK and 256-QAM, float32
 input), full-scale amplitudes, the zero-energy status, argument errors,
 the host-buffer entry point, determinism, and the 1000-frame 64-antenna
-N=1024 workload in the launch configuration the benchmark times.
+N=1024 workload in the launch configuration the benchmark times (device
+resident, and from pinned host memory as the end-to-end leg runs it).
 """
 
 import numpy as np
@@ -281,3 +282,28 @@ def test_scale_workload_full_size_sampled(L):
     assert torch.equal(Hr, Hr[:1].expand_as(Hr))
     br = bits.view(cfg.F // pool, pool, -1)
     assert torch.equal(br, br[:1].expand_as(br))
+
+
+def test_scale_workload_full_size_host_path(L):
+    """The end-to-end leg of the benchmark: 1000 frames from pinned host memory
+    through lsas_run_frame_host (chunked uploads with the cyclic prefixes
+    stripped, kernels, downloads) equal the device-resident call byte for byte,
+    and two sampled frames meet the oracle bars."""
+    import torch
+    cfg = synth.CONFIGS["scale"]
+    pool = 8
+    b = synth.generate(cfg, frame_ids=range(pool))
+    plan = make_plan(L, cfg)
+    x = to_torch_frames(b).repeat(cfg.F // pool, 1, 1, 1)
+    H, bits, _ = plan.run_frame(x)
+    plan.sync()
+    xh = x.cpu().pin_memory()
+    del x
+    Hh = torch.empty(H.shape, dtype=H.dtype).pin_memory()
+    bh = torch.empty(bits.shape, dtype=bits.dtype).pin_memory()
+    plan.run_frame_host(xh, Hh, bh)
+    plan.sync()
+    assert torch.equal(Hh, H.cpu()) and torch.equal(bh, bits.cpu())
+    for f in (3, 998):
+        ref = oracle_run(cfg, synth.generate(cfg, frame_ids=[f % pool]))
+        check_frame_outputs(cfg, ref, Hh[f:f + 1].numpy(), bh[f:f + 1].numpy(), None)
