@@ -260,13 +260,14 @@ def blas_threads():
     return os.cpu_count() or 1
 
 
-def fp32_roofline(cfg, F, ms_step, clocks):
+def fp32_roofline(cfg, F, ms_step, clocks, sms=None):
     """The FFT's FP32 rate against the CUDA cores' FP32 peak: nominal
     5 N log2 N flop per FFT (every symbol of every antenna), peak = SMs x 128
     FP32 lanes x 2 flop (FMA) x the maximum SM clock."""
     import math
-    import torch
-    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    if sms is None:
+        import torch
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
     mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
     peak = sms * 128 * 2 * mhz * 1e6 / 1e12
     flops = F * cfg.M * cfg.S * 5.0 * cfg.N * math.log2(cfg.N)

@@ -1,0 +1,65 @@
+"""The benchmark's output contract, on CPU.
+
+* The reference arm (the FP64 oracle) prints one JSON line with the
+  contract's keys, its cpu_baseline describing the run, and an e2e block of
+  its own value with no host-device bytes.
+* roofline_fp32: nominal 5 N log2 N flop per FFT over every symbol of every
+  antenna, against SMs x 128 lanes x 2 flop x clock.
+* roofline.traffic: the committed capture's bytes scaled by frames while the
+  kernel source hash and workload match, None otherwise.
+"""
+
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+import synth  # noqa: E402
+
+
+def test_reference_arm_json_line():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--steps", "2", "--warmup", "1"],
+                         capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    d = json.loads(out.stdout.strip().splitlines()[-1])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["steps"] == 2 and d["warmup"] == 1
+    assert d["metric"] == "antenna*subcarrier samples/s" and d["unit"] == "samples/s"
+    assert d["higher_is_better"] is True and d["value"] > 0
+    assert "workload" in d["config"]
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
+    e2e = d["e2e"]
+    assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_fp32_roofline_arithmetic():
+    cfg = synth.config_by_name("scale")
+    r = bench.fp32_roofline(cfg, 1000, 2.0, {"sm_max_mhz": 2000.0}, sms=100)
+    flops = 1000 * cfg.M * cfg.S * 5 * cfg.N * 10          # log2(1024) = 10
+    assert r["flop_per_frame"] == pytest.approx(flops / 1000)
+    assert r["achieved"] == pytest.approx(flops / 2e-3 / 1e12)
+    assert r["peak"] == pytest.approx(100 * 128 * 2 * 2000e6 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+
+
+def test_traffic_follows_the_source_hash(monkeypatch):
+    cfg = synth.config_by_name("scale")
+    with open(bench.TRAFFIC_FILE) as fh:
+        rec = json.load(fh)
+    monkeypatch.setattr(bench, "kernel_hash", lambda: rec["kernel_sha"])
+    assert bench.ncu_traffic(cfg, 1000) == pytest.approx(rec["dram_bytes_per_frame"] * 1000)
+    assert bench.ncu_traffic(synth.config_by_name("tiny"), 1000) is None   # other workload
+    monkeypatch.setattr(bench, "kernel_hash", lambda: "0" * 16)
+    assert bench.ncu_traffic(cfg, 1000) is None                           # kernel changed
