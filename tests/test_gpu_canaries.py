@@ -10,7 +10,8 @@ staged estimate / demodulate / FFT path, the antenna split (caller partials
 and the static scratch), the tensor-core FFT and receive_y, packet detection
 and the fftshift, the learned refinement (apply, tensor-core apply,
 gradient, Adam, bf16 rounding), and the host-buffer path (guards in pinned
-host memory).
+host memory).  Zero-frame calls of every frame-based entry point return OK
+and write nothing.
 """
 
 import numpy as np
@@ -223,3 +224,41 @@ def test_host_buffer_path(L):
     plan.sync()
     for g, n in ((H, "host H"), (bits, "host bits"), (z, "host eq")):
         g.check(n)
+
+
+def test_zero_frames_is_a_no_op(L):
+    """Every frame-based entry point accepts n_frames = 0: it returns OK,
+    launches nothing and leaves its (guarded) outputs untouched."""
+    import torch
+    cfg = sweep_config(8, 1024)
+    plan = _plan(L, cfg, 4)
+    plan.set_pn(synth.pn_sequence())
+    s = torch.cuda.current_stream().cuda_stream
+    x = torch.zeros((1, cfg.M, cfg.S * (cfg.N + cfg.cp), 2), dtype=torch.int16, device="cuda")
+    bufs = {name: Guarded((1 << 16,), torch.uint8) for name in
+            ("H", "bits", "eq", "Y", "P", "E", "off", "peak", "frames")}
+    pt = {k: v.t.data_ptr() for k, v in bufs.items()}
+    h = plan.handle
+    calls = {
+        "lsas_run_frame": lambda: L.lsas_run_frame(h, x.data_ptr(), 0, pt["H"], pt["bits"], pt["eq"], s),
+        "lsas_estimate": lambda: L.lsas_estimate(h, x.data_ptr(), 0, pt["H"], s),
+        "lsas_demodulate": lambda: L.lsas_demodulate(h, x.data_ptr(), pt["H"], 0, pt["bits"], pt["eq"], s),
+        "lsas_fft": lambda: L.lsas_fft(h, x.data_ptr(), 0, pt["Y"], s),
+        "lsas_fft_tc": lambda: L.lsas_fft_tc(h, x.data_ptr(), 0, 3, pt["Y"], s),
+        "lsas_receive_y": lambda: L.lsas_receive_y(h, pt["Y"], 0, pt["H"], pt["bits"], pt["eq"], s),
+        "lsas_mrc_partial": lambda: L.lsas_mrc_partial(h, x.data_ptr(), 0, 0, cfg.M, pt["H"], pt["P"], pt["E"], s),
+        "lsas_mrc_combine": lambda: L.lsas_mrc_combine(h, pt["P"], pt["E"], 2, 0, pt["bits"], pt["eq"], s),
+        "lsas_run_frame_split_static": lambda: L.lsas_run_frame_split_static(h, x.data_ptr(), 0, 2, pt["H"],
+                                                                             pt["bits"], pt["eq"], s),
+        "lsas_pn_sync": lambda: L.lsas_pn_sync(h, x.data_ptr(), 0, 4096, 300, pt["off"], pt["peak"], s),
+        "lsas_pn_extract": lambda: L.lsas_pn_extract(h, x.data_ptr(), 0, 4096, pt["off"], 0, pt["frames"], s),
+        "lsas_fftshift": lambda: L.lsas_fftshift(h, L.LSAS_SHIFT_H, pt["H"], 0, s),
+    }
+    for name, call in calls.items():
+        assert call() == L.LSAS_OK, name
+    plan.sync()
+    torch.cuda.synchronize()
+    for name, g in bufs.items():
+        assert bool((g.store == FILL).all()), f"{name} written by a zero-frame call"
+    xh = torch.zeros((1,), dtype=torch.int16).pin_memory()
+    assert L.lsas_run_frame_host(h, xh.data_ptr(), 0, pt["H"], pt["bits"], None, s) == L.LSAS_OK
