@@ -290,6 +290,7 @@ def reference_arm(args, cfg):
     if rank != 0:
         return 0
     per_step = 2
+    F = args.frames or cfg.F
     times = []
     for i in range(args.warmup + args.steps):
         import oracle
@@ -307,10 +308,12 @@ def reference_arm(args, cfg):
         "unit": "samples/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator)",
-        "config": workload_config(cfg, per_step, per_step),
+        # the same workload as the GPU arm; each step times a bounded sample of it
+        "config": workload_config(cfg, F, min(args.pool, F)),
         "cpu_baseline": {"value": value, "unit": "samples/s", "cores": blas_threads(),
                          "kind": "oracle",
-                         "sample": f"{per_step} frames per step, generation excluded"},
+                         "sample": f"{per_step} of the workload's {F} frames per step "
+                                   f"({args.steps} timed steps), generation excluded"},
         "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }

@@ -36,6 +36,8 @@ def test_reference_arm_json_line():
     assert d["metric"] == "antenna*subcarrier samples/s" and d["unit"] == "samples/s"
     assert d["higher_is_better"] is True and d["value"] > 0
     assert "workload" in d["config"]
+    # the GPU arm's workload, not the size of the sample
+    assert d["config"]["frames"] == synth.config_by_name("scale").F
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
     e2e = d["e2e"]
