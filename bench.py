@@ -55,6 +55,10 @@ def parse():
     ap.add_argument("--latency-calls", type=int, default=1000)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fma-peak", action="store_true",
+                    help="skip the FP32 FMA peak measurement (roofline_fp32 then nominal)")
+    ap.add_argument("--host-link", action="store_true",
+                    help="host<->device copy bandwidth report (one JSON line per path)")
     ap.add_argument("--serving", action="store_true",
                     help="serving-loop report: latency vs offered load (one JSON line per load)")
     ap.add_argument("--serving-loads", default="1,5,10,20,40", help="offered loads, G samples/s")
@@ -260,21 +264,67 @@ def blas_threads():
     return os.cpu_count() or 1
 
 
-def fp32_roofline(cfg, F, ms_step, clocks, sms=None):
+def measure_fma_peak(lsas, torch, index, reps=5):
+    """The CUDA cores' FP32 FMA throughput measured on this GPU
+    (lsas_fma_peak_run: independent packed-FMA chains on every SM), best of
+    ``reps`` launches timed with CUDA events, with the SM clock sampled
+    during the launches."""
+    import ctypes
+    sms = torch.cuda.get_device_properties(index).multi_processor_count
+    blocks, threads, iters = 4 * sms, 512, 1 << 15
+    out = torch.empty(blocks * threads, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    flops = ctypes.c_double(0.0)
+
+    def run():
+        lsas.check(lsas.lsas_fma_peak_run(blocks, threads, iters, out.data_ptr(),
+                                          ctypes.byref(flops), stream.cuda_stream),
+                   "lsas_fma_peak_run")
+    run()
+    torch.cuda.synchronize()
+    clk = ClockSampler(index)
+    clk.start()
+    time.sleep(0.3)
+    best = float("inf")
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(20):
+            run()
+        b.record(stream)
+        b.synchronize()
+        best = min(best, a.elapsed_time(b) / 20)
+    clocks = clk.stop()
+    tflops = flops.value / (best * 1e-3) / 1e12
+    return {"tflops": tflops, "ms_per_launch": best, "clocks": clocks,
+            "launch": f"{blocks} blocks x {threads} threads x {iters} iterations x 8 chains "
+                      "of packed FMAs (lsas_fma_peak_run)"}
+
+
+def fp32_roofline(cfg, F, ms_step, clocks, fma=None, sms=None):
     """The FFT's FP32 rate against the CUDA cores' FP32 peak: nominal
-    5 N log2 N flop per FFT (every symbol of every antenna), peak = SMs x 128
-    FP32 lanes x 2 flop (FMA) x the maximum SM clock."""
+    5 N log2 N flop per FFT (every symbol of every antenna).  The peak is the
+    FMA throughput measured in the same run (``fma``, from
+    measure_fma_peak); without it, SMs x 128 FP32 lanes x 2 flop x the
+    maximum SM clock, marked nominal."""
     import math
-    if sms is None:
-        import torch
-        sms = torch.cuda.get_device_properties(0).multi_processor_count
-    mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
-    peak = sms * 128 * 2 * mhz * 1e6 / 1e12
     flops = F * cfg.M * cfg.S * 5.0 * cfg.N * math.log2(cfg.N)
     achieved = flops / (ms_step * 1e-3) / 1e12
+    if fma is not None:
+        peak = fma["tflops"]
+        src = "measured"
+        how = fma["launch"] + f", SM clock median {fma['clocks'].get('sm_mhz')} MHz"
+    else:
+        if sms is None:
+            import torch
+            sms = torch.cuda.get_device_properties(0).multi_processor_count
+        mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+        peak = sms * 128 * 2 * mhz * 1e6 / 1e12
+        src = "nominal"
+        how = f"{sms} SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz"
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "flop_per_frame": flops / F,
-            "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz"}
+            "peak_source": src, "peak_how": how}
 
 
 def workload_config(cfg, F, pool):
@@ -493,9 +543,55 @@ def denoiser_report(args):
         sys.stdout.flush()
 
 
+def host_link_report(args):
+    """Bandwidth of this machine's host<->device link, which bounds the e2e
+    figure: 1 GiB from pinned host memory to the device through the copy
+    engines in 1, 2, 4 and 8 concurrent streams, and device to pinned host in
+    one, best of five, CUDA events.  One JSON line per path."""
+    import torch
+    n = 1 << 30
+    h = torch.empty(n, dtype=torch.uint8, pin_memory=True)
+    h.fill_(1)
+    d = torch.empty(n, dtype=torch.uint8, device="cuda")
+
+    def best_ms(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            best = min(best, a.elapsed_time(b))
+        return best
+
+    for ns in (1, 2, 4, 8):
+        streams = [torch.cuda.Stream() for _ in range(ns)]
+
+        def up():
+            cur = torch.cuda.current_stream()
+            part = n // ns
+            for i, st in enumerate(streams):
+                st.wait_stream(cur)
+                with torch.cuda.stream(st):
+                    d[i * part:(i + 1) * part].copy_(h[i * part:(i + 1) * part], non_blocking=True)
+            for st in streams:
+                cur.wait_stream(st)
+        print(json.dumps({"mode": "host-link", "path": "h2d copy engines", "streams": ns,
+                          "GB/s": n / best_ms(up) / 1e6}), flush=True)
+    print(json.dumps({"mode": "host-link", "path": "d2h copy engine", "streams": 1,
+                      "GB/s": n / best_ms(lambda: h.copy_(d, non_blocking=True)) / 1e6}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     cfg = synth.config_by_name(args.config)
+    if args.host_link:
+        return host_link_report(args)
     if args.serving:
         return serving_report(args)
     if args.denoiser:
@@ -584,6 +680,9 @@ def main():
                 lat_s.append(a.elapsed_time(c))
         lat_s.sort()
 
+    # the CUDA cores' FP32 peak on this GPU, for the ALU roofline
+    fma = measure_fma_peak(lsas, torch, local) if not args.no_fma_peak else None
+
     # end to end through the host-buffer entry point
     xh = x[:F].cpu().pin_memory()
     Hh = torch.empty((F, cfg.M, cfg.N), dtype=torch.complex64).pin_memory()
@@ -621,7 +720,7 @@ def main():
                          "peak_source": peak_src,
                          "kernel": "warp_kernel (fused CP strip+FFT+LS+MRC+demap, per-warp pipelines)" if cfg.N <= 1024 else "frame_kernel (fused CP strip+FFT+LS+MRC+demap)",
                          "algorithmic_bytes_per_frame": in_b + h_b + bit_b},
-            "roofline_fp32": fp32_roofline(cfg, F, ms_step, clocks),
+            "roofline_fp32": fp32_roofline(cfg, F, ms_step, clocks, fma),
             "e2e": {"value": samples / t_e2e, "unit": "samples/s",
                     "h2d_bytes_per_step": F * plan.host_input_bytes_per_frame(),
                     "d2h_bytes_per_step": F * (h_b + bit_b)},

@@ -371,8 +371,8 @@ lsas_status lsas_dn_apply_tc(const uint16_t* d_params_bf16, const float* d_H, in
  * copies, skips its remaining waits and finishes.  kind = 1 makes that
  * happen without any fault: block 0's first staging phase also waits for 16
  * bytes that no copy delivers.  kind = 0 (the default) turns it off.
- * Applies to the per-warp fused kernel (N <= 1024).  INVALID_ARG for other
- * kinds.
+ * Applies to both fused kernels: the per-warp kernel (N <= 1024) and the
+ * warp-specialised kernel (N = 2048).  INVALID_ARG for other kinds.
  */
 lsas_status lsas_plan_set_fault(lsas_plan plan, int kind);
 
@@ -409,15 +409,19 @@ lsas_status lsas_plan_set_fault(lsas_plan plan, int kind);
  * symbols into their groups, each block repeating the pilot transform.
  * Otherwise there is one launch per shard.  Every form gives the same
  * partial sums, hence the same results.
- * The first call on each device looks up the scratch address
- * (cudaGetSymbolAddress) with that device current; a caller that captures
- * its stream must make that first call before capture begins.
+ * The scratch address is looked up (cudaGetSymbolAddress) by
+ * lsas_plan_create, with the plan's device current, and kept in the plan, so
+ * loading the library's device code and committing the array happen when
+ * the plan is made, and no call of this entry point does either.  After a
+ * cudaDeviceReset every plan made before it is invalid (its tables and its
+ * cached scratch address belong to the destroyed context): make new plans.
  * The scratch is shared by all plans and streams of a device: calls whose
  * execution overlaps on one device race on it and give wrong results, so
  * serialise them (one stream, or synchronise between calls).
- * Errors: INVALID_ARG for a null plan or pointer, n_shards outside [1, M] or
- * n_frames < 0; CAPACITY as above or for n_frames > max_frames; CUDA if the
- * scratch cannot be looked up or a launch fails.  Asynchronous.
+ * Errors: INVALID_ARG for a null plan or pointer, n_shards outside [1, M],
+ * n_frames < 0 or a d_eq that is not 8-byte aligned (all checked before any
+ * launch); CAPACITY as above or for n_frames > max_frames; CUDA if a launch
+ * fails.  Asynchronous.
  */
 lsas_status lsas_run_frame_split_static(lsas_plan plan, const void* d_in,
                                         int n_frames, int n_shards,
@@ -476,6 +480,21 @@ lsas_status lsas_plan_info(lsas_plan plan, int out[8]);
 
 /* Release the plan's device memory (synchronises its device first). */
 lsas_status lsas_plan_destroy(lsas_plan plan);
+
+/*
+ * Measurement helper, not a step of the method (the paper has no
+ * counterpart): the CUDA cores' FP32 FMA throughput on this GPU, against
+ * which the FFT's arithmetic rate is reported (an ALU roofline).  Launches
+ * blocks x threads threads, each running 8 independent chains of iters packed
+ * (f32x2) fused multiply-adds, and writes one float per thread to d_out
+ * (blocks * threads floats, caller-owned device memory).  *flops (nullable)
+ * receives the FP32 flop count of the launch (an FMA counts 2), which the
+ * caller divides by its own CUDA-event time of the launch.  threads must be a
+ * multiple of 32 in [32, 512].  INVALID_ARG for bad sizes or a null d_out,
+ * CUDA if the launch fails.  Asynchronous on stream.
+ */
+lsas_status lsas_fma_peak_run(int blocks, int threads, int iters, float* d_out,
+                              double* flops, void* stream);
 
 #ifdef __cplusplus
 }

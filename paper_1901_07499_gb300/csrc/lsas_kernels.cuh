@@ -946,16 +946,23 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T, 1) frame_kernel(const KParams p
     }
     float2 wpre[32];   // writer-side twiddles (N <= 1024)
     if constexpr (N <= 1024) writer_twiddles<LOG2N>(wpre, jt, tw);
+    int issued = 0;    // steps whose copies warp 0 has issued (steps 0 .. issued-1)
     for (int g = 0; g < p.groups; ++g) {
       gend += p.chunks * group_items(p, g);
       // loads never run ahead into the next data-symbol group: its staging
-      // ring holds the demapped codes at the end of each group
-      if (warp == 0 && p.use_tma) {
+      // ring holds the demapped codes at the end of each group; once a wait
+      // has given up no copy is issued any more
+      if (warp == 0 && p.use_tma && !*abort_flag) {
         fence_proxy_async();
         for (int i = step; i < step + K && i < gend; ++i) {
           issue_step<LOG2N, FC32>(p, f, cur.c, cur.symbol(p), stage + (i % K) * slot_bytes,
                                   lay.team_stage, smem_u32(&bars[i % K]), pol, lane);
+          // test hook: the first staging phase of block 0 also waits for 16
+          // bytes that no copy delivers, so its bounded wait runs out
+          if (p.fault == 1 && blockIdx.x == 0 && i == 0 && lane == 0)
+            mbar_expect_tx_only(smem_u32(&bars[0]), 16);
           cur.next(p);
+          issued = i + 1;
         }
       }
       StepCursor me;    // the step this thread processes
@@ -993,11 +1000,12 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T, 1) frame_kernel(const KParams p
         final_exchange_write<LOG2N>(v, b ? ex0 + A * G::XS : ex0, jt);
         bar_arrive(kBarFull0 + b, T);
         bar_sync(kBarProd, TW);   // every producer is done with this staging slot
-        if (warp == 0 && p.use_tma && step + K < gend) {
+        if (warp == 0 && p.use_tma && step + K < gend && !*abort_flag) {
           fence_proxy_async();
           issue_step<LOG2N, FC32>(p, f, cur.c, cur.symbol(p), stage + slot * slot_bytes,
                                   lay.team_stage, smem_u32(&bars[slot]), pol, lane);
           cur.next(p);
+          issued = step + K + 1;
         }
       }
       bar_sync(0, T);   // group's loop done (consumers finished too)
@@ -1022,9 +1030,10 @@ __global__ void __launch_bounds__(Geo<LOG2N>::T, 1) frame_kernel(const KParams p
     if (step >= 2) bar_sync(kBarEmpty0 + (step & 1), T);
     if (step >= 1) bar_sync(kBarEmpty0 + ((step + 1) & 1), T);
     if (tid == 0 && p.use_tma && *abort_flag) {
-      // a wait gave up: give any copy still in flight a bounded chance to land
-      for (int s = 0; s < K && s < step; ++s) {
-        const int last = step - 1 - ((step - 1 - s) % K);
+      // a wait gave up: give any copy still in flight a bounded chance to
+      // land (at most one per slot: the last K steps whose copies were issued)
+      for (int s = 0; s < K && s < issued; ++s) {
+        const int last = issued - 1 - ((issued - 1 - s) % K);
         (void)mbar_wait_bounded(smem_u32(&bars[last % K]), (last / K) & 1);
       }
     }

@@ -80,6 +80,7 @@ struct lsas_plan_s {
   float* d_pn = nullptr;
   int pn_len = 0;
   int fault = 0;   // test hook of the bounded waits (lsas_plan_set_fault)
+  void* d_split_scratch = nullptr;   // device address of g_split_scratch on this device
   Geometry geo;
   LaunchFn launch = nullptr;
   // host-transfer staging (lsas_run_frame_host), allocated on first use
@@ -394,34 +395,13 @@ lsas_status launch_frame(lsas_plan p, const void* d_in, int n_frames, float* d_H
 // Fixed device scratch for lsas_run_frame_split_static: the antenna-split
 // partial sums of one call live here instead of in caller or library
 // allocations, so that the call allocates nothing.  One array per device
-// (a __device__ variable exists once in every context); its address is looked
-// up once per device with cudaGetSymbolAddress.  Calls that overlap in time on
-// one device share it and race.
+// (a __device__ variable exists once in every context).  Host code cannot
+// use the symbol's name as a device address: lsas_plan_create looks the
+// address up with cudaGetSymbolAddress, with the plan's device current, and
+// keeps it in the plan, so that loading the module and committing the array
+// happen there and never inside the entry point.  Calls that overlap in time
+// on one device share the array and race.
 static __device__ __align__(256) unsigned char g_split_scratch[LSAS_STATIC_SCRATCH_BYTES];
-
-namespace {
-
-constexpr int kMaxDevices = 64;
-std::mutex g_split_scratch_mu;
-void* g_split_scratch_ptr[kMaxDevices] = {};
-
-// Address of this device's scratch (the device must be current); null on
-// failure.  Only the first call per device talks to the runtime.
-void* split_scratch_for(int dev) {
-  if (dev < 0 || dev >= kMaxDevices) return nullptr;
-  std::lock_guard<std::mutex> lock(g_split_scratch_mu);
-  if (!g_split_scratch_ptr[dev]) {
-    void* ptr = nullptr;
-    if (cudaGetSymbolAddress(&ptr, g_split_scratch) != cudaSuccess) {
-      cudaGetLastError();
-      return nullptr;
-    }
-    g_split_scratch_ptr[dev] = ptr;
-  }
-  return g_split_scratch_ptr[dev];
-}
-
-}  // namespace
 
 extern "C" {
 
@@ -541,6 +521,13 @@ lsas_status lsas_plan_create(int M, int N, int cp_len, int n_sym, int pilot_idx,
     }
   }
   if (cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
+    lsas_plan_destroy(p);
+    return LSAS_ERR_CUDA;
+  }
+  // address of the static split scratch on this device (the device is
+  // current here); lsas_run_frame_split_static never looks it up itself
+  if (cudaGetSymbolAddress(&p->d_split_scratch, g_split_scratch) != cudaSuccess) {
+    cudaGetLastError();
     lsas_plan_destroy(p);
     return LSAS_ERR_CUDA;
   }
@@ -1071,9 +1058,12 @@ lsas_status lsas_run_frame_split_static(lsas_plan p, const void* d_in, int n_fra
   if (s != LSAS_OK) return s;
   if (n_frames == 0) return LSAS_OK;
   if (!d_in || !d_H || !d_bits) return LSAS_ERR_INVALID_ARG;
+  // everything the combine pass would reject is rejected here, before the
+  // shard pass is launched
+  if (d_eq && reinterpret_cast<uintptr_t>(d_eq) % 8 != 0) return LSAS_ERR_INVALID_ARG;
   if (set_device(p) != LSAS_OK) return LSAS_ERR_CUDA;
   ProfScope prof(p, "lsas_run_frame_split_static", stream);
-  unsigned char* scratch = static_cast<unsigned char*>(split_scratch_for(p->device));
+  unsigned char* scratch = static_cast<unsigned char*>(p->d_split_scratch);
   if (!scratch) return LSAS_ERR_CUDA;
   float* P = reinterpret_cast<float*>(scratch);
   float* E = reinterpret_cast<float*>(scratch + p_bytes);   // p_bytes is a multiple of 512

@@ -96,6 +96,7 @@ lsas_plan_profile = _proto("lsas_plan_profile", [_vp, C.c_char_p, C.c_size_t, C.
 lsas_plan_sync = _proto("lsas_plan_sync", [_vp, _vp])
 lsas_plan_info = _proto("lsas_plan_info", [_vp, C.POINTER(_i)])
 lsas_plan_destroy = _proto("lsas_plan_destroy", [_vp])
+lsas_fma_peak_run = _proto("lsas_fma_peak_run", [_i, _i, _i, _vp, C.POINTER(C.c_double), _vp])
 
 EXPORTED = ["lsas_status_str", "lsas_check_config", "lsas_frame_bytes",
             "lsas_plan_create", "lsas_plan_set", "lsas_plan_set_pilot",
@@ -110,7 +111,7 @@ EXPORTED = ["lsas_status_str", "lsas_check_config", "lsas_frame_bytes",
             "lsas_dn_to_bf16", "lsas_dn_apply_tc", "lsas_plan_set_fault",
             "lsas_plan_set_profile", "lsas_plan_profile",
             "lsas_plan_sync", "lsas_plan_info",
-            "lsas_plan_destroy"]
+            "lsas_plan_destroy", "lsas_fma_peak_run"]
 
 
 class LsasError(RuntimeError):

@@ -4,7 +4,8 @@
   contract's keys, its cpu_baseline describing the run, and an e2e block of
   its own value with no host-device bytes.
 * roofline_fp32: nominal 5 N log2 N flop per FFT over every symbol of every
-  antenna, against SMs x 128 lanes x 2 flop x clock.
+  antenna, against the FMA peak measured in the same run, or (marked
+  nominal) SMs x 128 lanes x 2 flop x clock when there is none.
 * roofline.traffic: the committed capture's bytes scaled by frames while the
   kernel source hash and workload match, None otherwise.
 """
@@ -54,6 +55,12 @@ def test_fp32_roofline_arithmetic():
     assert r["peak"] == pytest.approx(100 * 128 * 2 * 2000e6 / 1e12)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
     assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert r["peak_source"] == "nominal"
+    # with a measured FMA peak the roofline uses it
+    fma = {"tflops": 70.0, "launch": "x", "clocks": {"sm_mhz": 1900.0}}
+    m = bench.fp32_roofline(cfg, 1000, 2.0, {"sm_max_mhz": 2000.0}, fma=fma, sms=100)
+    assert m["peak"] == 70.0 and m["peak_source"] == "measured"
+    assert m["frac"] == pytest.approx(m["achieved"] / 70.0)
 
 
 def test_traffic_follows_the_source_hash(monkeypatch):

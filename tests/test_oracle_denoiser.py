@@ -2,6 +2,9 @@
 
 * conv equals numpy's correlation of the zero-padded row (the definition, by
   an independent library routine), channel by channel.
+* prepare: every row of x0 has unit mean power and rms is the row's norm
+  over sqrt(N); the refinement is scale-equivariant per row (c H -> c out
+  for real c > 0, any weights).
 * With every weight zero the residual network is the identity.
 * The backward pass equals central finite differences of the forward pass
   (sampled parameters, tiny rows), and the MSE gradient likewise.
@@ -31,6 +34,41 @@ def test_conv_is_padded_correlation():
         for o in range(4):
             want = b[o] + sum(np.correlate(np.pad(x[r, c], 2), W[o, c], "valid") for c in range(3))
             assert np.allclose(out[r, o], want, rtol=1e-12, atol=1e-12)
+
+
+def test_prepare_normalises_each_row_to_unit_power():
+    # rows of very different scale: each row of x0 has mean |x0|^2 = 1 and
+    # rms is that row's root-mean-square magnitude (the norm divided by
+    # sqrt(N), computed independently of the definition)
+    rng = np.random.default_rng(11)
+    scales = np.array([1e-3, 1.0, 37.0, 2e4])
+    H = (rng.standard_normal((4, 48)) + 1j * rng.standard_normal((4, 48))) * scales[:, None]
+    x0, rms = dn.prepare(H)
+    assert x0.shape == (4, 2, 48)
+    assert np.allclose(np.mean(x0[:, 0] ** 2 + x0[:, 1] ** 2, axis=-1), 1.0, rtol=0, atol=1e-12)
+    assert np.allclose(rms, np.linalg.norm(H, axis=-1) / np.sqrt(48), rtol=1e-13)
+    assert np.allclose(x0[:, 0] * rms[:, None], H.real, rtol=1e-13)
+    assert np.allclose(x0[:, 1] * rms[:, None], H.imag, rtol=1e-13)
+
+
+def test_refinement_is_scale_equivariant():
+    # the network sees each row normalised by its own rms, so scaling a row
+    # by a real c > 0 scales the refined row by c, for any weights (random
+    # biases included, so the map is far from linear)
+    rng = np.random.default_rng(12)
+    params = dn.init_params(5) * 2.0
+    params += 0.05 * rng.standard_normal(params.size)
+    H = rng.standard_normal((3, 40)) + 1j * rng.standard_normal((3, 40))
+    base = dn.apply(params, H)
+    assert not np.allclose(base, H)             # the weights do something
+    for c in (1e-3, 0.5, 7.0, 3e3):
+        assert np.allclose(dn.apply(params, c * H), c * base, rtol=1e-11, atol=1e-11 * c)
+    # per row: scaling one row leaves the others unchanged
+    H2 = H.copy()
+    H2[1] *= 9.0
+    out2 = dn.apply(params, H2)
+    assert np.allclose(out2[0], base[0], rtol=1e-12) and np.allclose(out2[2], base[2], rtol=1e-12)
+    assert np.allclose(out2[1], 9.0 * base[1], rtol=1e-11)
 
 
 def test_zero_weights_are_identity():

@@ -113,4 +113,13 @@ def test_static_split_refuses_sizes_beyond_scratch(L):
     assert call(0, 4) == L.LSAS_OK
     assert L.lsas_run_frame_split_static(plan.handle, None, 1, 1, H.data_ptr(),
                                          bits.data_ptr(), None, s) == L.LSAS_ERR_INVALID_ARG
+    # a misaligned eq buffer is refused before the shard pass runs: H keeps
+    # its sentinel
+    eq = torch.zeros(2 * cfg.D * cfg.N * 2 + 4, dtype=torch.float32, device="cuda")
+    H.fill_(7.0)
+    torch.cuda.synchronize()
+    assert L.lsas_run_frame_split_static(plan.handle, x.data_ptr(), 1, 4, H.data_ptr(),
+                                         bits.data_ptr(), eq.data_ptr() + 4, s) == L.LSAS_ERR_INVALID_ARG
+    torch.cuda.synchronize()
+    assert bool((H == 7.0).all())
     assert plan.sync_status() == L.LSAS_OK
