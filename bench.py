@@ -38,7 +38,7 @@ import synth  # noqa: E402
 
 FALLBACK_HBM_GBS = 6800.0
 KERNEL_SRC = [os.path.join(ROOT, "paper_1901_07499_gb300", "csrc", n)
-              for n in ("lsas_kernels.cuh", "lsas_warp.cuh")]
+              for n in ("lsas_kernels.cuh", "lsas_warp.cuh", "lsas_hyb.cuh")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fused_kernel_traffic.json")
 
 
@@ -325,6 +325,17 @@ def fp32_roofline(cfg, F, ms_step, clocks, fma=None, sms=None):
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "flop_per_frame": flops / F,
             "peak_source": src, "peak_how": how}
+
+
+def fused_kernel_name(cfg):
+    """The fused kernel lsas_run_frame launches for this workload (aligned
+    rows, as the benchmark's input is)."""
+    if cfg.N == 1024 and cfg.fmt == "sc16" and os.environ.get("LSAS_FUSED_KERNEL") == "tensor":
+        return ("hyb_kernel (fused CP strip + FFT + LS + MRC + demap; first FFT pass on the "
+                "CUDA cores, second on tcgen05)")
+    if cfg.N <= 1024:
+        return "warp_kernel (fused CP strip+FFT+LS+MRC+demap, per-warp pipelines)"
+    return "frame_kernel (fused CP strip+FFT+LS+MRC+demap)"
 
 
 def workload_config(cfg, F, pool):
@@ -718,7 +729,7 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": peak_src,
-                         "kernel": "warp_kernel (fused CP strip+FFT+LS+MRC+demap, per-warp pipelines)" if cfg.N <= 1024 else "frame_kernel (fused CP strip+FFT+LS+MRC+demap)",
+                         "kernel": fused_kernel_name(cfg),
                          "algorithmic_bytes_per_frame": in_b + h_b + bit_b},
             "roofline_fp32": fp32_roofline(cfg, F, ms_step, clocks, fma),
             "e2e": {"value": samples / t_e2e, "unit": "samples/s",

@@ -3,6 +3,7 @@
 #pragma once
 #include "lsas_kernels.cuh"
 #include "lsas_warp.cuh"
+#include "lsas_hyb.cuh"
 
 namespace lsas {
 
@@ -10,10 +11,22 @@ template <int LOG2N, bool FC32>
 static cudaError_t launch_t(int kind, const KParams& p, int grid, int smem, cudaStream_t st) {
   void (*fn)(const KParams) = nullptr;
   int threads = Geo<LOG2N>::TW;
+  int slot = kind;   // entry of the shared-memory attribute cache below
   if (kind == kKindFrame) {
-    // fused receiver: per-warp pipelines up to N = 1024, the warp-specialised
-    // producer/consumer kernel for N = 2048
-    if constexpr (LOG2N <= 10) {
+    // fused receiver: N = 1024 from aligned sc16 rows with the second FFT
+    // pass on the tensor cores; otherwise per-warp pipelines up to N = 1024
+    // and the warp-specialised producer/consumer kernel for N = 2048
+    if constexpr (LOG2N == 10 && !FC32) {
+      if (p.hybrid && p.use_tma) {
+        fn = hyb_kernel<false>;
+        threads = kHyThreads;
+        smem = kHySmem;
+        slot = 3;
+      } else {
+        fn = warp_kernel<LOG2N, FC32>;
+        threads = 32 * wgeo_warps(4);
+      }
+    } else if constexpr (LOG2N <= 10) {
       fn = warp_kernel<LOG2N, FC32>;
       threads = 32 * wgeo_warps(FC32 ? 8 : 4);
     } else {
@@ -26,14 +39,14 @@ static cudaError_t launch_t(int kind, const KParams& p, int grid, int smem, cuda
     fn = fft_kernel<LOG2N, FC32>;
   }
   // raise the kernel's dynamic shared memory limit once per device
-  static int limit[3][64] = {};
+  static int limit[4][64] = {};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 64 || smem > limit[kind][dev]) {
+  if (dev < 0 || dev >= 64 || smem > limit[slot][dev]) {
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    if (dev >= 0 && dev < 64) limit[kind][dev] = smem;
+    if (dev >= 0 && dev < 64) limit[slot][dev] = smem;
   }
   fn<<<dim3(grid, p.grid_y > 1 ? p.grid_y : 1, p.group_z ? p.groups : 1), threads, smem, st>>>(p);
   return cudaGetLastError();

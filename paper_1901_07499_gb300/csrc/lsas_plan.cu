@@ -21,6 +21,7 @@
 
 #include "lsas.h"
 #include "lsas_kernels.cuh"
+#include "lsas_hyb.cuh"
 
 namespace lsas {
 cudaError_t launch_n64(int, bool, const KParams&, int, int, cudaStream_t);
@@ -56,6 +57,7 @@ struct Geometry {
   int nslots, groups, dg, smem_frame;
   int smem_est, smem_fft, fft_slots;
   int tmem_cols, tmem_cth;
+  int hybrid;   // N = 1024, sc16: fused calls with aligned rows use hyb_kernel
 };
 
 }  // namespace
@@ -80,6 +82,7 @@ struct lsas_plan_s {
   float* d_pn = nullptr;
   int pn_len = 0;
   int fault = 0;   // test hook of the bounded waits (lsas_plan_set_fault)
+  bool allow_hybrid = false;   // LSAS_FUSED_KERNEL = "tensor" at creation
   void* d_split_scratch = nullptr;   // device address of g_split_scratch on this device
   Geometry geo;
   LaunchFn launch = nullptr;
@@ -212,7 +215,7 @@ LaunchFn launcher_for(int N) {
 // fused kernel fits the shared memory of one SM, its accumulators fit tensor
 // memory, and the demapped codes fit the staging ring they reuse: prefer one
 // data-symbol group (no second pass over H), then the deepest ring.
-bool plan_geometry(int M, int N, int D, lsas_input_fmt fmt, Geometry* g) {
+bool plan_geometry(int M, int N, int D, lsas_input_fmt fmt, bool allow_hybrid, Geometry* g) {
   g->A = geo_A(N);
   g->Af = geo_A(N);
   g->L = N / 32;
@@ -262,6 +265,20 @@ bool plan_geometry(int M, int N, int D, lsas_input_fmt fmt, Geometry* g) {
       }
     }
     if (!found) return false;
+  }
+  g->hybrid = 0;
+  if (allow_hybrid && N == 1024 && fmt == LSAS_IN_SC16) {
+    // the tensor-core kernel's TMEM holds two data symbols per warp; the
+    // per-warp kernel (unaligned rows) then runs the same groups
+    const int groups = (D + kHyDgMax - 1) / kHyDgMax;
+    const int dg = (D + groups - 1) / groups;
+    const WLayout l = make_wlayout(N, bps, g->nslots, dg);
+    if (l.total <= kSmemLimit) {
+      g->groups = groups;
+      g->dg = dg;
+      g->smem_frame = l.total;
+      g->hybrid = 1;
+    }
   }
   g->smem_est = make_layout(N, bps, 1, 1).total;
   g->fft_slots = 2;
@@ -324,6 +341,8 @@ void base_params(lsas_plan p, KParams* k) {
   k->xinv = p->d_xinv;
   k->status = p->d_status;
   k->fault = p->fault;
+  k->hybrid = p->geo.hybrid;
+  k->tc_w1 = p->d_tc_w1;
   k->M = p->M;
   k->m0 = 0;
   k->Mtot = p->M;
@@ -486,7 +505,14 @@ lsas_status lsas_plan_create(int M, int N, int cp_len, int n_sym, int pilot_idx,
     const char* e = std::getenv("LSAS_PROFILE");
     p->prof = e && e[0] == '1';
   }
-  if (!plan_geometry(M, N, p->D, p->fmt, &p->geo)) {
+  {
+    // LSAS_FUSED_KERNEL=tensor runs N = 1024 (sc16) with the second FFT pass
+    // on the tensor cores; the default keeps both passes on the CUDA cores,
+    // which measured faster
+    const char* e = std::getenv("LSAS_FUSED_KERNEL");
+    p->allow_hybrid = e && std::strcmp(e, "tensor") == 0;
+  }
+  if (!plan_geometry(M, N, p->D, p->fmt, p->allow_hybrid, &p->geo)) {
     delete p;
     return LSAS_ERR_UNSUPPORTED;
   }
@@ -548,7 +574,7 @@ lsas_status lsas_plan_set(lsas_plan p, lsas_input_fmt fmt, int max_frames) {
   if (fmt != LSAS_IN_SC16 && fmt != LSAS_IN_FC32) return LSAS_ERR_INVALID_ARG;
   if (max_frames < 1) return LSAS_ERR_INVALID_ARG;
   Geometry g;
-  if (!plan_geometry(p->M, p->N, p->D, fmt, &g)) return LSAS_ERR_UNSUPPORTED;
+  if (!plan_geometry(p->M, p->N, p->D, fmt, p->allow_hybrid, &g)) return LSAS_ERR_UNSUPPORTED;
   const bool realloc = fmt != p->fmt || max_frames != p->max_frames;
   p->fmt = fmt;
   p->max_frames = max_frames;

@@ -307,3 +307,34 @@ def test_scale_workload_full_size_host_path(L):
     for f in (3, 998):
         ref = oracle_run(cfg, synth.generate(cfg, frame_ids=[f % pool]))
         check_frame_outputs(cfg, ref, Hh[f:f + 1].numpy(), bh[f:f + 1].numpy(), None)
+
+
+@pytest.mark.parametrize("M", [13, 64])
+def test_tensor_core_and_cuda_core_fused_kernels(L, M, monkeypatch):
+    """N = 1024 with aligned sc16 rows: the default fused kernel (both FFT
+    passes on the CUDA cores) and, with LSAS_FUSED_KERNEL=tensor, the one
+    whose second pass runs on the tensor cores.  Both meet the oracle bars on
+    the same frames (full receiver and lsas_demodulate with the oracle's
+    channel), including an antenna count that leaves some warps of a quad
+    without antennas (M = 13)."""
+    cfg = synth.CONFIGS["scale"].replace(M=M)
+    b = synth.generate(cfg, frame_ids=range(3))
+    ref = oracle_run(cfg, b)
+    ref_d = oracle_run(cfg, b, H_given=ref.H)
+    x = to_torch_frames(b)
+    import torch
+    for kernel in ("tensor", "default"):
+        if kernel == "tensor":
+            monkeypatch.setenv("LSAS_FUSED_KERNEL", "tensor")
+        else:
+            monkeypatch.delenv("LSAS_FUSED_KERNEL", raising=False)
+        plan = make_plan(L, cfg, max_frames=4)
+        H, bits, eq = plan.run_frame(x, want_eq=True)
+        assert plan.sync_status() == L.LSAS_OK
+        check_frame_outputs(cfg, ref, H.cpu().numpy(), bits.cpu().numpy(), eq.cpu().numpy())
+        Hd = torch.from_numpy(ref.H.astype(np.complex64)).cuda()
+        bits_d, eq_d = plan.demodulate(x, Hd, want_eq=True)
+        assert plan.sync_status() == L.LSAS_OK
+        check_frame_outputs(cfg, ref_d, None, bits_d.cpu().numpy(), eq_d.cpu().numpy(),
+                            check_H=False)
+        plan.close()
