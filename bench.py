@@ -63,6 +63,8 @@ def parse():
                     help="serving-loop report: latency vs offered load (one JSON line per load)")
     ap.add_argument("--serving-loads", default="1,5,10,20,40", help="offered loads, G samples/s")
     ap.add_argument("--serving-seconds", type=float, default=2.0)
+    ap.add_argument("--serving-forms", default="plain,learned",
+                    help="receiver forms to serve: plain (FP32 LS), learned (LS + refinement)")
     ap.add_argument("--denoiser", action="store_true",
                     help="learned LS refinement: train, then MSE/BER against plain LS per SNR")
     ap.add_argument("--denoiser-rows", type=int, default=200_000)
@@ -407,8 +409,31 @@ def serving_report(args):
                                               name=f"serve_M{M}_N{N}_Q{Q}") for M, N, Q in combos]
     pools = [synth.generate(c, frame_ids=range(4)) for c in cfgs]
     max_batch, max_wait = 16, 200.0
+    for form in args.serving_forms.split(","):
+        serving_sweep(args, lsas, torch, form, cfgs, pools, max_batch, max_wait, rng)
+
+
+def serving_sweep(args, lsas, torch, form, cfgs, pools, max_batch, max_wait, rng):
+    """One form of the receiver ("plain": lsas_run_frame; "learned": LS ->
+    tensor-core refinement -> MRC) over the offered loads."""
+    import threading
+    pb = None
+    weights = None
+    if form == "learned":
+        import paper_1901_07499_gb300.denoiser as dnm
+        if args.denoiser_ckpt:
+            dn = dnm.Denoiser.load(args.denoiser_ckpt)
+            weights = f"checkpoint {os.path.basename(args.denoiser_ckpt)}"
+        else:
+            # the refinement's cost does not depend on its weights' values
+            dn = dnm.Denoiser(seed=1)
+            weights = "initial weights (timing does not depend on their values)"
+        pb = dn.bf16_params()
+    elif form != "plain":
+        raise ValueError(f"unknown serving form {form!r}")
     srv = lsas.Server(mem_budget=24 << 30, max_batch=max_batch, max_wait_us=max_wait)
-    ids = [srv.register(c.M, c.N, c.cp, c.S, c.pilot_idx, c.Q, fmt=c.fmt, pilot=b.pilot)
+    ids = [srv.register(c.M, c.N, c.cp, c.S, c.pilot_idx, c.Q, fmt=c.fmt, pilot=b.pilot,
+                        refine_params_bf16=pb)
            for c, b in zip(cfgs, pools)]
     xs = [[torch.from_numpy(np.ascontiguousarray(b.frames[i])).pin_memory() for i in range(4)]
           for b in pools]
@@ -475,7 +500,8 @@ def serving_report(args):
         st1 = srv.stats()
         lat_us = np.array(lat)
         print(json.dumps({
-            "mode": "serving", "offered_gsps": load, "achieved_gsps": done_samples[0] / wall / 1e9,
+            "mode": "serving", "form": form, "weights": weights,
+            "offered_gsps": load, "achieved_gsps": done_samples[0] / wall / 1e9,
             "frames": n, "launches": st1["launches"] - st0["launches"],
             "latency_us": {"p50": float(np.percentile(lat_us, 50)),
                            "p99": float(np.percentile(lat_us, 99)),

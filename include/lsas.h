@@ -199,6 +199,22 @@ lsas_status lsas_fft_tc(lsas_plan plan, const void* d_in, int n_frames, int term
                         float* d_Y, void* stream);
 
 /*
+ * lsas_fft_tc with a choice of operand type (Sec. II-C, the batched FFT as
+ * DFT-factor GEMMs): operand LSAS_TC_FP16 (lsas_fft_tc itself) or
+ * LSAS_TC_BF16, bfloat16 operands with fp32 accumulation.  terms = 1 uses
+ * each operand rounded once (bf16: 8 significant bits, ~1e-2 relative
+ * error); terms = 3 splits every operand into hi = round(v) and
+ * lo = round(v - hi) of the same type and sums a_hi b_hi + a_hi b_lo +
+ * a_lo b_hi (bf16: ~2^-16 relative).  The constant DFT operands of both
+ * types are tables the plan builds in double precision.  INVALID_ARG for
+ * another operand or terms; otherwise as lsas_fft_tc.
+ */
+#define LSAS_TC_FP16 0
+#define LSAS_TC_BF16 1
+lsas_status lsas_fft_tc_ex(lsas_plan plan, const void* d_in, int n_frames, int operand,
+                           int terms, float* d_Y, void* stream);
+
+/*
  * Steps a3-a5 from transformed symbols (the staged form of the receiver):
  * d_Y [F][M][S][N] complex (unitary FFT outputs, as lsas_fft or lsas_fft_tc
  * write them) -> LS estimate d_H [F][M][N] (Sec. II-C), MRC over the
@@ -279,11 +295,30 @@ lsas_status lsas_fftshift(lsas_plan plan, int what, void* d_buf, int n_frames,
  *   Its plan and the staging of both lanes (2 * max_batch frames) count
  *   against the budget: LSAS_ERR_CAPACITY when they do not fit.  Returns
  *   its id.
+ * lsas_server_register_refined: as lsas_server_register, for the learned
+ *   form of the receiver: each batch runs LS (lsas_estimate), the
+ *   tensor-core refinement (lsas_dn_apply_tc with d_params_bf16, a device
+ *   array of LSAS_DN_PARAMS bf16 values that must stay valid until the
+ *   server is destroyed) and MRC + demap with the refined channel
+ *   (lsas_demodulate); h_H receives the refined channel.  N must be a
+ *   multiple of 128 (UNSUPPORTED otherwise).  The LS estimate and the
+ *   refinement's scratch of both lanes count against the budget too.
+ * lsas_server_set_admission: per-frame memory admission.  Every submitted
+ *   frame is charged its device footprint (input, H, bits and, when h_eq is
+ *   given, z bytes per frame) from submission until its results are home.
+ *   Frames are admitted while the charged total stays within
+ *   frame_budget_bytes (0, the default: what the memory budget leaves after
+ *   registration).  A frame that does not fit is refused with
+ *   LSAS_ERR_CAPACITY at once (wait_ms = 0, the default) or after waiting up
+ *   to wait_ms for frames to complete.  INVALID_ARG for a null server or a
+ *   negative wait.
+ * lsas_server_frame_bytes: out[0] bytes charged by frames queued or in
+ *   flight, out[1] the frame budget in force.
  * lsas_server_submit: queue one frame of a registered configuration:
  *   h_in [M][S*(N+CP)] samples, results to h_H [M][N], h_bits [D*N*q/8],
  *   h_eq [D][N] (nullable), all host memory that stays valid until the wait
- *   returns (pinned memory for full copy speed).  Never blocks; gives a
- *   ticket.
+ *   returns (pinned memory for full copy speed).  Admission as above
+ *   (LSAS_ERR_CAPACITY when the frame does not fit); gives a ticket.
  * lsas_server_wait: wait up to timeout_ms for a ticket's results;
  *   LSAS_ERR_TIMEOUT if they are not ready (the ticket stays valid),
  *   INVALID_ARG for an unknown ticket.  latency_us (nullable) receives the
@@ -291,7 +326,7 @@ lsas_status lsas_fftshift(lsas_plan plan, int what, void* d_buf, int n_frames,
  * lsas_server_submit_many: lsas_server_submit for n frames in one call
  *   (arrays of n entries; h_eq may be NULL, or an array whose entries may be
  *   NULL).  Either every frame is queued (tickets[i] for frame i) or, on
- *   INVALID_ARG for any entry, none is.
+ *   INVALID_ARG for any entry or CAPACITY for their total, none is.
  * lsas_server_wait_many: waits up to timeout_ms in total for all n tickets.
  *   On LSAS_ERR_TIMEOUT every ticket stays valid.  Otherwise all n are
  *   consumed; latency_us[i] and status[i] (both nullable arrays) receive each
@@ -311,6 +346,13 @@ lsas_status lsas_server_create(size_t mem_budget_bytes, int max_batch, double ma
 lsas_status lsas_server_register(lsas_server server, int M, int N, int cp_len, int n_sym,
                                  int pilot_idx, int qam_order, lsas_input_fmt fmt,
                                  const float* host_pilot_iq, int* config_id);
+lsas_status lsas_server_register_refined(lsas_server server, int M, int N, int cp_len, int n_sym,
+                                         int pilot_idx, int qam_order, lsas_input_fmt fmt,
+                                         const float* host_pilot_iq,
+                                         const uint16_t* d_params_bf16, int* config_id);
+lsas_status lsas_server_set_admission(lsas_server server, size_t frame_budget_bytes,
+                                      double wait_ms);
+lsas_status lsas_server_frame_bytes(lsas_server server, uint64_t out[2]);
 lsas_status lsas_server_submit(lsas_server server, int config_id, const void* h_in,
                                float* h_H, uint8_t* h_bits, float* h_eq, uint64_t* ticket);
 lsas_status lsas_server_wait(lsas_server server, uint64_t ticket, double timeout_ms,

@@ -64,7 +64,8 @@ struct KParams {
   const void* tc_w1;     // tensor-core FFT: 32-point DFT operand images (hi, lo)
   const void* tc_w2;     //   N/32-point DFT operand images (hi, lo)
   const float2* tc_tw;   //   inter-stage twiddles W_N^(n2 k1), [n2][k1]
-  int terms;             //   1: fp16 operands; 3: hi+lo split operands
+  int terms;             //   1: plain operands; 3: hi+lo split operands
+  int tc_bf16;           //   0: fp16 operands; 1: bf16
   const float* pn;       // packet detection: PN chips (real), pn_len of them
   int pn_len, cap_len, window, backoff;
   int* offsets;          //   per frame: detected preamble start (out)

@@ -733,8 +733,14 @@ lsas_status lsas_mrc_combine(lsas_plan p, const float* d_P, const float* d_E, in
 
 lsas_status lsas_fft_tc(lsas_plan p, const void* d_in, int n_frames, int terms, float* d_Y,
                         void* stream) {
+  return lsas_fft_tc_ex(p, d_in, n_frames, LSAS_TC_FP16, terms, d_Y, stream);
+}
+
+lsas_status lsas_fft_tc_ex(lsas_plan p, const void* d_in, int n_frames, int operand, int terms,
+                           float* d_Y, void* stream) {
   if (!p) return LSAS_ERR_INVALID_ARG;
   if (terms != 1 && terms != 3) return LSAS_ERR_INVALID_ARG;
+  if (operand != LSAS_TC_FP16 && operand != LSAS_TC_BF16) return LSAS_ERR_INVALID_ARG;
   if (!p->d_tc_w1 || p->fmt != LSAS_IN_SC16) return LSAS_ERR_UNSUPPORTED;
   lsas_status s = check_frames(p, n_frames);
   if (s != LSAS_OK) return s;
@@ -747,6 +753,7 @@ lsas_status lsas_fft_tc(lsas_plan p, const void* d_in, int n_frames, int terms, 
   k.Y_out = reinterpret_cast<float2*>(d_Y);
   k.nframes = n_frames;
   k.terms = terms;
+  k.tc_bf16 = operand == LSAS_TC_BF16 ? 1 : 0;
   k.tc_w1 = p->d_tc_w1;
   k.tc_w2 = p->d_tc_w2;
   k.tc_tw = p->d_tc_tw;
@@ -757,7 +764,7 @@ lsas_status lsas_fft_tc(lsas_plan p, const void* d_in, int n_frames, int terms, 
   const int per_sm = tc_smem_bytes(p->N) * 2 <= kSmemLimit ? 2 : 1;
   const size_t cap = static_cast<size_t>(p->sms) * per_sm;
   const int grid = static_cast<int>(batches < cap ? batches : cap);
-  ProfScope prof(p, "lsas_fft_tc", stream);
+  ProfScope prof(p, operand == LSAS_TC_BF16 ? "lsas_fft_tc_ex(bf16)" : "lsas_fft_tc", stream);
   if (launch_tcfft(k, p->N, grid, static_cast<cudaStream_t>(stream)) != cudaSuccess)
     return LSAS_ERR_CUDA;
   return LSAS_OK;

@@ -17,8 +17,19 @@
 // instead of queueing many small launches (a launch of one frame costs about
 // as much device time as one of a full wave); the two lanes let one batch's
 // upload overlap the other's kernel.
+// Memory is admitted twice: a configuration when it is registered (its
+// plan, both lanes' staging and, for the learned form, the refinement's
+// buffers), and every frame when it is submitted: a frame is charged its
+// device footprint (input, H, bits and, when asked for, z) from submission
+// until its results are home, against the frame budget (by default what the
+// memory budget leaves after registration).  A frame that does not fit is
+// refused with LSAS_ERR_CAPACITY, or waits a bounded time for room, so the
+// queue can never hold more work than the device memory it stands for.
+// A configuration registered with refinement parameters runs the learned
+// form: LS estimate -> tensor-core refinement -> MRC and demap with the
+// refined channel (lsas_estimate, lsas_dn_apply_tc, lsas_demodulate).
 // Each frame is processed exactly as it would be alone (frames are
-// independent in the kernel), so the results do not depend on the mix.
+// independent in the kernels), so the results do not depend on the mix.
 // Device-side conditions (zero channel energy, a bounded wait that ran out)
 // latch in the configuration's plan and are returned by lsas_server_destroy.
 #include <chrono>
@@ -46,6 +57,7 @@ struct Request {
   uint8_t* h_bits;
   float* h_eq;
   Clock::time_point submitted;
+  size_t bytes;   // device footprint charged against the frame budget
 };
 
 struct Done {
@@ -60,6 +72,10 @@ struct Lane {
   float* d_H = nullptr;
   uint8_t* d_bits = nullptr;
   float* d_eq = nullptr;
+  // learned form: the LS estimate, the refinement's scratch and its status
+  float* d_Hls = nullptr;
+  float* d_work = nullptr;
+  int* d_status = nullptr;
   cudaStream_t stream = nullptr;
   bool busy = false;
 };
@@ -67,6 +83,7 @@ constexpr int kLanes = 2;
 
 struct Config {
   lsas_plan plan = nullptr;   // shared by the lanes (read-only tables, latched status)
+  const uint16_t* dn_params = nullptr;   // bf16 refinement parameters (learned form)
   int M, N, cp, S, Q, D;
   lsas_input_fmt fmt;
   size_t in_b, h_b, bits_b, eq_b;   // bytes per frame
@@ -86,6 +103,9 @@ struct Batch;
 
 struct lsas_server_s {
   size_t budget = 0, used = 0;
+  size_t frame_budget = 0;   // 0: what the budget leaves after registration
+  double admit_wait_ms = 0;  // how long a submit may wait for room
+  size_t inflight = 0;       // bytes of frames queued or on the device
   int max_batch = 1;
   double max_wait_us = 0;
   int device = 0;
@@ -106,6 +126,7 @@ struct Batch {
   lsas_server_s* s;
   std::vector<std::pair<uint64_t, Clock::time_point>> items;
   int config, lane;
+  size_t bytes;
 };
 
 // Runs on a CUDA callback thread (no CUDA calls here): marks the batch's
@@ -123,6 +144,7 @@ void CUDART_CB batch_done(void* arg) {
       d.latency_us = std::chrono::duration<double, std::micro>(now - it.second).count();
     }
     s->configs[b->config]->lanes[b->lane].busy = false;
+    s->inflight -= b->bytes;
   }
   s->cv_done.notify_all();
   s->cv_work.notify_one();
@@ -130,12 +152,45 @@ void CUDART_CB batch_done(void* arg) {
 }
 
 void fail_batch(lsas_server_s* s, const std::vector<Request>& reqs, lsas_status st) {
-  std::lock_guard<std::mutex> lock(s->mu);
-  for (const Request& r : reqs) {
-    Done& d = s->done[r.ticket];
-    d.done = true;
-    d.status = st;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    for (const Request& r : reqs) {
+      Done& d = s->done[r.ticket];
+      d.done = true;
+      d.status = st;
+      s->inflight -= r.bytes;
+    }
   }
+  s->cv_done.notify_all();
+}
+
+// The frame budget in force: the one set, else what registration left.
+size_t frame_budget(const lsas_server_s* s) {
+  if (s->frame_budget) return s->frame_budget;
+  return s->budget > s->used ? s->budget - s->used : 0;
+}
+
+// Charge `bytes` of frames against the frame budget (caller holds the lock):
+// LSAS_OK once they fit, LSAS_ERR_CAPACITY if they never can or the admission
+// wait runs out.
+lsas_status admit(lsas_server_s* s, std::unique_lock<std::mutex>& lock, size_t bytes) {
+  if (bytes > frame_budget(s)) return LSAS_ERR_CAPACITY;
+  if (s->inflight + bytes > frame_budget(s)) {
+    if (s->admit_wait_ms <= 0) return LSAS_ERR_CAPACITY;
+    const auto until = Clock::now() + std::chrono::duration<double, std::milli>(s->admit_wait_ms);
+    while (s->inflight + bytes > frame_budget(s)) {
+      if (s->cv_done.wait_until(lock, until) == std::cv_status::timeout &&
+          s->inflight + bytes > frame_budget(s))
+        return LSAS_ERR_CAPACITY;
+      if (s->stop) return LSAS_ERR_INVALID_ARG;
+    }
+  }
+  s->inflight += bytes;
+  return LSAS_OK;
+}
+
+size_t frame_bytes_of(const Config& cf, bool eq) {
+  return cf.in_b + cf.h_b + cf.bits_b + (eq ? cf.eq_b : 0);
 }
 
 void worker_loop(lsas_server_s* s) {
@@ -198,7 +253,19 @@ void worker_loop(lsas_server_s* s) {
     if (st == LSAS_OK) {
       bool eq = false;   // z is computed when any frame of the batch asks for it
       for (const Request& r : reqs) eq = eq || r.h_eq != nullptr;
-      st = lsas_run_frame(cf.plan, ln.d_in, F, ln.d_H, ln.d_bits, eq ? ln.d_eq : nullptr, ln.stream);
+      if (cf.dn_params) {
+        // learned form: LS, refinement on the tensor cores, MRC with it
+        st = lsas_estimate(cf.plan, ln.d_in, F, ln.d_Hls, ln.stream);
+        if (st == LSAS_OK)
+          st = lsas_dn_apply_tc(cf.dn_params, ln.d_Hls, F * cf.M, cf.N, ln.d_work, ln.d_H,
+                                ln.d_status, ln.stream);
+        if (st == LSAS_OK)
+          st = lsas_demodulate(cf.plan, ln.d_in, ln.d_H, F, ln.d_bits, eq ? ln.d_eq : nullptr,
+                               ln.stream);
+      } else {
+        st = lsas_run_frame(cf.plan, ln.d_in, F, ln.d_H, ln.d_bits, eq ? ln.d_eq : nullptr,
+                            ln.stream);
+      }
     }
     for (int i = 0; i < F && st == LSAS_OK; ++i) {
       const Request& r = reqs[i];
@@ -211,8 +278,11 @@ void worker_loop(lsas_server_s* s) {
         st = LSAS_ERR_CUDA;
     }
     if (st == LSAS_OK) {
-      Batch* b = new Batch{s, {}, pick, li};
-      for (const Request& r : reqs) b->items.emplace_back(r.ticket, r.submitted);
+      Batch* b = new Batch{s, {}, pick, li, 0};
+      for (const Request& r : reqs) {
+        b->items.emplace_back(r.ticket, r.submitted);
+        b->bytes += r.bytes;
+      }
       if (cudaLaunchHostFunc(ln.stream, batch_done, b) != cudaSuccess) {
         delete b;
         st = LSAS_ERR_CUDA;
@@ -256,12 +326,18 @@ lsas_status lsas_server_create(size_t mem_budget_bytes, int max_batch, double ma
   return LSAS_OK;
 }
 
-lsas_status lsas_server_register(lsas_server s, int M, int N, int cp_len, int n_sym,
-                                 int pilot_idx, int qam_order, lsas_input_fmt fmt,
-                                 const float* host_pilot_iq, int* config_id) {
+}  // extern "C"
+
+namespace {
+
+lsas_status register_config(lsas_server s, int M, int N, int cp_len, int n_sym, int pilot_idx,
+                            int qam_order, lsas_input_fmt fmt, const float* host_pilot_iq,
+                            const uint16_t* dn_params, int* config_id) {
   if (!s || !config_id) return LSAS_ERR_INVALID_ARG;
   lsas_status st = lsas_check_config(M, N, cp_len, n_sym, pilot_idx, qam_order);
   if (st != LSAS_OK) return st;
+  // the refinement runs over rows of N subcarriers in tiles of 128
+  if (dn_params && (N % 128 != 0)) return LSAS_ERR_UNSUPPORTED;
   size_t fb[4];
   st = lsas_frame_bytes(M, N, cp_len, n_sym, qam_order, fmt, fb);
   if (st != LSAS_OK) return st;
@@ -277,9 +353,20 @@ lsas_status lsas_server_register(lsas_server s, int M, int N, int cp_len, int n_
   cf->h_b = fb[1];
   cf->bits_b = fb[2];
   cf->eq_b = fb[3];
-  // admission: staging for max_batch frames on each lane plus the plan's own tables
+  cf->dn_params = dn_params;
+  const size_t B = static_cast<size_t>(s->max_batch);
+  size_t work_floats = 0;
+  if (dn_params) {
+    st = lsas_dn_work_size(static_cast<int>(B) * M, N, &work_floats);
+    if (st != LSAS_OK) return st;
+  }
+  // admission: staging for max_batch frames on each lane (plus, for the
+  // learned form, the LS estimate and the refinement's scratch) and the
+  // plan's own tables
   const size_t plan_b = static_cast<size_t>(N) * 64 + (1u << 20);
-  cf->bytes = kLanes * static_cast<size_t>(s->max_batch) * (fb[0] + fb[1] + fb[2] + fb[3]) + plan_b;
+  const size_t lane_b = B * (fb[0] + fb[1] + fb[2] + fb[3]) +
+                        (dn_params ? B * fb[1] + work_floats * 4 + 256 : 0);
+  cf->bytes = kLanes * lane_b + plan_b;
   {
     std::lock_guard<std::mutex> lock(s->mu);
     if (s->used + cf->bytes > s->budget) return LSAS_ERR_CAPACITY;
@@ -292,6 +379,9 @@ lsas_status lsas_server_register(lsas_server s, int M, int N, int cp_len, int n_
       cudaFree(ln.d_H);
       cudaFree(ln.d_bits);
       cudaFree(ln.d_eq);
+      cudaFree(ln.d_Hls);
+      cudaFree(ln.d_work);
+      cudaFree(ln.d_status);
       if (ln.stream) cudaStreamDestroy(ln.stream);
     }
     std::lock_guard<std::mutex> lock(s->mu);
@@ -304,15 +394,19 @@ lsas_status lsas_server_register(lsas_server s, int M, int N, int cp_len, int n_
   st = lsas_plan_set(cf->plan, fmt, s->max_batch);
   if (st == LSAS_OK && host_pilot_iq) st = lsas_plan_set_pilot(cf->plan, host_pilot_iq);
   if (st != LSAS_OK) return undo(st);
-  const size_t B = static_cast<size_t>(s->max_batch);
   for (Lane& ln : cf->lanes) {
     if (cudaMalloc(&ln.d_in, B * cf->in_b) != cudaSuccess ||
         cudaMalloc(&ln.d_H, B * cf->h_b) != cudaSuccess ||
         cudaMalloc(&ln.d_bits, B * cf->bits_b) != cudaSuccess ||
-        cudaMalloc(&ln.d_eq, B * cf->eq_b) != cudaSuccess) {
+        cudaMalloc(&ln.d_eq, B * cf->eq_b) != cudaSuccess ||
+        (dn_params && (cudaMalloc(&ln.d_Hls, B * cf->h_b) != cudaSuccess ||
+                       cudaMalloc(&ln.d_work, work_floats * 4) != cudaSuccess ||
+                       cudaMalloc(&ln.d_status, sizeof(int)) != cudaSuccess))) {
       cudaGetLastError();
       return undo(LSAS_ERR_OOM);
     }
+    if (dn_params && cudaMemset(ln.d_status, 0, sizeof(int)) != cudaSuccess)
+      return undo(LSAS_ERR_CUDA);
     if (cudaStreamCreateWithFlags(&ln.stream, cudaStreamNonBlocking) != cudaSuccess)
       return undo(LSAS_ERR_CUDA);
   }
@@ -322,16 +416,47 @@ lsas_status lsas_server_register(lsas_server s, int M, int N, int cp_len, int n_
   return LSAS_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+lsas_status lsas_server_register(lsas_server s, int M, int N, int cp_len, int n_sym,
+                                 int pilot_idx, int qam_order, lsas_input_fmt fmt,
+                                 const float* host_pilot_iq, int* config_id) {
+  return register_config(s, M, N, cp_len, n_sym, pilot_idx, qam_order, fmt, host_pilot_iq,
+                         nullptr, config_id);
+}
+
+lsas_status lsas_server_register_refined(lsas_server s, int M, int N, int cp_len, int n_sym,
+                                         int pilot_idx, int qam_order, lsas_input_fmt fmt,
+                                         const float* host_pilot_iq,
+                                         const uint16_t* d_params_bf16, int* config_id) {
+  if (!d_params_bf16) return LSAS_ERR_INVALID_ARG;
+  return register_config(s, M, N, cp_len, n_sym, pilot_idx, qam_order, fmt, host_pilot_iq,
+                         d_params_bf16, config_id);
+}
+
+lsas_status lsas_server_set_admission(lsas_server s, size_t frame_budget_bytes, double wait_ms) {
+  if (!s || wait_ms < 0) return LSAS_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(s->mu);
+  s->frame_budget = frame_budget_bytes;
+  s->admit_wait_ms = wait_ms;
+  return LSAS_OK;
+}
+
 lsas_status lsas_server_submit(lsas_server s, int config_id, const void* h_in, float* h_H,
                                uint8_t* h_bits, float* h_eq, uint64_t* ticket) {
   if (!s || !h_in || !h_H || !h_bits || !ticket) return LSAS_ERR_INVALID_ARG;
   {
-    std::lock_guard<std::mutex> lock(s->mu);
+    std::unique_lock<std::mutex> lock(s->mu);
     if (config_id < 0 || config_id >= static_cast<int>(s->configs.size())) return LSAS_ERR_INVALID_ARG;
     if (s->stop) return LSAS_ERR_INVALID_ARG;
+    const size_t fb = frame_bytes_of(*s->configs[config_id], h_eq != nullptr);
+    const lsas_status st = admit(s, lock, fb);
+    if (st != LSAS_OK) return st;
     Config& cf = *s->configs[config_id];
     const uint64_t t = s->next_ticket++;
-    cf.queue.push_back(Request{t, config_id, h_in, h_H, h_bits, h_eq, Clock::now()});
+    cf.queue.push_back(Request{t, config_id, h_in, h_H, h_bits, h_eq, Clock::now(), fb});
     s->done[t] = Done{};
     *ticket = t;
   }
@@ -346,18 +471,25 @@ lsas_status lsas_server_submit_many(lsas_server s, int n, const int* config_ids,
   if (!s || n < 0 || (n > 0 && (!config_ids || !h_in || !h_H || !h_bits || !tickets)))
     return LSAS_ERR_INVALID_ARG;
   {
-    std::lock_guard<std::mutex> lock(s->mu);
+    std::unique_lock<std::mutex> lock(s->mu);
     if (s->stop) return LSAS_ERR_INVALID_ARG;
-    // validate everything first: either all frames are queued or none
-    for (int i = 0; i < n; ++i)
+    // validate and admit everything first: either all frames are queued or none
+    size_t total = 0;
+    for (int i = 0; i < n; ++i) {
       if (config_ids[i] < 0 || config_ids[i] >= static_cast<int>(s->configs.size()) || !h_in[i] ||
           !h_H[i] || !h_bits[i])
         return LSAS_ERR_INVALID_ARG;
+      total += frame_bytes_of(*s->configs[config_ids[i]], h_eq && h_eq[i]);
+    }
+    const lsas_status st = admit(s, lock, total);
+    if (st != LSAS_OK) return st;
     const Clock::time_point now = Clock::now();
     for (int i = 0; i < n; ++i) {
       const uint64_t t = s->next_ticket++;
+      float* eq = h_eq ? h_eq[i] : nullptr;
       s->configs[config_ids[i]]->queue.push_back(
-          Request{t, config_ids[i], h_in[i], h_H[i], h_bits[i], h_eq ? h_eq[i] : nullptr, now});
+          Request{t, config_ids[i], h_in[i], h_H[i], h_bits[i], eq, now,
+                  frame_bytes_of(*s->configs[config_ids[i]], eq != nullptr)});
       s->done[t] = Done{};
       tickets[i] = t;
     }
@@ -417,6 +549,14 @@ lsas_status lsas_server_stats(lsas_server s, uint64_t out[4]) {
   return LSAS_OK;
 }
 
+lsas_status lsas_server_frame_bytes(lsas_server s, uint64_t out[2]) {
+  if (!s || !out) return LSAS_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(s->mu);
+  out[0] = s->inflight;
+  out[1] = frame_budget(s);
+  return LSAS_OK;
+}
+
 lsas_status lsas_server_destroy(lsas_server s) {
   if (!s) return LSAS_ERR_INVALID_ARG;
   {
@@ -433,10 +573,20 @@ lsas_status lsas_server_destroy(lsas_server s) {
     if (ps != LSAS_OK && st == LSAS_OK) st = ps;
     lsas_plan_destroy(cf->plan);
     for (Lane& ln : cf->lanes) {
+      if (ln.d_status) {
+        // the refinement's bounded waits latch here
+        int code = 0;
+        if (cudaMemcpy(&code, ln.d_status, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess &&
+            code != 0 && st == LSAS_OK)
+          st = static_cast<lsas_status>(code);
+      }
       cudaFree(ln.d_in);
       cudaFree(ln.d_H);
       cudaFree(ln.d_bits);
       cudaFree(ln.d_eq);
+      cudaFree(ln.d_Hls);
+      cudaFree(ln.d_work);
+      cudaFree(ln.d_status);
       if (ln.stream) cudaStreamDestroy(ln.stream);
     }
   }

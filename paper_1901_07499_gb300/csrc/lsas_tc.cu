@@ -9,11 +9,12 @@
 // Each complex GEMM is a real one over [re | im] halves: a data row is
 // [x_re(0..K-1) | x_im(0..K-1)] and the DFT operand row of output (re, k) is
 // [cos | sin], of (im, k) [-sin | cos] (angle 2 pi n k / K).  Operands are
-// fp16, accumulators fp32 in tensor memory (tcgen05.mma kind::f16, M = 128).
-// With terms = 3 every operand is split into hi = fp16(v) and
-// lo = fp16(v - hi), and a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi (the lo*lo
-// term, ~2^-22 relative, is dropped); terms = 1 uses a_hi b_hi alone
-// (~2^-11 relative).  Stage-2 inputs are scaled by 2^-6 (exact) to stay in
+// fp16 or bf16 (both of one type in an MMA), accumulators fp32 in tensor
+// memory (tcgen05.mma kind::f16, M = 128).  With terms = 3 every operand is
+// split into hi = round(v) and lo = round(v - hi), and
+// a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi (the lo*lo term is dropped: ~2^-22
+// relative for fp16, ~2^-16 for bf16); terms = 1 uses a_hi b_hi alone
+// (~2^-11 relative for fp16, ~2^-8 for bf16).  Stage-2 inputs are scaled by 2^-6 (exact) to stay in
 // fp16 range; the output is scaled back with the unitary 1/sqrt(N).
 //
 // Operand tiles use the canonical no-swizzle K-major layout: 8-row x 16-byte
@@ -22,6 +23,9 @@
 #include <cmath>
 #include <vector>
 
+#include <cstring>
+
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include "lsas_kernels.cuh"
@@ -35,10 +39,26 @@ __host__ __device__ inline int tc_off(int row, int k, int K) {
   return (row >> 3) * (16 * K) + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
 }
 
-// Host: operand image (hi, lo) of the K-point DFT, 2K rows x 2K columns.
+// bfloat16 of a double, round to nearest even, by way of float
+static uint16_t bf16_bits(double v) {
+  const float f = static_cast<float>(v);
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return static_cast<uint16_t>(u >> 16);
+}
+static double bf16_value(uint16_t b) {
+  const uint32_t u = static_cast<uint32_t>(b) << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+
+// Host: operand images of the K-point DFT, 2K rows x 2K columns: fp16 hi and
+// lo, then bf16 hi and lo (each image 2K x 2K halves, in that order).
 static void dft_image(int K, std::vector<uint16_t>& img) {
   const int R = 2 * K, C = 2 * K;
-  img.assign(2 * R * C, 0);
+  img.assign(4 * R * C, 0);
   for (int r = 0; r < R; ++r) {
     const int k = r % K;
     for (int c = 0; c < C; ++c) {
@@ -49,9 +69,13 @@ static void dft_image(int K, std::vector<uint16_t>& img) {
                                : (c < K ? -std::sin(a) : std::cos(a));
       const __half hi = __double2half(w);
       const __half lo = __double2half(w - static_cast<double>(__half2float(hi)));
+      const uint16_t bhi = bf16_bits(w);
+      const uint16_t blo = bf16_bits(w - bf16_value(bhi));
       const int o = tc_off(r, c, C) / 2;
       img[o] = __half_as_ushort(hi);
       img[R * C + o] = __half_as_ushort(lo);
+      img[2 * R * C + o] = bhi;
+      img[3 * R * C + o] = blo;
     }
   }
 }
@@ -86,11 +110,21 @@ __device__ __forceinline__ void split16x2(float a, float b, uint32_t& hi, uint32
   hi = *reinterpret_cast<const uint32_t*>(&h);
   lo = *reinterpret_cast<const uint32_t*>(&l);
 }
+// the same with bf16 pieces: hi = bf16(v), lo = bf16(v - hi)
+__device__ __forceinline__ void splitbf16x2(float a, float b, uint32_t& hi, uint32_t& lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  const float2 hf = __bfloat1622float2(h);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
+}
 
-// Store one operand row of 2K values (re[0..K) then im[0..K)), hi and lo images.
+// Store one operand row of 2K values (re[0..K) then im[0..K)), hi and lo
+// images, in fp16 or bf16.
 template <int K>
 __device__ __forceinline__ void store_row(unsigned char* hi_img, unsigned char* lo_img, int row,
-                                          const float* re, const float* im, bool want_lo) {
+                                          const float* re, const float* im, bool want_lo,
+                                          bool bf16) {
 #pragma unroll
   for (int c = 0; c < 2 * K; c += 8) {
     uint32_t h[4], l[4];
@@ -98,7 +132,8 @@ __device__ __forceinline__ void store_row(unsigned char* hi_img, unsigned char* 
     for (int j = 0; j < 8; j += 2) {
       const float a = c + j < K ? re[c + j] : im[c + j - K];
       const float b = c + j + 1 < K ? re[c + j + 1] : im[c + j + 1 - K];
-      split16x2(a, b, h[j / 2], l[j / 2]);
+      if (bf16) splitbf16x2(a, b, h[j / 2], l[j / 2]);
+      else split16x2(a, b, h[j / 2], l[j / 2]);
     }
     const int o = tc_off(row, c, 2 * K);
     *reinterpret_cast<uint4*>(hi_img + o) = make_uint4(h[0], h[1], h[2], h[3]);
@@ -138,6 +173,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tcfft_kernel(const KParams p) {
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
   const bool split = p.terms == 3;
+  const bool bf16 = p.tc_bf16 != 0;
   unsigned char* w1 = smem + G::OFF_W1;
   unsigned char* w2 = smem + G::OFF_W2;
   unsigned char* a1 = smem + G::OFF_A1;
@@ -145,10 +181,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) tcfft_kernel(const KParams p) {
   unsigned char* a2 = smem + G::OFF_A2;
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + G::OFF_BAR);
   uint32_t* tmem_base = reinterpret_cast<uint32_t*>(smem + G::OFF_BAR + 16);
-  // constant DFT operands into shared memory
+  // constant DFT operands (hi, lo of the operand type) into shared memory
   {
-    const uint4* s1 = static_cast<const uint4*>(p.tc_w1);
-    const uint4* s2 = static_cast<const uint4*>(p.tc_w2);
+    const uint4* s1 = static_cast<const uint4*>(p.tc_w1) + (bf16 ? 2 * G::W1_BYTES / 16 : 0);
+    const uint4* s2 = static_cast<const uint4*>(p.tc_w2) + (bf16 ? 2 * G::W2_BYTES / 16 : 0);
     for (int i = tid; i < 2 * G::W1_BYTES / 16; i += kTcThreads) reinterpret_cast<uint4*>(w1)[i] = s1[i];
     for (int i = tid; i < 2 * G::W2_BYTES / 16; i += kTcThreads) reinterpret_cast<uint4*>(w2)[i] = s2[i];
   }
@@ -191,7 +227,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tcfft_kernel(const KParams p) {
 #pragma unroll
         for (int n1 = 0; n1 < 32; ++n1) re[n1] = im[n1] = 0.f;
       }
-      store_row<32>(a1 + (2 * t) * G::A1_BYTES, a1 + (2 * t + 1) * G::A1_BYTES, tid, re, im, split);
+      store_row<32>(a1 + (2 * t) * G::A1_BYTES, a1 + (2 * t + 1) * G::A1_BYTES, tid, re, im, split,
+                    bf16);
     }
     fence_proxy_async();
     tmem_fence_before();
@@ -204,7 +241,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tcfft_kernel(const KParams p) {
           const uint32_t bbase = smem_u32(w1 + (term == 1 ? 1 : 0) * G::W1_BYTES);
           for (int kc = 0; kc < 4; ++kc)
             umma_f16(tmem + t * 64, tc_desc(abase + kc * 256, 64), tc_desc(bbase + kc * 256, 64),
-                     umma_idesc(64, false), (term > 0 || kc > 0) ? 1u : 0u);
+                     umma_idesc(64, bf16), (term > 0 || kc > 0) ? 1u : 0u);
         }
       umma_commit(smem_u32(bar));
     }
@@ -244,7 +281,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tcfft_kernel(const KParams p) {
         re[n2] = c.x;
         im[n2] = c.y;
       }
-      store_row<N2>(a2 + (2 * t) * G::A2_BYTES, a2 + (2 * t + 1) * G::A2_BYTES, tid, re, im, split);
+      store_row<N2>(a2 + (2 * t) * G::A2_BYTES, a2 + (2 * t + 1) * G::A2_BYTES, tid, re, im, split,
+                    bf16);
     }
     fence_proxy_async();
     tmem_fence_before();
@@ -257,7 +295,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tcfft_kernel(const KParams p) {
           const uint32_t bbase = smem_u32(w2 + (term == 1 ? 1 : 0) * G::W2_BYTES);
           for (int kc = 0; kc < (2 * N2) / 16; ++kc)
             umma_f16(tmem + 128 + t * (2 * N2), tc_desc(abase + kc * 256, 2 * N2),
-                     tc_desc(bbase + kc * 256, 2 * N2), umma_idesc(2 * N2, false),
+                     tc_desc(bbase + kc * 256, 2 * N2), umma_idesc(2 * N2, bf16),
                      (term > 0 || kc > 0) ? 1u : 0u);
         }
       umma_commit(smem_u32(bar));

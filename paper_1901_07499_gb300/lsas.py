@@ -65,6 +65,8 @@ lsas_mrc_combine = _proto("lsas_mrc_combine", [_vp, _vp, _vp, _i, _i, _vp, _vp, 
 lsas_run_frame_split_static = _proto("lsas_run_frame_split_static",
                                      [_vp, _vp, _i, _i, _vp, _vp, _vp, _vp])
 lsas_fft_tc = _proto("lsas_fft_tc", [_vp, _vp, _i, _i, _vp, _vp])
+lsas_fft_tc_ex = _proto("lsas_fft_tc_ex", [_vp, _vp, _i, _i, _i, _vp, _vp])
+LSAS_TC_FP16, LSAS_TC_BF16 = 0, 1
 lsas_receive_y = _proto("lsas_receive_y", [_vp, _vp, _i, _vp, _vp, _vp, _vp])
 lsas_plan_set_pn = _proto("lsas_plan_set_pn", [_vp, C.POINTER(_f), _i])
 lsas_pn_sync = _proto("lsas_pn_sync", [_vp, _vp, _i, _i, _i, _vp, _vp, _vp])
@@ -84,6 +86,11 @@ lsas_server_wait_many = _proto("lsas_server_wait_many",
                                [_vp, _i, C.POINTER(C.c_uint64), C.c_double, C.POINTER(C.c_double),
                                 C.POINTER(_i)])
 lsas_server_destroy = _proto("lsas_server_destroy", [_vp])
+lsas_server_register_refined = _proto("lsas_server_register_refined",
+                                      [_vp, _i, _i, _i, _i, _i, _i, _i, C.POINTER(_f), _vp,
+                                       C.POINTER(_i)])
+lsas_server_set_admission = _proto("lsas_server_set_admission", [_vp, C.c_size_t, C.c_double])
+lsas_server_frame_bytes = _proto("lsas_server_frame_bytes", [_vp, C.POINTER(C.c_uint64)])
 lsas_dn_work_size = _proto("lsas_dn_work_size", [_i, _i, C.POINTER(C.c_size_t)])
 lsas_dn_apply = _proto("lsas_dn_apply", [_vp, _i, _vp, _i, _i, _vp, _vp, _vp])
 lsas_dn_grad = _proto("lsas_dn_grad", [_vp, _vp, _vp, _i, _i, _vp, _vp, _vp, _vp])
@@ -102,11 +109,13 @@ EXPORTED = ["lsas_status_str", "lsas_check_config", "lsas_frame_bytes",
             "lsas_plan_create", "lsas_plan_set", "lsas_plan_set_pilot",
             "lsas_fft", "lsas_estimate", "lsas_demodulate", "lsas_run_frame",
             "lsas_run_frame_host", "lsas_mrc_partial", "lsas_mrc_combine",
-            "lsas_run_frame_split_static", "lsas_fft_tc", "lsas_receive_y",
+            "lsas_run_frame_split_static", "lsas_fft_tc", "lsas_fft_tc_ex", "lsas_receive_y",
             "lsas_plan_set_pn", "lsas_pn_sync", "lsas_pn_extract", "lsas_fftshift",
             "lsas_server_create", "lsas_server_register", "lsas_server_submit",
             "lsas_server_wait", "lsas_server_stats", "lsas_server_destroy",
             "lsas_server_submit_many", "lsas_server_wait_many",
+            "lsas_server_register_refined", "lsas_server_set_admission",
+            "lsas_server_frame_bytes",
             "lsas_dn_work_size", "lsas_dn_apply", "lsas_dn_grad", "lsas_dn_adam",
             "lsas_dn_to_bf16", "lsas_dn_apply_tc", "lsas_plan_set_fault",
             "lsas_plan_set_profile", "lsas_plan_profile",
@@ -244,14 +253,16 @@ class Plan:
         check(lsas_fft(self._h, _ptr(x), F, _ptr(Y), _stream(stream)), "lsas_fft")
         return Y
 
-    def fft_tc(self, x, terms=3, Y=None, stream=None):
-        """The FFT on the tensor cores (fp16 operands; terms=3 splits them
-        into hi + lo parts), Y [F][M][S][N] complex64."""
+    def fft_tc(self, x, terms=3, Y=None, stream=None, operand="fp16"):
+        """The FFT on the tensor cores (fp16 or bf16 operands; terms=3 splits
+        them into hi + lo parts), Y [F][M][S][N] complex64."""
         import torch
         F = self._frames(x)
         if Y is None:
             Y = torch.empty((F, self.M, self.S, self.N), dtype=torch.complex64, device=x.device)
-        check(lsas_fft_tc(self._h, _ptr(x), F, terms, _ptr(Y), _stream(stream)), "lsas_fft_tc")
+        op = {"fp16": LSAS_TC_FP16, "bf16": LSAS_TC_BF16}[operand]
+        check(lsas_fft_tc_ex(self._h, _ptr(x), F, op, terms, _ptr(Y), _stream(stream)),
+              "lsas_fft_tc_ex")
         return Y
 
     def receive_y(self, Y, H=None, bits=None, eq=None, want_eq=False, stream=None):
@@ -431,20 +442,41 @@ class Server:
               "lsas_server_create")
         self._h = h
         self._live = {}
+        self._params = []
         self.configs = {}
 
-    def register(self, M, N, cp, n_sym, pilot_idx=0, qam_order=4, fmt="sc16", pilot=None) -> int:
+    def register(self, M, N, cp, n_sym, pilot_idx=0, qam_order=4, fmt="sc16", pilot=None,
+                 refine_params_bf16=None) -> int:
+        """Register a configuration; with ``refine_params_bf16`` (a device
+        tensor of LSAS_DN_PARAMS bf16 values, kept alive here) its frames run
+        the learned form (LS -> tensor-core refinement -> MRC)."""
         ptr = None
         if pilot is not None:
             x = np.asarray(pilot, dtype=np.complex128)
             iq = np.ascontiguousarray(np.stack([x.real, x.imag], -1).astype(np.float32))
             ptr = iq.ctypes.data_as(C.POINTER(_f))
         cid = _i()
-        check(lsas_server_register(self._h, M, N, cp, n_sym, pilot_idx, qam_order, _fmt(fmt), ptr,
-                                   C.byref(cid)), "lsas_server_register")
+        if refine_params_bf16 is None:
+            check(lsas_server_register(self._h, M, N, cp, n_sym, pilot_idx, qam_order, _fmt(fmt),
+                                       ptr, C.byref(cid)), "lsas_server_register")
+        else:
+            check(lsas_server_register_refined(self._h, M, N, cp, n_sym, pilot_idx, qam_order,
+                                               _fmt(fmt), ptr, _ptr(refine_params_bf16),
+                                               C.byref(cid)), "lsas_server_register_refined")
+            self._params.append(refine_params_bf16)
         q = int(round(np.log2(qam_order)))
-        self.configs[cid.value] = dict(M=M, N=N, cp=cp, S=n_sym, D=n_sym - 1, q=q)
+        self.configs[cid.value] = dict(M=M, N=N, cp=cp, S=n_sym, D=n_sym - 1, q=q,
+                                       refined=refine_params_bf16 is not None)
         return cid.value
+
+    def set_admission(self, frame_budget_bytes: int = 0, wait_ms: float = 0.0) -> None:
+        check(lsas_server_set_admission(self._h, int(frame_budget_bytes), float(wait_ms)),
+              "lsas_server_set_admission")
+
+    def frame_bytes(self) -> dict:
+        out = (C.c_uint64 * 2)()
+        check(lsas_server_frame_bytes(self._h, out), "lsas_server_frame_bytes")
+        return dict(charged=int(out[0]), budget=int(out[1]))
 
     def submit(self, cid, x, H, bits, eq=None) -> int:
         t = C.c_uint64()
