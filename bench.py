@@ -552,8 +552,12 @@ def denoiser_report(args):
         bits_dn, _ = plan.demodulate(x, H_dn)
         H_tc = dn.apply(H_ls, params_bf16=pb, tensor_cores=True)
         bits_tc, _ = plan.demodulate(x, H_tc)
+        # the refinement fused after LS, then MRC (one call)
+        work = dn.work(F * cfg.M, cfg.N)
+        st = torch.zeros(1, dtype=torch.int32, device="cuda")
+        H_fu, bits_fu, _ = plan.run_frame_refined(x, pb, work, st)
         plan.sync()
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(8)]
         ev[0].record()
         for _ in range(5):
             dn.apply(H_ls, out=H_dn, params_bf16=pb)
@@ -562,7 +566,17 @@ def denoiser_report(args):
         for _ in range(5):
             dn.apply(H_ls, out=H_tc, params_bf16=pb, tensor_cores=True)
         ev[3].record()
+        ev[4].record()
+        for _ in range(5):
+            plan.run_frame_refined(x, pb, work, st, H=H_fu, bits=bits_fu)
+        ev[5].record()
+        ev[6].record()
+        for _ in range(5):
+            plan.run_frame(x, H_ls, bits_ls)
+        ev[7].record()
         torch.cuda.synchronize()
+        if int(st.item()) != 0:
+            raise RuntimeError("fused refinement reported a timeout")
         if int(dn.status().item()) != 0:
             raise RuntimeError("tensor-core refinement reported a timeout")
         Htrue = np.fft.fft(b.taps, cfg.N, axis=-1) * b.gain[:, None, None]
@@ -573,10 +587,13 @@ def denoiser_report(args):
             return float(np.mean(got != b.bits.reshape(F, -1)))
         print(json.dumps({"mode": "denoiser-eval", "snr_db": snr, "frames": F, "M": cfg.M, "N": cfg.N,
                           "qam": cfg.Q, "nmse_ls": mse(H_ls), "nmse_dn": mse(H_dn),
-                          "nmse_dn_tc": mse(H_tc), "ber_ls": ber(bits_ls), "ber_dn": ber(bits_dn),
-                          "ber_dn_tc": ber(bits_tc),
+                          "nmse_dn_tc": mse(H_tc), "nmse_fused": mse(H_fu),
+                          "ber_ls": ber(bits_ls), "ber_dn": ber(bits_dn),
+                          "ber_dn_tc": ber(bits_tc), "ber_fused": ber(bits_fu),
                           "refine_us_per_frame": 1e3 * ev[0].elapsed_time(ev[1]) / 5 / F,
-                          "refine_tc_us_per_frame": 1e3 * ev[2].elapsed_time(ev[3]) / 5 / F}))
+                          "refine_tc_us_per_frame": 1e3 * ev[2].elapsed_time(ev[3]) / 5 / F,
+                          "fused_receiver_us_per_frame": 1e3 * ev[4].elapsed_time(ev[5]) / 5 / F,
+                          "plain_receiver_us_per_frame": 1e3 * ev[6].elapsed_time(ev[7]) / 5 / F}))
         sys.stdout.flush()
 
 

@@ -407,6 +407,24 @@ lsas_status lsas_dn_apply_tc(const uint16_t* d_params_bf16, const float* d_H, in
                              float* d_work, float* d_Hout, int* d_status, void* stream);
 
 /*
+ * The learned form of the receiver with the refinement fused after LS
+ * (Sec. II-C's LS estimate is its input): per antenna row, the pilot
+ * symbol's FFT, LS and the row normalisation feed the tensor-core refinement
+ * (as lsas_dn_apply_tc, bf16 parameters d_params_bf16) on chip, so the
+ * unrefined estimate is never written to memory; then MRC and demapping
+ * with the refined channel (as lsas_demodulate).  Outputs as lsas_run_frame:
+ * d_H receives the refined channel.  d_work: lsas_dn_work_size(n_frames * M,
+ * N) floats, 16-byte aligned; d_status as lsas_dn_apply_tc.  The plan's
+ * other device conditions latch as usual (lsas_plan_sync).
+ * Supported: N = 1024 with sc16 input (UNSUPPORTED otherwise); INVALID_ARG
+ * for null or misaligned pointers, CAPACITY for n_frames > max_frames.
+ * Asynchronous.
+ */
+lsas_status lsas_run_frame_refined(lsas_plan plan, const void* d_in, int n_frames,
+                                   const uint16_t* d_params_bf16, float* d_work, float* d_H,
+                                   uint8_t* d_bits, float* d_eq, int* d_status, void* stream);
+
+/*
  * Test hook of failure detection (no counterpart in the paper).  Every wait
  * of the fused kernel on a staging copy is bounded (~2 s, %globaltimer):
  * when it runs out the block latches LSAS_ERR_TIMEOUT, stops issuing

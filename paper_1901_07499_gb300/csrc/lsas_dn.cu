@@ -463,6 +463,181 @@ __global__ void __launch_bounds__(128 * kTcSlots, 2) dn_tc_kernel(const float* _
   if (warp == 0) tmem_dealloc(*tbase, 32 * kTcSlots);
 }
 
+// ------------------------------------------- LS estimate fused with the refinement
+//
+// For N = 1024 and sc16 input: the LS channel estimate of each antenna row
+// never leaves the SM before it is refined.  A slot of 128 threads (four
+// warps, one per TMEM lane quarter) takes one row at a time: its first warp
+// transforms the row's pilot symbol (radix 32 x 32 in registers, as the
+// fused receiver), forms H = Y conj(X)/|X|^2 (Sec. II-C), the row RMS and
+// x0 = H / rms, and writes x0 as the split bf16 input rows of the whole row
+// (1024 positions and 8 zero halo rows on each side) into shared memory;
+// then all four warps run the refinement's nine tiles over that buffer
+// exactly as dn_tc_kernel does (layer 1 reads the row buffer at the tile's
+// offset instead of a per-tile copy) and write the refined row.
+constexpr int kLsN = 1024;
+constexpr int kLsHalo = 8;
+constexpr int kLsXRows = kLsN + 5 * kLsHalo;               // 1064 rows of 16 bytes
+constexpr int kLsXBytes = kLsXRows * 16;
+constexpr int kLsSlotBytes = kLsXBytes + kTcActBytes;      // x rows, then act / FFT exchange
+constexpr int kLsTw = kTcImgBytes;                         // pass twiddles (8 KB)
+constexpr int kLsSlots0 = kLsTw + kLsN * 8;
+constexpr int kLsSmem = kLsSlots0 + kTcSlots * kLsSlotBytes + kTcSlots * 8 + kTcSlots * 4 + 16;
+static_assert(kTcActBytes >= (kLsN + kLsN / 32) * 8, "the FFT exchange fits the act buffer");
+static_assert(kLsSlots0 % 16 == 0 && kLsSlotBytes % 16 == 0, "16-byte operand alignment");
+
+__global__ void __launch_bounds__(128 * kTcSlots, 1) dn_ls_tc_kernel(const KParams p,
+                                                             const float* __restrict__ img_g,
+                                                             int R, float2* __restrict__ Hout,
+                                                             int* status) {
+  constexpr int N = kLsN;
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned char* wimg = smem;
+  float2* tws = reinterpret_cast<float2*>(smem + kLsTw);
+  const int t = threadIdx.x;
+  const int slot = t >> 7, u = t & 127, warp = t >> 5, lane = t & 31;
+  unsigned char* xbuf = smem + kLsSlots0 + slot * kLsSlotBytes;
+  unsigned char* act = xbuf + kLsXBytes;
+  float2* ex = reinterpret_cast<float2*>(act);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kLsSlots0 + kTcSlots * kLsSlotBytes);
+  float* rms_s = reinterpret_cast<float*>(bars + kTcSlots);
+  uint32_t* tbase = reinterpret_cast<uint32_t*>(rms_s + kTcSlots);
+  uint64_t* bar = &bars[slot];
+  if (t == 0) {
+    for (int g = 0; g < kTcSlots; ++g) mbar_init(smem_u32(&bars[g]), 1);
+    fence_mbar_init();
+    mbar_expect_tx(smem_u32(&bars[0]), kTcImgBytes);        // phase 0 of slot 0's barrier
+    bulk_load(smem_u32(wimg), img_g, kTcImgBytes, smem_u32(&bars[0]), evict_last_policy());
+  }
+  for (int i = t; i < N; i += blockDim.x) tws[i] = __ldg(p.twP + i);
+  __syncwarp();
+  if (warp == 0) tmem_alloc(smem_u32(tbase), 32 * kTcSlots);
+  // halo rows of the x buffer (positions < 0 and >= N) stay zero
+  for (int j = u; j < kLsXRows - N; j += 128) {
+    const int row = j < kLsHalo ? j : N + j;
+    *reinterpret_cast<uint4*>(xbuf + row * 16) = make_uint4(0u, 0u, 0u, 0u);
+  }
+  tmem_fence_before();
+  __syncthreads();
+  tmem_fence_after();
+  const uint32_t tm = *tbase + 32 * slot + (static_cast<uint32_t>(32 * (warp & 3)) << 16);
+  const uint32_t tm_mma = *tbase + 32 * slot;
+  const uint32_t id32 = umma_idesc(32, true), id16 = umma_idesc(16, true);
+  const uint64_t da = umma_desc(smem_u32(act), kTcLbo, 128);
+  const uint64_t dw1 = umma_desc(smem_u32(wimg), 128, 256);
+  const uint64_t dw = umma_desc(smem_u32(wimg), 128, 512);
+  const uint64_t dones = umma_desc(smem_u32(wimg + kTcOnes), 16, 128);
+  bool ok = mbar_wait_bounded(smem_u32(&bars[0]), 0);
+  if (!ok) latch(status, kStTimeout);
+  uint32_t phase = slot == 0 ? 1u : 0u;
+  const int tiles_row = (N + kTcValid - 1) / kTcValid;
+  for (int r = blockIdx.x * kTcSlots + slot; r < R; r += gridDim.x * kTcSlots) {
+    // ---- the row's LS estimate, normalised, by the slot's first warp
+    if ((warp & 3) == 0) {
+      const int f = r / p.M, m = r % p.M;
+      float2 v[32];
+      load_row<10, false>(v, row_ptr<10, false>(p, f, m, p.pilot_idx), lane, true);
+      dft<32>(v, p);
+      final_exchange_write<10>(v, ex, lane);
+      __syncwarp();
+      final_exchange_read<10>(v, ex, lane, tws);
+      final_dft<10>(v, p);
+      float e2 = 0.f;
+#pragma unroll
+      for (int e = 0; e < 32; ++e) {
+        v[e] = cmul(v[e], __ldg(p.xinv + lane + 32 * e));   // bin lane + 32 e
+        e2 = fmaf(v[e].x, v[e].x, fmaf(v[e].y, v[e].y, e2));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+      const float rr = sqrtf(e2 / N);
+      const float inv = rr > 0.f ? 1.0f / rr : 0.f;
+      if (lane == 0) rms_s[slot] = rr;
+#pragma unroll
+      for (int e = 0; e < 32; ++e)
+        *reinterpret_cast<uint4*>(xbuf + (kLsHalo + lane + 32 * e) * 16) =
+            x_row(v[e].x * inv, v[e].y * inv);
+    }
+    // the x rows (and the exchange's last use) before the slot's MMAs
+    fence_proxy_async();
+    named_sync(1 + slot, 128);
+    const float rr = rms_s[slot];
+    for (int ti = 0; ti < tiles_row; ++ti) {
+      const int s0 = ti * kTcValid - kTcFirst;                  // position of MMA row 0
+      // the tile's input rows start at position s0 - 2, buffer row s0 - 2 + halo
+      const uint64_t dx = umma_desc(smem_u32(xbuf + (s0 - 2 + kLsHalo) * 16), 16, 128);
+      const int q = s0 + u;                                      // position of MMA row u
+      const bool inside = q >= 0 && q < N;
+      auto issue_wait = [&](int layer) {
+        fence_proxy_async();
+        tmem_fence_before();
+        named_sync(1 + slot, 128);
+        tmem_fence_after();
+        if (u == 0) {
+          umma_f16(tm_mma, dones, dw1 + ((kTcBias + 1024 * (layer - 1)) >> 4),
+                   layer == 4 ? id16 : id32, 0u);
+          if (layer == 1) {
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+              umma_f16(tm_mma, dx + 2 * j, dw1 + ((kTcL1 + 1024 * j) >> 4), id32, 1u);
+          } else {
+            const int boff = layer == 2 ? kTcL2 : layer == 3 ? kTcL3 : kTcL4;
+            const int tapb = layer == 4 ? 1024 : 2048;
+            const uint32_t idesc = layer == 4 ? id16 : id32;
+#pragma unroll
+            for (int k = 0; k < 5; ++k)
+#pragma unroll
+              for (int kh = 0; kh < 2; ++kh)
+                umma_f16(tm_mma, da + ((k * 16 + kh * 2 * kTcLbo) >> 4),
+                         dw + ((boff + k * tapb + kh * 256) >> 4), idesc, 1u);
+          }
+          umma_commit(smem_u32(bar));
+          if (ok && !mbar_wait_bounded(smem_u32(bar), phase)) {
+            ok = false;
+            latch(status, kStTimeout);
+          }
+        }
+        phase ^= 1;
+        tmem_fence_before();
+        named_sync(1 + slot, 128);
+        tmem_fence_after();
+      };
+      float d[32];
+      issue_wait(1);
+      Tmem<32>::ld(tm, d);
+      tmem_wait_ld();
+      tc_epilogue(d, inside, act, u);
+      issue_wait(2);
+      Tmem<32>::ld(tm, d);
+      tmem_wait_ld();
+      tc_epilogue(d, inside, act, u);
+      issue_wait(3);
+      Tmem<32>::ld(tm, d);
+      tmem_wait_ld();
+      tc_epilogue(d, inside, act, u);
+      issue_wait(4);
+      float y[2];
+      Tmem<2>::ld(tm, y);
+      tmem_wait_ld();
+      if (u >= kTcFirst && u < kTcFirst + kTcValid && q < N) {
+        // residual: x0 from its three bf16 terms (exact to float32)
+        const __nv_bfloat16* xr =
+            reinterpret_cast<const __nv_bfloat16*>(xbuf + (q + kLsHalo) * 16);
+        const float x_re = __bfloat162float(xr[0]) + __bfloat162float(xr[2]) + __bfloat162float(xr[4]);
+        const float x_im = __bfloat162float(xr[1]) + __bfloat162float(xr[3]) + __bfloat162float(xr[5]);
+        Hout[static_cast<size_t>(r) * N + q] = make_float2((x_re + y[0]) * rr, (x_im + y[1]) * rr);
+      }
+    }
+    // every read of the x rows and the act buffer is done before the next
+    // row's transform overwrites them
+    named_sync(1 + slot, 128);
+  }
+  tmem_fence_before();
+  __syncthreads();
+  tmem_fence_after();
+  if (warp == 0) tmem_dealloc(*tbase, 32 * kTcSlots);
+}
+
 // ------------------------------------------------------------- host side
 
 // Work buffer (floats): the tensor-core weight image [kTcImgFloats] (first,
@@ -528,6 +703,28 @@ cudaError_t dn_apply_tc(const void* params_bf16, const float2* H, int R, int N, 
   const int want = (tiles + kTcSlots - 1) / kTcSlots;
   const int grid = want < sms * 2 ? want : sms * 2;
   dn_tc_kernel<<<grid, 128 * kTcSlots, kTcSmem, st>>>(d.img, d.x0, d.rms, R, N, Hout, status);
+  return cudaGetLastError();
+}
+
+// LS estimate of every antenna row from the pilot symbol, refined on the
+// tensor cores, for N = 1024 sc16 frames (k: the plan's parameters with the
+// input set); rows = n_frames * k.M.
+cudaError_t dn_ls_tc(const KParams& k, const void* params_bf16, int n_frames, float* work,
+                     float2* Hout, int* status, int sms, cudaStream_t st) {
+  const int R = n_frames * k.M;
+  const DnWork d = dn_work(work, R, kLsN);
+  static bool attr = false;
+  if (!attr) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(dn_ls_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kLsSmem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const auto* P = static_cast<const __nv_bfloat16*>(params_bf16);
+  dn_tc_image_kernel<<<(kTcImgBytes / 2 + 255) / 256, 256, 0, st>>>(P, d.img);
+  const int want = (R + kTcSlots - 1) / kTcSlots;
+  const int grid = want < sms ? want : sms;
+  dn_ls_tc_kernel<<<grid, 128 * kTcSlots, kLsSmem, st>>>(k, d.img, R, Hout, status);
   return cudaGetLastError();
 }
 

@@ -34,6 +34,9 @@ cudaError_t launch_combine(const KParams&, cudaStream_t);
 cudaError_t launch_tcfft(const KParams&, int N, int grid, cudaStream_t);
 cudaError_t launch_yrx(const KParams&, int n_frames, cudaStream_t);
 int tc_smem_bytes(int N);
+cudaError_t dn_ls_tc(const KParams& k, const void* params_bf16, int n_frames, float* work,
+                     float2* Hout, int* status, int sms, cudaStream_t st);
+size_t dn_work_floats(int R, int N);
 cudaError_t launch_pn(const KParams&, bool fc32, int n_frames, cudaStream_t);
 cudaError_t launch_extract(const KParams&, bool fc32, int n_frames, cudaStream_t);
 cudaError_t launch_shift(void* buf, int kind, size_t rows, int N, int rowbytes, int sms,
@@ -768,6 +771,31 @@ lsas_status lsas_fft_tc_ex(lsas_plan p, const void* d_in, int n_frames, int oper
   if (launch_tcfft(k, p->N, grid, static_cast<cudaStream_t>(stream)) != cudaSuccess)
     return LSAS_ERR_CUDA;
   return LSAS_OK;
+}
+
+lsas_status lsas_run_frame_refined(lsas_plan p, const void* d_in, int n_frames,
+                                   const uint16_t* d_params_bf16, float* d_work, float* d_H,
+                                   uint8_t* d_bits, float* d_eq, int* d_status, void* stream) {
+  if (!p) return LSAS_ERR_INVALID_ARG;
+  if (p->N != 1024 || p->fmt != LSAS_IN_SC16) return LSAS_ERR_UNSUPPORTED;
+  lsas_status s = check_frames(p, n_frames);
+  if (s != LSAS_OK) return s;
+  if (n_frames == 0) return LSAS_OK;
+  if (!d_in || !d_params_bf16 || !d_work || !d_H || !d_bits || !d_status)
+    return LSAS_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(d_work) % 16 != 0 || reinterpret_cast<uintptr_t>(d_in) % 4 != 0)
+    return LSAS_ERR_INVALID_ARG;
+  if (d_eq && reinterpret_cast<uintptr_t>(d_eq) % 8 != 0) return LSAS_ERR_INVALID_ARG;
+  if (set_device(p) != LSAS_OK) return LSAS_ERR_CUDA;
+  ProfScope prof(p, "lsas_run_frame_refined", stream);
+  KParams k;
+  base_params(p, &k);
+  k.in = d_in;
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (dn_ls_tc(k, d_params_bf16, n_frames, d_work, reinterpret_cast<float2*>(d_H), d_status,
+               p->sms, st) != cudaSuccess)
+    return LSAS_ERR_CUDA;
+  return launch_frame(p, d_in, n_frames, nullptr, d_H, d_bits, d_eq, kModeDemod, st);
 }
 
 lsas_status lsas_receive_y(lsas_plan p, const float* d_Y, int n_frames, float* d_H,

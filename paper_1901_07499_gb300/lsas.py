@@ -98,6 +98,8 @@ lsas_dn_adam = _proto("lsas_dn_adam", [_vp, _vp, _vp, _vp, _i, C.c_float, _vp])
 lsas_dn_to_bf16 = _proto("lsas_dn_to_bf16", [_vp, _vp, _vp])
 lsas_dn_apply_tc = _proto("lsas_dn_apply_tc", [_vp, _vp, _i, _i, _vp, _vp, _vp, _vp])
 lsas_plan_set_fault = _proto("lsas_plan_set_fault", [_vp, _i])
+lsas_run_frame_refined = _proto("lsas_run_frame_refined",
+                                [_vp, _vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp])
 lsas_plan_set_profile = _proto("lsas_plan_set_profile", [_vp, _i])
 lsas_plan_profile = _proto("lsas_plan_profile", [_vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)])
 lsas_plan_sync = _proto("lsas_plan_sync", [_vp, _vp])
@@ -118,6 +120,7 @@ EXPORTED = ["lsas_status_str", "lsas_check_config", "lsas_frame_bytes",
             "lsas_server_frame_bytes",
             "lsas_dn_work_size", "lsas_dn_apply", "lsas_dn_grad", "lsas_dn_adam",
             "lsas_dn_to_bf16", "lsas_dn_apply_tc", "lsas_plan_set_fault",
+            "lsas_run_frame_refined",
             "lsas_plan_set_profile", "lsas_plan_profile",
             "lsas_plan_sync", "lsas_plan_info",
             "lsas_plan_destroy", "lsas_fma_peak_run"]
@@ -328,6 +331,20 @@ class Plan:
         check(lsas_demodulate(self._h, _ptr(x), _ptr(H), F, _ptr(bits), _ptr(eq),
                               _stream(stream)), "lsas_demodulate")
         return bits, eq
+
+    def run_frame_refined(self, x, params_bf16, work, status, H=None, bits=None, eq=None,
+                          want_eq=False, stream=None):
+        """lsas_run_frame_refined: LS fused with the tensor-core refinement,
+        then MRC and demap with the refined channel (N = 1024, sc16)."""
+        F = self._frames(x)
+        H = self.empty_H(F, x.device) if H is None else H
+        bits = self.empty_bits(F, x.device) if bits is None else bits
+        if eq is None and want_eq:
+            eq = self.empty_eq(F, x.device)
+        check(lsas_run_frame_refined(self._h, _ptr(x), F, _ptr(params_bf16), _ptr(work), _ptr(H),
+                                     _ptr(bits), _ptr(eq), _ptr(status), _stream(stream)),
+              "lsas_run_frame_refined")
+        return H, bits, eq
 
     def run_frame(self, x, H=None, bits=None, eq=None, want_eq=False, stream=None):
         F = self._frames(x)

@@ -14,6 +14,10 @@ reference in oracle/denoiser.py, on LS-domain rows from synth.ls_pairs.
   network trained on 49k rows, run through lsas_dn_apply_tc at SNR 0 and
   10 dB, has channel MSE below plain LS (by at least 2x) on held-out rows
   and on seeded 64-antenna frames, and no more bit errors than LS.
+* The refinement fused after LS (lsas_run_frame_refined: pilot FFT, LS and
+  normalisation feed the tensor-core network on chip) meets the same LS bar
+  and the tensor-core form's bar against the reference, and its bits equal
+  lsas_demodulate on its refined channel.
 * Secondary check: tensor-core inference (bf16 operands and activations,
   fp32 sums) against the reference with the same bf16 parameters and every ReLU output rounded
   to bf16.  The two sides round sums that differ in their last float32 bits
@@ -204,14 +208,84 @@ def test_tensor_core_refinement_beats_plain_ls(D, trained, snr):
     H_tc = trained.apply(H_ls, params_bf16=pb, tensor_cores=True)
     bits_tc, _ = plan.demodulate(x, H_tc)
     assert plan.sync_status() == L.LSAS_OK and int(trained.status().item()) == 0
+    # the same network fused after LS (the unrefined estimate stays on chip)
+    H_fu, bits_fu, _ = _refined_call(L, plan, x, pb, F * cfg.M, cfg.N)
     Htrue = np.fft.fft(b.taps, cfg.N, axis=-1) * b.gain[:, None, None]
     f_ls = np.mean(np.abs(H_ls.cpu().numpy() - Htrue) ** 2)
     f_tc = np.mean(np.abs(H_tc.cpu().numpy() - Htrue) ** 2)
     assert f_tc < 0.5 * f_ls, (f_tc, f_ls)
+    f_fu = np.mean(np.abs(H_fu.cpu().numpy() - Htrue) ** 2)
+    assert f_fu < 0.5 * f_ls, (f_fu, f_ls)
 
     def errors(bits):
         got = np.unpackbits(bits.cpu().numpy(), axis=-1, bitorder="big")[:, :cfg.D * cfg.N * cfg.q]
         return int(np.sum(got != b.bits.reshape(F, -1)))
-    e_ls, e_tc = errors(bits_ls), errors(bits_tc)
+    e_ls, e_tc, e_fu = errors(bits_ls), errors(bits_tc), errors(bits_fu)
     assert e_tc <= e_ls, (e_tc, e_ls)
+    assert e_fu <= e_ls, (e_fu, e_ls)
     plan.close()
+
+
+def _refined_call(L, plan, x, pb, R, N):
+    import torch
+    import paper_1901_07499_gb300.denoiser as D
+    dn = D.Denoiser(np.zeros(L.LSAS_DN_PARAMS, np.float32))
+    work = dn.work(R, N)
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    H, bits, eq = plan.run_frame_refined(x, pb, work, status, want_eq=True)
+    assert plan.sync_status() == L.LSAS_OK
+    assert int(status.item()) == 0
+    return H, bits, eq
+
+
+def test_fused_ls_refinement_matches_reference(D):
+    """lsas_run_frame_refined: the pilot FFT, LS and row normalisation feed
+    the tensor-core refinement on chip.  Its refined channel meets the
+    tensor-core form's bar against the FP64 reference applied to the
+    oracle's LS estimate (bf16 parameters and activations), and its bits
+    and z equal lsas_demodulate run on that refined channel."""
+    import torch
+    import paper_1901_07499_gb300.lsas as L
+    from tests.parity_util import oracle_run
+    cfg = synth.frames.sweep_config(16, 1024).replace(Q=16, F=3)
+    b = synth.generate(cfg, frame_ids=range(3))
+    plan = L.Plan(cfg.M, cfg.N, cfg.cp, cfg.S, cfg.pilot_idx, cfg.Q, fmt=cfg.fmt, max_frames=3,
+                  pilot=b.pilot)
+    p = D.init_params(3) * np.float32(4.0)
+    dn = D.Denoiser(p)
+    pb = dn.bf16_params()
+    x = _t(b.frames)
+    H, bits, eq = _refined_call(L, plan, x, pb, 3 * cfg.M, cfg.N)
+    ref = oracle_run(cfg, b)
+    want = odn.apply(_bf16_round(p), ref.H.reshape(-1, cfg.N), act=odn.bf16_round)
+    got = H.cpu().numpy().reshape(-1, cfg.N)
+    rms = np.sqrt(np.mean(np.abs(want) ** 2))
+    _check_tc(got, want, rms)
+    bits_d, eq_d = plan.demodulate(x, H, want_eq=True)
+    plan.sync()
+    assert np.array_equal(bits.cpu().numpy(), bits_d.cpu().numpy())
+    assert np.array_equal(eq.cpu().numpy().view(np.uint32), eq_d.cpu().numpy().view(np.uint32))
+
+
+def test_fused_ls_refinement_refusals(D):
+    import torch
+    import paper_1901_07499_gb300.lsas as L
+    cfg = synth.frames.sweep_config(8, 512)
+    plan = L.Plan(cfg.M, cfg.N, cfg.cp, cfg.S, cfg.pilot_idx, cfg.Q, fmt=cfg.fmt, max_frames=2)
+    x = torch.zeros((1, cfg.M, cfg.T, 2), dtype=torch.int16, device="cuda")
+    work = torch.zeros(1 << 20, dtype=torch.float32, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    H = plan.empty_H(1)
+    bits = plan.empty_bits(1)
+    pb = D.Denoiser(seed=1).bf16_params()
+    s = torch.cuda.current_stream().cuda_stream
+    call = lambda pl, xx, F, w: L.lsas_run_frame_refined(pl.handle, xx.data_ptr(), F, pb.data_ptr(),
+                                                         w, H.data_ptr(), bits.data_ptr(), None,
+                                                         st.data_ptr(), s)
+    assert call(plan, x, 1, work.data_ptr()) == L.LSAS_ERR_UNSUPPORTED     # N = 512
+    c2 = synth.frames.sweep_config(8, 1024)
+    plan2 = L.Plan(c2.M, c2.N, c2.cp, c2.S, c2.pilot_idx, c2.Q, fmt=c2.fmt, max_frames=2)
+    x2 = torch.zeros((3, c2.M, c2.T, 2), dtype=torch.int16, device="cuda")
+    assert call(plan2, x2, 3, work.data_ptr()) == L.LSAS_ERR_CAPACITY
+    assert call(plan2, x2, 1, work.data_ptr() + 4) == L.LSAS_ERR_INVALID_ARG
+    assert call(plan2, x2, 0, work.data_ptr()) == L.LSAS_OK
