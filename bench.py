@@ -525,20 +525,40 @@ def denoiser_report(args):
     import torch
     import paper_1901_07499_gb300.lsas as lsas
     import paper_1901_07499_gb300.denoiser as dnm
-    t0 = time.perf_counter()
-    losses = []
-    dn = dnm.train(rows=args.denoiser_rows, N=1024, batch=256, epochs=1, lr=1e-3, seed=1,
-                   log=lambda ep, rows, loss: losses.append(loss))
-    torch.cuda.synchronize()
-    print(json.dumps({"mode": "denoiser-train", "rows": dn.rows_seen, "steps": dn.step,
-                      "final_loss": losses[-1] if losses else None,
-                      "first_chunk_loss": losses[0] if losses else None,
-                      "seconds": time.perf_counter() - t0, "params": lsas.LSAS_DN_PARAMS,
-                      "data": "synthetic LS-domain pairs (synth.ls_pairs)"}))
-    sys.stdout.flush()
+    nets = {}
+    for form in ("fp32", "bf16-tc"):
+        t0 = time.perf_counter()
+        losses = []
+        net = dnm.train(rows=args.denoiser_rows, N=1024, batch=256, epochs=1, lr=1e-3, seed=1,
+                        log=lambda ep, rows, loss: losses.append(loss),
+                        tensor_cores=(form == "bf16-tc"))
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        # device time of one gradient + Adam step on a 256-row batch
+        Hs, Hl, _ = synth.ls_pairs(256, 1024, seed=99)
+        Ht_ = torch.from_numpy(Hs.astype(np.complex64)).cuda()
+        Hl_ = torch.from_numpy(Hl.astype(np.complex64)).cuda()
+        probe = dnm.Denoiser(seed=2)
+        probe.train_step(Hl_, Ht_, 1e-3, tensor_cores=(form == "bf16-tc"))
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e[0].record()
+        for _ in range(10):
+            probe.train_step(Hl_, Ht_, 1e-3, tensor_cores=(form == "bf16-tc"))
+        e[1].record()
+        torch.cuda.synchronize()
+        print(json.dumps({"mode": "denoiser-train", "form": form, "rows": net.rows_seen,
+                          "steps": net.step, "final_loss": losses[-1] if losses else None,
+                          "first_chunk_loss": losses[0] if losses else None,
+                          "seconds": wall, "step_ms_256_rows": e[0].elapsed_time(e[1]) / 10,
+                          "params": lsas.LSAS_DN_PARAMS,
+                          "data": "synthetic LS-domain pairs (synth.ls_pairs)"}))
+        sys.stdout.flush()
+        nets[form] = net
+    dn = nets["fp32"]
     if args.denoiser_ckpt:
         dn.save(args.denoiser_ckpt)
     pb = dn.bf16_params()
+    pb_tc = nets["bf16-tc"].bf16_params()
     F = 16
     for snr in (0.0, 5.0, 10.0, 20.0, 30.0):
         cfg = synth.frames.sweep_config(64, 1024).replace(Q=16, taps=8, decay_db=2.0, snr_db=snr, F=F,
@@ -556,6 +576,8 @@ def denoiser_report(args):
         work = dn.work(F * cfg.M, cfg.N)
         st = torch.zeros(1, dtype=torch.int32, device="cuda")
         H_fu, bits_fu, _ = plan.run_frame_refined(x, pb, work, st)
+        # the network trained in BF16 on the tensor cores, fused after LS
+        H_bt, bits_bt, _ = plan.run_frame_refined(x, pb_tc, work, st)
         plan.sync()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(8)]
         ev[0].record()
@@ -588,6 +610,7 @@ def denoiser_report(args):
         print(json.dumps({"mode": "denoiser-eval", "snr_db": snr, "frames": F, "M": cfg.M, "N": cfg.N,
                           "qam": cfg.Q, "nmse_ls": mse(H_ls), "nmse_dn": mse(H_dn),
                           "nmse_dn_tc": mse(H_tc), "nmse_fused": mse(H_fu),
+                          "nmse_bf16_trained": mse(H_bt), "ber_bf16_trained": ber(bits_bt),
                           "ber_ls": ber(bits_ls), "ber_dn": ber(bits_dn),
                           "ber_dn_tc": ber(bits_tc), "ber_fused": ber(bits_fu),
                           "refine_us_per_frame": 1e3 * ev[0].elapsed_time(ev[1]) / 5 / F,

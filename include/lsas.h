@@ -405,6 +405,21 @@ lsas_status lsas_dn_adam(float* d_params, const float* d_grad, float* d_m, float
 lsas_status lsas_dn_to_bf16(const float* d_params, uint16_t* d_params_bf16, void* stream);
 lsas_status lsas_dn_apply_tc(const uint16_t* d_params_bf16, const float* d_H, int R, int N,
                              float* d_work, float* d_Hout, int* d_status, void* stream);
+/*
+ * lsas_dn_grad in BF16 on the tensor cores: the same loss and gradient,
+ * with the fp32 parameters d_params rounded to bf16 for the pass (the
+ * caller's Adam step keeps them in fp32).  Forward: the tensor-core
+ * inference network, storing each ReLU output in bf16 as the next layer
+ * reads it.  Backward: the data gradients as tensor-core convolutions with
+ * transposed, flipped weights masked by the stored ReLU outputs (bf16), the
+ * weight gradients of the two 32 -> 32 layers as tensor-core reductions over
+ * positions, those of the two-channel layers and the biases on the CUDA
+ * cores; every sum fp32, every reduction in a fixed order.  d_status as
+ * lsas_dn_apply_tc.  Errors as lsas_dn_grad (d_work 16-byte aligned).
+ */
+lsas_status lsas_dn_grad_tc(const float* d_params, const float* d_Hls, const float* d_Htrue,
+                            int R, int N, float* d_work, float* d_grad, float* d_loss,
+                            int* d_status, void* stream);
 
 /*
  * The learned form of the receiver with the refinement fused after LS

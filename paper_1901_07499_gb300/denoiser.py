@@ -65,16 +65,26 @@ class Denoiser:
             self._work = torch.empty(n.value, dtype=torch.float32, device=self.device)
         return self._work
 
-    def compute_grad(self, Hls, Ht):
-        """Loss and gradient on rows Hls, Ht [R][N] complex64 (device)."""
+    def compute_grad(self, Hls, Ht, tensor_cores: bool = False):
+        """Loss and gradient on rows Hls, Ht [R][N] complex64 (device).
+
+        ``tensor_cores``: the BF16 pass on tcgen05 (bf16 operands and stored
+        tensors, fp32 sums; the fp32 parameters are rounded to bf16 for it);
+        otherwise the FP32 pass on the CUDA cores."""
         R, N = int(Hls.shape[0]), int(Hls.shape[1])
-        L.check(L.lsas_dn_grad(L._ptr(self.params), L._ptr(Hls), L._ptr(Ht), R, N,
-                               L._ptr(self.work(R, N)), L._ptr(self.grad), L._ptr(self.loss),
-                               L._stream(None)), "lsas_dn_grad")
+        if tensor_cores:
+            L.check(L.lsas_dn_grad_tc(L._ptr(self.params), L._ptr(Hls), L._ptr(Ht), R, N,
+                                      L._ptr(self.work(R, N)), L._ptr(self.grad),
+                                      L._ptr(self.loss), L._ptr(self.status()), L._stream(None)),
+                    "lsas_dn_grad_tc")
+        else:
+            L.check(L.lsas_dn_grad(L._ptr(self.params), L._ptr(Hls), L._ptr(Ht), R, N,
+                                   L._ptr(self.work(R, N)), L._ptr(self.grad), L._ptr(self.loss),
+                                   L._stream(None)), "lsas_dn_grad")
         return self.loss, self.grad
 
-    def train_step(self, Hls, Ht, lr: float = 1e-3):
-        self.compute_grad(Hls, Ht)
+    def train_step(self, Hls, Ht, lr: float = 1e-3, tensor_cores: bool = False):
+        self.compute_grad(Hls, Ht, tensor_cores=tensor_cores)
         self.step += 1
         L.check(L.lsas_dn_adam(L._ptr(self.params), L._ptr(self.grad), L._ptr(self.m),
                                L._ptr(self.v), self.step, lr, L._stream(None)), "lsas_dn_adam")
@@ -146,8 +156,10 @@ class Denoiser:
 
 
 def train(rows: int = 200_000, N: int = 1024, batch: int = 256, epochs: int = 1,
-          lr: float = 1e-3, seed: int = 0, chunk: int = 8192, log=None) -> Denoiser:
-    """Train on LS-domain pairs (SNR U[0, 30] dB, 4..16 taps, 1..3 dB/tap)."""
+          lr: float = 1e-3, seed: int = 0, chunk: int = 8192, log=None,
+          tensor_cores: bool = False) -> Denoiser:
+    """Train on LS-domain pairs (SNR U[0, 30] dB, 4..16 taps, 1..3 dB/tap);
+    ``tensor_cores`` runs every gradient pass in BF16 on tcgen05."""
     import torch
     import synth
     dn = Denoiser(seed=seed)
@@ -162,7 +174,8 @@ def train(rows: int = 200_000, N: int = 1024, batch: int = 256, epochs: int = 1,
             perm = torch.randperm(n, generator=torch.Generator().manual_seed(seed + ep * 7919 + c))
             for i in range(0, n - batch + 1, batch):
                 idx = perm[i:i + batch].to(dn.device)
-                loss = dn.train_step(Hl[idx].contiguous(), Ht[idx].contiguous(), lr)
+                loss = dn.train_step(Hl[idx].contiguous(), Ht[idx].contiguous(), lr,
+                                     tensor_cores=tensor_cores)
             if log is not None:
                 log(ep, done + n, float(loss.item()))
             done += n

@@ -97,6 +97,7 @@ lsas_dn_grad = _proto("lsas_dn_grad", [_vp, _vp, _vp, _i, _i, _vp, _vp, _vp, _vp
 lsas_dn_adam = _proto("lsas_dn_adam", [_vp, _vp, _vp, _vp, _i, C.c_float, _vp])
 lsas_dn_to_bf16 = _proto("lsas_dn_to_bf16", [_vp, _vp, _vp])
 lsas_dn_apply_tc = _proto("lsas_dn_apply_tc", [_vp, _vp, _i, _i, _vp, _vp, _vp, _vp])
+lsas_dn_grad_tc = _proto("lsas_dn_grad_tc", [_vp, _vp, _vp, _i, _i, _vp, _vp, _vp, _vp, _vp])
 lsas_plan_set_fault = _proto("lsas_plan_set_fault", [_vp, _i])
 lsas_run_frame_refined = _proto("lsas_run_frame_refined",
                                 [_vp, _vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp])
@@ -120,7 +121,7 @@ EXPORTED = ["lsas_status_str", "lsas_check_config", "lsas_frame_bytes",
             "lsas_server_frame_bytes",
             "lsas_dn_work_size", "lsas_dn_apply", "lsas_dn_grad", "lsas_dn_adam",
             "lsas_dn_to_bf16", "lsas_dn_apply_tc", "lsas_plan_set_fault",
-            "lsas_run_frame_refined",
+            "lsas_run_frame_refined", "lsas_dn_grad_tc",
             "lsas_plan_set_profile", "lsas_plan_profile",
             "lsas_plan_sync", "lsas_plan_info",
             "lsas_plan_destroy", "lsas_fma_peak_run"]

@@ -10,6 +10,10 @@ reference in oracle/denoiser.py, on LS-domain rows from synth.ls_pairs.
 * Training: 120 steps lower the MSE on held-out rows below that of plain LS
   (the untrained network's identity), deterministically, and a checkpoint
   round-trips exactly.
+* BF16 training on the tensor cores (lsas_dn_grad_tc): the loss and every
+  weight-gradient block match the FP64 reference of the bf16 forward within
+  the bf16 rounding of the stored data gradients, and 120 such steps beat
+  plain LS on held-out rows, deterministically.
 * The learned estimator's bar for the tensor-core form (the one timed): a
   network trained on 49k rows, run through lsas_dn_apply_tc at SNR 0 and
   10 dB, has channel MSE below plain LS (by at least 2x) on held-out rows
@@ -289,3 +293,68 @@ def test_fused_ls_refinement_refusals(D):
     assert call(plan2, x2, 3, work.data_ptr()) == L.LSAS_ERR_CAPACITY
     assert call(plan2, x2, 1, work.data_ptr() + 4) == L.LSAS_ERR_INVALID_ARG
     assert call(plan2, x2, 0, work.data_ptr()) == L.LSAS_OK
+
+
+@pytest.mark.parametrize("R,N", [(8, 256), (6, 1024)])
+def test_tensor_core_gradient_matches_reference(D, R, N):
+    """lsas_dn_grad_tc (BF16 forward and backward on tcgen05, fp32 sums)
+    against the FP64 reference run on the same bf16-rounded parameters with
+    every ReLU output rounded to bf16 (the forward the kernel runs).  The
+    kernel also rounds the data gradients g3, g2, g1 to bf16 (8 significant
+    bits, relative error <= 2^-9 per value, unbiased); summed over thousands
+    of positions that leaves each weight-gradient block within 2e-2 of the
+    block's largest entry, and the loss within 1e-3.  A wrong tap, flip,
+    channel or mask moves a block by O(1)."""
+    H, Hls, _ = synth.ls_pairs(R, N, seed=41 + N)
+    p = D.init_params(4) * np.float32(3.0)
+    dn = D.Denoiser(p)
+    loss, g = dn.compute_grad(_t(Hls.astype(np.complex64)), _t(H.astype(np.complex64)),
+                              tensor_cores=True)
+    assert int(dn.status().item()) == 0
+    pr = _bf16_round(p)
+    x0, rms = odn.prepare(Hls.astype(np.complex64))
+    t = np.stack([H.astype(np.complex64).real, H.astype(np.complex64).imag], 1) / rms[:, None, None]
+    y, cache = odn.forward(pr, x0, act=odn.bf16_round)
+    Lref, dy = odn.mse(y, t)
+    # the backward of that forward: each layer's input is its rounded ReLU
+    # output (non-negative, so the reference's max(., 0) keeps it and its
+    # mask is the rounded output's support, as the kernel's)
+    x0c, a1, a2, a3 = cache
+    rounded = (x0c,) + tuple(odn.bf16_round(np.maximum(a, 0)) for a in (a1, a2, a3))
+    gw = odn.backward(pr, rounded, dy)
+    gg = g.cpu().numpy()
+    assert abs(float(loss.item()) - Lref) <= 1e-3 * Lref, (float(loss.item()), Lref)
+    o = 0
+    errs = []
+    for s in odn.SHAPES:
+        n = int(np.prod(s))
+        blk = gw[o:o + n]
+        err = np.max(np.abs(gg[o:o + n] - blk)) / np.max(np.abs(blk))
+        errs.append(float(err))
+        assert err <= 2e-2, (s, err)
+        o += n
+    print("tensor-core gradient, block errors / block max:", ["%.2e" % e for e in errs],
+          "loss rel err %.2e" % (abs(float(loss.item()) - Lref) / Lref))
+
+
+def test_tensor_core_training_beats_plain_ls(D):
+    """120 BF16 tensor-core training steps (fp32 master weights and Adam)
+    lower the refinement's MSE on held-out rows below 0.8 x plain LS,
+    deterministically."""
+    H, Hls, _ = synth.ls_pairs(4096, 256, seed=13)
+    Hv, Hlsv, _ = synth.ls_pairs(256, 256, seed=14)
+    Ht, Hl = _t(H.astype(np.complex64)), _t(Hls.astype(np.complex64))
+    runs = []
+    for _ in range(2):
+        dn = D.Denoiser(seed=5)
+        for i in range(120):
+            j = (i * 64) % 4096
+            dn.train_step(Hl[j:j + 64].contiguous(), Ht[j:j + 64].contiguous(), lr=2e-3,
+                          tensor_cores=True)
+        assert int(dn.status().item()) == 0
+        runs.append(dn.params.cpu().numpy())
+    assert np.array_equal(runs[0], runs[1])     # deterministic
+    out = dn.apply(_t(Hlsv.astype(np.complex64)), tensor_cores=True).cpu().numpy()
+    mse_ls = np.mean(np.abs(Hlsv - Hv) ** 2)
+    mse_dn = np.mean(np.abs(out - Hv) ** 2)
+    assert mse_dn < 0.8 * mse_ls, (mse_dn, mse_ls)
