@@ -301,9 +301,10 @@ def test_tensor_core_gradient_matches_reference(D, R, N):
     against the FP64 reference run on the same bf16-rounded parameters with
     every ReLU output rounded to bf16 (the forward the kernel runs).  The
     kernel also rounds the data gradients g3, g2, g1 to bf16 (8 significant
-    bits, relative error <= 2^-9 per value, unbiased); summed over thousands
-    of positions that leaves each weight-gradient block within 2e-2 of the
-    block's largest entry, and the loss within 1e-3.  A wrong tap, flip,
+    bits, relative error <= 2^-9 = 2e-3 per value, unbiased); summed over
+    thousands of positions the errors average out, and each weight-gradient
+    block stays within 2e-3 of the block's largest entry (measured: at most
+    3.2e-4), the loss within 1e-4 (measured 2e-6).  A wrong tap, flip,
     channel or mask moves a block by O(1)."""
     H, Hls, _ = synth.ls_pairs(R, N, seed=41 + N)
     p = D.init_params(4) * np.float32(3.0)
@@ -323,7 +324,7 @@ def test_tensor_core_gradient_matches_reference(D, R, N):
     rounded = (x0c,) + tuple(odn.bf16_round(np.maximum(a, 0)) for a in (a1, a2, a3))
     gw = odn.backward(pr, rounded, dy)
     gg = g.cpu().numpy()
-    assert abs(float(loss.item()) - Lref) <= 1e-3 * Lref, (float(loss.item()), Lref)
+    assert abs(float(loss.item()) - Lref) <= 1e-4 * Lref, (float(loss.item()), Lref)
     o = 0
     errs = []
     for s in odn.SHAPES:
@@ -331,7 +332,7 @@ def test_tensor_core_gradient_matches_reference(D, R, N):
         blk = gw[o:o + n]
         err = np.max(np.abs(gg[o:o + n] - blk)) / np.max(np.abs(blk))
         errs.append(float(err))
-        assert err <= 2e-2, (s, err)
+        assert err <= 2e-3, (s, err)
         o += n
     print("tensor-core gradient, block errors / block max:", ["%.2e" % e for e in errs],
           "loss rel err %.2e" % (abs(float(loss.item()) - Lref) / Lref))
