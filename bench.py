@@ -38,7 +38,7 @@ import synth  # noqa: E402
 
 FALLBACK_HBM_GBS = 6800.0
 KERNEL_SRC = [os.path.join(ROOT, "paper_1901_07499_gb300", "csrc", n)
-              for n in ("lsas_kernels.cuh", "lsas_warp.cuh", "lsas_hyb.cuh")]
+              for n in ("lsas_kernels.cuh", "lsas_warp.cuh", "lsas_hyb.cuh", "lsas_pair.cuh")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fused_kernel_traffic.json")
 
 
@@ -337,6 +337,8 @@ def fused_kernel_name(cfg):
                 "CUDA cores, second on tcgen05)")
     if cfg.N <= 1024:
         return "warp_kernel (fused CP strip+FFT+LS+MRC+demap, per-warp pipelines)"
+    if cfg.fmt == "sc16":
+        return "pair_kernel (fused CP strip+FFT+LS+MRC+demap, pipelines of warp pairs)"
     return "frame_kernel (fused CP strip+FFT+LS+MRC+demap)"
 
 

@@ -146,6 +146,16 @@ lsas_status lsas_demodulate(lsas_plan plan, const void* d_in,
 /*
  * The whole receiver in one fused pass per frame: estimation (writes d_H)
  * then demodulation (writes d_bits and optionally d_eq).  Asynchronous.
+ * Whole waves of frames (one frame per SM) run in one launch.  The frames
+ * after the last whole wave, or all of them for a batch smaller than one
+ * wave, may run split into equal antenna shards so that they occupy more
+ * SMs: the shards' MRC partial sums go to a scratch array the plan owns
+ * (lsas_plan_create reserves at most 64 MiB for it), and the combine pass
+ * forms z and the bits from them, summing the shards in a fixed order.
+ * Outputs agree with the unsplit pass to rounding (the antenna sums are
+ * ordered differently).  Calls on one plan from several streams take turns
+ * on the scratch array: a split waits for the previous split's combine.
+ * lsas_plan_set_batch_split turns the split off.
  */
 lsas_status lsas_run_frame(lsas_plan plan, const void* d_in, int n_frames,
                            float* d_H, uint8_t* d_bits, float* d_eq,
@@ -446,10 +456,27 @@ lsas_status lsas_run_frame_refined(lsas_plan plan, const void* d_in, int n_frame
  * copies, skips its remaining waits and finishes.  kind = 1 makes that
  * happen without any fault: block 0's first staging phase also waits for 16
  * bytes that no copy delivers.  kind = 0 (the default) turns it off.
- * Applies to both fused kernels: the per-warp kernel (N <= 1024) and the
- * warp-specialised kernel (N = 2048).  INVALID_ARG for other kinds.
+ * Applies to every fused kernel: the per-warp kernel (N <= 1024), the
+ * warp-pair kernel (N = 2048, sc16 input) and the warp-specialised kernel
+ * (N = 2048, fc32 input).  INVALID_ARG for other kinds.
  */
 lsas_status lsas_plan_set_fault(lsas_plan plan, int kind);
+
+/*
+ * enable = 1 (the default): lsas_run_frame may split the frames after a
+ * batch's last whole wave into antenna shards (see lsas_run_frame); 0: every
+ * frame runs unsplit.  INVALID_ARG for other values.  Takes effect from the
+ * next call.
+ */
+lsas_status lsas_plan_set_batch_split(lsas_plan plan, int enable);
+
+/*
+ * The antenna shards lsas_run_frame would use for the frames after the last
+ * whole wave of an n_frames batch (1: no split), into *out_shards.  The
+ * choice depends on the plan's shape, the SM count and the batch split
+ * setting only.  INVALID_ARG for null pointers or n_frames < 0.
+ */
+lsas_status lsas_plan_batch_split_shards(lsas_plan plan, int n_frames, int* out_shards);
 
 /*
  * Size of the library's fixed device scratch used by

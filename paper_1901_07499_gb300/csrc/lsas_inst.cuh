@@ -4,6 +4,7 @@
 #include "lsas_kernels.cuh"
 #include "lsas_warp.cuh"
 #include "lsas_hyb.cuh"
+#include "lsas_pair.cuh"
 
 namespace lsas {
 
@@ -14,8 +15,9 @@ static cudaError_t launch_t(int kind, const KParams& p, int grid, int smem, cuda
   int slot = kind;   // entry of the shared-memory attribute cache below
   if (kind == kKindFrame) {
     // fused receiver: N = 1024 from aligned sc16 rows with the second FFT
-    // pass on the tensor cores; otherwise per-warp pipelines up to N = 1024
-    // and the warp-specialised producer/consumer kernel for N = 2048
+    // pass on the tensor cores; otherwise per-warp pipelines up to N = 1024,
+    // pipelines of warp pairs for N = 2048 from sc16 rows and the
+    // warp-specialised producer/consumer kernel for N = 2048 from fc32 rows
     if constexpr (LOG2N == 10 && !FC32) {
       if (p.hybrid && p.use_tma) {
         fn = hyb_kernel<false>;
@@ -29,6 +31,9 @@ static cudaError_t launch_t(int kind, const KParams& p, int grid, int smem, cuda
     } else if constexpr (LOG2N <= 10) {
       fn = warp_kernel<LOG2N, FC32>;
       threads = 32 * wgeo_warps(FC32 ? 8 : 4);
+    } else if constexpr (!FC32) {
+      fn = pair_kernel<LOG2N>;
+      threads = kPThreads;
     } else {
       fn = frame_kernel<LOG2N, FC32>;
       threads = Geo<LOG2N>::T;

@@ -204,10 +204,11 @@ __host__ __device__ constexpr int wgeo_spad(int N, int bps) {
   return bps == 4 ? (N / 32 >= 4 ? N / 32 : 4) : (N / 32 >= 4 ? N / 64 : 2);
 }
 
-// Shared memory of the warp kernel: header, last-pass twiddles, 1/E per
-// subcarrier, the demapped codes of one group, then one region per warp
-// (staging ring + exchange).  At group ends the per-warp regions together
-// hold the warps' partial sums for the cross-warp reduction.
+// Shared memory of the warp kernel: header, last-pass twiddles (each as the
+// pair {w, -j w} for the packed multiply), 1/E per subcarrier, the demapped
+// codes of one group, then one region per warp (staging ring + exchange).
+// At group ends the per-warp regions together hold the warps' partial sums
+// for the cross-warp reduction.
 struct WLayout {
   int tw_off, ie_off, codes_off, warp_off;
   int team_stage;    // bytes per antenna row in a slot
@@ -219,7 +220,7 @@ __host__ __device__ inline WLayout make_wlayout(int N, int bps, int nslots, int 
   const int warps = wgeo_warps(bps);
   WLayout l;
   l.tw_off = kWHeader;
-  l.ie_off = l.tw_off + N * 8;
+  l.ie_off = l.tw_off + N * 16;
   l.codes_off = l.ie_off + N * 4;
   l.warp_off = align_up(l.codes_off + dg * N, 128);
   l.team_stage = (N + wgeo_spad(N, bps)) * bps;
@@ -501,13 +502,12 @@ __host__ __device__ constexpr int brev(int i, int bits) {
   return r;
 }
 
-// b * W_32^e for a compile-time e in [0, 16)
+// b * W_32^e for a compile-time e in [0, 16): free for e = 0 and -j, two
+// packed instructions otherwise (W_8 included: a sum and a difference
+// before one packed product would take three)
 __device__ __forceinline__ float2 tw32(float2 b, int e, const KParams& p) {
-  constexpr float kS = 0.70710678118654752440f;  // 1/sqrt(2)
   if (e == 0) return b;
   if (e == 8) return make_float2(b.y, -b.x);                                     // -j
-  if (e == 4) return __fmul2_rn(make_float2(b.x + b.y, b.y - b.x), make_float2(kS, kS));
-  if (e == 12) return __fmul2_rn(make_float2(b.y - b.x, -(b.x + b.y)), make_float2(kS, kS));
   return cmulw(b, p.w32[e], p.w32n[e]);
 }
 

@@ -7,6 +7,7 @@
 // conj(X)/|X|^2/sqrt(N) (Sec. II-C: LS is a division by the pilot), and a
 // status word the kernels latch device-side conditions into.  Every argument
 // is checked here before anything is enqueued.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -22,6 +23,7 @@
 #include "lsas.h"
 #include "lsas_kernels.cuh"
 #include "lsas_hyb.cuh"
+#include "lsas_pair.cuh"
 
 namespace lsas {
 cudaError_t launch_n64(int, bool, const KParams&, int, int, cudaStream_t);
@@ -51,6 +53,10 @@ using namespace lsas;
 namespace {
 
 constexpr int kSmemLimit = 232448;   // opt-in dynamic shared memory per block
+constexpr size_t kTailBytes = 64u << 20;   // cap of a plan's split-tail partial sums
+// Share of a fused block's time that does not shrink with its antenna count
+// (the group-end reductions, demap and pack), for the split decision.
+constexpr double kBlockFixed = 0.08;
 constexpr int kHostChunk = 64;       // frames per transfer chunk (host path)
 constexpr int kMaxPnLen = 1024;      // longest PN sequence lsas_plan_set_pn takes
 
@@ -87,6 +93,15 @@ struct lsas_plan_s {
   int fault = 0;   // test hook of the bounded waits (lsas_plan_set_fault)
   bool allow_hybrid = false;   // LSAS_FUSED_KERNEL = "tensor" at creation
   void* d_split_scratch = nullptr;   // device address of g_split_scratch on this device
+  // lsas_run_frame: the frames after a batch's last whole wave of blocks (all
+  // of them, for a batch smaller than one wave) may run split into equal
+  // antenna shards so that they fill the GPU; their partial sums live here,
+  // P [G][frames][D][N] complex then E [G][frames][N]
+  float* d_tail = nullptr;
+  int tail_units = 0;               // shard-frames d_tail holds
+  bool batch_split = true;          // lsas_plan_set_batch_split
+  cudaEvent_t tail_ev = nullptr;    // the last split's combine has read d_tail
+  std::mutex tail_mu;
   Geometry geo;
   LaunchFn launch = nullptr;
   // host-transfer staging (lsas_run_frame_host), allocated on first use
@@ -268,6 +283,29 @@ bool plan_geometry(int M, int N, int D, lsas_input_fmt fmt, bool allow_hybrid, G
       }
     }
     if (!found) return false;
+  } else if (fmt == LSAS_IN_SC16) {
+    // N = 2048 from sc16 rows: pipelines of warp pairs, the same bounds
+    // (TMEM per warp, the deepest ring that fits)
+    found = false;
+    const int dgmax = pgeo_dg_max();
+    for (int groups = (D + dgmax - 1) / dgmax; groups <= D && !found; ++groups) {
+      const int dg = (D + groups - 1) / groups;
+      for (int slots = kMaxSlots; slots >= 2; --slots) {
+        const PLayout l = make_playout(slots, dg);
+        if (l.total > kSmemLimit || l.pair_bytes < N * 8) continue;
+        g->groups = groups;
+        g->dg = dg;
+        g->nslots = slots;
+        g->smem_frame = l.total;
+        g->T = kPThreads;
+        g->Af = 1;
+        g->tmem_cols = kWTmemCols;
+        g->tmem_cth = kPTmemWarp;
+        found = true;
+        break;
+      }
+    }
+    if (!found) return false;
   }
   g->hybrid = 0;
   if (allow_hybrid && N == 1024 && fmt == LSAS_IN_SC16) {
@@ -409,6 +447,77 @@ lsas_status launch_frame(lsas_plan p, const void* d_in, int n_frames, float* d_H
       cudaSuccess)
     return LSAS_ERR_CUDA;
   return LSAS_OK;
+}
+
+// Antenna shards G for nf frames that do not fill a whole wave of blocks
+// (one block per SM): the split runs nf * G blocks of M / G antennas each,
+// ceil(nf G / sms) waves of about (1 - f) / G + f of a frame's block time
+// (f = kBlockFixed), against one wave unsplit.  Equal shards only (one
+// launch), each with at least one antenna per pipeline of the fused kernel;
+// 1 when no split saves 10 % of the wave.
+int tail_shards(lsas_plan p, int nf) {
+  if (nf <= 0 || !p->batch_split || p->tail_units == 0 || p->geo.hybrid) return 1;
+  const int pipes = p->N <= 1024 ? wgeo_warps(p->fmt == LSAS_IN_SC16 ? 4 : 8)
+                                  : (p->fmt == LSAS_IN_SC16 ? kPPairs : 1);
+  const int min_ant = pipes * p->geo.Af;
+  double best = 0.9;
+  int bestG = 1;
+  for (int G = 2; G <= 32; G *= 2) {
+    if (p->M % G != 0 || p->M / G < min_ant) continue;
+    if (static_cast<long>(nf) * G > p->tail_units) continue;
+    const double waves = std::ceil(static_cast<double>(nf) * G / p->sms);
+    const double t = waves * ((1.0 - kBlockFixed) / G + kBlockFixed);
+    if (t < best) {
+      best = t;
+      bestG = G;
+    }
+  }
+  return bestG;
+}
+
+// Frames [f0, f0 + nf) of a lsas_run_frame batch as G antenna shards: the
+// fused kernel's partial mode writes the shards' partial sums and H, the
+// combine kernel forms z and the bits.  Calls on different streams share
+// d_tail: each waits for the previous split's combine.
+lsas_status run_split_tail(lsas_plan p, const void* d_in, int f0, int nf, int G, float* d_H,
+                           uint8_t* d_bits, float* d_eq, cudaStream_t st) {
+  const size_t in_b = in_bytes_per_frame(p->M, p->N, p->cp, p->S, p->fmt);
+  const size_t bits_b = bits_bytes_per_frame(p->N, p->S, p->Q);
+  const unsigned char* in = static_cast<const unsigned char*>(d_in) + f0 * in_b;
+  float* P = p->d_tail;
+  float* E = P + static_cast<size_t>(G) * nf * p->D * p->N * 2;
+  std::lock_guard<std::mutex> lock(p->tail_mu);
+  if (cudaStreamWaitEvent(st, p->tail_ev, 0) != cudaSuccess) return LSAS_ERR_CUDA;
+  KParams k;
+  base_params(p, &k);
+  k.in = in;
+  k.H_out = reinterpret_cast<float2*>(d_H + static_cast<size_t>(f0) * p->M * p->N * 2);
+  k.P_out = reinterpret_cast<float2*>(P);
+  k.E_out = E;
+  k.M = p->M / G;
+  k.shard_y = k.M;
+  k.grid_y = G;
+  k.group_z = 0;
+  k.chunks = (k.M + p->geo.Af - 1) / p->geo.Af;
+  k.mode = kModePartial;
+  k.use_tma = tma_ok(p, in) ? 1 : 0;
+  lsas_status s = LSAS_OK;
+  if (p->launch(kKindFrame, p->fmt == LSAS_IN_FC32, k, nf, p->geo.smem_frame, st) != cudaSuccess) {
+    s = LSAS_ERR_CUDA;
+  } else {
+    KParams c;
+    base_params(p, &c);
+    c.P_in = reinterpret_cast<const float2*>(P);
+    c.E_in = E;
+    c.shards = G;
+    c.nframes = nf;
+    c.bits = d_bits + f0 * bits_b;
+    c.eq = d_eq ? reinterpret_cast<float2*>(d_eq + static_cast<size_t>(f0) * p->D * p->N * 2)
+                : nullptr;
+    if (launch_combine(c, st) != cudaSuccess) s = LSAS_ERR_CUDA;
+  }
+  if (cudaEventRecord(p->tail_ev, st) != cudaSuccess) s = LSAS_ERR_CUDA;
+  return s;
 }
 
 }  // namespace
@@ -553,6 +662,21 @@ lsas_status lsas_plan_create(int M, int N, int cp_len, int n_sym, int pilot_idx,
     lsas_plan_destroy(p);
     return LSAS_ERR_CUDA;
   }
+  {
+    // partial sums of split tails (lsas_run_frame): up to two waves of
+    // shard-frames, within kTailBytes; without them every batch runs unsplit
+    const size_t unit = (static_cast<size_t>(p->D) * N * 2 + N) * sizeof(float);
+    const size_t units = std::min(static_cast<size_t>(2 * p->sms), kTailBytes / unit);
+    if (units >= 2 && cudaMalloc(&p->d_tail, units * unit) == cudaSuccess &&
+        cudaEventCreateWithFlags(&p->tail_ev, cudaEventDisableTiming) == cudaSuccess) {
+      p->tail_units = static_cast<int>(units);
+    } else {
+      cudaGetLastError();
+      cudaFree(p->d_tail);
+      p->d_tail = nullptr;
+      p->tail_units = 0;
+    }
+  }
   // address of the static split scratch on this device (the device is
   // current here); lsas_run_frame_split_static never looks it up itself
   if (cudaGetSymbolAddress(&p->d_split_scratch, g_split_scratch) != cudaSuccess) {
@@ -677,8 +801,17 @@ lsas_status lsas_run_frame(lsas_plan p, const void* d_in, int n_frames, float* d
   if (!d_in || !d_H || !d_bits) return LSAS_ERR_INVALID_ARG;
   if (set_device(p) != LSAS_OK) return LSAS_ERR_CUDA;
   ProfScope prof(p, "lsas_run_frame", stream);
-  return launch_frame(p, d_in, n_frames, d_H, nullptr, d_bits, d_eq, kModeRun,
-                      static_cast<cudaStream_t>(stream));
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // whole waves of blocks run one frame per block; the frames after them may
+  // run split into antenna shards (tail_shards)
+  const int full = (n_frames / p->sms) * p->sms;
+  const int G = tail_shards(p, n_frames - full);
+  if (G == 1) return launch_frame(p, d_in, n_frames, d_H, nullptr, d_bits, d_eq, kModeRun, st);
+  if (full > 0) {
+    s = launch_frame(p, d_in, full, d_H, nullptr, d_bits, d_eq, kModeRun, st);
+    if (s != LSAS_OK) return s;
+  }
+  return run_split_tail(p, d_in, full, n_frames - full, G, d_H, d_bits, d_eq, st);
 }
 
 lsas_status lsas_mrc_partial(lsas_plan p, const void* d_in, int n_frames, int m_begin,
@@ -911,6 +1044,18 @@ lsas_status lsas_plan_set_fault(lsas_plan p, int kind) {
   return LSAS_OK;
 }
 
+lsas_status lsas_plan_set_batch_split(lsas_plan p, int enable) {
+  if (!p || enable < 0 || enable > 1) return LSAS_ERR_INVALID_ARG;
+  p->batch_split = enable != 0;
+  return LSAS_OK;
+}
+
+lsas_status lsas_plan_batch_split_shards(lsas_plan p, int n_frames, int* out_shards) {
+  if (!p || !out_shards || n_frames < 0) return LSAS_ERR_INVALID_ARG;
+  *out_shards = tail_shards(p, n_frames - (n_frames / p->sms) * p->sms);
+  return LSAS_OK;
+}
+
 lsas_status lsas_run_frame_host(lsas_plan p, const void* h_in, int n_frames, float* h_H,
                                 uint8_t* h_bits, float* h_eq, void* stream) {
   if (!p) return LSAS_ERR_INVALID_ARG;
@@ -1084,6 +1229,8 @@ lsas_status lsas_plan_destroy(lsas_plan p) {
   cudaFree(p->d_tc_w2);
   cudaFree(p->d_tc_tw);
   cudaFree(p->d_pn);
+  cudaFree(p->d_tail);
+  if (p->tail_ev) cudaEventDestroy(p->tail_ev);
   for (int i = 0; i < 2; ++i) {
     cudaFree(p->d_in_stage[i]);
     cudaFree(p->d_H_stage[i]);
@@ -1142,7 +1289,8 @@ lsas_status lsas_run_frame_split_static(lsas_plan p, const void* d_in, int n_fra
     k.grid_y = n_shards;
     // small batches: one block per data-symbol group as well (each repeats
     // the pilot transform), so a frame's groups also run side by side
-    k.group_z = (p->N <= 1024 && p->geo.groups > 1 && n_frames * n_shards * 2 <= p->sms) ? 1 : 0;
+    k.group_z = ((p->N <= 1024 || p->fmt == LSAS_IN_SC16) && p->geo.groups > 1 &&
+                 n_frames * n_shards * 2 <= p->sms) ? 1 : 0;
     k.chunks = (k.M + p->geo.Af - 1) / p->geo.Af;
     k.mode = kModePartial;
     k.use_tma = tma_ok(p, d_in) ? 1 : 0;

@@ -53,6 +53,28 @@ __device__ __forceinline__ int witem_symbol(const KParams& p, bool pilot_here, i
   return d < p.pilot_idx ? d : d + 1;
 }
 
+// Load the inputs of the last FFT pass times its twiddles, held in shared
+// memory as {w, -j w} pairs (two packed instructions per product).
+template <int LOG2N>
+__device__ __forceinline__ void wfinal_exchange_read(float2 (&v)[32], const float2* ex, int jt,
+                                                     const float4* tw) {
+  constexpr int L = (1 << LOG2N) / 32;
+#pragma unroll
+  for (int i = 0; i < 32 / L; ++i) {
+    const int j = jt + i * L;
+#pragma unroll
+    for (int r = 0; r < L; ++r) {
+      const float2 u = ex[xpad(j + 32 * r)];
+      if (r == 0) {
+        v[i * L + r] = u;
+      } else {
+        const float4 t = tw[r * 32 + j];
+        v[i * L + r] = cmulw(u, make_float2(t.x, t.y), make_float2(t.z, t.w));
+      }
+    }
+  }
+}
+
 template <int LOG2N, bool FC32>
 __global__ void __launch_bounds__(32 * wgeo_warps(FC32 ? 8 : 4), 1) warp_kernel(const KParams p) {
   constexpr int N = 1 << LOG2N;
@@ -75,14 +97,17 @@ __global__ void __launch_bounds__(32 * wgeo_warps(FC32 ? 8 : 4), 1) warp_kernel(
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem) + warp * kMaxSlots;
   uint32_t* tmem_base = reinterpret_cast<uint32_t*>(smem + kWTmemAddr);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + kWAbort);
-  float2* tws = reinterpret_cast<float2*>(smem + lay.tw_off);
+  float4* tws = reinterpret_cast<float4*>(smem + lay.tw_off);
   float* ie_s = reinterpret_cast<float*>(smem + lay.ie_off);
   uint8_t* codes = smem + lay.codes_off;
   unsigned char* stage = smem + lay.warp_off + warp * lay.warp_bytes;
   float2* ex = reinterpret_cast<float2*>(stage + lay.stage_bytes) + alpha * XS;
   const int slot_bytes = A * lay.team_stage;
 
-  for (int i = tid; i < N; i += NT) tws[i] = __ldg(p.twP + i);
+  for (int i = tid; i < N; i += NT) {
+    const float2 w = __ldg(p.twP + i);
+    tws[i] = make_float4(w.x, w.y, -w.y, w.x);
+  }
   if (tid == 0) *abort_flag = 0;
   if (lane == 0 && p.use_tma) {
     for (int s = 0; s < K; ++s) mbar_init(smem_u32(&bars[s]), 1);
@@ -225,7 +250,7 @@ __global__ void __launch_bounds__(32 * wgeo_warps(FC32 ? 8 : 4), 1) warp_kernel(
         dft<32>(v, p);
         final_exchange_write<LOG2N>(v, ex, jt);
         __syncwarp();
-        final_exchange_read<LOG2N>(v, ex, jt, tws);
+        wfinal_exchange_read<LOG2N>(v, ex, jt, tws);
         final_dft<LOG2N>(v, p);
         if (pilot_here && it == 0) {
           // LS estimate H = Y conj(X) / |X|^2 (1/sqrt(N) folded into xinv)

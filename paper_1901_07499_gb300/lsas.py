@@ -99,6 +99,8 @@ lsas_dn_to_bf16 = _proto("lsas_dn_to_bf16", [_vp, _vp, _vp])
 lsas_dn_apply_tc = _proto("lsas_dn_apply_tc", [_vp, _vp, _i, _i, _vp, _vp, _vp, _vp])
 lsas_dn_grad_tc = _proto("lsas_dn_grad_tc", [_vp, _vp, _vp, _i, _i, _vp, _vp, _vp, _vp, _vp])
 lsas_plan_set_fault = _proto("lsas_plan_set_fault", [_vp, _i])
+lsas_plan_set_batch_split = _proto("lsas_plan_set_batch_split", [_vp, _i])
+lsas_plan_batch_split_shards = _proto("lsas_plan_batch_split_shards", [_vp, _i, C.POINTER(_i)])
 lsas_run_frame_refined = _proto("lsas_run_frame_refined",
                                 [_vp, _vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp])
 lsas_plan_set_profile = _proto("lsas_plan_set_profile", [_vp, _i])
@@ -121,6 +123,7 @@ EXPORTED = ["lsas_status_str", "lsas_check_config", "lsas_frame_bytes",
             "lsas_server_frame_bytes",
             "lsas_dn_work_size", "lsas_dn_apply", "lsas_dn_grad", "lsas_dn_adam",
             "lsas_dn_to_bf16", "lsas_dn_apply_tc", "lsas_plan_set_fault",
+            "lsas_plan_set_batch_split", "lsas_plan_batch_split_shards",
             "lsas_run_frame_refined", "lsas_dn_grad_tc",
             "lsas_plan_set_profile", "lsas_plan_profile",
             "lsas_plan_sync", "lsas_plan_info",
@@ -217,6 +220,19 @@ class Plan:
         keys = ["antennas_per_step", "threads", "smem_bytes", "groups", "slots",
                 "tma", "fmt", "max_frames"]
         return dict(zip(keys, list(out)))
+
+    def set_batch_split(self, enable: bool) -> None:
+        """lsas_plan_set_batch_split: whether lsas_run_frame may split the
+        frames after a batch's last whole wave into antenna shards."""
+        check(lsas_plan_set_batch_split(self._h, 1 if enable else 0), "lsas_plan_set_batch_split")
+
+    def batch_split_shards(self, n_frames: int) -> int:
+        """lsas_plan_batch_split_shards: the antenna shards lsas_run_frame
+        would use for the frames after the last whole wave (1: none)."""
+        out = _i(0)
+        check(lsas_plan_batch_split_shards(self._h, int(n_frames), C.byref(out)),
+              "lsas_plan_batch_split_shards")
+        return int(out.value)
 
     @property
     def handle(self):
@@ -548,6 +564,19 @@ class Server:
         check(lsas_server_stats(self._h, out), "lsas_server_stats")
         return dict(launches=int(out[0]), frames=int(out[1]), admitted_bytes=int(out[2]),
                     configs=int(out[3]))
+
+    def set_batch_split(self, enable: bool) -> None:
+        """lsas_plan_set_batch_split: whether lsas_run_frame may split the
+        frames after a batch's last whole wave into antenna shards."""
+        check(lsas_plan_set_batch_split(self._h, 1 if enable else 0), "lsas_plan_set_batch_split")
+
+    def batch_split_shards(self, n_frames: int) -> int:
+        """lsas_plan_batch_split_shards: the antenna shards lsas_run_frame
+        would use for the frames after the last whole wave (1: none)."""
+        out = _i(0)
+        check(lsas_plan_batch_split_shards(self._h, int(n_frames), C.byref(out)),
+              "lsas_plan_batch_split_shards")
+        return int(out.value)
 
     @property
     def handle(self):

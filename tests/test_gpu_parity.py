@@ -16,6 +16,7 @@ resident, and from pinned host memory as the end-to-end leg runs it).
 import numpy as np
 import pytest
 
+import oracle
 import synth
 from synth.frames import FrameConfig, sweep_config, paper_config
 from tests.parity_util import (check_frame_outputs, oracle_run, rel_err,
@@ -78,6 +79,40 @@ def test_odd_antenna_counts(L, M, N):
     run_and_check(L, sweep_config(M, N).replace(M=M), F=3)
 
 
+@pytest.mark.parametrize("M", [2, 3, 5, 13])
+def test_odd_antenna_counts_n2048(L, M):
+    """N = 2048 from sc16 rows runs four warp pairs per frame, antenna m on
+    pair m mod 4: fewer antennas than pairs, and a last round that leaves
+    some pairs idle."""
+    run_and_check(L, sweep_config(16, 2048).replace(M=M), F=2)
+
+
+def test_single_antenna_n2048(L):
+    """M = 1: MRC is single-antenna zero forcing, z = Y / H.  Near a deep fade
+    (the seeded channel has a subcarrier at 5e-5 of the mean power) the
+    float32 error of Y and H is divided by |H_k|, so the plain 1e-4 bar on z
+    does not follow from the arithmetic there.  H keeps the 1e-4 bar; z is
+    held to the error that the 1e-4 bars on Y and H imply through z = Y / H:
+    |dz_k| <= 1e-4 (rms(Y) + |z_k| rms(H)) / |H_k|; bits as everywhere."""
+    import torch
+    cfg = sweep_config(16, 2048).replace(M=1)
+    b = synth.generate(cfg, frame_ids=range(2))
+    plan = make_plan(L, cfg)
+    H, bits, eq = plan.run_frame(to_torch_frames(b), want_eq=True)
+    plan.sync()
+    ref = oracle_run(cfg, b, keep_Y=True)
+    check_frame_outputs(cfg, ref, H.cpu().numpy(), bits.cpu().numpy(), None)
+    z = eq.cpu().numpy()
+    rmsY = np.sqrt(np.mean(np.abs(ref.Y) ** 2, axis=(1, 2, 3)))[:, None, None]
+    rmsH = np.sqrt(np.mean(np.abs(ref.H) ** 2, axis=(1, 2)))[:, None, None]
+    Hk = np.abs(ref.H[:, 0, :])[:, None, :]
+    bound = TOL_REL * (rmsY + np.abs(ref.z) * rmsH) / Hk
+    assert np.all(np.abs(z - ref.z) <= bound)
+    same_prec, _ = oracle.demap(z.astype(np.complex64), cfg.Q, dtype=np.float32)
+    q = int(round(np.log2(cfg.Q)))
+    assert np.array_equal(same_prec, unpack(bits.cpu().numpy(), cfg.D, cfg.N, q))
+
+
 @pytest.mark.parametrize("M,N", [(16, 64), (16, 1024), (5, 1024)])
 def test_paper_shapes(L, M, N):
     run_and_check(L, paper_config(M, N, F=2))
@@ -95,7 +130,7 @@ def test_fewest_symbols(L, N, S):
     run_and_check(L, sweep_config(16, N).replace(S=S), F=3)
 
 
-@pytest.mark.parametrize("N", [64, 1024])
+@pytest.mark.parametrize("N", [64, 1024, 2048])
 def test_longest_cyclic_prefix(L, N):
     """CP = N - 1, the largest the interface takes (rows no longer 16-byte
     aligned: the plain-load path)."""
@@ -105,6 +140,11 @@ def test_longest_cyclic_prefix(L, N):
 @pytest.mark.parametrize("pilot_idx", [1, 6, 13])
 def test_pilot_not_first(L, pilot_idx):
     run_and_check(L, sweep_config(24, 512).replace(pilot_idx=pilot_idx), F=2)
+
+
+@pytest.mark.parametrize("pilot_idx", [4, 13])
+def test_pilot_not_first_n2048(L, pilot_idx):
+    run_and_check(L, sweep_config(12, 2048).replace(pilot_idx=pilot_idx), F=2)
 
 
 @pytest.mark.parametrize("Q", [2, 4, 64, 256])
@@ -255,6 +295,68 @@ def test_deterministic(L):
     r2 = plan.run_frame(x, want_eq=True)
     plan.sync()
     assert all(torch.equal(a, c) for a, c in zip(r1, r2))
+
+
+# ---------------------------------------------------- batch split ----
+
+@pytest.mark.parametrize("name,F", [("scale", 3), ("precision", 2)])
+def test_batch_split_small_batch(L, name, F):
+    """A batch smaller than one wave runs split into antenna shards (partial
+    sums, then the combine pass): split and unsplit both meet the oracle
+    bars, and H is the same bytes (each antenna's LS is the same
+    arithmetic either way)."""
+    import torch
+    cfg = synth.CONFIGS[name]
+    b = synth.generate(cfg, frame_ids=range(F))
+    plan = make_plan(L, cfg, max_frames=8)
+    assert plan.batch_split_shards(F) > 1
+    x = to_torch_frames(b)
+    ref = oracle_run(cfg, b)
+    H1, bits1, eq1 = plan.run_frame(x, want_eq=True)
+    plan.sync()
+    check_frame_outputs(cfg, ref, H1.cpu().numpy(), bits1.cpu().numpy(), eq1.cpu().numpy())
+    plan.set_batch_split(False)
+    assert plan.batch_split_shards(F) == 1
+    H0, bits0, eq0 = plan.run_frame(x, want_eq=True)
+    plan.sync()
+    check_frame_outputs(cfg, ref, H0.cpu().numpy(), bits0.cpu().numpy(), eq0.cpu().numpy())
+    assert torch.equal(H0, H1)
+    with pytest.raises(L.LsasError):
+        L.check(L.lsas_plan_set_batch_split(plan.handle, 2), "lsas_plan_set_batch_split")
+
+
+def test_batch_split_tail_after_whole_wave(L):
+    """One whole wave of frames plus two: the wave runs one frame per block,
+    the two after it split into antenna shards; every frame meets the
+    oracle bars.  Two such calls on one plan from two streams at once take
+    turns on the plan's partial-sum array and both stay right."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    cfg = sweep_config(64, 256)
+    F = sms + 2
+    b = synth.generate(cfg, frame_ids=range(F))
+    plan = make_plan(L, cfg, max_frames=F)
+    assert plan.batch_split_shards(F) == 2
+    assert plan.batch_split_shards(sms) == 1
+    ref = oracle_run(cfg, b)
+    x = to_torch_frames(b)
+    x2 = torch.flip(x, dims=[0]).contiguous()
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    torch.cuda.synchronize()
+    outs = []
+    for xs, st in zip((x, x2), streams):
+        with torch.cuda.stream(st):
+            outs.append(plan.run_frame(xs, want_eq=True, stream=st))
+    torch.cuda.synchronize()
+    assert plan.sync_status() == L.LSAS_OK
+    H, bits, eq = (t.cpu().numpy() for t in outs[0])
+    check_frame_outputs(cfg, ref, H, bits, eq)
+    H2, bits2, eq2 = (t.cpu().numpy() for t in outs[1])
+    # the flipped batch: its last two frames (split) are frames 1 and 0
+    for f2, f in ((F - 2, 1), (F - 1, 0), (0, F - 1)):
+        assert np.array_equal(H2[f2], H[f])
+    tail = synth.generate(cfg, frame_ids=[1, 0])
+    check_frame_outputs(cfg, oracle_run(cfg, tail), H2[F - 2:], bits2[F - 2:], eq2[F - 2:])
 
 
 # ------------------------------------------------ full-size workload ----

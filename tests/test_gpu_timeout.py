@@ -1,7 +1,8 @@
 """Failure detection on the GPU without a fault: the fused kernel's bounded
 wait on a staging copy runs out (lsas_plan_set_fault(1): block 0 waits for
-16 bytes that no copy delivers), in both fused kernels: the per-warp kernel
-(N = 1024) and the warp-specialised one (N = 2048).  The call finishes,
+16 bytes that no copy delivers), in each fused kernel: the per-warp kernel
+(N = 1024), the warp-pair kernel (N = 2048 from sc16 rows) and the
+warp-specialised one (N = 2048 from fc32 rows).  The call finishes,
 lsas_plan_sync returns LSAS_ERR_TIMEOUT (and clears it), the other frames of
 the same launch are still right, and the same plan then runs normally and
 meets the oracle bars.
@@ -20,11 +21,11 @@ from tests.parity_util import check_frame_outputs, oracle_run
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("N", [1024, 2048])
-def test_bounded_wait_runs_out_and_recovers(N):
+@pytest.mark.parametrize("N,fmt", [(1024, "sc16"), (2048, "sc16"), (2048, "fc32")])
+def test_bounded_wait_runs_out_and_recovers(N, fmt):
     import torch
     import paper_1901_07499_gb300.lsas as L
-    cfg = sweep_config(16, N)
+    cfg = sweep_config(16, N).replace(fmt=fmt)
     b = synth.generate(cfg, frame_ids=range(3))
     plan = L.Plan(cfg.M, cfg.N, cfg.cp, cfg.S, cfg.pilot_idx, cfg.Q, fmt=cfg.fmt, max_frames=4,
                   pilot=b.pilot)
