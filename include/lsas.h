@@ -150,7 +150,7 @@ lsas_status lsas_demodulate(lsas_plan plan, const void* d_in,
  * after the last whole wave, or all of them for a batch smaller than one
  * wave, may run split into equal antenna shards so that they occupy more
  * SMs: the shards' MRC partial sums go to a scratch array the plan owns
- * (lsas_plan_create reserves at most 64 MiB for it), and the combine pass
+ * (lsas_plan_create reserves at most 96 MiB for it), and the combine pass
  * forms z and the bits from them, summing the shards in a fixed order.
  * Outputs agree with the unsplit pass to rounding (the antenna sums are
  * ordered differently).  Calls on one plan from several streams take turns

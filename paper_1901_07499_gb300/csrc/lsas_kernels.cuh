@@ -503,45 +503,51 @@ __host__ __device__ constexpr int brev(int i, int bits) {
 }
 
 // b * W_32^e for a compile-time e in [0, 16): free for e = 0 and -j, two
-// packed instructions otherwise (W_8 included: a sum and a difference
-// before one packed product would take three)
+// packed instructions otherwise.  W8SUM: the eighth roots W_8 and W_8^3 as
+// a sum and a difference scaled by 1/sqrt(2) instead (three instructions
+// but a shorter chain; which is faster depends on the kernel, so each
+// kernel picks the form that measured faster).
+template <bool W8SUM>
 __device__ __forceinline__ float2 tw32(float2 b, int e, const KParams& p) {
+  constexpr float kS = 0.70710678118654752440f;  // 1/sqrt(2)
   if (e == 0) return b;
   if (e == 8) return make_float2(b.y, -b.x);                                     // -j
+  if (W8SUM && e == 4) return __fmul2_rn(make_float2(b.x + b.y, b.y - b.x), make_float2(kS, kS));
+  if (W8SUM && e == 12) return __fmul2_rn(make_float2(b.y - b.x, -(b.x + b.y)), make_float2(kS, kS));
   return cmulw(b, p.w32[e], p.w32n[e]);
 }
 
 // One radix-2 decimation-in-time stage of half-span S on R registers.
-template <int R, int S>
+template <int R, int S, bool W8SUM>
 __device__ __forceinline__ void dit_stage(float2* a, const KParams& p) {
 #pragma unroll
   for (int base = 0; base < R; base += 2 * S) {
 #pragma unroll
     for (int i = 0; i < S; ++i) {
-      const float2 b = tw32(a[base + i + S], i * (16 / S), p);
+      const float2 b = tw32<W8SUM>(a[base + i + S], i * (16 / S), p);
       const float2 x = a[base + i];
       a[base + i] = cadd(x, b);
       a[base + i + S] = csub(x, b);
     }
   }
 }
-template <int R, int S>
+template <int R, int S, bool W8SUM>
 __device__ __forceinline__ void dit_stages(float2* a, const KParams& p) {
   if constexpr (S < R) {
-    dit_stage<R, S>(a, p);
-    dit_stages<R, 2 * S>(a, p);
+    dit_stage<R, S, W8SUM>(a, p);
+    dit_stages<R, 2 * S, W8SUM>(a, p);
   }
 }
 
 // In-register R-point DFT (R <= 32), natural order in and out: radix-2
 // decimation in time over bit-reversed register indices (free renaming).
-template <int R>
+template <int R, bool W8SUM = false>
 __device__ __forceinline__ void dft(float2* v, const KParams& p) {
   constexpr int LOGR = ilog2c(R);
   float2 a[R];
 #pragma unroll
   for (int i = 0; i < R; ++i) a[i] = v[brev(i, LOGR)];
-  dit_stages<R, 1>(a, p);
+  dit_stages<R, 1, W8SUM>(a, p);
 #pragma unroll
   for (int i = 0; i < R; ++i) v[i] = a[i];
 }
@@ -745,15 +751,15 @@ __device__ __forceinline__ void final_exchange_read(float2 (&v)[32], const float
 }
 
 // Last FFT pass; on return v[e] = Y[bin_of(jt, e)] (unscaled).
-template <int LOG2N>
+template <int LOG2N, bool W8SUM = false>
 __device__ __forceinline__ void final_dft(float2 (&v)[32], const KParams& p) {
   using G = Geo<LOG2N>;
   if constexpr (G::N <= 1024) {
 #pragma unroll
-    for (int i = 0; i < 32 / G::L; ++i) dft<G::L>(v + i * G::L, p);
+    for (int i = 0; i < 32 / G::L; ++i) dft<G::L, W8SUM>(v + i * G::L, p);
   } else {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) dft<8>(v + i * 8, p);
+    for (int i = 0; i < 4; ++i) dft<8, W8SUM>(v + i * 8, p);
   }
 }
 

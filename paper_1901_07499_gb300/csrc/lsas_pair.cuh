@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(kPThreads, 1) pair_kernel(const KParams p) {
           load_row<LOG2N, false>(v, row_ptr<LOG2N, false>(p, f, m, witem_symbol(p, pilot_here, d0, it)),
                                  jt, true);
         }
-        dft<32>(v, p);
+        dft<32, true>(v, p);
         // middle pass: Y1[jt * 32 + r] out, Y1[j + 256 r] in (j = jt + 64 i)
 #pragma unroll
         for (int r = 0; r < 32; ++r) exM[xpad(jt * 32 + r)] = v[r];

@@ -53,10 +53,14 @@ using namespace lsas;
 namespace {
 
 constexpr int kSmemLimit = 232448;   // opt-in dynamic shared memory per block
-constexpr size_t kTailBytes = 64u << 20;   // cap of a plan's split-tail partial sums
+constexpr size_t kTailBytes = 96u << 20;   // cap of a plan's split-tail partial sums
 // Share of a fused block's time that does not shrink with its antenna count
-// (the group-end reductions, demap and pack), for the split decision.
-constexpr double kBlockFixed = 0.08;
+// (the group-end reductions, demap and pack), for the split decision, from
+// single-frame timings on GB300: about 0.08 for the per-warp kernel
+// (N <= 1024, 64 antennas) and 0.035 for the warp-pair kernel (N = 2048,
+// 128 antennas), whose group ends weigh less against its longer steps.
+constexpr double kBlockFixedWarp = 0.08;
+constexpr double kBlockFixedPair = 0.035;
 constexpr int kHostChunk = 64;       // frames per transfer chunk (host path)
 constexpr int kMaxPnLen = 1024;      // longest PN sequence lsas_plan_set_pn takes
 
@@ -261,13 +265,15 @@ bool plan_geometry(int M, int N, int D, lsas_input_fmt fmt, bool allow_hybrid, G
   g->tmem_cth = tmem_cols_thread(N, g->dg);
   if (N <= 1024) {
     // per-warp kernel: TMEM bounds the data symbols per group; the deepest
-    // staging ring that fits, with room for one symbol of every warp's
-    // partial sums in the per-warp regions
+    // staging ring that fits (at most three rows per warp for N = 1024,
+    // which measured faster there than four), with room for one symbol of
+    // every warp's partial sums in the per-warp regions
     found = false;
     const int dgmax = wgeo_dg_max(N, bps);
+    const int max_slots = N == 1024 ? 3 : kMaxSlots;
     for (int groups = (D + dgmax - 1) / dgmax; groups <= D && !found; ++groups) {
       const int dg = (D + groups - 1) / groups;
-      for (int slots = kMaxSlots; slots >= 2; --slots) {
+      for (int slots = max_slots; slots >= 2; --slots) {
         const WLayout l = make_wlayout(N, bps, slots, dg);
         if (l.total > kSmemLimit || l.warp_bytes < N * 8) continue;
         g->groups = groups;
@@ -452,7 +458,7 @@ lsas_status launch_frame(lsas_plan p, const void* d_in, int n_frames, float* d_H
 // Antenna shards G for nf frames that do not fill a whole wave of blocks
 // (one block per SM): the split runs nf * G blocks of M / G antennas each,
 // ceil(nf G / sms) waves of about (1 - f) / G + f of a frame's block time
-// (f = kBlockFixed), against one wave unsplit.  Equal shards only (one
+// (f: kBlockFixedWarp or kBlockFixedPair), against one wave unsplit.  Equal shards only (one
 // launch), each with at least one antenna per pipeline of the fused kernel;
 // 1 when no split saves 10 % of the wave.
 int tail_shards(lsas_plan p, int nf) {
@@ -460,13 +466,14 @@ int tail_shards(lsas_plan p, int nf) {
   const int pipes = p->N <= 1024 ? wgeo_warps(p->fmt == LSAS_IN_SC16 ? 4 : 8)
                                   : (p->fmt == LSAS_IN_SC16 ? kPPairs : 1);
   const int min_ant = pipes * p->geo.Af;
+  const double fixed = p->N > 1024 ? kBlockFixedPair : kBlockFixedWarp;
   double best = 0.9;
   int bestG = 1;
   for (int G = 2; G <= 32; G *= 2) {
     if (p->M % G != 0 || p->M / G < min_ant) continue;
     if (static_cast<long>(nf) * G > p->tail_units) continue;
     const double waves = std::ceil(static_cast<double>(nf) * G / p->sms);
-    const double t = waves * ((1.0 - kBlockFixed) / G + kBlockFixed);
+    const double t = waves * ((1.0 - fixed) / G + fixed);
     if (t < best) {
       best = t;
       bestG = G;
@@ -663,10 +670,10 @@ lsas_status lsas_plan_create(int M, int N, int cp_len, int n_sym, int pilot_idx,
     return LSAS_ERR_CUDA;
   }
   {
-    // partial sums of split tails (lsas_run_frame): up to two waves of
+    // partial sums of split tails (lsas_run_frame): up to three waves of
     // shard-frames, within kTailBytes; without them every batch runs unsplit
     const size_t unit = (static_cast<size_t>(p->D) * N * 2 + N) * sizeof(float);
-    const size_t units = std::min(static_cast<size_t>(2 * p->sms), kTailBytes / unit);
+    const size_t units = std::min(static_cast<size_t>(3 * p->sms), kTailBytes / unit);
     if (units >= 2 && cudaMalloc(&p->d_tail, units * unit) == cudaSuccess &&
         cudaEventCreateWithFlags(&p->tail_ev, cudaEventDisableTiming) == cudaSuccess) {
       p->tail_units = static_cast<int>(units);

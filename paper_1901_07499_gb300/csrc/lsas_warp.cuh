@@ -247,11 +247,11 @@ __global__ void __launch_bounds__(32 * wgeo_warps(FC32 ? 8 : 4), 1) warp_kernel(
           slot = 0;
           phase ^= 1;
         }
-        dft<32>(v, p);
+        dft<32, true>(v, p);
         final_exchange_write<LOG2N>(v, ex, jt);
         __syncwarp();
         wfinal_exchange_read<LOG2N>(v, ex, jt, tws);
-        final_dft<LOG2N>(v, p);
+        final_dft<LOG2N, true>(v, p);
         if (pilot_here && it == 0) {
           // LS estimate H = Y conj(X) / |X|^2 (1/sqrt(N) folded into xinv)
 #pragma unroll
