@@ -234,6 +234,17 @@ class Plan:
               "lsas_plan_batch_split_shards")
         return int(out.value)
 
+    def run_frame_launches(self, n_frames: int) -> int:
+        """Kernel launches lsas_run_frame makes for an n_frames batch: one,
+        or, when the frames after the last whole wave run split, the
+        whole-wave launch (if there is a whole wave), the shard launch and
+        the combine pass."""
+        if self.batch_split_shards(n_frames) == 1:
+            return 1
+        import torch
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        return (1 if n_frames >= sms else 0) + 2
+
     @property
     def handle(self):
         return self._h

@@ -66,7 +66,9 @@ def test_fp32_roofline_arithmetic():
 def test_traffic_follows_the_source_hash(monkeypatch):
     cfg = synth.config_by_name("scale")
     with open(bench.TRAFFIC_FILE) as fh:
-        rec = json.load(fh)
+        recs = json.load(fh)
+    recs = recs if isinstance(recs, list) else [recs]
+    rec = next(r for r in recs if r["workload"] == "scale")
     monkeypatch.setattr(bench, "kernel_hash", lambda: rec["kernel_sha"])
     assert bench.ncu_traffic(cfg, 1000) == pytest.approx(rec["dram_bytes_per_frame"] * 1000)
     assert bench.ncu_traffic(synth.config_by_name("tiny"), 1000) is None   # other workload
