@@ -20,6 +20,7 @@ Prints one JSON line (rank 0):
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import os
@@ -449,7 +450,7 @@ def serving_sweep(args, lsas, torch, form, cfgs, pools, max_batch, max_wait, rng
     mean_samples = float(np.mean(samples))
     for load in [float(v) for v in args.serving_loads.split(",")]:
         rate = load * 1e9 / mean_samples          # frames per second
-        lat, done_samples = [], [0]
+        lat, lat_ci, lat_t, done_samples = [], [], [], [0]
         tickets = []
         cv = threading.Condition()
         finished = [False]
@@ -464,13 +465,19 @@ def serving_sweep(args, lsas, torch, form, cfgs, pools, max_batch, max_wait, rng
                     if i >= len(tickets):
                         return
                     chunk = tickets[i:i + 64]
-                got = srv.wait_many([t for t, _ in chunk])
-                done_samples[0] += sum(samples[ci] for _, ci in chunk)
+                got = srv.wait_many([t for t, _, _ in chunk])
+                done_samples[0] += sum(samples[ci] for _, ci, _ in chunk)
                 lat.extend(got)
+                lat_ci.extend(ci for _, ci, _ in chunk)
+                lat_t.extend(ts for _, _, ts in chunk)
                 i += len(chunk)
 
         th = threading.Thread(target=waiter)
         th.start()
+        # a garbage-collector pause in the generator would turn ~10 ms of
+        # Poisson arrivals into one burst; collect now, not during the window
+        gc.collect()
+        gc.disable()
         st0 = srv.stats()
         t0 = time.perf_counter()
         t_next = t0
@@ -492,17 +499,38 @@ def serving_sweep(args, lsas, torch, form, cfgs, pools, max_batch, max_wait, rng
                 cis.append(ci)
                 n += 1
                 t_next += rng.exponential(1.0 / rate)
+            t_sub = time.perf_counter() - t0
             ts = srv.submit_many(batch)
             with cv:
-                tickets.extend(zip(ts, cis))
+                tickets.extend((t, c, t_sub) for t, c in zip(ts, cis))
                 cv.notify()
         with cv:
             finished[0] = True
             cv.notify()
         th.join()
         wall = time.perf_counter() - t0
+        gc.enable()
         st1 = srv.stats()
         lat_us = np.array(lat)
+        lat_c = np.array(lat_ci)
+        lat_s = np.array(lat_t)
+        # frames slower than 4x the median: how many, and when they were
+        # submitted (one burst of a few ms, or spread over the window)
+        slow = lat_us > 4 * np.percentile(lat_us, 50)
+        slow_rec = {"frames": int(slow.sum())}
+        if slow.any():
+            st = np.sort(lat_s[slow])
+            gaps = np.diff(st)
+            slow_rec.update({"first_ms": float(st[0] * 1e3), "last_ms": float(st[-1] * 1e3),
+                             "bursts": int(1 + np.sum(gaps > 0.05)),
+                             "max_us": float(lat_us[slow].max())})
+        per_config = {}
+        for ci, c in enumerate(cfgs):
+            sel = lat_us[lat_c == ci]
+            if sel.size:
+                per_config[c.name] = {"frames": int(sel.size),
+                                      "p50": float(np.percentile(sel, 50)),
+                                      "p99": float(np.percentile(sel, 99))}
         print(json.dumps({
             "mode": "serving", "form": form, "weights": weights,
             "offered_gsps": load, "achieved_gsps": done_samples[0] / wall / 1e9,
@@ -511,6 +539,8 @@ def serving_sweep(args, lsas, torch, form, cfgs, pools, max_batch, max_wait, rng
                            "p99": float(np.percentile(lat_us, 99)),
                            "max": float(lat_us.max())},
             "max_batch": max_batch, "max_wait_us": max_wait,
+            "per_config_latency_us": per_config,
+            "slow_frames": slow_rec,
             "configs": [c.name for c in cfgs], "data": "synthetic (seeded generator)"}))
         sys.stdout.flush()
     code = srv.close()
