@@ -120,7 +120,8 @@ def test_paper_shapes(L, M, N):
 
 @pytest.mark.parametrize("M,N,F", [(256, 256, 2), (256, 1024, 1), (256, 2048, 1)])
 def test_maximum_antenna_count(L, M, N, F):
-    """M = 256, the largest the interface takes, on both fused kernels."""
+    """M = 256, the largest the interface takes, on the per-warp (N <= 1024) and
+    warp-pair (N = 2048) fused kernels."""
     run_and_check(L, sweep_config(M, N).replace(M=M), F=F)
 
 
