@@ -448,6 +448,11 @@ def serving_sweep(args, lsas, torch, form, cfgs, pools, max_batch, max_wait, rng
              for _ in range(ring)] for c in cfgs]
     samples = [c.M * c.S * c.N for c in cfgs]
     mean_samples = float(np.mean(samples))
+    # warm-up, not measured: a few frames of every configuration (first
+    # launches, host-side first touches)
+    warm = [srv.submit(ids[ci], xs[ci][k % 4], *outs[ci][k]) for ci in range(len(cfgs))
+            for k in range(8)]
+    srv.wait_many(warm)
     for load in [float(v) for v in args.serving_loads.split(",")]:
         rate = load * 1e9 / mean_samples          # frames per second
         lat, lat_ci, lat_t, done_samples = [], [], [], [0]
@@ -482,11 +487,13 @@ def serving_sweep(args, lsas, torch, form, cfgs, pools, max_batch, max_wait, rng
         t0 = time.perf_counter()
         t_next = t0
         n = 0
+        max_lag = 0.0   # how late the generator submitted an arrival
         while t_next - t0 < args.serving_seconds:
             while time.perf_counter() < t_next:
                 pass
             # every arrival that is due goes to the server in one call
             now = time.perf_counter()
+            max_lag = max(max_lag, now - t_next)
             batch, cis = [], []
             while t_next <= now and t_next - t0 < args.serving_seconds and len(batch) < 64:
                 ci = int(rng.integers(len(cfgs)))
@@ -541,6 +548,7 @@ def serving_sweep(args, lsas, torch, form, cfgs, pools, max_batch, max_wait, rng
             "max_batch": max_batch, "max_wait_us": max_wait,
             "per_config_latency_us": per_config,
             "slow_frames": slow_rec,
+            "generator_max_lag_ms": max_lag * 1e3,
             "configs": [c.name for c in cfgs], "data": "synthetic (seeded generator)"}))
         sys.stdout.flush()
     code = srv.close()

@@ -464,9 +464,13 @@ lsas_status lsas_plan_set_fault(lsas_plan plan, int kind);
 
 /*
  * enable = 1 (the default): lsas_run_frame may split the frames after a
- * batch's last whole wave into antenna shards (see lsas_run_frame); 0: every
- * frame runs unsplit.  INVALID_ARG for other values.  Takes effect from the
- * next call.
+ * batch's last whole wave into antenna shards (see lsas_run_frame), with the
+ * shard count chosen for the number of those frames; 2: the same with one
+ * shard count for every batch (the single frame's choice, limited so that
+ * max_frames frames fit the scratch), so that a frame's results do not
+ * depend on how many frames share its call when batches are smaller than
+ * one wave (the serving loop uses this); 0: every frame runs unsplit.
+ * INVALID_ARG for other values.  Takes effect from the next call.
  */
 lsas_status lsas_plan_set_batch_split(lsas_plan plan, int enable);
 
@@ -579,6 +583,14 @@ lsas_status lsas_plan_sync(lsas_plan plan, void* stream);
  * out[6] input format, out[7] max_frames.
  */
 lsas_status lsas_plan_info(lsas_plan plan, int out[8]);
+
+/*
+ * Device memory the plan allocated when it was created, in bytes, into
+ * *out_bytes: its tables and the partial-sum scratch of split batch tails
+ * (lsas_run_frame).  Buffers made later by the host-buffer entry point or
+ * by packet detection are not included.  INVALID_ARG for null pointers.
+ */
+lsas_status lsas_plan_device_bytes(lsas_plan plan, size_t* out_bytes);
 
 /* Release the plan's device memory (synchronises its device first). */
 lsas_status lsas_plan_destroy(lsas_plan plan);

@@ -103,9 +103,10 @@ struct lsas_plan_s {
   // P [G][frames][D][N] complex then E [G][frames][N]
   float* d_tail = nullptr;
   int tail_units = 0;               // shard-frames d_tail holds
-  bool batch_split = true;          // lsas_plan_set_batch_split
+  int batch_split = 1;              // lsas_plan_set_batch_split: 0 off, 1 per batch, 2 fixed
   cudaEvent_t tail_ev = nullptr;    // the last split's combine has read d_tail
   std::mutex tail_mu;
+  size_t dev_bytes = 0;             // device memory allocated at creation
   Geometry geo;
   LaunchFn launch = nullptr;
   // host-transfer staging (lsas_run_frame_host), allocated on first use
@@ -458,11 +459,10 @@ lsas_status launch_frame(lsas_plan p, const void* d_in, int n_frames, float* d_H
 // Antenna shards G for nf frames that do not fill a whole wave of blocks
 // (one block per SM): the split runs nf * G blocks of M / G antennas each,
 // ceil(nf G / sms) waves of about (1 - f) / G + f of a frame's block time
-// (f: kBlockFixedWarp or kBlockFixedPair), against one wave unsplit.  Equal shards only (one
-// launch), each with at least one antenna per pipeline of the fused kernel;
-// 1 when no split saves 10 % of the wave.
-int tail_shards(lsas_plan p, int nf) {
-  if (nf <= 0 || !p->batch_split || p->tail_units == 0 || p->geo.hybrid) return 1;
+// (f: kBlockFixedWarp or kBlockFixedPair), against one wave unsplit.  Equal
+// shards only (one launch), each with at least one antenna per pipeline of
+// the fused kernel, nf G within cap; 1 when no split saves 10 % of the wave.
+int best_shards(lsas_plan p, int nf, long cap) {
   const int pipes = p->N <= 1024 ? wgeo_warps(p->fmt == LSAS_IN_SC16 ? 4 : 8)
                                   : (p->fmt == LSAS_IN_SC16 ? kPPairs : 1);
   const int min_ant = pipes * p->geo.Af;
@@ -471,7 +471,7 @@ int tail_shards(lsas_plan p, int nf) {
   int bestG = 1;
   for (int G = 2; G <= 32; G *= 2) {
     if (p->M % G != 0 || p->M / G < min_ant) continue;
-    if (static_cast<long>(nf) * G > p->tail_units) continue;
+    if (static_cast<long>(nf) * G > cap) continue;
     const double waves = std::ceil(static_cast<double>(nf) * G / p->sms);
     const double t = waves * ((1.0 - fixed) / G + fixed);
     if (t < best) {
@@ -480,6 +480,16 @@ int tail_shards(lsas_plan p, int nf) {
     }
   }
   return bestG;
+}
+
+int tail_shards(lsas_plan p, int nf) {
+  if (nf <= 0 || p->batch_split == 0 || p->tail_units == 0 || p->geo.hybrid) return 1;
+  if (p->batch_split == 2) {
+    // one shard count for every batch: the single frame's choice, among the
+    // counts whose scratch holds a batch of max_frames
+    return best_shards(p, 1, p->tail_units / (p->max_frames > 0 ? p->max_frames : 1));
+  }
+  return best_shards(p, nf, p->tail_units);
 }
 
 // Frames [f0, f0 + nf) of a lsas_run_frame batch as G antenna shards: the
@@ -647,6 +657,7 @@ lsas_status lsas_plan_create(int M, int N, int cp_len, int n_sym, int pilot_idx,
     lsas_plan_destroy(p);
     return LSAS_ERR_OOM;
   }
+  p->dev_bytes = sizeof(float2) * (tw.size() + N) + sizeof(int);
   std::vector<uint16_t> tcw1, tcw2;
   std::vector<float2> tctw;
   if (tc_tables(N, tcw1, tcw2, tctw)) {
@@ -657,6 +668,7 @@ lsas_status lsas_plan_create(int M, int N, int cp_len, int n_sym, int pilot_idx,
       lsas_plan_destroy(p);
       return LSAS_ERR_OOM;
     }
+    p->dev_bytes += (tcw1.size() + tcw2.size()) * 2 + tctw.size() * sizeof(float2);
     if (cudaMemcpy(p->d_tc_w1, tcw1.data(), tcw1.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(p->d_tc_w2, tcw2.data(), tcw2.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(p->d_tc_tw, tctw.data(), tctw.size() * sizeof(float2), cudaMemcpyHostToDevice) !=
@@ -677,6 +689,7 @@ lsas_status lsas_plan_create(int M, int N, int cp_len, int n_sym, int pilot_idx,
     if (units >= 2 && cudaMalloc(&p->d_tail, units * unit) == cudaSuccess &&
         cudaEventCreateWithFlags(&p->tail_ev, cudaEventDisableTiming) == cudaSuccess) {
       p->tail_units = static_cast<int>(units);
+      p->dev_bytes += units * unit;
     } else {
       cudaGetLastError();
       cudaFree(p->d_tail);
@@ -1051,9 +1064,15 @@ lsas_status lsas_plan_set_fault(lsas_plan p, int kind) {
   return LSAS_OK;
 }
 
+lsas_status lsas_plan_device_bytes(lsas_plan p, size_t* out_bytes) {
+  if (!p || !out_bytes) return LSAS_ERR_INVALID_ARG;
+  *out_bytes = p->dev_bytes;
+  return LSAS_OK;
+}
+
 lsas_status lsas_plan_set_batch_split(lsas_plan p, int enable) {
-  if (!p || enable < 0 || enable > 1) return LSAS_ERR_INVALID_ARG;
-  p->batch_split = enable != 0;
+  if (!p || enable < 0 || enable > 2) return LSAS_ERR_INVALID_ARG;
+  p->batch_split = enable;
   return LSAS_OK;
 }
 

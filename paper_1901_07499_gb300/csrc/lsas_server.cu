@@ -29,7 +29,9 @@
 // form: LS estimate -> tensor-core refinement -> MRC and demap with the
 // refined channel (lsas_estimate, lsas_dn_apply_tc, lsas_demodulate).
 // Each frame is processed exactly as it would be alone (frames are
-// independent in the kernels), so the results do not depend on the mix.
+// independent in the kernels, and a configuration's plan splits every batch
+// smaller than a wave into the same number of antenna shards), so the
+// results do not depend on the mix.
 // Device-side conditions (zero channel energy, a bounded wait that ran out)
 // latch in the configuration's plan and are returned by lsas_server_destroy.
 #include <chrono>
@@ -362,7 +364,8 @@ lsas_status register_config(lsas_server s, int M, int N, int cp_len, int n_sym, 
   }
   // admission: staging for max_batch frames on each lane (plus, for the
   // learned form, the LS estimate and the refinement's scratch) and the
-  // plan's own tables
+  // plan's own memory (estimated here, replaced by what the plan reports
+  // once it exists)
   const size_t plan_b = static_cast<size_t>(N) * 64 + (1u << 20);
   const size_t lane_b = B * (fb[0] + fb[1] + fb[2] + fb[3]) +
                         (dn_params ? B * fb[1] + work_floats * 4 + 256 : 0);
@@ -394,6 +397,27 @@ lsas_status register_config(lsas_server s, int M, int N, int cp_len, int n_sym, 
   st = lsas_plan_set(cf->plan, fmt, s->max_batch);
   if (st == LSAS_OK && host_pilot_iq) st = lsas_plan_set_pilot(cf->plan, host_pilot_iq);
   if (st != LSAS_OK) return undo(st);
+  // batches smaller than a wave run split into antenna shards, with one shard
+  // count for every batch size, so that a frame's results do not depend on
+  // how many frames share its batch
+  if (st == LSAS_OK) st = lsas_plan_set_batch_split(cf->plan, 2);
+  if (st != LSAS_OK) return undo(st);
+  {
+    // the plan's own allocation (tables, split-tail scratch) replaces the
+    // estimate, and is admitted against the budget like the rest
+    size_t held = 0;
+    if (lsas_plan_device_bytes(cf->plan, &held) != LSAS_OK) return undo(LSAS_ERR_CUDA);
+    std::lock_guard<std::mutex> lock(s->mu);
+    const size_t actual = cf->bytes - plan_b + held;
+    if (s->used - cf->bytes + actual > s->budget) {
+      s->used -= cf->bytes;
+      cf->bytes = 0;
+    } else {
+      s->used += actual - cf->bytes;
+      cf->bytes = actual;
+    }
+  }
+  if (cf->bytes == 0) return undo(LSAS_ERR_CAPACITY);
   for (Lane& ln : cf->lanes) {
     if (cudaMalloc(&ln.d_in, B * cf->in_b) != cudaSuccess ||
         cudaMalloc(&ln.d_H, B * cf->h_b) != cudaSuccess ||

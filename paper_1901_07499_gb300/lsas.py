@@ -107,6 +107,7 @@ lsas_plan_set_profile = _proto("lsas_plan_set_profile", [_vp, _i])
 lsas_plan_profile = _proto("lsas_plan_profile", [_vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)])
 lsas_plan_sync = _proto("lsas_plan_sync", [_vp, _vp])
 lsas_plan_info = _proto("lsas_plan_info", [_vp, C.POINTER(_i)])
+lsas_plan_device_bytes = _proto("lsas_plan_device_bytes", [_vp, C.POINTER(C.c_size_t)])
 lsas_plan_destroy = _proto("lsas_plan_destroy", [_vp])
 lsas_fma_peak_run = _proto("lsas_fma_peak_run", [_i, _i, _i, _vp, C.POINTER(C.c_double), _vp])
 
@@ -126,7 +127,7 @@ EXPORTED = ["lsas_status_str", "lsas_check_config", "lsas_frame_bytes",
             "lsas_plan_set_batch_split", "lsas_plan_batch_split_shards",
             "lsas_run_frame_refined", "lsas_dn_grad_tc",
             "lsas_plan_set_profile", "lsas_plan_profile",
-            "lsas_plan_sync", "lsas_plan_info",
+            "lsas_plan_sync", "lsas_plan_info", "lsas_plan_device_bytes",
             "lsas_plan_destroy", "lsas_fma_peak_run"]
 
 
@@ -221,10 +222,13 @@ class Plan:
                 "tma", "fmt", "max_frames"]
         return dict(zip(keys, list(out)))
 
-    def set_batch_split(self, enable: bool) -> None:
+    def set_batch_split(self, enable) -> None:
         """lsas_plan_set_batch_split: whether lsas_run_frame may split the
-        frames after a batch's last whole wave into antenna shards."""
-        check(lsas_plan_set_batch_split(self._h, 1 if enable else 0), "lsas_plan_set_batch_split")
+        frames after a batch's last whole wave into antenna shards (True or
+        1: shard count per batch size; 2: one shard count for every batch;
+        False or 0: never)."""
+        mode = int(enable) if not isinstance(enable, bool) else (1 if enable else 0)
+        check(lsas_plan_set_batch_split(self._h, mode), "lsas_plan_set_batch_split")
 
     def batch_split_shards(self, n_frames: int) -> int:
         """lsas_plan_batch_split_shards: the antenna shards lsas_run_frame
@@ -232,6 +236,13 @@ class Plan:
         out = _i(0)
         check(lsas_plan_batch_split_shards(self._h, int(n_frames), C.byref(out)),
               "lsas_plan_batch_split_shards")
+        return int(out.value)
+
+    def device_bytes(self) -> int:
+        """lsas_plan_device_bytes: device memory the plan allocated at
+        creation (tables and the split-tail scratch)."""
+        out = C.c_size_t(0)
+        check(lsas_plan_device_bytes(self._h, C.byref(out)), "lsas_plan_device_bytes")
         return int(out.value)
 
     def run_frame_launches(self, n_frames: int) -> int:
@@ -576,10 +587,13 @@ class Server:
         return dict(launches=int(out[0]), frames=int(out[1]), admitted_bytes=int(out[2]),
                     configs=int(out[3]))
 
-    def set_batch_split(self, enable: bool) -> None:
+    def set_batch_split(self, enable) -> None:
         """lsas_plan_set_batch_split: whether lsas_run_frame may split the
-        frames after a batch's last whole wave into antenna shards."""
-        check(lsas_plan_set_batch_split(self._h, 1 if enable else 0), "lsas_plan_set_batch_split")
+        frames after a batch's last whole wave into antenna shards (True or
+        1: shard count per batch size; 2: one shard count for every batch;
+        False or 0: never)."""
+        mode = int(enable) if not isinstance(enable, bool) else (1 if enable else 0)
+        check(lsas_plan_set_batch_split(self._h, mode), "lsas_plan_set_batch_split")
 
     def batch_split_shards(self, n_frames: int) -> int:
         """lsas_plan_batch_split_shards: the antenna shards lsas_run_frame

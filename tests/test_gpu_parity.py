@@ -323,7 +323,17 @@ def test_batch_split_small_batch(L, name, F):
     check_frame_outputs(cfg, ref, H0.cpu().numpy(), bits0.cpu().numpy(), eq0.cpu().numpy())
     assert torch.equal(H0, H1)
     with pytest.raises(L.LsasError):
-        L.check(L.lsas_plan_set_batch_split(plan.handle, 2), "lsas_plan_set_batch_split")
+        L.check(L.lsas_plan_set_batch_split(plan.handle, 3), "lsas_plan_set_batch_split")
+    # one shard count for every batch smaller than a wave: a frame gives the
+    # same bytes alone and in a batch
+    plan.set_batch_split(2)
+    shards = {plan.batch_split_shards(n) for n in range(1, 9)}
+    assert len(shards) == 1 and shards.pop() > 1
+    H2, bits2, eq2 = plan.run_frame(x, want_eq=True)
+    Ha, bitsa, eqa = plan.run_frame(x[:1].contiguous(), want_eq=True)
+    plan.sync()
+    assert torch.equal(H2[:1], Ha) and torch.equal(bits2[:1], bitsa) and torch.equal(eq2[:1], eqa)
+    check_frame_outputs(cfg, ref, H2.cpu().numpy(), bits2.cpu().numpy(), eq2.cpu().numpy())
 
 
 def test_batch_split_tail_after_whole_wave(L):

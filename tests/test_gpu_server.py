@@ -195,6 +195,11 @@ def test_frames_admitted_by_memory_budget(L):
     srv = L.Server(mem_budget=1 << 30, max_batch=16, max_wait_us=2e6)
     cid = srv.register(c.M, c.N, c.cp, c.S, c.pilot_idx, c.Q, fmt=c.fmt, pilot=b.pilot)
     assert srv.frame_bytes()["budget"] == (1 << 30) - srv.stats()["admitted_bytes"]
+    # registration admits the plan's own device memory (tables and the
+    # split-tail scratch) on top of both lanes' staging for 16 frames
+    plan = L.Plan(c.M, c.N, c.cp, c.S, c.pilot_idx, c.Q, fmt=c.fmt, max_frames=16)
+    assert srv.stats()["admitted_bytes"] >= plan.device_bytes() + 2 * 16 * (fb + eq_b)
+    plan.close()
     srv.set_admission(int(2.5 * fb), 0.0)
     assert srv.frame_bytes() == {"charged": 0, "budget": int(2.5 * fb)}
     xs = [_pinned(b.frames[f]) for f in range(3)]
