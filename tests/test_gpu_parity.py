@@ -336,6 +336,28 @@ def test_batch_split_small_batch(L, name, F):
     check_frame_outputs(cfg, ref, H2.cpu().numpy(), bits2.cpu().numpy(), eq2.cpu().numpy())
 
 
+@pytest.mark.parametrize("N,fmt", [(2048, "fc32"), (512, "sc16")])
+def test_batch_split_other_kernels(L, N, fmt):
+    """The shard pass of the warp-specialised kernel (N = 2048 from fc32 rows)
+    and of the per-warp kernel with two antennas per lane team (N = 512):
+    split and unsplit small batches both meet the oracle bars, H equal."""
+    import torch
+    cfg = sweep_config(16, N).replace(fmt=fmt, M=64 if N == 512 else 16)
+    b = synth.generate(cfg, frame_ids=range(2))
+    plan = make_plan(L, cfg, max_frames=4)
+    assert plan.batch_split_shards(2) > 1
+    x = to_torch_frames(b)
+    ref = oracle_run(cfg, b)
+    H1, bits1, eq1 = plan.run_frame(x, want_eq=True)
+    plan.sync()
+    check_frame_outputs(cfg, ref, H1.cpu().numpy(), bits1.cpu().numpy(), eq1.cpu().numpy())
+    plan.set_batch_split(False)
+    H0, bits0, eq0 = plan.run_frame(x, want_eq=True)
+    plan.sync()
+    check_frame_outputs(cfg, ref, H0.cpu().numpy(), bits0.cpu().numpy(), eq0.cpu().numpy())
+    assert torch.equal(H0, H1)
+
+
 def test_batch_split_tail_after_whole_wave(L):
     """One whole wave of frames plus two: the wave runs one frame per block,
     the two after it split into antenna shards; every frame meets the
