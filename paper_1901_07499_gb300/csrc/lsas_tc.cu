@@ -32,7 +32,11 @@
 
 namespace lsas {
 
-constexpr int kTcThreads = 128;
+// threads per block: 128 (one per operand row), or 256 for N = 2048, where
+// two threads share each row of the twiddle, stage-2 and output phases
+// (halves of the columns) and one batch's phases are the critical path
+template <int LOG2N>
+__host__ __device__ constexpr int tc_threads() { return LOG2N == 11 ? 256 : 128; }
 
 // byte offset of element (row, k) of a rows x K fp16 operand tile
 __host__ __device__ inline int tc_off(int row, int k, int K) {
@@ -119,14 +123,14 @@ __device__ __forceinline__ void splitbf16x2(float a, float b, uint32_t& hi, uint
   lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
-// Store one operand row of 2K values (re[0..K) then im[0..K)), hi and lo
-// images, in fp16 or bf16.
-template <int K>
+// Store columns [C0, C1) of one operand row of 2K values (re[0..K) then
+// im[0..K)), hi and lo images, in fp16 or bf16.
+template <int K, int C0 = 0, int C1 = 2 * K>
 __device__ __forceinline__ void store_row(unsigned char* hi_img, unsigned char* lo_img, int row,
                                           const float* re, const float* im, bool want_lo,
                                           bool bf16) {
 #pragma unroll
-  for (int c = 0; c < 2 * K; c += 8) {
+  for (int c = C0; c < C1; c += 8) {
     uint32_t h[4], l[4];
 #pragma unroll
     for (int j = 0; j < 8; j += 2) {
@@ -161,14 +165,17 @@ struct TcGeo {
   static constexpr int OFF_A2 = OFF_A1 + A1_REGION;
   static constexpr int OFF_BAR = OFF_A2 + 2 * T2 * A2_BYTES;
   static constexpr int SMEM = OFF_BAR + 64;
+  static constexpr int TT = tc_threads<LOG2N>();            // threads per block
+  static constexpr int PARTS = TT / 128;                    // threads per operand row
+  static_assert(PARTS == 1 || T2 == 1, "two threads per row need one stage-2 tile");
 };
 
 // Tensor-core FFT: p.nframes rows of N samples (antenna-symbols, CP dropped)
 // -> Y rows (unitary).  Persistent: block b takes batches b, b + grid, ...
 template <int LOG2N, bool FC32>
-__global__ void __launch_bounds__(kTcThreads, 1) tcfft_kernel(const KParams p) {
+__global__ void __launch_bounds__(tc_threads<LOG2N>(), 1) tcfft_kernel(const KParams p) {
   using G = TcGeo<LOG2N>;
-  constexpr int N = G::N, N2 = G::N2, R = G::R;
+  constexpr int N = G::N, N2 = G::N2, R = G::R, TT = G::TT, PARTS = G::PARTS;
   extern __shared__ __align__(128) unsigned char smem[];
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
@@ -185,8 +192,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tcfft_kernel(const KParams p) {
   {
     const uint4* s1 = static_cast<const uint4*>(p.tc_w1) + (bf16 ? 2 * G::W1_BYTES / 16 : 0);
     const uint4* s2 = static_cast<const uint4*>(p.tc_w2) + (bf16 ? 2 * G::W2_BYTES / 16 : 0);
-    for (int i = tid; i < 2 * G::W1_BYTES / 16; i += kTcThreads) reinterpret_cast<uint4*>(w1)[i] = s1[i];
-    for (int i = tid; i < 2 * G::W2_BYTES / 16; i += kTcThreads) reinterpret_cast<uint4*>(w2)[i] = s2[i];
+    for (int i = tid; i < 2 * G::W1_BYTES / 16; i += TT) reinterpret_cast<uint4*>(w1)[i] = s1[i];
+    for (int i = tid; i < 2 * G::W2_BYTES / 16; i += TT) reinterpret_cast<uint4*>(w2)[i] = s2[i];
   }
   if (tid == 0) {
     mbar_init(smem_u32(bar), 1);
@@ -198,18 +205,57 @@ __global__ void __launch_bounds__(kTcThreads, 1) tcfft_kernel(const KParams p) {
   __syncthreads();
   tmem_fence_after();
   const uint32_t tmem = *tmem_base;
-  const uint32_t lane_off = static_cast<uint32_t>(32 * warp) << 16;
+  const uint32_t lane_off = static_cast<uint32_t>(32 * (warp & 3)) << 16;
+  const int rt = tid & 127;          // operand row of this thread within a tile
+  const int part = tid >> 7;         // which column half it takes (PARTS = 2)
+  // this thread's inter-stage twiddles W_N^(n2 k1): n2 = rt mod N2 is the
+  // same for every tile and batch (128 is a multiple of N2), so they are
+  // loaded once
+  constexpr int KH = 32 / PARTS;
+  float2 wtw[KH];
+#pragma unroll
+  for (int j = 0; j < KH; ++j) wtw[j] = __ldg(p.tc_tw + (rt % N2) * 32 + part * KH + j);
   const size_t total = static_cast<size_t>(p.nframes) * p.M * p.S;
   const size_t nbatch = (total + R - 1) / R;
   constexpr int bps = FC32 ? 8 : 4;
+  static_assert(G::T1 == PARTS, "one stage-1 operand row per thread");
+  // sc16: this thread's stage-1 samples of the next batch are loaded while
+  // the current batch runs (raw words, converted when the batch starts)
+  const int b1 = (part * 128 + rt) / N2, n21 = (part * 128 + rt) % N2;
+  uint32_t raw[32];
+  auto load_raw = [&](size_t batch) {
+    const size_t row = batch * R + b1;
+    if (batch < nbatch && row < total) {
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(
+          static_cast<const unsigned char*>(p.in) + (row * (N + p.cp) + p.cp) * bps);
+#pragma unroll
+      for (int n1 = 0; n1 < 32; ++n1) raw[n1] = __ldg(src + N2 * n1 + n21);
+    } else {
+#pragma unroll
+      for (int n1 = 0; n1 < 32; ++n1) raw[n1] = 0x00000000u;   // converts to 0
+    }
+  };
+  if constexpr (!FC32) load_raw(blockIdx.x);
   uint32_t phase = 0;
   bool timed_out = false;
   for (size_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
     const size_t row0 = batch * R;
     // ---- stage-1 operands: row (b, n2) = x[N2 n1 + n2], n1 < 32
+    if constexpr (!FC32) {
+      float re[32], im[32];
 #pragma unroll
-    for (int t = 0; t < G::T1; ++t) {
-      const int lr = t * 128 + tid;
+      for (int n1 = 0; n1 < 32; ++n1) {
+        const float2 x = sc16_to_float2(raw[n1]);
+        re[n1] = x.x;
+        im[n1] = x.y;
+      }
+      store_row<32>(a1 + (2 * part) * G::A1_BYTES, a1 + (2 * part + 1) * G::A1_BYTES, rt, re, im,
+                    split, bf16);
+      load_raw(batch + gridDim.x);
+    }
+#pragma unroll
+    for (int t = part; t < G::T1 && FC32; t += PARTS) {
+      const int lr = t * 128 + rt;
       const int b = lr / N2, n2 = lr % N2;
       float re[32], im[32];
       if (row0 + b < total) {
@@ -227,7 +273,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tcfft_kernel(const KParams p) {
 #pragma unroll
         for (int n1 = 0; n1 < 32; ++n1) re[n1] = im[n1] = 0.f;
       }
-      store_row<32>(a1 + (2 * t) * G::A1_BYTES, a1 + (2 * t + 1) * G::A1_BYTES, tid, re, im, split,
+      store_row<32>(a1 + (2 * t) * G::A1_BYTES, a1 + (2 * t + 1) * G::A1_BYTES, rt, re, im, split,
                     bf16);
     }
     fence_proxy_async();
@@ -251,38 +297,53 @@ __global__ void __launch_bounds__(kTcThreads, 1) tcfft_kernel(const KParams p) {
     }
     phase ^= 1;
     tmem_fence_after();
-    // ---- twiddle, scale by 2^-6, transpose to T[b][k1][n2]
+    // ---- twiddle, scale by 2^-6, transpose to T[b][k1][n2]; with two
+    // threads per row each takes 32 / PARTS of the k1
 #pragma unroll
     for (int t = 0; t < G::T1; ++t) {
-      float d[64];
-      Tmem<64>::ld(tmem + lane_off + t * 64, d);
+      float dr[KH], di[KH];
+      Tmem<KH>::ld(tmem + lane_off + t * 64 + part * KH, dr);
+      Tmem<KH>::ld(tmem + lane_off + t * 64 + 32 + part * KH, di);
       tmem_wait_ld();
-      const int lr = t * 128 + tid;
+      const int lr = t * 128 + rt;
       const int b = lr / N2, n2 = lr % N2;
 #pragma unroll
-      for (int k1 = 0; k1 < 32; ++k1) {
-        const float2 w = __ldg(p.tc_tw + n2 * 32 + k1);
-        const float2 c = cmul(make_float2(d[k1], d[32 + k1]), w);
+      for (int j = 0; j < KH; ++j) {
+        const int k1 = part * KH + j;
+        const float2 c = cmul(make_float2(dr[j], di[j]), wtw[j]);
         tbuf[(b * 32 + k1) * G::TS + n2] = make_float2(c.x * 0.015625f, c.y * 0.015625f);
       }
     }
     tmem_fence_before();
     __syncthreads();
     tmem_fence_after();
-    // ---- stage-2 operands: row (b, k1) = B1[n2][k1], n2 < N2
+    // ---- stage-2 operands: row (b, k1) = B1[n2][k1], n2 < N2; with two
+    // threads per row, one stores the real half and one the imaginary half
 #pragma unroll
     for (int t = 0; t < G::T2; ++t) {
-      const int lr = t * 128 + tid;
+      const int lr = t * 128 + rt;
       const int b = lr / 32, k1 = lr % 32;
       float re[N2], im[N2];
+      if constexpr (PARTS == 1) {
 #pragma unroll
-      for (int n2 = 0; n2 < N2; ++n2) {
-        const float2 c = tbuf[(b * 32 + k1) * G::TS + n2];
-        re[n2] = c.x;
-        im[n2] = c.y;
+        for (int n2 = 0; n2 < N2; ++n2) {
+          const float2 c = tbuf[(b * 32 + k1) * G::TS + n2];
+          re[n2] = c.x;
+          im[n2] = c.y;
+        }
+        store_row<N2>(a2 + (2 * t) * G::A2_BYTES, a2 + (2 * t + 1) * G::A2_BYTES, rt, re, im, split,
+                      bf16);
+      } else if (part == 0) {
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) re[n2] = tbuf[(b * 32 + k1) * G::TS + n2].x;
+        store_row<N2, 0, N2>(a2 + (2 * t) * G::A2_BYTES, a2 + (2 * t + 1) * G::A2_BYTES, rt, re, im,
+                             split, bf16);
+      } else {
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) im[n2] = tbuf[(b * 32 + k1) * G::TS + n2].y;
+        store_row<N2, N2, 2 * N2>(a2 + (2 * t) * G::A2_BYTES, a2 + (2 * t + 1) * G::A2_BYTES, rt, re,
+                                  im, split, bf16);
       }
-      store_row<N2>(a2 + (2 * t) * G::A2_BYTES, a2 + (2 * t + 1) * G::A2_BYTES, tid, re, im, split,
-                    bf16);
     }
     fence_proxy_async();
     tmem_fence_before();
@@ -310,12 +371,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) tcfft_kernel(const KParams p) {
     const float so = p.inv_sqrtN * 64.f;
 #pragma unroll
     for (int t = 0; t < G::T2; ++t) {
-      const int lr = t * 128 + tid;
+      const int lr = t * 128 + rt;
       const int b = lr / 32, k1 = lr % 32;
       const bool ok = row0 + b < total;
       float2* dst = p.Y_out + (row0 + b) * N + k1;
 #pragma unroll
-      for (int c0 = 0; c0 < N2; c0 += 16) {
+      for (int c0 = part * (N2 / PARTS); c0 < (part + 1) * (N2 / PARTS); c0 += 16) {
         float dr[16], di[16];
         Tmem<16>::ld(tmem + lane_off + 128 + t * (2 * N2) + c0, dr);
         Tmem<16>::ld(tmem + lane_off + 128 + t * (2 * N2) + N2 + c0, di);
@@ -346,7 +407,7 @@ static cudaError_t launch_tc_t(const KParams& p, int grid, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) limit[dev] = G::SMEM;
   }
-  tcfft_kernel<LOG2N, FC32><<<grid, kTcThreads, G::SMEM, st>>>(p);
+  tcfft_kernel<LOG2N, FC32><<<grid, G::TT, G::SMEM, st>>>(p);
   return cudaGetLastError();
 }
 
