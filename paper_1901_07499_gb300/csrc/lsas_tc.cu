@@ -17,8 +17,11 @@
 // (~2^-11 relative for fp16, ~2^-8 for bf16).  Stage-2 inputs are scaled by 2^-6 (exact) to stay in
 // fp16 range; the output is scaled back with the unitary 1/sqrt(N).
 //
-// Operand tiles use the canonical no-swizzle K-major layout: 8-row x 16-byte
-// core matrices, adjacent along K at 128 B, row groups at 128 * K / 8 B.
+// Operand tiles use the canonical no-swizzle K-major layout (8-row x 16-byte
+// core matrices, adjacent along K at 128 B, row groups at 128 * K / 8 B),
+// except the stage-2 data operand, which the twiddle phase writes MN-major
+// (8 rows contiguous): each thread holds one of its columns, so no transpose
+// buffer is needed between the stages.
 #include <cfloat>
 #include <cmath>
 #include <vector>
@@ -41,6 +44,12 @@ __host__ __device__ constexpr int tc_threads() { return LOG2N == 11 ? 256 : 128;
 // byte offset of element (row, k) of a rows x K fp16 operand tile
 __host__ __device__ inline int tc_off(int row, int k, int K) {
   return (row >> 3) * (16 * K) + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
+// byte offset of element (row, k) of a 128-row MN-major operand tile: 8 rows
+// contiguous (16 B), then 8 columns of them (a 128 B core matrix), the 16
+// row groups of a column group 128 B apart, column groups 2048 B apart
+__host__ __device__ inline int tc_mn_off(int row, int k) {
+  return (row >> 3) * 128 + (k >> 3) * 2048 + (k & 7) * 16 + (row & 7) * 2;
 }
 
 // bfloat16 of a double, round to nearest even, by way of float
@@ -156,12 +165,10 @@ struct TcGeo {
   static constexpr int W2_BYTES = (2 * N2) * (2 * N2) * 2;
   static constexpr int A1_BYTES = 128 * 64 * 2;             // one tile, one image
   static constexpr int A2_BYTES = 128 * (2 * N2) * 2;
-  static constexpr int TS = N2 + 1;                         // transpose row stride (float2)
-  static constexpr int T_BYTES = R * 32 * TS * 8;
   static constexpr int OFF_W1 = 0;
   static constexpr int OFF_W2 = OFF_W1 + 2 * W1_BYTES;
-  static constexpr int OFF_A1 = OFF_W2 + 2 * W2_BYTES;      // A1 tiles, then (aliased) T
-  static constexpr int A1_REGION = (2 * T1 * A1_BYTES > T_BYTES) ? 2 * T1 * A1_BYTES : T_BYTES;
+  static constexpr int OFF_A1 = OFF_W2 + 2 * W2_BYTES;      // A1 tiles [tile][hi, lo]
+  static constexpr int A1_REGION = 2 * T1 * A1_BYTES;
   static constexpr int OFF_A2 = OFF_A1 + A1_REGION;
   static constexpr int OFF_BAR = OFF_A2 + 2 * T2 * A2_BYTES;
   static constexpr int SMEM = OFF_BAR + 64;
@@ -184,7 +191,6 @@ __global__ void __launch_bounds__(tc_threads<LOG2N>(), 1) tcfft_kernel(const KPa
   unsigned char* w1 = smem + G::OFF_W1;
   unsigned char* w2 = smem + G::OFF_W2;
   unsigned char* a1 = smem + G::OFF_A1;
-  float2* tbuf = reinterpret_cast<float2*>(smem + G::OFF_A1);
   unsigned char* a2 = smem + G::OFF_A2;
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + G::OFF_BAR);
   uint32_t* tmem_base = reinterpret_cast<uint32_t*>(smem + G::OFF_BAR + 16);
@@ -197,6 +203,7 @@ __global__ void __launch_bounds__(tc_threads<LOG2N>(), 1) tcfft_kernel(const KPa
   }
   if (tid == 0) {
     mbar_init(smem_u32(bar), 1);
+    mbar_init(smem_u32(bar + 1), 1);
     fence_mbar_init();
   }
   if (warp == 0) tmem_alloc(smem_u32(tmem_base), 256);
@@ -219,6 +226,7 @@ __global__ void __launch_bounds__(tc_threads<LOG2N>(), 1) tcfft_kernel(const KPa
   const size_t nbatch = (total + R - 1) / R;
   constexpr int bps = FC32 ? 8 : 4;
   static_assert(G::T1 == PARTS, "one stage-1 operand row per thread");
+  static_assert(!FC32, "the tensor-core FFT takes sc16 rows");
   // sc16: this thread's stage-1 samples of the next batch are loaded while
   // the current batch runs (raw words, converted when the batch starts)
   const int b1 = (part * 128 + rt) / N2, n21 = (part * 128 + rt) % N2;
@@ -235,51 +243,43 @@ __global__ void __launch_bounds__(tc_threads<LOG2N>(), 1) tcfft_kernel(const KPa
       for (int n1 = 0; n1 < 32; ++n1) raw[n1] = 0x00000000u;   // converts to 0
     }
   };
-  if constexpr (!FC32) load_raw(blockIdx.x);
-  uint32_t phase = 0;
+  // MMA completion: stage 1 commits to bar[0], stage 2 to bar[1]; each has
+  // at most one commit outstanding when it is waited on (a second commit to
+  // one barrier before its wait would complete the next phase too, and the
+  // parity wait could then not see the first)
+  uint32_t phase[2] = {0, 0};
   bool timed_out = false;
-  for (size_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
-    const size_t row0 = batch * R;
-    // ---- stage-1 operands: row (b, n2) = x[N2 n1 + n2], n1 < 32
-    if constexpr (!FC32) {
-      float re[32], im[32];
-#pragma unroll
-      for (int n1 = 0; n1 < 32; ++n1) {
-        const float2 x = sc16_to_float2(raw[n1]);
-        re[n1] = x.x;
-        im[n1] = x.y;
-      }
-      store_row<32>(a1 + (2 * part) * G::A1_BYTES, a1 + (2 * part + 1) * G::A1_BYTES, rt, re, im,
-                    split, bf16);
-      load_raw(batch + gridDim.x);
+  auto wait_mma = [&](int st) {
+    if (!timed_out && !mbar_wait_bounded(smem_u32(bar + st), phase[st])) {
+      timed_out = true;
+      latch(p.status, kStTimeout);
     }
-#pragma unroll
-    for (int t = part; t < G::T1 && FC32; t += PARTS) {
-      const int lr = t * 128 + rt;
-      const int b = lr / N2, n2 = lr % N2;
-      float re[32], im[32];
-      if (row0 + b < total) {
-        const unsigned char* src = static_cast<const unsigned char*>(p.in) +
-                                   ((row0 + b) * (N + p.cp) + p.cp) * bps;
-#pragma unroll
-        for (int n1 = 0; n1 < 32; ++n1) {
-          float2 x;
-          if constexpr (FC32) x = __ldg(reinterpret_cast<const float2*>(src) + N2 * n1 + n2);
-          else x = sc16_to_float2(__ldg(reinterpret_cast<const uint32_t*>(src) + N2 * n1 + n2));
-          re[n1] = x.x;
-          im[n1] = x.y;
-        }
-      } else {
-#pragma unroll
-        for (int n1 = 0; n1 < 32; ++n1) re[n1] = im[n1] = 0.f;
-      }
-      store_row<32>(a1 + (2 * t) * G::A1_BYTES, a1 + (2 * t + 1) * G::A1_BYTES, rt, re, im, split,
-                    bf16);
-    }
+    phase[st] ^= 1;
+    tmem_fence_after();
+  };
+  // operands of every thread visible to the MMA and this thread's TMEM
+  // loads done before the issuing thread goes on
+  auto to_mma = [&]() {
     fence_proxy_async();
     tmem_fence_before();
     __syncthreads();
     tmem_fence_after();
+  };
+  // ---- stage-1 operands of a batch: row (b, n2) = x[N2 n1 + n2], n1 < 32,
+  // from the raw words loaded ahead; then the next batch's words are loaded
+  auto build_stage1 = [&](size_t batch) {
+    float re[32], im[32];
+#pragma unroll
+    for (int n1 = 0; n1 < 32; ++n1) {
+      const float2 x = sc16_to_float2(raw[n1]);
+      re[n1] = x.x;
+      im[n1] = x.y;
+    }
+    store_row<32>(a1 + (2 * part) * G::A1_BYTES, a1 + (2 * part + 1) * G::A1_BYTES, rt, re, im,
+                  split, bf16);
+    load_raw(batch + gridDim.x);
+  };
+  auto issue_stage1 = [&]() {
     if (tid == 0) {
       for (int t = 0; t < G::T1; ++t)
         for (int term = 0; term < p.terms; ++term) {
@@ -291,14 +291,44 @@ __global__ void __launch_bounds__(tc_threads<LOG2N>(), 1) tcfft_kernel(const KPa
         }
       umma_commit(smem_u32(bar));
     }
-    if (!timed_out && !mbar_wait_bounded(smem_u32(bar), phase)) {
-      timed_out = true;
-      latch(p.status, kStTimeout);
+  };
+  auto issue_stage2 = [&]() {
+    if (tid == 0) {
+      for (int t = 0; t < G::T2; ++t)
+        for (int term = 0; term < p.terms; ++term) {
+          const uint32_t abase = smem_u32(a2 + (2 * t + (term == 2 ? 1 : 0)) * G::A2_BYTES);
+          const uint32_t bbase = smem_u32(w2 + (term == 1 ? 1 : 0) * G::W2_BYTES);
+          // A2 MN-major: 8-row groups 128 B apart, 8-column groups 2048 B
+          // apart (16 row groups), two column groups per K = 16 step
+          for (int kc = 0; kc < (2 * N2) / 16; ++kc)
+            umma_f16(tmem + 128 + t * (2 * N2), umma_desc(abase + kc * 4096, 2048, 128),
+                     tc_desc(bbase + kc * 256, 2 * N2), umma_idesc(2 * N2, bf16) | (1u << 15),
+                     (term > 0 || kc > 0) ? 1u : 0u);
+        }
+      umma_commit(smem_u32(bar + 1));
     }
-    phase ^= 1;
-    tmem_fence_after();
-    // ---- twiddle, scale by 2^-6, transpose to T[b][k1][n2]; with two
-    // threads per row each takes 32 / PARTS of the k1
+  };
+  // Software pipeline over this block's batches: the stage-2 MMAs of batch
+  // i run while the threads build the stage-1 operands of batch i + 1 (A1 is
+  // free once batch i's stage-1 MMAs completed), and batch i + 1's stage-1
+  // MMAs are queued behind them while batch i's output is stored.  The two
+  // stages use separate TMEM columns, and every operand buffer is rewritten
+  // only after the MMAs reading it have been waited for.
+  if (blockIdx.x < nbatch) {
+    load_raw(blockIdx.x);
+    build_stage1(blockIdx.x);
+    to_mma();
+    issue_stage1();
+  }
+  for (size_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
+    const size_t row0 = batch * R;
+    const bool more = batch + gridDim.x < nbatch;
+    wait_mma(0);   // stage 1 of this batch
+    // ---- twiddle, scale by 2^-6 and store the stage-2 operand directly in
+    // the MN-major layout: row m = (b, k1) of A2 is output k1 of batch row b,
+    // column n2 (real) or N2 + n2 (imaginary) is this thread's D1 row, so a
+    // thread holds one column of A2 for its k1 and writes 8 rows (16 bytes)
+    // per store; with two threads per D1 row each takes 32 / PARTS of the k1
 #pragma unroll
     for (int t = 0; t < G::T1; ++t) {
       float dr[KH], di[KH];
@@ -308,65 +338,42 @@ __global__ void __launch_bounds__(tc_threads<LOG2N>(), 1) tcfft_kernel(const KPa
       const int lr = t * 128 + rt;
       const int b = lr / N2, n2 = lr % N2;
 #pragma unroll
-      for (int j = 0; j < KH; ++j) {
-        const int k1 = part * KH + j;
-        const float2 c = cmul(make_float2(dr[j], di[j]), wtw[j]);
-        tbuf[(b * 32 + k1) * G::TS + n2] = make_float2(c.x * 0.015625f, c.y * 0.015625f);
+      for (int j0 = 0; j0 < KH; j0 += 8) {
+        uint32_t hr[4], lr_[4], hi_[4], li[4];
+#pragma unroll
+        for (int j = 0; j < 8; j += 2) {
+          const float2 c0 = cmul(make_float2(dr[j0 + j], di[j0 + j]), wtw[j0 + j]);
+          const float2 c1 = cmul(make_float2(dr[j0 + j + 1], di[j0 + j + 1]), wtw[j0 + j + 1]);
+          const float r0 = c0.x * 0.015625f, r1 = c1.x * 0.015625f;
+          const float i0 = c0.y * 0.015625f, i1 = c1.y * 0.015625f;
+          if (bf16) {
+            splitbf16x2(r0, r1, hr[j / 2], lr_[j / 2]);
+            splitbf16x2(i0, i1, hi_[j / 2], li[j / 2]);
+          } else {
+            split16x2(r0, r1, hr[j / 2], lr_[j / 2]);
+            split16x2(i0, i1, hi_[j / 2], li[j / 2]);
+          }
+        }
+        const int m = b * 32 + part * KH + j0;           // first of 8 rows
+        unsigned char* img = a2 + (2 * (m >> 7)) * G::A2_BYTES;
+        const int ore = tc_mn_off(m & 127, n2);
+        const int oim = tc_mn_off(m & 127, N2 + n2);
+        *reinterpret_cast<uint4*>(img + ore) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
+        *reinterpret_cast<uint4*>(img + oim) = make_uint4(hi_[0], hi_[1], hi_[2], hi_[3]);
+        if (split) {
+          *reinterpret_cast<uint4*>(img + G::A2_BYTES + ore) = make_uint4(lr_[0], lr_[1], lr_[2], lr_[3]);
+          *reinterpret_cast<uint4*>(img + G::A2_BYTES + oim) = make_uint4(li[0], li[1], li[2], li[3]);
+        }
       }
     }
-    tmem_fence_before();
-    __syncthreads();
-    tmem_fence_after();
-    // ---- stage-2 operands: row (b, k1) = B1[n2][k1], n2 < N2; with two
-    // threads per row, one stores the real half and one the imaginary half
-#pragma unroll
-    for (int t = 0; t < G::T2; ++t) {
-      const int lr = t * 128 + rt;
-      const int b = lr / 32, k1 = lr % 32;
-      float re[N2], im[N2];
-      if constexpr (PARTS == 1) {
-#pragma unroll
-        for (int n2 = 0; n2 < N2; ++n2) {
-          const float2 c = tbuf[(b * 32 + k1) * G::TS + n2];
-          re[n2] = c.x;
-          im[n2] = c.y;
-        }
-        store_row<N2>(a2 + (2 * t) * G::A2_BYTES, a2 + (2 * t + 1) * G::A2_BYTES, rt, re, im, split,
-                      bf16);
-      } else if (part == 0) {
-#pragma unroll
-        for (int n2 = 0; n2 < N2; ++n2) re[n2] = tbuf[(b * 32 + k1) * G::TS + n2].x;
-        store_row<N2, 0, N2>(a2 + (2 * t) * G::A2_BYTES, a2 + (2 * t + 1) * G::A2_BYTES, rt, re, im,
-                             split, bf16);
-      } else {
-#pragma unroll
-        for (int n2 = 0; n2 < N2; ++n2) im[n2] = tbuf[(b * 32 + k1) * G::TS + n2].y;
-        store_row<N2, N2, 2 * N2>(a2 + (2 * t) * G::A2_BYTES, a2 + (2 * t + 1) * G::A2_BYTES, rt, re,
-                                  im, split, bf16);
-      }
+    to_mma();
+    issue_stage2();
+    if (more) {
+      build_stage1(batch + gridDim.x);
+      to_mma();
+      issue_stage1();
     }
-    fence_proxy_async();
-    tmem_fence_before();
-    __syncthreads();
-    tmem_fence_after();
-    if (tid == 0) {
-      for (int t = 0; t < G::T2; ++t)
-        for (int term = 0; term < p.terms; ++term) {
-          const uint32_t abase = smem_u32(a2 + (2 * t + (term == 2 ? 1 : 0)) * G::A2_BYTES);
-          const uint32_t bbase = smem_u32(w2 + (term == 1 ? 1 : 0) * G::W2_BYTES);
-          for (int kc = 0; kc < (2 * N2) / 16; ++kc)
-            umma_f16(tmem + 128 + t * (2 * N2), tc_desc(abase + kc * 256, 2 * N2),
-                     tc_desc(bbase + kc * 256, 2 * N2), umma_idesc(2 * N2, bf16),
-                     (term > 0 || kc > 0) ? 1u : 0u);
-        }
-      umma_commit(smem_u32(bar));
-    }
-    if (!timed_out && !mbar_wait_bounded(smem_u32(bar), phase)) {
-      timed_out = true;
-      latch(p.status, kStTimeout);
-    }
-    phase ^= 1;
-    tmem_fence_after();
+    wait_mma(1);   // stage 2 of this batch
     // ---- output: row (b, k1) holds X[k1 + 32 k2], re at column k2, im at N2 + k2
     const float so = p.inv_sqrtN * 64.f;
 #pragma unroll
@@ -387,10 +394,11 @@ __global__ void __launch_bounds__(tc_threads<LOG2N>(), 1) tcfft_kernel(const KPa
         }
       }
     }
-    tmem_fence_before();
-    __syncthreads();
-    tmem_fence_after();
   }
+  // every thread's last TMEM loads are done before the columns are freed
+  tmem_fence_before();
+  __syncthreads();
+  tmem_fence_after();
   if (warp == 0) tmem_dealloc(tmem, 256);
 }
 
