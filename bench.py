@@ -39,7 +39,8 @@ import synth  # noqa: E402
 
 FALLBACK_HBM_GBS = 6800.0
 KERNEL_SRC = [os.path.join(ROOT, "paper_1901_07499_gb300", "csrc", n)
-              for n in ("lsas_kernels.cuh", "lsas_warp.cuh", "lsas_hyb.cuh", "lsas_pair.cuh")]
+              for n in ("lsas_kernels.cuh", "lsas_warp.cuh", "lsas_hyb.cuh", "lsas_pair.cuh",
+                        "lsas_twin.cuh")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fused_kernel_traffic.json")
 
 
@@ -335,9 +336,13 @@ def fp32_roofline(cfg, F, ms_step, clocks, fma=None, sms=None):
 def fused_kernel_name(cfg):
     """The fused kernel lsas_run_frame launches for this workload (aligned
     rows, as the benchmark's input is)."""
-    if cfg.N == 1024 and cfg.fmt == "sc16" and os.environ.get("LSAS_FUSED_KERNEL") == "tensor":
+    choice = os.environ.get("LSAS_FUSED_KERNEL")
+    if cfg.N == 1024 and cfg.fmt == "sc16" and choice == "tensor":
         return ("hyb_kernel (fused CP strip + FFT + LS + MRC + demap; first FFT pass on the "
                 "CUDA cores, second on tcgen05)")
+    if cfg.N == 1024 and cfg.fmt == "sc16" and choice != "warp":
+        return ("twin_kernel (fused CP strip+FFT+LS+MRC+demap, per-warp pipelines, two "
+                "symbols per step in split real/imaginary form)")
     if cfg.N <= 1024:
         return "warp_kernel (fused CP strip+FFT+LS+MRC+demap, per-warp pipelines)"
     if cfg.fmt == "sc16":

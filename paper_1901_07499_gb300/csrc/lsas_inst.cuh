@@ -5,6 +5,7 @@
 #include "lsas_warp.cuh"
 #include "lsas_hyb.cuh"
 #include "lsas_pair.cuh"
+#include "lsas_twin.cuh"
 
 namespace lsas {
 
@@ -14,8 +15,9 @@ static cudaError_t launch_t(int kind, const KParams& p, int grid, int smem, cuda
   int threads = Geo<LOG2N>::TW;
   int slot = kind;   // entry of the shared-memory attribute cache below
   if (kind == kKindFrame) {
-    // fused receiver: N = 1024 from aligned sc16 rows with the second FFT
-    // pass on the tensor cores; otherwise per-warp pipelines up to N = 1024,
+    // fused receiver: N = 1024 from aligned sc16 rows with two symbols per
+    // step (or, opt-in, the second FFT pass on the tensor cores); otherwise
+    // per-warp pipelines up to N = 1024,
     // pipelines of warp pairs for N = 2048 from sc16 rows and the
     // warp-specialised producer/consumer kernel for N = 2048 from fc32 rows
     if constexpr (LOG2N == 10 && !FC32) {
@@ -24,6 +26,11 @@ static cudaError_t launch_t(int kind, const KParams& p, int grid, int smem, cuda
         threads = kHyThreads;
         smem = kHySmem;
         slot = 3;
+      } else if (p.twin && p.use_tma && (p.mode == kModeRun || p.mode == kModePartial)) {
+        fn = twin_kernel<LOG2N>;
+        slot = 4;
+        threads = kTwThreads;
+        smem = make_twlayout().total;
       } else {
         fn = warp_kernel<LOG2N, FC32>;
         threads = 32 * wgeo_warps(4);
@@ -44,7 +51,7 @@ static cudaError_t launch_t(int kind, const KParams& p, int grid, int smem, cuda
     fn = fft_kernel<LOG2N, FC32>;
   }
   // raise the kernel's dynamic shared memory limit once per device
-  static int limit[4][64] = {};
+  static int limit[5][64] = {};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -53,7 +60,10 @@ static cudaError_t launch_t(int kind, const KParams& p, int grid, int smem, cuda
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) limit[slot][dev] = smem;
   }
-  fn<<<dim3(grid, p.grid_y > 1 ? p.grid_y : 1, p.group_z ? p.groups : 1), threads, smem, st>>>(p);
+  // group layers (partial mode, small batches): the two-symbol kernel groups
+  // the data symbols its own way
+  const int gz = !p.group_z ? 1 : (slot == 4 ? twin_groups(p.D) : p.groups);
+  fn<<<dim3(grid, p.grid_y > 1 ? p.grid_y : 1, gz), threads, smem, st>>>(p);
   return cudaGetLastError();
 }
 

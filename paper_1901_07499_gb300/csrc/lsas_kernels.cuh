@@ -73,6 +73,7 @@ struct KParams {
   const int* offsets_in; //   per frame: preamble start (extraction)
   int fault;             // test hook: 1 = block 0 waits for 16 bytes that never come
   int hybrid;            // N = 1024, sc16, staged: second FFT pass on the tensor cores
+  int twin;              // N = 1024, sc16, staged: two symbols per step (twin_kernel)
   int shard_y;           // partial mode, one launch for all shards: antennas per grid row
                          // blockIdx.y (its first antenna is m0 + blockIdx.y * shard_y, its
                          // partials start at shard blockIdx.y of [G][F][...]); 0 otherwise

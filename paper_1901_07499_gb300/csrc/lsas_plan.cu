@@ -96,6 +96,7 @@ struct lsas_plan_s {
   int pn_len = 0;
   int fault = 0;   // test hook of the bounded waits (lsas_plan_set_fault)
   bool allow_hybrid = false;   // LSAS_FUSED_KERNEL = "tensor" at creation
+  bool twin = true;            // N = 1024 sc16: two symbols per step (LSAS_FUSED_KERNEL)
   void* d_split_scratch = nullptr;   // device address of g_split_scratch on this device
   // lsas_run_frame: the frames after a batch's last whole wave of blocks (all
   // of them, for a batch smaller than one wave) may run split into equal
@@ -390,6 +391,7 @@ void base_params(lsas_plan p, KParams* k) {
   k->status = p->d_status;
   k->fault = p->fault;
   k->hybrid = p->geo.hybrid;
+  k->twin = (p->twin && p->N == 1024 && p->fmt == LSAS_IN_SC16) ? 1 : 0;
   k->tc_w1 = p->d_tc_w1;
   k->M = p->M;
   k->m0 = 0;
@@ -635,11 +637,13 @@ lsas_status lsas_plan_create(int M, int N, int cp_len, int n_sym, int pilot_idx,
     p->prof = e && e[0] == '1';
   }
   {
-    // LSAS_FUSED_KERNEL=tensor runs N = 1024 (sc16) with the second FFT pass
-    // on the tensor cores; the default keeps both passes on the CUDA cores,
-    // which measured faster
+    // Fused kernel for N = 1024 from sc16 rows: by default two symbols per
+    // warp step (twin_kernel); LSAS_FUSED_KERNEL=warp selects one symbol per
+    // step (warp_kernel) and LSAS_FUSED_KERNEL=tensor the second FFT pass on
+    // the tensor cores (hyb_kernel), both measured slower
     const char* e = std::getenv("LSAS_FUSED_KERNEL");
     p->allow_hybrid = e && std::strcmp(e, "tensor") == 0;
+    p->twin = !(e && (std::strcmp(e, "warp") == 0 || std::strcmp(e, "tensor") == 0));
   }
   if (!plan_geometry(M, N, p->D, p->fmt, p->allow_hybrid, &p->geo)) {
     delete p;

@@ -1,0 +1,494 @@
+// lsas_twin.cuh -- fused receiver for N = 1024 from sc16 rows, two OFDM
+// symbols of one antenna per warp step, in split real / imaginary form.
+//
+// One block per frame, 8 warps, each an independent pipeline over antenna
+// rows (warp w takes antennas w, w + 8, ...), as in the per-warp kernel.
+// What differs is the unit of a step: a lane holds 32 points of TWO symbols
+// of its antenna, the real parts of point r of both symbols in one packed
+// register pair and the imaginary parts in another.  Every packed FP32
+// instruction then applies one operation to both symbols: a product by a
+// twiddle takes four packed instructions for two points and no operand
+// rearrangement, a product by -j is a renaming, and each warp has two
+// independent transforms in flight.  The antenna's channel, held in
+// registers, serves both symbols of a step.
+//
+// Per step a warp
+//   * waits for its staging slot (bulk copies of the two CP-stripped rows:
+//     the CP removal of Sec. II-B done as addressing) and refills it two
+//     steps ahead,
+//   * runs the radix-32 pass (the batched FFT of Sec. II-C) in registers,
+//     transposes through its own padded exchange region one plane at a
+//     time (real parts, then imaginary parts), applies the pass twiddles and
+//     runs the second radix-32 pass,
+//   * pilot: LS estimate H = Y conj(X) / |X|^2 (Sec. II-C), written out and
+//     kept in registers, and |H|^2 added to the channel energy (Sec. III);
+//     data symbol: P += conj(H) Y per subcarrier in the warp's tensor-memory
+//     columns (the MRC numerator, Sec. II-C).
+// Data-symbol groups: the pilot with the first three data symbols, then four
+// data symbols at a time (a warp's 256 TMEM columns hold the energy and three
+// symbols' sums, or four symbols' sums), so the 14 rows of a frame with 13
+// data symbols pair up exactly.  At a group's end the block adds the warps'
+// sums in warp order through shared memory, forms z = P / E and demaps
+// (Sec. II-B), or writes the block's partial sums (antenna split).
+#pragma once
+
+#include "lsas_kernels.cuh"
+#include "lsas_warp.cuh"
+
+namespace lsas {
+
+constexpr int kTwWarps = 8;
+constexpr int kTwThreads = 32 * kTwWarps;
+constexpr int kTwSlots = 2;                 // staging slots per warp, two rows each
+constexpr int kTwRow = 1024 * 4;            // one CP-stripped sc16 row
+constexpr int kTwTmemWarp = 256;            // TMEM columns per warp
+constexpr int kTwOwn = 32;                  // subcarriers per lane
+constexpr int kTwDg0 = (kTwTmemWarp - kTwOwn) / (2 * kTwOwn);   // 3: group 0
+constexpr int kTwDg = kTwTmemWarp / (2 * kTwOwn);                // 4: later groups
+constexpr int kTwXS = 1024 + 1024 / 32;     // exchange plane (float2), one pad per 32
+
+// Shared memory: header (mbarriers, TMEM address, flags), the pass twiddles
+// W_1024^(j r) as {wr, wr, wi, wi} at [r * 32 + j], 1/E per subcarrier, the
+// demapped codes of one group, then one region per warp: its staging ring
+// and its exchange plane.  At group ends the per-warp regions together hold
+// the warps' partial sums for the cross-warp reduction.
+struct TwLayout {
+  int tw_off, ie_off, codes_off, warp_off, stage_bytes, warp_bytes, total;
+};
+__host__ __device__ inline TwLayout make_twlayout() {
+  TwLayout l;
+  l.tw_off = kWHeader;
+  l.ie_off = l.tw_off + 1024 * 16;
+  l.codes_off = l.ie_off + 1024 * 4;
+  l.warp_off = align_up(l.codes_off + kTwDg * 1024, 128);
+  l.stage_bytes = kTwSlots * 2 * kTwRow;
+  l.warp_bytes = align_up(l.stage_bytes + kTwXS * 8, 128);
+  l.total = l.warp_off + kTwWarps * l.warp_bytes;
+  return l;
+}
+// data-symbol groups of a frame with D data symbols
+__host__ __device__ inline int twin_groups(int D) {
+  const int rest = D > kTwDg0 ? D - kTwDg0 : 0;
+  return 1 + (rest + kTwDg - 1) / kTwDg;
+}
+
+#ifdef __CUDACC__
+
+// Two complex values, one per symbol of a step: re = {Re a, Re b},
+// im = {Im a, Im b}.
+struct Cx2 {
+  float2 re, im;
+};
+
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+
+// x, y <- x + W_32^e y, x - W_32^e y for a compile-time e in [0, 16), with
+// W_32^e = {cos(2 pi e/32), -sin(2 pi e/32)}; kC[e] = cos(2 pi e / 32) to
+// double precision, rounded once to float (the compiler then takes each
+// constant pair as an immediate or keeps it in registers).
+__device__ __forceinline__ void twin_bfly(Cx2& x, Cx2& y, int e) {
+  constexpr float kS = 0.70710678118654752440f;   // 1/sqrt(2)
+  const Cx2 a = x, b = y;
+  if (e == 0) {
+    x = {cadd(a.re, b.re), cadd(a.im, b.im)};
+    y = {csub(a.re, b.re), csub(a.im, b.im)};
+  } else if (e == 8) {
+    // W = -j: W b = {Im b, -Re b}
+    x = {cadd(a.re, b.im), csub(a.im, b.re)};
+    y = {csub(a.re, b.im), cadd(a.im, b.re)};
+  } else if (e == 4) {
+    // W = (1 - j)/sqrt2: W b = s {Re b + Im b, Im b - Re b}
+    const float2 t = cadd(b.re, b.im), u = csub(b.im, b.re);
+    x = {__ffma2_rn(t, f2(kS), a.re), __ffma2_rn(u, f2(kS), a.im)};
+    y = {__ffma2_rn(t, f2(-kS), a.re), __ffma2_rn(u, f2(-kS), a.im)};
+  } else if (e == 12) {
+    // W = (-1 - j)/sqrt2: W b = s {Im b - Re b, -(Re b + Im b)}
+    const float2 t = cadd(b.re, b.im), u = csub(b.im, b.re);
+    x = {__ffma2_rn(u, f2(kS), a.re), __ffma2_rn(t, f2(-kS), a.im)};
+    y = {__ffma2_rn(u, f2(-kS), a.re), __ffma2_rn(t, f2(kS), a.im)};
+  } else {
+    // W b = {Re b wr - Im b wi, Re b wi + Im b wr}, folded into the sums
+    constexpr float kC[9] = {1.0f,
+                             0.98078528040323043f, 0.92387953251128674f,
+                             0.83146961230254524f, 0.70710678118654757f,
+                             0.55557023301960229f, 0.38268343236508984f,
+                             0.19509032201612833f, 0.0f};
+    const float c = e <= 8 ? kC[e] : -kC[16 - e];
+    const float s = e <= 8 ? kC[8 - e] : kC[e - 8];
+    const float2 wr = f2(c), wi = f2(-s), nwr = f2(-c), nwi = f2(s);
+    x = {__ffma2_rn(b.im, nwi, __ffma2_rn(b.re, wr, a.re)),
+         __ffma2_rn(b.im, wr, __ffma2_rn(b.re, wi, a.im))};
+    y = {__ffma2_rn(b.im, wi, __ffma2_rn(b.re, nwr, a.re)),
+         __ffma2_rn(b.im, nwr, __ffma2_rn(b.re, nwi, a.im))};
+  }
+}
+
+// Radix-2 decimation-in-time stages of half-span S, 2S, ... 16 on 32 points.
+template <int S>
+__device__ __forceinline__ void twin_stages(Cx2 (&a)[32]) {
+  if constexpr (S < 32) {
+#pragma unroll
+    for (int base = 0; base < 32; base += 2 * S) {
+#pragma unroll
+      for (int i = 0; i < S; ++i) twin_bfly(a[base + i], a[base + i + S], i * (16 / S));
+    }
+    twin_stages<2 * S>(a);
+  }
+}
+
+// In-register 32-point DFT of both symbols, natural order in and out: radix-2
+// decimation in time over bit-reversed register indices.
+__device__ __forceinline__ void twin_dft32(float2 (&re)[32], float2 (&im)[32]) {
+  Cx2 a[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) a[i] = {re[brev(i, 5)], im[brev(i, 5)]};
+  twin_stages<1>(a);
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    re[i] = a[i].re;
+    im[i] = a[i].im;
+  }
+}
+
+// Issue the bulk copies of one step (antenna m, symbols sa and sb; sb < 0:
+// one row) into a slot: lane 0 registers the bytes and copies row a, lane 1
+// copies row b.
+__device__ __forceinline__ void twin_issue(const KParams& p, int f, int m, int sa, int sb,
+                                           unsigned char* slot, uint32_t bar, uint64_t pol,
+                                           int lane) {
+  if (lane == 0) {
+    mbar_expect_tx(bar, sb >= 0 ? 2 * kTwRow : kTwRow);
+    bulk_load(smem_u32(slot), row_ptr<10, false>(p, f, m, sa), kTwRow, bar, pol);
+  } else if (lane == 1 && sb >= 0) {
+    bulk_load(smem_u32(slot + kTwRow), row_ptr<10, false>(p, f, m, sb), kTwRow, bar, pol);
+  }
+}
+
+// P += conj(H) Y for one symbol of the step (half 0: .x, half 1: .y) into
+// the 64 accumulator columns at tp (column 2c, 2c + 1 = subcarrier
+// lane + 32 c), as four FMAs per subcarrier.
+template <int HALF, int QC = 16>
+__device__ __forceinline__ void twin_mrc(const float2 (&re)[32], const float2 (&im)[32],
+                                         const float2 (&h)[32], uint32_t tp) {
+  tmem_wait_st();
+#pragma unroll
+  for (int q0 = 0; q0 < 64; q0 += QC) {
+    float acc[QC];
+    Tmem<QC>::ld(tp + q0, acc);
+    tmem_wait_ld();
+#pragma unroll
+    for (int i = 0; i < QC / 2; ++i) {
+      const int e = q0 / 2 + i;
+      const float2 hh = h[e];
+      const float yr = HALF ? re[e].y : re[e].x;
+      const float yi = HALF ? im[e].y : im[e].x;
+      acc[2 * i] = fmaf(hh.x, yr, fmaf(hh.y, yi, acc[2 * i]));
+      acc[2 * i + 1] = fmaf(hh.x, yi, fmaf(-hh.y, yr, acc[2 * i + 1]));
+    }
+    Tmem<QC>::st(tp + q0, acc);
+  }
+}
+
+template <int LOG2N>
+__global__ void __launch_bounds__(kTwThreads, 1) twin_kernel(const KParams p) {
+  static_assert(LOG2N == 10, "the two-symbol kernel is written for N = 1024");
+  constexpr int N = 1 << LOG2N;
+  constexpr int NW = kTwWarps;
+  constexpr int NT = kTwThreads;
+  constexpr int OWN = kTwOwn;
+  constexpr int K = kTwSlots;
+  using TmP = Tmem<2 * OWN>;   // one data symbol of partial sums (complex)
+  using TmE = Tmem<OWN>;       // channel energy
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int f = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const int lane = tid & 31;
+  const TwLayout lay = make_twlayout();
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem) + warp * kMaxSlots;
+  uint32_t* tmem_base = reinterpret_cast<uint32_t*>(smem + kWTmemAddr);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + kWAbort);
+  float4* tws = reinterpret_cast<float4*>(smem + lay.tw_off);
+  float* ie_s = reinterpret_cast<float*>(smem + lay.ie_off);
+  uint8_t* codes = smem + lay.codes_off;
+  unsigned char* stage = smem + lay.warp_off + warp * lay.warp_bytes;
+  float2* ex = reinterpret_cast<float2*>(stage + lay.stage_bytes);
+  constexpr int slot_bytes = 2 * kTwRow;
+
+  for (int i = tid; i < N; i += NT) {
+    const float2 w = __ldg(p.twP + i);
+    tws[i] = make_float4(w.x, w.x, w.y, w.y);
+  }
+  if (tid == 0) *abort_flag = 0;
+  if (lane == 0) {
+    for (int s = 0; s < K; ++s) mbar_init(smem_u32(&bars[s]), 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) tmem_alloc(smem_u32(tmem_base), kWTmemCols);
+  tmem_fence_before();
+  __syncthreads();
+  tmem_fence_after();
+  // this warp's columns: 256 columns of its lane quarter
+  const uint32_t tE = *tmem_base + (static_cast<uint32_t>(32 * (warp & 3)) << 16) +
+                      static_cast<uint32_t>((warp >> 2) * kTwTmemWarp);
+  uint64_t pol = 0;
+  if (lane == 0) pol = evict_first_policy();
+  pol = __shfl_sync(0xffffffffu, pol, 0);
+  float zero[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) zero[i] = 0.f;
+
+  const int nch = warp < p.chunks ? (p.chunks - 1 - warp) / NW + 1 : 0;
+  // start the warps of the upper half a little later, so that the two warps
+  // sharing a scheduler tend to be in different phases of their steps
+  if (warp >= 4) __nanosleep(1400);
+  int issued = 0;  // steps whose copies this warp has issued
+  int slot = 0;    // ring slot of the next step to consume ...
+  int phase = 0;   // ... and its mbarrier phase
+  // one data-symbol group per grid z index (partial mode, small batches):
+  // every group's block transforms the pilot itself; group 0 alone writes H
+  // and the channel energy
+  const int g_lo = p.group_z ? static_cast<int>(blockIdx.z) : 0;
+  const int g_hi = p.group_z ? g_lo + 1 : twin_groups(p.D);
+  for (int g = g_lo; g < g_hi; ++g) {
+    const int d0 = g == 0 ? 0 : kTwDg0 + (g - 1) * kTwDg;
+    const int nd = min(g == 0 ? kTwDg0 : kTwDg, p.D - d0);
+    const bool pilot_here = g == 0 || p.group_z;
+    const bool energy_here = g == 0;
+    const int items = nd + (pilot_here ? 1 : 0);
+    const int npairs = (items + 1) / 2;
+    const uint32_t tP = energy_here ? tE + OWN : tE;   // data symbol dl at tP + 2 OWN dl
+    if (energy_here) {
+#pragma unroll
+      for (int q0 = 0; q0 < OWN; q0 += 16) Tmem<16>::st(tE + q0, zero);
+    }
+    for (int dl = 0; dl < nd; ++dl) {
+#pragma unroll
+      for (int q0 = 0; q0 < 2 * OWN; q0 += 16) Tmem<16>::st(tP + 2 * OWN * dl + q0, zero);
+    }
+    // issue cursor: local chunk and pair of the next step to stage, and how
+    // many steps of this group are still to be staged
+    int ic = 0, ipi = 0;
+    int to_issue = nch * npairs;
+    if (!*abort_flag) {
+      // the ring held generic data (last group's reduction): order it before
+      // the copies, then fill the first K slots of this group
+      fence_proxy_async();
+      int is = slot;
+      for (int s = 0; s < K && to_issue > 0; ++s, --to_issue) {
+        const int ia = 2 * ipi;
+        twin_issue(p, f, warp + ic * NW, witem_symbol(p, pilot_here, d0, ia),
+                   ia + 1 < items ? witem_symbol(p, pilot_here, d0, ia + 1) : -1,
+                   stage + is * slot_bytes, smem_u32(&bars[is]), pol, lane);
+        // test hook: the first staging phase of block 0 also waits for 16
+        // bytes that no copy delivers, so its bounded wait runs out
+        if (p.fault == 1 && blockIdx.x == 0 && warp == 0 && g == 0 && s == 0 && lane == 0)
+          mbar_expect_tx_only(smem_u32(&bars[is]), 16);
+        ++issued;
+        is = (is + 1 == K) ? 0 : is + 1;
+        if (++ipi == npairs) {
+          ipi = 0;
+          ++ic;
+        }
+      }
+    }
+    for (int lc = 0; lc < nch; ++lc) {
+      const int m = warp + lc * NW;
+      const size_t hrow = (static_cast<size_t>(f) * p.Mtot + p.m0 + blockIdx.y * p.shard_y + m) * N;
+      float2 h[32];
+      if (!pilot_here) {
+#pragma unroll
+        for (int e = 0; e < 32; ++e) h[e] = p.H_out[hrow + lane + 32 * e];
+      }
+      for (int ip = 0; ip < npairs; ++ip) {
+        float2 re[32], im[32];
+        wait_slot(smem_u32(&bars[slot]), phase, abort_flag, p.status);
+        // both rows; a missing second row leaves earlier samples in the slot
+        // (finite integers), whose transform is not used
+        const uint32_t* sa = reinterpret_cast<const uint32_t*>(stage + slot * slot_bytes);
+        const uint32_t* sb = sa + kTwRow / 4;
+        {
+#pragma unroll
+          for (int r = 0; r < 32; ++r) {
+            // sc16 -> float exactly: sign bits flipped to offset binary, each
+            // half placed under the exponent bytes of 2^23, one packed
+            // subtraction of 2^23 + 32768
+            const uint32_t ua = sa[lane + 32 * r] ^ 0x80008000u;
+            const uint32_t ub = sb[lane + 32 * r] ^ 0x80008000u;
+            re[r] = __fadd2_rn(make_float2(__uint_as_float(__byte_perm(ua, 0x4b000000u, 0x7610)),
+                                           __uint_as_float(__byte_perm(ub, 0x4b000000u, 0x7610))),
+                               f2(-8421376.0f));
+            im[r] = __fadd2_rn(make_float2(__uint_as_float(__byte_perm(ua, 0x4b000000u, 0x7632)),
+                                           __uint_as_float(__byte_perm(ub, 0x4b000000u, 0x7632))),
+                               f2(-8421376.0f));
+          }
+        }
+        // every lane is done with the slot (and with the exchange of the
+        // previous step): refill the slot K steps ahead
+        __syncwarp();
+        if (to_issue > 0 && !*abort_flag) {
+          ++issued;
+          fence_proxy_async();
+          const int ia = 2 * ipi;
+          twin_issue(p, f, warp + ic * NW, witem_symbol(p, pilot_here, d0, ia),
+                     ia + 1 < items ? witem_symbol(p, pilot_here, d0, ia + 1) : -1,
+                     stage + slot * slot_bytes, smem_u32(&bars[slot]), pol, lane);
+          --to_issue;
+          if (++ipi == npairs) {
+            ipi = 0;
+            ++ic;
+          }
+        }
+        if (++slot == K) {
+          slot = 0;
+          phase ^= 1;
+        }
+        // pass 1: 32-point DFTs over n1 (n = lane + 32 n1)
+        twin_dft32(re, im);
+        // transpose one plane at a time: lane n2 writes its outputs k1 at
+        // n2 * 32 + k1, lane k1 reads n2 = 0..31
+#pragma unroll
+        for (int r = 0; r < 32; ++r) ex[xpad(lane * 32 + r)] = re[r];
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < 32; ++r) re[r] = ex[xpad(lane + 32 * r)];
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < 32; ++r) ex[xpad(lane * 32 + r)] = im[r];
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < 32; ++r) im[r] = ex[xpad(lane + 32 * r)];
+        // pass twiddles W_1024^(n2 k1), n2 = r, k1 = lane
+#pragma unroll
+        for (int r = 1; r < 32; ++r) {
+          const float4 w = tws[r * 32 + lane];
+          const float2 wr = make_float2(w.x, w.y), wi = make_float2(w.z, w.w);
+          const float2 xr = re[r], xi = im[r];
+          re[r] = csub(__fmul2_rn(xr, wr), __fmul2_rn(xi, wi));
+          im[r] = __ffma2_rn(xr, wi, __fmul2_rn(xi, wr));
+        }
+        // pass 2: 32-point DFTs over n2; register e holds bin lane + 32 e
+        twin_dft32(re, im);
+        const int ia = 2 * ip;
+        if (pilot_here && ip == 0) {
+          // first row: the pilot.  LS estimate H = Y conj(X) / |X|^2 (1/sqrt(N)
+          // folded into xinv); group 0 writes it out and adds |H|^2 into the
+          // energy
+#pragma unroll
+          for (int e = 0; e < 32; ++e) {
+            const int k = lane + 32 * e;
+            const float2 hv = cmul(make_float2(re[e].x, im[e].x), __ldg(p.xinv + k));
+            h[e] = hv;
+            if (energy_here) p.H_out[hrow + k] = hv;
+          }
+          if (energy_here) {
+            float acc[OWN];
+            tmem_wait_st();
+            TmE::ld(tE, acc);
+            tmem_wait_ld();
+#pragma unroll
+            for (int e = 0; e < 32; ++e) acc[e] = fmaf(h[e].x, h[e].x, fmaf(h[e].y, h[e].y, acc[e]));
+            TmE::st(tE, acc);
+          }
+        } else {
+          twin_mrc<0>(re, im, h, tP + 2 * OWN * (ia - (pilot_here ? 1 : 0)));
+        }
+        if (ia + 1 < items) twin_mrc<1>(re, im, h, tP + 2 * OWN * (ia + 1 - (pilot_here ? 1 : 0)));
+      }
+    }
+    tmem_wait_st();
+    // ---- group end: every warp's steps are done, every copy of the group
+    // has landed; the per-warp regions are free for the reduction
+    __syncthreads();
+    if (energy_here) {
+      float* RE = reinterpret_cast<float*>(smem + lay.warp_off);   // [NW][N]
+      float e[OWN];
+      TmE::ld(tE, e);
+      tmem_wait_ld();
+#pragma unroll
+      for (int cc = 0; cc < OWN; ++cc) RE[warp * N + lane + 32 * cc] = e[cc];
+      __syncthreads();
+      for (int k = tid; k < N; k += NT) {
+        float E = 0.f;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) E += RE[w * N + k];
+        if (p.mode == kModePartial) {
+          p.E_out[(static_cast<size_t>(blockIdx.y) * gridDim.x + f) * N + k] = E;
+        } else {
+          // zero or non-finite energy flags the frame; z = 0 there
+          const bool ok = (E > 0.f) && (E <= 3.4028234663852886e38f);
+          if (!ok) latch(p.status, kStDevice);
+          ie_s[k] = ok ? (1.0f / E) * p.inv_sqrtN : 0.f;
+        }
+      }
+      __syncthreads();
+    }
+    float2* RP = reinterpret_cast<float2*>(smem + lay.warp_off);   // [NW][dlc][N]
+    const int dlc = lay.warp_bytes / (N * 8);
+    for (int dl0 = 0; dl0 < nd; dl0 += dlc) {
+      const int n = min(dlc, nd - dl0);
+      for (int j = 0; j < n; ++j) {
+        float acc[2 * OWN];
+        TmP::ld(tP + 2 * OWN * (dl0 + j), acc);
+        tmem_wait_ld();
+        float2* dst = RP + static_cast<size_t>(warp * dlc + j) * N;
+#pragma unroll
+        for (int cc = 0; cc < OWN; ++cc)
+          dst[lane + 32 * cc] = make_float2(acc[2 * cc], acc[2 * cc + 1]);
+      }
+      __syncthreads();
+      for (int idx = tid; idx < n * N; idx += NT) {
+        const int j = idx >> 10;
+        const int k = idx & (N - 1);
+        float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int w = 0; w < NW; ++w) s = cadd(s, RP[static_cast<size_t>(w * dlc + j) * N + k]);
+        const int dl = dl0 + j;
+        if (p.mode == kModePartial) {
+          p.P_out[((static_cast<size_t>(blockIdx.y) * gridDim.x + f) * p.D + d0 + dl) * N + k] =
+              make_float2(s.x * p.inv_sqrtN, s.y * p.inv_sqrtN);
+        } else {
+          const float ie = ie_s[k];
+          const float2 z = (ie != 0.f) ? make_float2(s.x * ie, s.y * ie) : make_float2(0.f, 0.f);
+          if (p.eq) p.eq[(static_cast<size_t>(f) * p.D + d0 + dl) * N + k] = z;
+          uint32_t code = gray(axis_level(z.x, p));
+          if (p.axes == 2) code = (code << p.wbits) | gray(axis_level(z.y, p));
+          codes[dl * N + k] = static_cast<uint8_t>(code);
+        }
+      }
+      __syncthreads();
+    }
+    if (p.mode != kModePartial) {
+      // pack: 8 consecutive subcarriers -> q bytes
+      const int items8 = nd * (N / 8);
+      const size_t frame_bytes = static_cast<size_t>(p.D) * N * p.q / 8;
+      for (int it = tid; it < items8; it += NT) {
+        const int dl = it / (N / 8);
+        const int k0 = (it % (N / 8)) * 8;
+        uint64_t acc = 0;
+#pragma unroll
+        for (int bb = 0; bb < 8; ++bb) acc = (acc << p.q) | codes[dl * N + k0 + bb];
+        uint8_t* dst = p.bits + f * frame_bytes + (static_cast<size_t>(d0 + dl) * N + k0) * p.q / 8;
+        for (int jb = 0; jb < p.q; ++jb) dst[jb] = static_cast<uint8_t>(acc >> (8 * (p.q - 1 - jb)));
+      }
+      __syncthreads();   // codes consumed before the next group writes them
+    }
+  }
+  if (lane == 0 && *abort_flag) {
+    // a wait gave up: give any copy of this warp still in flight a bounded
+    // chance to land before the block's shared memory is released (copies
+    // stop being issued after the abort: only the issued steps count)
+    for (int s = 0; s < K && s < issued; ++s) {
+      const int last = issued - 1 - ((issued - 1 - s) % K);
+      (void)mbar_wait_bounded(smem_u32(&bars[last % K]), (last / K) & 1);
+    }
+  }
+  tmem_fence_before();
+  __syncthreads();
+  tmem_fence_after();
+  if (warp == 0) tmem_dealloc(*tmem_base, kWTmemCols);
+}
+
+#endif  // __CUDACC__
+
+}  // namespace lsas

@@ -446,23 +446,24 @@ def test_scale_workload_full_size_host_path(L):
 
 @pytest.mark.parametrize("M", [13, 64])
 def test_tensor_core_and_cuda_core_fused_kernels(L, M, monkeypatch):
-    """N = 1024 with aligned sc16 rows: the default fused kernel (both FFT
-    passes on the CUDA cores) and, with LSAS_FUSED_KERNEL=tensor, the one
-    whose second pass runs on the tensor cores.  Both meet the oracle bars on
-    the same frames (full receiver and lsas_demodulate with the oracle's
-    channel), including an antenna count that leaves some warps of a quad
-    without antennas (M = 13)."""
+    """N = 1024 with aligned sc16 rows: the default fused kernel (two symbols
+    per warp step, both FFT passes on the CUDA cores), with
+    LSAS_FUSED_KERNEL=warp the one-symbol-per-step kernel, and with
+    LSAS_FUSED_KERNEL=tensor the one whose second pass runs on the tensor
+    cores.  All meet the oracle bars on the same frames (full receiver and
+    lsas_demodulate with the oracle's channel), including an antenna count
+    that leaves some warps without a second antenna (M = 13)."""
     cfg = synth.CONFIGS["scale"].replace(M=M)
     b = synth.generate(cfg, frame_ids=range(3))
     ref = oracle_run(cfg, b)
     ref_d = oracle_run(cfg, b, H_given=ref.H)
     x = to_torch_frames(b)
     import torch
-    for kernel in ("tensor", "default"):
-        if kernel == "tensor":
-            monkeypatch.setenv("LSAS_FUSED_KERNEL", "tensor")
-        else:
+    for kernel in ("tensor", "warp", "default"):
+        if kernel == "default":
             monkeypatch.delenv("LSAS_FUSED_KERNEL", raising=False)
+        else:
+            monkeypatch.setenv("LSAS_FUSED_KERNEL", kernel)
         plan = make_plan(L, cfg, max_frames=4)
         H, bits, eq = plan.run_frame(x, want_eq=True)
         assert plan.sync_status() == L.LSAS_OK
