@@ -136,6 +136,29 @@ __device__ __forceinline__ void twin_stages(Cx2 (&a)[32]) {
   }
 }
 
+// Pass 1 of both symbols from offset samples v + c (c = 2^23 + 32768, each
+// an exact float): the first radix-2 stage (twiddle 1) forms a + (b - 2c)
+// and a - b, both exact, so the offset costs one packed subtraction per
+// butterfly instead of one per sample; the other stages as in twin_dft32.
+__device__ __forceinline__ void twin_dft32_offset(float2 (&re)[32], float2 (&im)[32]) {
+  Cx2 a[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) a[i] = {re[brev(i, 5)], im[brev(i, 5)]};
+#pragma unroll
+  for (int i = 0; i < 32; i += 2) {
+    const Cx2 x = a[i], y = a[i + 1];
+    const float2 yr = cadd(y.re, f2(-16842752.0f)), yi = cadd(y.im, f2(-16842752.0f));
+    a[i] = {cadd(x.re, yr), cadd(x.im, yi)};
+    a[i + 1] = {csub(x.re, y.re), csub(x.im, y.im)};
+  }
+  twin_stages<2>(a);
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    re[i] = a[i].re;
+    im[i] = a[i].im;
+  }
+}
+
 // In-register 32-point DFT of both symbols, natural order in and out: radix-2
 // decimation in time over bit-reversed register indices.
 __device__ __forceinline__ void twin_dft32(float2 (&re)[32], float2 (&im)[32]) {
@@ -310,17 +333,15 @@ __global__ void __launch_bounds__(kTwThreads, 1) twin_kernel(const KParams p) {
         {
 #pragma unroll
           for (int r = 0; r < 32; ++r) {
-            // sc16 -> float exactly: sign bits flipped to offset binary, each
-            // half placed under the exponent bytes of 2^23, one packed
-            // subtraction of 2^23 + 32768
+            // sc16 -> float v + 2^23 + 32768 exactly: sign bits flipped to
+            // offset binary, each half placed under the exponent bytes of
+            // 2^23 (the offset leaves in pass 1's first stage)
             const uint32_t ua = sa[lane + 32 * r] ^ 0x80008000u;
             const uint32_t ub = sb[lane + 32 * r] ^ 0x80008000u;
-            re[r] = __fadd2_rn(make_float2(__uint_as_float(__byte_perm(ua, 0x4b000000u, 0x7610)),
-                                           __uint_as_float(__byte_perm(ub, 0x4b000000u, 0x7610))),
-                               f2(-8421376.0f));
-            im[r] = __fadd2_rn(make_float2(__uint_as_float(__byte_perm(ua, 0x4b000000u, 0x7632)),
-                                           __uint_as_float(__byte_perm(ub, 0x4b000000u, 0x7632))),
-                               f2(-8421376.0f));
+            re[r] = make_float2(__uint_as_float(__byte_perm(ua, 0x4b000000u, 0x7610)),
+                                __uint_as_float(__byte_perm(ub, 0x4b000000u, 0x7610)));
+            im[r] = make_float2(__uint_as_float(__byte_perm(ua, 0x4b000000u, 0x7632)),
+                                __uint_as_float(__byte_perm(ub, 0x4b000000u, 0x7632)));
           }
         }
         // every lane is done with the slot (and with the exchange of the
@@ -344,7 +365,7 @@ __global__ void __launch_bounds__(kTwThreads, 1) twin_kernel(const KParams p) {
           phase ^= 1;
         }
         // pass 1: 32-point DFTs over n1 (n = lane + 32 n1)
-        twin_dft32(re, im);
+        twin_dft32_offset(re, im);
         // transpose one plane at a time: lane n2 writes its outputs k1 at
         // n2 * 32 + k1, lane k1 reads n2 = 0..31
 #pragma unroll
