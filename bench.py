@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fma-peak", action="store_true",
                     help="skip the FP32 FMA peak measurement (roofline_fp32 then nominal)")
+    ap.add_argument("--sweep", action="store_true",
+                    help="throughput over the antenna x FFT-length grid (one JSON line per shape)")
+    ap.add_argument("--sweep-steps", type=int, default=10, help="timed steps per sweep shape")
     ap.add_argument("--host-link", action="store_true",
                     help="host<->device copy bandwidth report (one JSON line per path)")
     ap.add_argument("--serving", action="store_true",
@@ -667,6 +670,71 @@ def denoiser_report(args):
         sys.stdout.flush()
 
 
+def sweep_shapes():
+    """The antenna x FFT-length grid of the scale workload (CP = N/8) and the
+    paper's own (N, CP) shapes (64, 16) and (1024, 72) at 16 antennas."""
+    grid = [synth.frames.sweep_config(M, N) for M in (8, 16, 32, 64, 128)
+            for N in (64, 256, 512, 1024, 2048)]
+    return grid + [synth.frames.paper_config(16, 64), synth.frames.paper_config(16, 1024)]
+
+
+def sweep_report(args):
+    """Throughput of lsas_run_frame over the sweep shapes, one JSON line per
+    shape.  A step is one call over four waves of frames (4 x SMs, one block
+    per frame, so no batch split), tiled from 4 seeded frames; the L2 is
+    flushed (a 256 MB write) before each timed step, and each step is timed
+    alone with CUDA events on the launching stream; the line reports the
+    median of the steps."""
+    import torch
+    import paper_1901_07499_gb300.lsas as lsas
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    F = args.frames or 4 * sms
+    steps = args.sweep_steps
+    peak, peak_src = measured_peaks()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for cfg in sweep_shapes():
+        b = synth.generate(cfg.replace(F=4), frame_ids=range(4))
+        plan = lsas.Plan(cfg.M, cfg.N, cfg.cp, cfg.S, cfg.pilot_idx, cfg.Q, fmt=cfg.fmt,
+                         max_frames=F, pilot=b.pilot)
+        xp = torch.from_numpy(np.ascontiguousarray(b.frames)).cuda()
+        x = xp.repeat((F + 3) // 4, 1, 1, 1)[:F].contiguous()
+        del xp
+        H, bits = plan.empty_H(F), plan.empty_bits(F)
+        for _ in range(max(args.warmup, 3)):
+            plan.run_frame(x, H, bits)
+        plan.sync()
+        times = []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plan.run_frame(x, H, bits)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        plan.sync()
+        ms = statistics.median(times)
+        in_b, h_b, bit_b, _ = lsas.frame_bytes(cfg.M, cfg.N, cfg.cp, cfg.S, cfg.Q, cfg.fmt)
+        alg = F * (in_b + h_b + bit_b)
+        print(json.dumps({
+            "mode": "sweep", "shape": cfg.name, "M": cfg.M, "N": cfg.N, "cp": cfg.cp,
+            "n_sym": cfg.S, "qam": cfg.Q, "input": cfg.fmt, "frames": F,
+            "kernel": fused_kernel_name(cfg).split(" ")[0], "launches": plan.run_frame_launches(F),
+            "ms_per_step": ms, "metric": "antenna*subcarrier samples/s",
+            "value": F * cfg.M * cfg.S * cfg.N / (ms * 1e-3),
+            "us_per_frame": ms * 1e3 / F,
+            "roofline": {"bound": "hbm", "achieved": alg / (ms * 1e-3) / 1e9, "peak": peak,
+                         "unit": "GB/s", "frac": alg / (ms * 1e-3) / 1e9 / peak,
+                         "peak_source": peak_src,
+                         "algorithmic_bytes_per_frame": in_b + h_b + bit_b},
+            "l2": "flushed before each timed step"}), flush=True)
+        plan.close()
+        del x, H, bits
+        torch.cuda.empty_cache()
+    return 0
+
+
 def host_link_report(args):
     """Bandwidth of this machine's host<->device link, which bounds the e2e
     figure: 1 GiB from pinned host memory to the device through the copy
@@ -716,6 +784,8 @@ def main():
     cfg = synth.config_by_name(args.config)
     if args.host_link:
         return host_link_report(args)
+    if args.sweep:
+        return sweep_report(args)
     if args.serving:
         return serving_report(args)
     if args.denoiser:

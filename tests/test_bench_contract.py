@@ -8,6 +8,8 @@
   nominal) SMs x 128 lanes x 2 flop x clock when there is none.
 * roofline.traffic: the committed capture's bytes scaled by frames while the
   kernel source hash and workload match, None otherwise.
+* --sweep: the antenna x FFT-length grid of the scale workload (CP = N/8)
+  and the paper's own (N, CP) shapes.
 """
 
 import json
@@ -74,3 +76,13 @@ def test_traffic_follows_the_source_hash(monkeypatch):
     assert bench.ncu_traffic(synth.config_by_name("tiny"), 1000) is None   # other workload
     monkeypatch.setattr(bench, "kernel_hash", lambda: "0" * 16)
     assert bench.ncu_traffic(cfg, 1000) is None                           # kernel changed
+
+
+def test_sweep_shapes_cover_the_grid():
+    shapes = bench.sweep_shapes()
+    grid = {(c.M, c.N, c.cp) for c in shapes[:-2]}
+    assert grid == {(M, N, N // 8) for M in (8, 16, 32, 64, 128) for N in (64, 256, 512, 1024, 2048)}
+    assert [(c.M, c.N, c.cp) for c in shapes[-2:]] == [(16, 64, 16), (16, 1024, 72)]
+    scale = synth.CONFIGS["scale"]
+    for c in shapes:
+        assert (c.S, c.Q, c.fmt, c.pilot_idx) == (scale.S, scale.Q, scale.fmt, scale.pilot_idx)
