@@ -14,12 +14,11 @@
 //
 // Per step a warp
 //   * waits for its staging slot (bulk copies of the two CP-stripped rows:
-//     the CP removal of Sec. II-B done as addressing) and refills it two
-//     steps ahead,
+//     the CP removal of Sec. II-B done as addressing),
 //   * runs the radix-32 pass (the batched FFT of Sec. II-C) in registers,
-//     transposes through its own padded exchange region one plane at a
-//     time (real parts, then imaginary parts), applies the pass twiddles and
-//     runs the second radix-32 pass,
+//     transposes through the slot it has just read and its own exchange
+//     region, refills the slot, applies the pass twiddles and runs the
+//     second radix-32 pass,
 //   * pilot: LS estimate H = Y conj(X) / |X|^2 (Sec. II-C), written out and
 //     kept in registers, and |H|^2 added to the channel energy (Sec. III);
 //     data symbol: P += conj(H) Y per subcarrier in the warp's tensor-memory
@@ -45,12 +44,19 @@ constexpr int kTwTmemWarp = 256;            // TMEM columns per warp
 constexpr int kTwOwn = 32;                  // subcarriers per lane
 constexpr int kTwDg0 = (kTwTmemWarp - kTwOwn) / (2 * kTwOwn);   // 3: group 0
 constexpr int kTwDg = kTwTmemWarp / (2 * kTwOwn);                // 4: later groups
-constexpr int kTwXS = 1024 + 1024 / 32;     // exchange plane (float2), one pad per 32
+// The exchange between the passes is one round of 16-byte stores of
+// {Re a, Re b, Im a, Im b} per point: row n2 (32 points, 528 bytes with a
+// 16-byte pad, so that both the row stores and the column loads are free of
+// bank conflicts) goes to the slot just read for n2 < 16 and to the warp's
+// exchange region for n2 >= 16.
+constexpr int kTwXRow = 32 * 16 + 16;       // one padded exchange row
+constexpr int kTwSlotB = 16 * kTwXRow;      // a slot: two sc16 rows, or 16 exchange rows
+constexpr int kTwXS = 16 * kTwXRow / 8;     // exchange region (float2): the other 16 rows
 
 // Shared memory: header (mbarriers, TMEM address, flags), the pass twiddles
 // W_1024^(j r) as {wr, wr, wi, wi} at [r * 32 + j], 1/E per subcarrier, the
 // demapped codes of one group, then one region per warp: its staging ring
-// and its exchange plane.  At group ends the per-warp regions together hold
+// (two slots) and its exchange region.  At group ends the per-warp regions together hold
 // the warps' partial sums for the cross-warp reduction.
 struct TwLayout {
   int tw_off, ie_off, codes_off, warp_off, stage_bytes, warp_bytes, total;
@@ -61,7 +67,7 @@ __host__ __device__ inline TwLayout make_twlayout() {
   l.ie_off = l.tw_off + 1024 * 16;
   l.codes_off = l.ie_off + 1024 * 4;
   l.warp_off = align_up(l.codes_off + kTwDg * 1024, 128);
-  l.stage_bytes = kTwSlots * 2 * kTwRow;
+  l.stage_bytes = kTwSlots * kTwSlotB;
   l.warp_bytes = align_up(l.stage_bytes + kTwXS * 8, 128);
   l.total = l.warp_off + kTwWarps * l.warp_bytes;
   return l;
@@ -236,7 +242,7 @@ __global__ void __launch_bounds__(kTwThreads, 1) twin_kernel(const KParams p) {
   uint8_t* codes = smem + lay.codes_off;
   unsigned char* stage = smem + lay.warp_off + warp * lay.warp_bytes;
   float2* ex = reinterpret_cast<float2*>(stage + lay.stage_bytes);
-  constexpr int slot_bytes = 2 * kTwRow;
+  constexpr int slot_bytes = kTwSlotB;
 
   for (int i = tid; i < N; i += NT) {
     const float2 w = __ldg(p.twP + i);
@@ -344,8 +350,32 @@ __global__ void __launch_bounds__(kTwThreads, 1) twin_kernel(const KParams p) {
                                 __uint_as_float(__byte_perm(ub, 0x4b000000u, 0x7632)));
           }
         }
-        // every lane is done with the slot (and with the exchange of the
-        // previous step): refill the slot K steps ahead
+        unsigned char* const yslot = stage + slot * slot_bytes;
+        const uint32_t ybar = smem_u32(&bars[slot]);
+        if (++slot == K) {
+          slot = 0;
+          phase ^= 1;
+        }
+        // pass 1: 32-point DFTs over n1 (n = lane + 32 n1)
+        twin_dft32_offset(re, im);
+        // every lane is done with the exchange of the previous step (and with
+        // this step's slot): transpose in one round of 16-byte stores, rows
+        // n2 < 16 in the slot just read, the others in the exchange region
+        __syncwarp();
+        {
+          unsigned char* wrow = (lane < 16 ? yslot : reinterpret_cast<unsigned char*>(ex)) + (lane & 15) * kTwXRow;
+#pragma unroll
+          for (int r = 0; r < 32; ++r)
+            *reinterpret_cast<float4*>(wrow + 16 * r) = make_float4(re[r].x, re[r].y, im[r].x, im[r].y);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+          const float4 v = *reinterpret_cast<const float4*>(
+              (r < 16 ? yslot : reinterpret_cast<const unsigned char*>(ex)) + (r & 15) * kTwXRow + 16 * lane);
+          re[r] = make_float2(v.x, v.y);
+          im[r] = make_float2(v.z, v.w);
+        }
         __syncwarp();
         if (to_issue > 0 && !*abort_flag) {
           ++issued;
@@ -353,32 +383,13 @@ __global__ void __launch_bounds__(kTwThreads, 1) twin_kernel(const KParams p) {
           const int ia = 2 * ipi;
           twin_issue(p, f, warp + ic * NW, witem_symbol(p, pilot_here, d0, ia),
                      ia + 1 < items ? witem_symbol(p, pilot_here, d0, ia + 1) : -1,
-                     stage + slot * slot_bytes, smem_u32(&bars[slot]), pol, lane);
+                     yslot, ybar, pol, lane);
           --to_issue;
           if (++ipi == npairs) {
             ipi = 0;
             ++ic;
           }
         }
-        if (++slot == K) {
-          slot = 0;
-          phase ^= 1;
-        }
-        // pass 1: 32-point DFTs over n1 (n = lane + 32 n1)
-        twin_dft32_offset(re, im);
-        // transpose one plane at a time: lane n2 writes its outputs k1 at
-        // n2 * 32 + k1, lane k1 reads n2 = 0..31
-#pragma unroll
-        for (int r = 0; r < 32; ++r) ex[xpad(lane * 32 + r)] = re[r];
-        __syncwarp();
-#pragma unroll
-        for (int r = 0; r < 32; ++r) re[r] = ex[xpad(lane + 32 * r)];
-        __syncwarp();
-#pragma unroll
-        for (int r = 0; r < 32; ++r) ex[xpad(lane * 32 + r)] = im[r];
-        __syncwarp();
-#pragma unroll
-        for (int r = 0; r < 32; ++r) im[r] = ex[xpad(lane + 32 * r)];
         // pass twiddles W_1024^(n2 k1), n2 = r, k1 = lane
 #pragma unroll
         for (int r = 1; r < 32; ++r) {
