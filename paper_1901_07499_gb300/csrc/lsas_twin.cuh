@@ -22,7 +22,8 @@
 //   * pilot: LS estimate H = Y conj(X) / |X|^2 (Sec. II-C), written out and
 //     kept in registers, and |H|^2 added to the channel energy (Sec. III);
 //     data symbol: P += conj(H) Y per subcarrier in the warp's tensor-memory
-//     columns (the MRC numerator, Sec. II-C).
+//     columns (the MRC numerator, Sec. II-C); for two data symbols as four
+//     packed FMAs per subcarrier on their interleaved columns.
 // Data-symbol groups: the pilot with the first three data symbols, then four
 // data symbols at a time (a warp's 256 TMEM columns hold the energy and three
 // symbols' sums, or four symbols' sums), so the 14 rows of a frame with 13
@@ -218,6 +219,44 @@ __device__ __forceinline__ void twin_mrc(const float2 (&re)[32], const float2 (&
   }
 }
 
+// P += conj(H) Y for both symbols of a step into the 128 interleaved
+// columns at tp (4c: Re a, 4c + 1: Re b, 4c + 2: Im a, 4c + 3: Im b for
+// subcarrier lane + 32 c): the symbols' values are already packed pairs, so
+// four packed FMAs per subcarrier, in the scalar form's order of operations.
+__device__ __forceinline__ void twin_mrc2(const float2 (&re)[32], const float2 (&im)[32],
+                                          const float2 (&h)[32], uint32_t tp) {
+  tmem_wait_st();
+#pragma unroll
+  for (int q0 = 0; q0 < 128; q0 += 32) {
+    float acc[32];
+    Tmem<32>::ld(tp + q0, acc);
+    tmem_wait_ld();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int e = q0 / 4 + i;
+      const float2 hr = f2(h[e].x), hi = f2(h[e].y), nhi = f2(-h[e].y);
+      const float2 pr = __ffma2_rn(hr, re[e], __ffma2_rn(hi, im[e], make_float2(acc[4 * i], acc[4 * i + 1])));
+      const float2 pi = __ffma2_rn(hr, im[e], __ffma2_rn(nhi, re[e], make_float2(acc[4 * i + 2], acc[4 * i + 3])));
+      acc[4 * i] = pr.x;
+      acc[4 * i + 1] = pr.y;
+      acc[4 * i + 2] = pi.x;
+      acc[4 * i + 3] = pi.y;
+    }
+    Tmem<32>::st(tp + q0, acc);
+  }
+}
+
+// Accumulator columns of item `it` of a group (data items only; the pilot,
+// when the group transforms it, is item 0), relative to the group's first
+// partial-sum column: a step whose two items are both data symbols keeps
+// them interleaved in 128 columns (twin_mrc2), a data item alone in its step
+// (beside the pilot, or last of an odd count) 64 columns (2c: Re, 2c + 1: Im).
+__device__ __forceinline__ int twin_block_col(int it, bool pilot, bool* pair, int items) {
+  const int ip = it >> 1;
+  *pair = !(pilot && ip == 0) && (2 * ip + 1 < items);
+  return pilot ? (ip == 0 ? 0 : 64 + 128 * (ip - 1)) : 128 * ip;
+}
+
 template <int LOG2N>
 __global__ void __launch_bounds__(kTwThreads, 1) twin_kernel(const KParams p) {
   static_assert(LOG2N == 10, "the two-symbol kernel is written for N = 1024");
@@ -291,10 +330,7 @@ __global__ void __launch_bounds__(kTwThreads, 1) twin_kernel(const KParams p) {
 #pragma unroll
       for (int q0 = 0; q0 < OWN; q0 += 16) Tmem<16>::st(tE + q0, zero);
     }
-    for (int dl = 0; dl < nd; ++dl) {
-#pragma unroll
-      for (int q0 = 0; q0 < 2 * OWN; q0 += 16) Tmem<16>::st(tP + 2 * OWN * dl + q0, zero);
-    }
+    for (uint32_t c = tP; c < tE + kTwTmemWarp; c += 16) Tmem<16>::st(c, zero);
     // issue cursor: local chunk and pair of the next step to stage, and how
     // many steps of this group are still to be staged
     int ic = 0, ipi = 0;
@@ -422,10 +458,17 @@ __global__ void __launch_bounds__(kTwThreads, 1) twin_kernel(const KParams p) {
             for (int e = 0; e < 32; ++e) acc[e] = fmaf(h[e].x, h[e].x, fmaf(h[e].y, h[e].y, acc[e]));
             TmE::st(tE, acc);
           }
+          bool pr;
+          if (1 < items) twin_mrc<1>(re, im, h, tP + twin_block_col(1, true, &pr, items));
         } else {
-          twin_mrc<0>(re, im, h, tP + 2 * OWN * (ia - (pilot_here ? 1 : 0)));
+          bool pr;
+          const uint32_t tb = tP + twin_block_col(ia, pilot_here, &pr, items);
+          if (pr) {
+            twin_mrc2(re, im, h, tb);
+          } else {
+            twin_mrc<0>(re, im, h, tb);
+          }
         }
-        if (ia + 1 < items) twin_mrc<1>(re, im, h, tP + 2 * OWN * (ia + 1 - (pilot_here ? 1 : 0)));
       }
     }
     tmem_wait_st();
@@ -460,13 +503,29 @@ __global__ void __launch_bounds__(kTwThreads, 1) twin_kernel(const KParams p) {
     for (int dl0 = 0; dl0 < nd; dl0 += dlc) {
       const int n = min(dlc, nd - dl0);
       for (int j = 0; j < n; ++j) {
-        float acc[2 * OWN];
-        TmP::ld(tP + 2 * OWN * (dl0 + j), acc);
-        tmem_wait_ld();
+        const int it = dl0 + j + (pilot_here ? 1 : 0);
+        bool pr;
+        const uint32_t tb = tP + twin_block_col(it, pilot_here, &pr, items);
         float2* dst = RP + static_cast<size_t>(warp * dlc + j) * N;
+        if (pr) {
+          const int hf = it & 1;
 #pragma unroll
-        for (int cc = 0; cc < OWN; ++cc)
-          dst[lane + 32 * cc] = make_float2(acc[2 * cc], acc[2 * cc + 1]);
+          for (int q0 = 0; q0 < 128; q0 += 32) {
+            float t[32];
+            Tmem<32>::ld(tb + q0, t);
+            tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+              dst[lane + 32 * (q0 / 4 + i)] = make_float2(hf ? t[4 * i + 1] : t[4 * i], hf ? t[4 * i + 3] : t[4 * i + 2]);
+          }
+        } else {
+          float acc[2 * OWN];
+          TmP::ld(tb, acc);
+          tmem_wait_ld();
+#pragma unroll
+          for (int cc = 0; cc < OWN; ++cc)
+            dst[lane + 32 * cc] = make_float2(acc[2 * cc], acc[2 * cc + 1]);
+        }
       }
       __syncthreads();
       for (int idx = tid; idx < n * N; idx += NT) {
