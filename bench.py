@@ -38,9 +38,16 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_SRC = [os.path.join(ROOT, "paper_1901_07499_gb300", "csrc", n)
-              for n in ("lsas_kernels.cuh", "lsas_warp.cuh", "lsas_hyb.cuh", "lsas_pair.cuh",
-                        "lsas_twin.cuh")]
+CSRC = os.path.join(ROOT, "paper_1901_07499_gb300", "csrc")
+# the sources of each fused kernel (its own file, the shared helpers and the
+# per-warp kernel's item walk), whose hash keys a committed traffic capture
+KERNEL_SRC = {
+    "twin_kernel": ("lsas_kernels.cuh", "lsas_warp.cuh", "lsas_twin.cuh"),
+    "warp_kernel": ("lsas_kernels.cuh", "lsas_warp.cuh"),
+    "hyb_kernel": ("lsas_kernels.cuh", "lsas_warp.cuh", "lsas_hyb.cuh"),
+    "pair_kernel": ("lsas_kernels.cuh", "lsas_warp.cuh", "lsas_pair.cuh"),
+    "frame_kernel": ("lsas_kernels.cuh",),
+}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fused_kernel_traffic.json")
 
 
@@ -112,10 +119,11 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_hash():
+def kernel_hash(kernel):
+    """Hash of the sources of one fused kernel (a name of KERNEL_SRC)."""
     h = hashlib.sha256()
-    for path in KERNEL_SRC:
-        with open(path, "rb") as fh:
+    for name in KERNEL_SRC[kernel]:
+        with open(os.path.join(CSRC, name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
@@ -128,7 +136,8 @@ def ncu_traffic(cfg, frames):
         with open(TRAFFIC_FILE) as fh:
             d = json.load(fh)
         for e in (d if isinstance(d, list) else [d]):
-            if e.get("kernel_sha") == kernel_hash() and e.get("workload") == cfg.name:
+            if (e.get("workload") == cfg.name and
+                    e.get("kernel_sha") == kernel_hash(fused_kernel_name(cfg).split(" ")[0])):
                 return float(e["dram_bytes_per_frame"]) * frames
         return None
     except Exception:

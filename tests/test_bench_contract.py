@@ -71,10 +71,10 @@ def test_traffic_follows_the_source_hash(monkeypatch):
         recs = json.load(fh)
     recs = recs if isinstance(recs, list) else [recs]
     rec = next(r for r in recs if r["workload"] == "scale")
-    monkeypatch.setattr(bench, "kernel_hash", lambda: rec["kernel_sha"])
+    monkeypatch.setattr(bench, "kernel_hash", lambda kernel: rec["kernel_sha"])
     assert bench.ncu_traffic(cfg, 1000) == pytest.approx(rec["dram_bytes_per_frame"] * 1000)
     assert bench.ncu_traffic(synth.config_by_name("tiny"), 1000) is None   # other workload
-    monkeypatch.setattr(bench, "kernel_hash", lambda: "0" * 16)
+    monkeypatch.setattr(bench, "kernel_hash", lambda kernel: "0" * 16)
     assert bench.ncu_traffic(cfg, 1000) is None                           # kernel changed
 
 
