@@ -5,8 +5,8 @@ Covers the whole path (lsas_run_frame), each step alone (lsas_fft = CP
 removal + FFT, lsas_estimate = LS, lsas_demodulate = MRC + demap with the
 oracle's channel), the antenna-count x FFT-length grid, odd shapes (M not a
 multiple of the antennas per block, M = 1, M = 256, one data symbol,
-CP = N - 1, pilot not first, the paper's
-CP 72, a CP that defeats the bulk-copy alignment, BPSK and 256-QAM, float32
+CP = N - 1, pilot not first, the two-symbol kernel's step pairings and
+group layers, the paper's CP 72, a CP that defeats the bulk-copy alignment, BPSK and 256-QAM, float32
 input), full-scale amplitudes, the zero-energy status, argument errors,
 the host-buffer entry point, determinism, and the 1000-frame 64-antenna
 N=1024 workload in the launch configuration the benchmark times (device
@@ -129,6 +129,43 @@ def test_maximum_antenna_count(L, M, N, F):
 def test_fewest_symbols(L, N, S):
     """One pilot and one (or two) data symbols: a single data-symbol group."""
     run_and_check(L, sweep_config(16, N).replace(S=S), F=3)
+
+
+@pytest.mark.parametrize("M,S,pilot_idx", [
+    (1, 2, 0), (9, 3, 2), (13, 4, 0), (64, 5, 4), (16, 6, 3), (24, 9, 0), (40, 14, 7),
+    (72, 17, 16)])
+def test_two_symbol_kernel_groupings(L, M, S, pilot_idx):
+    """N = 1024 from aligned sc16 rows runs the two-symbol kernel, whose steps
+    pair up the rows of a data-symbol group (the pilot with the first three
+    data symbols, then four at a time): odd item counts leave a step with one
+    row, a data symbol beside the pilot or alone accumulates on its own
+    columns and the others interleaved in pairs; idle warps (M < 8, M not a
+    multiple of 8), one to sixteen data symbols, the pilot anywhere."""
+    run_and_check(L, sweep_config(M, 1024).replace(S=S, pilot_idx=pilot_idx), F=2)
+
+
+@pytest.mark.parametrize("S,pilot_idx", [(17, 5), (6, 0)])
+def test_two_symbol_kernel_group_layers(L, S, pilot_idx):
+    """The one-launch antenna split of a small batch gives every data-symbol
+    group its own block (each transforms the pilot, group 0 alone writes H and
+    the energy): against the oracle, and H equal to the unsplit call's."""
+    import torch
+    cfg = sweep_config(16, 1024).replace(S=S, pilot_idx=pilot_idx)
+    F, G = 2, 2
+    b = synth.generate(cfg, frame_ids=range(F))
+    plan = make_plan(L, cfg, max_frames=4)
+    x = to_torch_frames(b)
+    H, bits, eq = plan.empty_H(F), plan.empty_bits(F), plan.empty_eq(F)
+    st = L.lsas_run_frame_split_static(plan.handle, x.data_ptr(), F, G, H.data_ptr(),
+                                       bits.data_ptr(), eq.data_ptr(),
+                                       torch.cuda.current_stream().cuda_stream)
+    assert st == L.LSAS_OK
+    assert plan.sync_status() == L.LSAS_OK
+    ref = oracle_run(cfg, b)
+    check_frame_outputs(cfg, ref, H.cpu().numpy(), bits.cpu().numpy(), eq.cpu().numpy())
+    H1, _, _ = plan.run_frame(x)
+    plan.sync()
+    assert torch.equal(H, H1)
 
 
 @pytest.mark.parametrize("N", [64, 1024, 2048])
