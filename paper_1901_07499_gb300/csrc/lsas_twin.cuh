@@ -89,94 +89,102 @@ struct Cx2 {
 
 __device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
 
-// x, y <- x + W_32^e y, x - W_32^e y for a compile-time e in [0, 16), with
-// W_32^e = {cos(2 pi e/32), -sin(2 pi e/32)}; kC[e] = cos(2 pi e / 32) to
-// double precision, rounded once to float (the compiler then takes each
-// constant pair as an immediate or keeps it in registers).
-__device__ __forceinline__ void twin_bfly(Cx2& x, Cx2& y, int e) {
+// cos(2 pi e / 32) for a compile-time e, from the first octant: kC[e] =
+// cos(2 pi e / 32) to double precision, rounded once to float.
+__device__ __forceinline__ float twin_cos32(int e) {
+  constexpr float kC[9] = {1.0f,
+                           0.98078528040323043f, 0.92387953251128674f,
+                           0.83146961230254524f, 0.70710678118654757f,
+                           0.55557023301960229f, 0.38268343236508984f,
+                           0.19509032201612833f, 0.0f};
+  e &= 31;
+  return e <= 8 ? kC[e] : e <= 16 ? -kC[16 - e] : e <= 24 ? -kC[e - 16] : kC[32 - e];
+}
+
+// W_32^e z for a compile-time e: W = {c, -s}, W z = {Re z c + Im z s,
+// Im z c - Re z s}, four packed instructions.
+__device__ __forceinline__ Cx2 twin_wmul(const Cx2& z, int e) {
+  const float c = twin_cos32(e), s = twin_cos32(8 - e);
+  return {__ffma2_rn(z.im, f2(s), __fmul2_rn(z.re, f2(c))),
+          __ffma2_rn(z.re, f2(-s), __fmul2_rn(z.im, f2(c)))};
+}
+
+// The split-radix step of an N-point DFT (Sec. II-C's FFT, split radix):
+// with U the N/2-point DFT of the even samples and Z, Z' the N/4-point DFTs
+// of samples 4n + 1 and 4n + 3, for k < N/4 and a = W_N^k Z[k],
+// b = W_N^3k Z'[k]:  X[k] = U[k] + (a + b), X[k + N/2] = U[k] - (a + b),
+// X[k + N/4] = U[k + N/4] - j (a - b), X[k + 3N/4] = U[k + N/4] + j (a - b),
+// in place on x0..x3 = U[k], U[k + N/4], Z[k], Z'[k].  OFS: Z and Z' are raw
+// samples carrying the offset c (N = 4), removed from their sum.
+template <int N, bool OFS>
+__device__ __forceinline__ void twin_lbfly(Cx2& x0, Cx2& x1, Cx2& x2, Cx2& x3, int k) {
   constexpr float kS = 0.70710678118654752440f;   // 1/sqrt(2)
-  const Cx2 a = x, b = y;
-  if (e == 0) {
-    x = {cadd(a.re, b.re), cadd(a.im, b.im)};
-    y = {csub(a.re, b.re), csub(a.im, b.im)};
-  } else if (e == 8) {
-    // W = -j: W b = {Im b, -Re b}
-    x = {cadd(a.re, b.im), csub(a.im, b.re)};
-    y = {csub(a.re, b.im), cadd(a.im, b.re)};
-  } else if (e == 4) {
-    // W = (1 - j)/sqrt2: W b = s {Re b + Im b, Im b - Re b}
-    const float2 t = cadd(b.re, b.im), u = csub(b.im, b.re);
-    x = {__ffma2_rn(t, f2(kS), a.re), __ffma2_rn(u, f2(kS), a.im)};
-    y = {__ffma2_rn(t, f2(-kS), a.re), __ffma2_rn(u, f2(-kS), a.im)};
-  } else if (e == 12) {
-    // W = (-1 - j)/sqrt2: W b = s {Im b - Re b, -(Re b + Im b)}
-    const float2 t = cadd(b.re, b.im), u = csub(b.im, b.re);
-    x = {__ffma2_rn(u, f2(kS), a.re), __ffma2_rn(t, f2(-kS), a.im)};
-    y = {__ffma2_rn(u, f2(-kS), a.re), __ffma2_rn(t, f2(kS), a.im)};
+  const int e = k * (32 / N);                      // W_N^k = W_32^e
+  const Cx2 U = x0, U2 = x1, Z = x2, Z2 = x3;
+  if (e == 4) {
+    // W_8 and W_8^3: a = s {Re Z + Im Z, Im Z - Re Z}, b = s {u, -t} with
+    // u = Im Z' - Re Z', t = Re Z' + Im Z'; the scale s = 1/sqrt2 enters the sums
+    const float2 ar = cadd(Z.re, Z.im), ai = csub(Z.im, Z.re);
+    const float2 u = csub(Z2.im, Z2.re), t = cadd(Z2.re, Z2.im);
+    const float2 sr = cadd(ar, u), si = csub(ai, t), dr = csub(ar, u), di = cadd(ai, t);
+    x0 = {__ffma2_rn(sr, f2(kS), U.re), __ffma2_rn(si, f2(kS), U.im)};
+    x2 = {__ffma2_rn(sr, f2(-kS), U.re), __ffma2_rn(si, f2(-kS), U.im)};
+    x1 = {__ffma2_rn(di, f2(kS), U2.re), __ffma2_rn(dr, f2(-kS), U2.im)};
+    x3 = {__ffma2_rn(di, f2(-kS), U2.re), __ffma2_rn(dr, f2(kS), U2.im)};
+    return;
+  }
+  Cx2 s, d;
+  if (k == 0) {
+    const Cx2 b = OFS ? Cx2{cadd(Z2.re, f2(-16842752.0f)), cadd(Z2.im, f2(-16842752.0f))} : Z2;
+    s = {cadd(Z.re, b.re), cadd(Z.im, b.im)};
+    d = {csub(Z.re, Z2.re), csub(Z.im, Z2.im)};
   } else {
-    // W b = {Re b wr - Im b wi, Re b wi + Im b wr}, folded into the sums
-    constexpr float kC[9] = {1.0f,
-                             0.98078528040323043f, 0.92387953251128674f,
-                             0.83146961230254524f, 0.70710678118654757f,
-                             0.55557023301960229f, 0.38268343236508984f,
-                             0.19509032201612833f, 0.0f};
-    const float c = e <= 8 ? kC[e] : -kC[16 - e];
-    const float s = e <= 8 ? kC[8 - e] : kC[e - 8];
-    const float2 wr = f2(c), wi = f2(-s), nwr = f2(-c), nwi = f2(s);
-    x = {__ffma2_rn(b.im, nwi, __ffma2_rn(b.re, wr, a.re)),
-         __ffma2_rn(b.im, wr, __ffma2_rn(b.re, wi, a.im))};
-    y = {__ffma2_rn(b.im, wi, __ffma2_rn(b.re, nwr, a.re)),
-         __ffma2_rn(b.im, nwr, __ffma2_rn(b.re, nwi, a.im))};
+    const Cx2 a = twin_wmul(Z, e), b = twin_wmul(Z2, 3 * e);
+    s = {cadd(a.re, b.re), cadd(a.im, b.im)};
+    d = {csub(a.re, b.re), csub(a.im, b.im)};
   }
+  x0 = {cadd(U.re, s.re), cadd(U.im, s.im)};
+  x2 = {csub(U.re, s.re), csub(U.im, s.im)};
+  x1 = {cadd(U2.re, d.im), csub(U2.im, d.re)};
+  x3 = {csub(U2.re, d.im), cadd(U2.im, d.re)};
 }
 
-// Radix-2 decimation-in-time stages of half-span S, 2S, ... 16 on 32 points.
-template <int S>
-__device__ __forceinline__ void twin_stages(Cx2 (&a)[32]) {
-  if constexpr (S < 32) {
-#pragma unroll
-    for (int base = 0; base < 32; base += 2 * S) {
-#pragma unroll
-      for (int i = 0; i < S; ++i) twin_bfly(a[base + i], a[base + i + S], i * (16 / S));
+// X[B + k], k < N: the N-point DFT of the samples re/im[O + S n], n < N,
+// by split radix (recursion at compile time).  OFS: the samples carry the
+// offset c = 2^23 + 32768 on each part, removed exactly where two raw
+// samples are first added (a + (b - 2c)); their differences are exact.
+template <int N, int O, int S, int B, bool OFS>
+__device__ __forceinline__ void twin_sr(const float2 (&re)[32], const float2 (&im)[32],
+                                        Cx2 (&out)[32]) {
+  if constexpr (N == 1) {
+    out[B] = {re[O], im[O]};
+  } else if constexpr (N == 2) {
+    const Cx2 a = {re[O], im[O]}, b = {re[O + S], im[O + S]};
+    if constexpr (OFS) {
+      out[B] = {cadd(a.re, cadd(b.re, f2(-16842752.0f))), cadd(a.im, cadd(b.im, f2(-16842752.0f)))};
+    } else {
+      out[B] = {cadd(a.re, b.re), cadd(a.im, b.im)};
     }
-    twin_stages<2 * S>(a);
+    out[B + 1] = {csub(a.re, b.re), csub(a.im, b.im)};
+  } else {
+    twin_sr<N / 2, O, 2 * S, B, OFS>(re, im, out);
+    twin_sr<N / 4, O + S, 4 * S, B + N / 2, OFS>(re, im, out);
+    twin_sr<N / 4, O + 3 * S, 4 * S, B + 3 * N / 4, OFS>(re, im, out);
+#pragma unroll
+    for (int k = 0; k < N / 4; ++k)
+      twin_lbfly<N, OFS && N == 4>(out[B + k], out[B + N / 4 + k], out[B + N / 2 + k],
+                                   out[B + 3 * N / 4 + k], k);
   }
 }
 
-// Pass 1 of both symbols from offset samples v + c (c = 2^23 + 32768, each
-// an exact float): the first radix-2 stage (twiddle 1) forms a + (b - 2c)
-// and a - b, both exact, so the offset costs one packed subtraction per
-// butterfly instead of one per sample; the other stages as in twin_dft32.
-__device__ __forceinline__ void twin_dft32_offset(float2 (&re)[32], float2 (&im)[32]) {
-  Cx2 a[32];
-#pragma unroll
-  for (int i = 0; i < 32; ++i) a[i] = {re[brev(i, 5)], im[brev(i, 5)]};
-#pragma unroll
-  for (int i = 0; i < 32; i += 2) {
-    const Cx2 x = a[i], y = a[i + 1];
-    const float2 yr = cadd(y.re, f2(-16842752.0f)), yi = cadd(y.im, f2(-16842752.0f));
-    a[i] = {cadd(x.re, yr), cadd(x.im, yi)};
-    a[i + 1] = {csub(x.re, y.re), csub(x.im, y.im)};
-  }
-  twin_stages<2>(a);
+template <bool OFS>
+__device__ __forceinline__ void twin_dft32_sr(float2 (&re)[32], float2 (&im)[32]) {
+  Cx2 out[32];
+  twin_sr<32, 0, 1, 0, OFS>(re, im, out);
 #pragma unroll
   for (int i = 0; i < 32; ++i) {
-    re[i] = a[i].re;
-    im[i] = a[i].im;
-  }
-}
-
-// In-register 32-point DFT of both symbols, natural order in and out: radix-2
-// decimation in time over bit-reversed register indices.
-__device__ __forceinline__ void twin_dft32(float2 (&re)[32], float2 (&im)[32]) {
-  Cx2 a[32];
-#pragma unroll
-  for (int i = 0; i < 32; ++i) a[i] = {re[brev(i, 5)], im[brev(i, 5)]};
-  twin_stages<1>(a);
-#pragma unroll
-  for (int i = 0; i < 32; ++i) {
-    re[i] = a[i].re;
-    im[i] = a[i].im;
+    re[i] = out[i].re;
+    im[i] = out[i].im;
   }
 }
 
@@ -377,7 +385,7 @@ __global__ void __launch_bounds__(kTwThreads, 1) twin_kernel(const KParams p) {
           for (int r = 0; r < 32; ++r) {
             // sc16 -> float v + 2^23 + 32768 exactly: sign bits flipped to
             // offset binary, each half placed under the exponent bytes of
-            // 2^23 (the offset leaves in pass 1's first stage)
+            // 2^23 (the offset leaves where pass 1 first adds two samples)
             const uint32_t ua = sa[lane + 32 * r] ^ 0x80008000u;
             const uint32_t ub = sb[lane + 32 * r] ^ 0x80008000u;
             re[r] = make_float2(__uint_as_float(__byte_perm(ua, 0x4b000000u, 0x7610)),
@@ -393,7 +401,7 @@ __global__ void __launch_bounds__(kTwThreads, 1) twin_kernel(const KParams p) {
           phase ^= 1;
         }
         // pass 1: 32-point DFTs over n1 (n = lane + 32 n1)
-        twin_dft32_offset(re, im);
+        twin_dft32_sr<true>(re, im);
         // every lane is done with the exchange of the previous step (and with
         // this step's slot): transpose in one round of 16-byte stores, rows
         // n2 < 16 in the slot just read, the others in the exchange region
@@ -436,7 +444,7 @@ __global__ void __launch_bounds__(kTwThreads, 1) twin_kernel(const KParams p) {
           im[r] = __ffma2_rn(xr, wi, __fmul2_rn(xi, wr));
         }
         // pass 2: 32-point DFTs over n2; register e holds bin lane + 32 e
-        twin_dft32(re, im);
+        twin_dft32_sr<false>(re, im);
         const int ia = 2 * ip;
         if (pilot_here && ip == 0) {
           // first row: the pilot.  LS estimate H = Y conj(X) / |X|^2 (1/sqrt(N)
