@@ -27,9 +27,11 @@
 // Data-symbol groups: the pilot with the first three data symbols, then four
 // data symbols at a time (a warp's 256 TMEM columns hold the energy and three
 // symbols' sums, or four symbols' sums), so the 14 rows of a frame with 13
-// data symbols pair up exactly.  At a group's end the block adds the warps'
-// sums in warp order through shared memory, forms z = P / E and demaps
-// (Sec. II-B), or writes the block's partial sums (antenna split).
+// data symbols pair up exactly.  At a group's end each warp w < 4 adds the
+// sums of warp w + 4 (its lane-quarter partner) in tensor memory, the four
+// results meet in warp order through shared memory, and the block forms
+// z = P / E and demaps (Sec. II-B), or writes its partial sums (antenna
+// split).
 #pragma once
 
 #include "lsas_kernels.cuh"
@@ -55,7 +57,7 @@ constexpr int kTwSlotB = 16 * kTwXRow;      // a slot: two sc16 rows, or 16 exch
 constexpr int kTwXS = 16 * kTwXRow / 8;     // exchange region (float2): the other 16 rows
 
 // Shared memory: header (mbarriers, TMEM address, flags), the pass twiddles
-// W_1024^(j r) as {wr, wr, wi, wi} at [r * 32 + j], 1/E per subcarrier, the
+// W_1024^(j r) as {wr, wi} at [r * 32 + j], 1/E per subcarrier, the
 // demapped codes of one group, then one region per warp: its staging ring
 // (two slots) and its exchange region.  At group ends the per-warp regions together hold
 // the warps' partial sums for the cross-warp reduction.
@@ -65,7 +67,7 @@ struct TwLayout {
 __host__ __device__ inline TwLayout make_twlayout() {
   TwLayout l;
   l.tw_off = kWHeader;
-  l.ie_off = l.tw_off + 1024 * 16;
+  l.ie_off = l.tw_off + 1024 * 8;
   l.codes_off = l.ie_off + 1024 * 4;
   l.warp_off = align_up(l.codes_off + kTwDg * 1024, 128);
   l.stage_bytes = kTwSlots * kTwSlotB;
@@ -284,7 +286,7 @@ __global__ void __launch_bounds__(kTwThreads, 1) twin_kernel(const KParams p) {
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem) + warp * kMaxSlots;
   uint32_t* tmem_base = reinterpret_cast<uint32_t*>(smem + kWTmemAddr);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + kWAbort);
-  float4* tws = reinterpret_cast<float4*>(smem + lay.tw_off);
+  float2* tws = reinterpret_cast<float2*>(smem + lay.tw_off);
   float* ie_s = reinterpret_cast<float*>(smem + lay.ie_off);
   uint8_t* codes = smem + lay.codes_off;
   unsigned char* stage = smem + lay.warp_off + warp * lay.warp_bytes;
@@ -293,7 +295,7 @@ __global__ void __launch_bounds__(kTwThreads, 1) twin_kernel(const KParams p) {
 
   for (int i = tid; i < N; i += NT) {
     const float2 w = __ldg(p.twP + i);
-    tws[i] = make_float4(w.x, w.x, w.y, w.y);
+    tws[i] = w;
   }
   if (tid == 0) *abort_flag = 0;
   if (lane == 0) {
@@ -437,11 +439,10 @@ __global__ void __launch_bounds__(kTwThreads, 1) twin_kernel(const KParams p) {
         // pass twiddles W_1024^(n2 k1), n2 = r, k1 = lane
 #pragma unroll
         for (int r = 1; r < 32; ++r) {
-          const float4 w = tws[r * 32 + lane];
-          const float2 wr = make_float2(w.x, w.y), wi = make_float2(w.z, w.w);
+          const float2 w = tws[r * 32 + lane];
           const float2 xr = re[r], xi = im[r];
-          re[r] = csub(__fmul2_rn(xr, wr), __fmul2_rn(xi, wi));
-          im[r] = __ffma2_rn(xr, wi, __fmul2_rn(xi, wr));
+          re[r] = __ffma2_rn(xi, f2(-w.y), __fmul2_rn(xr, f2(w.x)));
+          im[r] = __ffma2_rn(xr, f2(w.y), __fmul2_rn(xi, f2(w.x)));
         }
         // pass 2: 32-point DFTs over n2; register e holds bin lane + 32 e
         twin_dft32_sr<false>(re, im);
@@ -481,20 +482,29 @@ __global__ void __launch_bounds__(kTwThreads, 1) twin_kernel(const KParams p) {
     }
     tmem_wait_st();
     // ---- group end: every warp's steps are done, every copy of the group
-    // has landed; the per-warp regions are free for the reduction
+    // has landed; the per-warp regions are free for the reduction (and the
+    // tensor-memory stores of every warp are ordered before the loads of
+    // its lane-quarter partner)
+    tmem_fence_before();
     __syncthreads();
+    tmem_fence_after();
     if (energy_here) {
-      float* RE = reinterpret_cast<float*>(smem + lay.warp_off);   // [NW][N]
-      float e[OWN];
-      TmE::ld(tE, e);
-      tmem_wait_ld();
+      // warps w and w + 4 share a lane quarter: warp w < 4 adds the other's
+      // columns in tensor memory, then four warps go through shared memory
+      float* RE = reinterpret_cast<float*>(smem + lay.warp_off);   // [4][N]
+      if (warp < 4) {
+        float e[OWN], e2[OWN];
+        TmE::ld(tE, e);
+        TmE::ld(tE + kTwTmemWarp, e2);
+        tmem_wait_ld();
 #pragma unroll
-      for (int cc = 0; cc < OWN; ++cc) RE[warp * N + lane + 32 * cc] = e[cc];
+        for (int cc = 0; cc < OWN; ++cc) RE[warp * N + lane + 32 * cc] = e[cc] + e2[cc];
+      }
       __syncthreads();
       for (int k = tid; k < N; k += NT) {
         float E = 0.f;
 #pragma unroll
-        for (int w = 0; w < NW; ++w) E += RE[w * N + k];
+        for (int w = 0; w < 4; ++w) E += RE[w * N + k];
         if (p.mode == kModePartial) {
           p.E_out[(static_cast<size_t>(blockIdx.y) * gridDim.x + f) * N + k] = E;
         } else {
@@ -506,11 +516,13 @@ __global__ void __launch_bounds__(kTwThreads, 1) twin_kernel(const KParams p) {
       }
       __syncthreads();
     }
-    float2* RP = reinterpret_cast<float2*>(smem + lay.warp_off);   // [NW][dlc][N]
-    const int dlc = lay.warp_bytes / (N * 8);
+    // warps w < 4 add warp w + 4's sums (same lane quarter) in tensor
+    // memory and write both to shared memory: [4][nd][N]
+    float2* RP = reinterpret_cast<float2*>(smem + lay.warp_off);
+    const int dlc = kTwDg;
     for (int dl0 = 0; dl0 < nd; dl0 += dlc) {
       const int n = min(dlc, nd - dl0);
-      for (int j = 0; j < n; ++j) {
+      for (int j = 0; j < n && warp < 4; ++j) {
         const int it = dl0 + j + (pilot_here ? 1 : 0);
         bool pr;
         const uint32_t tb = tP + twin_block_col(it, pilot_here, &pr, items);
@@ -519,20 +531,27 @@ __global__ void __launch_bounds__(kTwThreads, 1) twin_kernel(const KParams p) {
           const int hf = it & 1;
 #pragma unroll
           for (int q0 = 0; q0 < 128; q0 += 32) {
-            float t[32];
+            float t[32], t2[32];
             Tmem<32>::ld(tb + q0, t);
+            Tmem<32>::ld(tb + kTwTmemWarp + q0, t2);
             tmem_wait_ld();
 #pragma unroll
             for (int i = 0; i < 8; ++i)
-              dst[lane + 32 * (q0 / 4 + i)] = make_float2(hf ? t[4 * i + 1] : t[4 * i], hf ? t[4 * i + 3] : t[4 * i + 2]);
+              dst[lane + 32 * (q0 / 4 + i)] =
+                  make_float2(hf ? t[4 * i + 1] + t2[4 * i + 1] : t[4 * i] + t2[4 * i],
+                              hf ? t[4 * i + 3] + t2[4 * i + 3] : t[4 * i + 2] + t2[4 * i + 2]);
           }
         } else {
-          float acc[2 * OWN];
-          TmP::ld(tb, acc);
-          tmem_wait_ld();
 #pragma unroll
-          for (int cc = 0; cc < OWN; ++cc)
-            dst[lane + 32 * cc] = make_float2(acc[2 * cc], acc[2 * cc + 1]);
+          for (int q0 = 0; q0 < 2 * OWN; q0 += 32) {
+            float t[32], t2[32];
+            Tmem<32>::ld(tb + q0, t);
+            Tmem<32>::ld(tb + kTwTmemWarp + q0, t2);
+            tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+              dst[lane + 32 * (q0 / 2 + i)] = make_float2(t[2 * i] + t2[2 * i], t[2 * i + 1] + t2[2 * i + 1]);
+          }
         }
       }
       __syncthreads();
@@ -541,7 +560,7 @@ __global__ void __launch_bounds__(kTwThreads, 1) twin_kernel(const KParams p) {
         const int k = idx & (N - 1);
         float2 s = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int w = 0; w < NW; ++w) s = cadd(s, RP[static_cast<size_t>(w * dlc + j) * N + k]);
+        for (int w = 0; w < 4; ++w) s = cadd(s, RP[static_cast<size_t>(w * dlc + j) * N + k]);
         const int dl = dl0 + j;
         if (p.mode == kModePartial) {
           p.P_out[((static_cast<size_t>(blockIdx.y) * gridDim.x + f) * p.D + d0 + dl) * N + k] =
