@@ -46,6 +46,7 @@ KERNEL_SRC = {
     "warp_kernel": ("lsas_kernels.cuh", "lsas_warp.cuh"),
     "hyb_kernel": ("lsas_kernels.cuh", "lsas_warp.cuh", "lsas_hyb.cuh"),
     "pair_kernel": ("lsas_kernels.cuh", "lsas_warp.cuh", "lsas_pair.cuh"),
+    "twinpair_kernel": ("lsas_kernels.cuh", "lsas_warp.cuh", "lsas_twin.cuh", "lsas_twinpair.cuh"),
     "frame_kernel": ("lsas_kernels.cuh",),
 }
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fused_kernel_traffic.json")
@@ -357,6 +358,9 @@ def fused_kernel_name(cfg):
                 "symbols per step in split real/imaginary form)")
     if cfg.N <= 1024:
         return "warp_kernel (fused CP strip+FFT+LS+MRC+demap, per-warp pipelines)"
+    if cfg.fmt == "sc16" and choice not in ("warp", "tensor"):
+        return ("twinpair_kernel (fused CP strip+FFT+LS+MRC+demap, pipelines of warp pairs, two "
+                "symbols per step in split real/imaginary form)")
     if cfg.fmt == "sc16":
         return "pair_kernel (fused CP strip+FFT+LS+MRC+demap, pipelines of warp pairs)"
     return "frame_kernel (fused CP strip+FFT+LS+MRC+demap)"

@@ -6,6 +6,7 @@
 #include "lsas_hyb.cuh"
 #include "lsas_pair.cuh"
 #include "lsas_twin.cuh"
+#include "lsas_twinpair.cuh"
 
 namespace lsas {
 
@@ -39,8 +40,15 @@ static cudaError_t launch_t(int kind, const KParams& p, int grid, int smem, cuda
       fn = warp_kernel<LOG2N, FC32>;
       threads = 32 * wgeo_warps(FC32 ? 8 : 4);
     } else if constexpr (!FC32) {
-      fn = pair_kernel<LOG2N>;
-      threads = kPThreads;
+      if (p.twin && p.use_tma && (p.mode == kModeRun || p.mode == kModePartial)) {
+        fn = twinpair_kernel<LOG2N>;
+        threads = kTpThreads;
+        smem = make_tplayout().total;
+        slot = 4;
+      } else {
+        fn = pair_kernel<LOG2N>;
+        threads = kPThreads;
+      }
     } else {
       fn = frame_kernel<LOG2N, FC32>;
       threads = Geo<LOG2N>::T;

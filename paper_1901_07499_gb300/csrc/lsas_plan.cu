@@ -391,7 +391,7 @@ void base_params(lsas_plan p, KParams* k) {
   k->status = p->d_status;
   k->fault = p->fault;
   k->hybrid = p->geo.hybrid;
-  k->twin = (p->twin && p->N == 1024 && p->fmt == LSAS_IN_SC16) ? 1 : 0;
+  k->twin = (p->twin && (p->N == 1024 || p->N == 2048) && p->fmt == LSAS_IN_SC16) ? 1 : 0;
   k->tc_w1 = p->d_tc_w1;
   k->M = p->M;
   k->m0 = 0;
