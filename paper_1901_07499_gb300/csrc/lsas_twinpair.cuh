@@ -55,21 +55,23 @@ constexpr int kTpSlotB = 16 * kTpMRow;       // 16,640 B: two rows, or half an e
 constexpr int kTpTwl = 7 * 256;              // last-pass twiddles W_2048^(j r), r = 1..7
 
 // Shared memory: header (mbarriers [pair][kMaxSlots], TMEM address, flags),
-// the last-pass twiddles as {wr, wi} at [(r - 1) * 256 + j] (the middle
-// pass's W_2048^(8 j r) are the entries j = 8 j'), 1/E per subcarrier, the
-// demapped codes of one group, then per pair: two staging slots and the
-// exchange region.  At group ends the pair regions hold the partial sums.
+// the last-pass twiddles as {wr, wi} at [(r - 1) * 256 + j], the middle-pass
+// twiddles W_2048^(8 b r) at [(r - 1) * 32 + b] (contiguous for the lanes of
+// a warp), 1/E per subcarrier, then per pair: two staging slots and the
+// exchange region.  At group ends the pair regions hold the partial sums
+// ([2][4][N] complex) and, after them, the demapped codes of the group.
 struct TpLayout {
-  int tw_off, ie_off, codes_off, pair_off, stage_bytes, pair_bytes, total;
+  int tw_off, mtw_off, ie_off, codes_off, pair_off, stage_bytes, pair_bytes, total;
 };
 __host__ __device__ inline TpLayout make_tplayout() {
   TpLayout l;
   l.tw_off = kWHeader;
-  l.ie_off = l.tw_off + kTpTwl * 8;
-  l.codes_off = l.ie_off + kTpN * 4;
-  l.pair_off = align_up(l.codes_off + kTwDg * kTpN, 128);
+  l.mtw_off = l.tw_off + kTpTwl * 8;
+  l.ie_off = l.mtw_off + 7 * 32 * 8;
+  l.pair_off = align_up(l.ie_off + kTpN * 4, 128);
   l.stage_bytes = 2 * kTpSlotB;
   l.pair_bytes = align_up(l.stage_bytes + kTpSlotB, 128);
+  l.codes_off = l.pair_off + 2 * kTwDg * kTpN * 8;
   l.total = l.pair_off + kTpPairs * l.pair_bytes;
   return l;
 }
@@ -132,12 +134,14 @@ __global__ void __launch_bounds__(kTpThreads, 1) twinpair_kernel(const KParams p
   uint32_t* tmem_base = reinterpret_cast<uint32_t*>(smem + kWTmemAddr);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + kWAbort);
   float2* twl = reinterpret_cast<float2*>(smem + lay.tw_off);   // [r - 1][j]
+  float2* mtw = reinterpret_cast<float2*>(smem + lay.mtw_off);  // [r - 1][b]
   float* ie_s = reinterpret_cast<float*>(smem + lay.ie_off);
   uint8_t* codes = smem + lay.codes_off;
   unsigned char* stage = smem + lay.pair_off + q * lay.pair_bytes;
   unsigned char* const X = stage + lay.stage_bytes;
 
   for (int i = tid; i < kTpTwl; i += kTpThreads) twl[i] = __ldg(p.twP + 512 + i);
+  for (int i = tid; i < 7 * 32; i += kTpThreads) mtw[i] = __ldg(p.twP + 32 + i);
   if (tid == 0) *abort_flag = 0;
   if (jt == 0) {
     for (int s = 0; s < K; ++s) mbar_init(smem_u32(&bars[s]), 1);
@@ -284,7 +288,7 @@ __global__ void __launch_bounds__(kTpThreads, 1) twinpair_kernel(const KParams p
         // middle-pass twiddles W_2048^(8 (jt & 31) rr)
 #pragma unroll
         for (int rr = 1; rr < 8; ++rr) {
-          const float2 w = twl[(rr - 1) * 256 + 8 * (jt & 31)];
+          const float2 w = mtw[(rr - 1) * 32 + (jt & 31)];
 #pragma unroll
           for (int i = 0; i < 4; ++i) tp_twiddle(re[i * 8 + rr], im[i * 8 + rr], w);
         }
