@@ -144,13 +144,24 @@ def test_two_symbol_kernel_groupings(L, M, S, pilot_idx):
     run_and_check(L, sweep_config(M, 1024).replace(S=S, pilot_idx=pilot_idx), F=2)
 
 
-@pytest.mark.parametrize("S,pilot_idx", [(17, 5), (6, 0)])
-def test_two_symbol_kernel_group_layers(L, S, pilot_idx):
-    """The one-launch antenna split of a small batch gives every data-symbol
-    group its own block (each transforms the pilot, group 0 alone writes H and
-    the energy): against the oracle, and H equal to the unsplit call's."""
+@pytest.mark.parametrize("M,S,pilot_idx", [
+    (1, 2, 0), (5, 3, 2), (4, 4, 0), (13, 5, 4), (8, 9, 0), (20, 14, 7), (9, 17, 16)])
+def test_two_symbol_pair_kernel_groupings(L, M, S, pilot_idx):
+    """N = 2048 from aligned sc16 rows runs the two-symbol pair kernel, with
+    the same step pairings as at N = 1024: odd item counts, a data symbol
+    beside the pilot or alone, idle pairs (M < 4, M not a multiple of 4),
+    one to sixteen data symbols, the pilot anywhere."""
+    run_and_check(L, sweep_config(M, 2048).replace(S=S, pilot_idx=pilot_idx), F=2)
+
+
+@pytest.mark.parametrize("N,S,pilot_idx", [(1024, 17, 5), (1024, 6, 0), (2048, 17, 16), (2048, 5, 2)])
+def test_two_symbol_kernel_group_layers(L, N, S, pilot_idx):
+    """Both two-symbol kernels: the one-launch antenna split of a small batch
+    gives every data-symbol group its own block (each transforms the pilot,
+    group 0 alone writes H and the energy): against the oracle, and H equal
+    to the unsplit call's."""
     import torch
-    cfg = sweep_config(16, 1024).replace(S=S, pilot_idx=pilot_idx)
+    cfg = sweep_config(16, N).replace(S=S, pilot_idx=pilot_idx)
     F, G = 2, 2
     b = synth.generate(cfg, frame_ids=range(F))
     plan = make_plan(L, cfg, max_frames=4)
