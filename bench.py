@@ -353,7 +353,8 @@ def fused_kernel_name(cfg):
     if cfg.N == 1024 and cfg.fmt == "sc16" and choice == "tensor":
         return ("hyb_kernel (fused CP strip + FFT + LS + MRC + demap; first FFT pass on the "
                 "CUDA cores, second on tcgen05)")
-    if cfg.N == 1024 and cfg.fmt == "sc16" and choice != "warp":
+    twin_n = cfg.N == 1024 or (cfg.N == 512 and cfg.M >= 32) or (cfg.N == 256 and cfg.M >= 128)
+    if twin_n and cfg.fmt == "sc16" and choice not in ("warp", "tensor"):
         return ("twin_kernel (fused CP strip+FFT+LS+MRC+demap, per-warp pipelines, two "
                 "symbols per step in split real/imaginary form)")
     if cfg.N <= 1024:

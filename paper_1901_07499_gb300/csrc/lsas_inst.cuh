@@ -16,10 +16,11 @@ static cudaError_t launch_t(int kind, const KParams& p, int grid, int smem, cuda
   int threads = Geo<LOG2N>::TW;
   int slot = kind;   // entry of the shared-memory attribute cache below
   if (kind == kKindFrame) {
-    // fused receiver: N = 1024 from aligned sc16 rows with two symbols per
-    // step (or, opt-in, the second FFT pass on the tensor cores); otherwise
-    // per-warp pipelines up to N = 1024,
-    // pipelines of warp pairs for N = 2048 from sc16 rows and the
+    // fused receiver: from aligned sc16 rows, two symbols per step for
+    // N = 1024 (and N = 256, 512 with enough antennas; per-warp pipelines)
+    // and N = 2048 (pipelines of warp pairs), or, opt-in at N = 1024, the
+    // second FFT pass on the tensor cores; otherwise one symbol per step: per-warp pipelines up to
+    // N = 1024, pipelines of warp pairs for N = 2048 from sc16 rows and the
     // warp-specialised producer/consumer kernel for N = 2048 from fc32 rows
     if constexpr (LOG2N == 10 && !FC32) {
       if (p.hybrid && p.use_tma) {
@@ -28,6 +29,17 @@ static cudaError_t launch_t(int kind, const KParams& p, int grid, int smem, cuda
         smem = kHySmem;
         slot = 3;
       } else if (p.twin && p.use_tma && (p.mode == kModeRun || p.mode == kModePartial)) {
+        fn = twin_kernel<LOG2N>;
+        slot = 4;
+        threads = kTwThreads;
+        smem = make_twlayout().total;
+      } else {
+        fn = warp_kernel<LOG2N, FC32>;
+        threads = 32 * wgeo_warps(4);
+      }
+    } else if constexpr ((LOG2N == 8 || LOG2N == 9) && !FC32) {
+      // p.twin is set by the plan only with enough antennas at these sizes
+      if (p.twin && p.use_tma && (p.mode == kModeRun || p.mode == kModePartial)) {
         fn = twin_kernel<LOG2N>;
         slot = 4;
         threads = kTwThreads;

@@ -96,7 +96,7 @@ struct lsas_plan_s {
   int pn_len = 0;
   int fault = 0;   // test hook of the bounded waits (lsas_plan_set_fault)
   bool allow_hybrid = false;   // LSAS_FUSED_KERNEL = "tensor" at creation
-  bool twin = true;            // N = 1024 sc16: two symbols per step (LSAS_FUSED_KERNEL)
+  bool twin = true;            // sc16: two symbols per step where it pays (LSAS_FUSED_KERNEL)
   void* d_split_scratch = nullptr;   // device address of g_split_scratch on this device
   // lsas_run_frame: the frames after a batch's last whole wave of blocks (all
   // of them, for a batch smaller than one wave) may run split into equal
@@ -391,7 +391,14 @@ void base_params(lsas_plan p, KParams* k) {
   k->status = p->d_status;
   k->fault = p->fault;
   k->hybrid = p->geo.hybrid;
-  k->twin = (p->twin && (p->N == 1024 || p->N == 2048) && p->fmt == LSAS_IN_SC16) ? 1 : 0;
+  // two symbols per step: N = 1024 and 2048 always; N = 512 and 256 only
+  // with enough antennas (each lane keeps 32 subcarriers of its antenna, so
+  // the data symbols take four groups where the one-symbol kernel needs one
+  // at N = 256).  Decided per plan on its total antenna count, so that the
+  // antenna shards of a split batch run the same arithmetic as a whole frame.
+  k->twin = (p->twin && p->fmt == LSAS_IN_SC16 &&
+             (p->N >= 1024 || (p->N == 512 && p->M >= 32) || (p->N == 256 && p->M >= 128)))
+                ? 1 : 0;
   k->tc_w1 = p->d_tc_w1;
   k->M = p->M;
   k->m0 = 0;
@@ -637,10 +644,11 @@ lsas_status lsas_plan_create(int M, int N, int cp_len, int n_sym, int pilot_idx,
     p->prof = e && e[0] == '1';
   }
   {
-    // Fused kernel for N = 1024 from sc16 rows: by default two symbols per
-    // warp step (twin_kernel); LSAS_FUSED_KERNEL=warp selects one symbol per
-    // step (warp_kernel) and LSAS_FUSED_KERNEL=tensor the second FFT pass on
-    // the tensor cores (hyb_kernel), both measured slower
+    // Fused kernel from sc16 rows: by default two symbols per step where it
+    // pays (twin_kernel, twinpair_kernel); LSAS_FUSED_KERNEL=warp selects one
+    // symbol per step (warp_kernel, pair_kernel) and LSAS_FUSED_KERNEL=tensor
+    // at N = 1024 the second FFT pass on the tensor cores (hyb_kernel), both
+    // measured slower
     const char* e = std::getenv("LSAS_FUSED_KERNEL");
     p->allow_hybrid = e && std::strcmp(e, "tensor") == 0;
     p->twin = !(e && (std::strcmp(e, "warp") == 0 || std::strcmp(e, "tensor") == 0));

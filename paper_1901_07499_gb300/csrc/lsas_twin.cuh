@@ -1,10 +1,14 @@
-// lsas_twin.cuh -- fused receiver for N = 1024 from sc16 rows, two OFDM
-// symbols of one antenna per warp step, in split real / imaginary form.
+// lsas_twin.cuh -- fused receiver for N = 256 .. 1024 from sc16 rows, two
+// OFDM symbols per warp step, in split real / imaginary form.
 //
 // One block per frame, 8 warps, each an independent pipeline over antenna
-// rows (warp w takes antennas w, w + 8, ...), as in the per-warp kernel.
-// What differs is the unit of a step: a lane holds 32 points of TWO symbols
-// of its antenna, the real parts of point r of both symbols in one packed
+// rows, as in the per-warp kernel.  At N = 1024 a warp step takes one
+// antenna (warp w takes antennas w, w + 8, ...); for smaller N the warp's
+// lanes form A = 1024 / N teams of L = N / 32 lanes, team t taking antenna
+// (w + 8 c) A + t at the warp's step c, so every step still moves 32 points
+// per lane.  What differs from the per-warp kernel is the unit of a step: a
+// lane holds 32 points of TWO symbols of its antenna, the real parts of
+// point r of both symbols in one packed
 // register pair and the imaginary parts in another.  Every packed FP32
 // instruction then applies one operation to both symbols: a product by a
 // twiddle takes four packed instructions for two points and no operand
@@ -24,10 +28,15 @@
 //     data symbol: P += conj(H) Y per subcarrier in the warp's tensor-memory
 //     columns (the MRC numerator, Sec. II-C); for two data symbols as four
 //     packed FMAs per subcarrier on their interleaved columns.
+// The second pass is radix L: it reads column jt of the exchange (32 rows of
+// L points per team) and takes 32 / L DFTs of L points per symbol.
 // Data-symbol groups: the pilot with the first three data symbols, then four
 // data symbols at a time (a warp's 256 TMEM columns hold the energy and three
 // symbols' sums, or four symbols' sums), so the 14 rows of a frame with 13
-// data symbols pair up exactly.  At a group's end each warp w < 4 adds the
+// data symbols pair up exactly.  Each lane keeps 32 subcarriers of its own
+// antenna whatever N is, so the grouping is the same for every N; that is
+// why the one-symbol kernel (which sums a step's antennas across lanes and
+// needs one group at N = 256) stays the choice for few antennas per launch.  At a group's end each warp w < 4 adds the
 // sums of warp w + 4 (its lane-quarter partner) in tensor memory, the four
 // results meet in warp order through shared memory, and the block forms
 // z = P / E and demaps (Sec. II-B), or writes its partial sums (antenna
@@ -42,7 +51,6 @@ namespace lsas {
 constexpr int kTwWarps = 8;
 constexpr int kTwThreads = 32 * kTwWarps;
 constexpr int kTwSlots = 2;                 // staging slots per warp, two rows each
-constexpr int kTwRow = 1024 * 4;            // one CP-stripped sc16 row
 constexpr int kTwTmemWarp = 256;            // TMEM columns per warp
 constexpr int kTwOwn = 32;                  // subcarriers per lane
 constexpr int kTwDg0 = (kTwTmemWarp - kTwOwn) / (2 * kTwOwn);   // 3: group 0
@@ -55,9 +63,13 @@ constexpr int kTwDg = kTwTmemWarp / (2 * kTwOwn);                // 4: later gro
 constexpr int kTwXRow = 32 * 16 + 16;       // one padded exchange row
 constexpr int kTwSlotB = 16 * kTwXRow;      // a slot: two sc16 rows, or 16 exchange rows
 constexpr int kTwXS = 16 * kTwXRow / 8;     // exchange region (float2): the other 16 rows
+// A slot holds the step's rows as two halves (the two symbols) of 1056 words:
+// the A = 32 / L antennas of a warp step (L = N / 32 lanes each) at N + L
+// words apart, so that the lanes' loads of a row position hit distinct banks.
+constexpr int kTwHalfB = 32 * 33 * 4;
 
 // Shared memory: header (mbarriers, TMEM address, flags), the pass twiddles
-// W_1024^(j r) as {wr, wi} at [r * 32 + j], 1/E per subcarrier, the
+// W_N^(j r) as {wr, wi} at [r * 32 + j] (N entries), 1/E per subcarrier, the
 // demapped codes of one group, then one region per warp: its staging ring
 // (two slots) and its exchange region.  At group ends the per-warp regions together hold
 // the warps' partial sums for the cross-warp reduction.
@@ -190,23 +202,60 @@ __device__ __forceinline__ void twin_dft32_sr(float2 (&re)[32], float2 (&im)[32]
   }
 }
 
-// Issue the bulk copies of one step (antenna m, symbols sa and sb; sb < 0:
-// one row) into a slot: lane 0 registers the bytes and copies row a, lane 1
-// copies row b.
-__device__ __forceinline__ void twin_issue(const KParams& p, int f, int m, int sa, int sb,
-                                           unsigned char* slot, uint32_t bar, uint64_t pol,
-                                           int lane) {
-  if (lane == 0) {
-    mbar_expect_tx(bar, sb >= 0 ? 2 * kTwRow : kTwRow);
-    bulk_load(smem_u32(slot), row_ptr<10, false>(p, f, m, sa), kTwRow, bar, pol);
-  } else if (lane == 1 && sb >= 0) {
-    bulk_load(smem_u32(slot + kTwRow), row_ptr<10, false>(p, f, m, sb), kTwRow, bar, pol);
+// Pass 2: the 32 / L radix-L DFTs of both symbols on register groups
+// i L .. i L + L - 1 (split radix, natural order in and out).
+template <int L>
+__device__ __forceinline__ void twin_pass2(float2 (&re)[32], float2 (&im)[32]) {
+  if constexpr (L == 32) {
+    twin_dft32_sr<false>(re, im);
+  } else {
+    Cx2 out[32];
+    twin_sr<L, 0, 1, 0, false>(re, im, out);
+    twin_sr<L, L, 1, L, false>(re, im, out);
+    if constexpr (L <= 8) {
+      twin_sr<L, 2 * L, 1, 2 * L, false>(re, im, out);
+      twin_sr<L, 3 * L, 1, 3 * L, false>(re, im, out);
+    }
+    if constexpr (L <= 4) {
+      twin_sr<L, 4 * L, 1, 4 * L, false>(re, im, out);
+      twin_sr<L, 5 * L, 1, 5 * L, false>(re, im, out);
+      twin_sr<L, 6 * L, 1, 6 * L, false>(re, im, out);
+      twin_sr<L, 7 * L, 1, 7 * L, false>(re, im, out);
+    }
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      re[i] = out[i].re;
+      im[i] = out[i].im;
+    }
+  }
+}
+
+// Issue the bulk copies of one step: items ia and ia + 1 of a group (the
+// second may be absent) for the A antennas of chunk c.  Lane h A + t copies
+// the row of symbol item ia + h of antenna c A + t to half h of the slot,
+// team t's place (rows L words apart, for conflict-free loads); lane 0
+// registers the bytes.
+template <int LOG2N>
+__device__ __forceinline__ void twin_issue(const KParams& p, int f, int c, bool pilot_here, int d0,
+                                           int items, int ia, unsigned char* slot, uint32_t bar,
+                                           uint64_t pol, int lane) {
+  constexpr int N = 1 << LOG2N, L = N / 32, A = 32 / L;
+  constexpr uint32_t bytes = N * 4;
+  const int nant = min(A, p.M - c * A);
+  const int nrow = ia + 1 < items ? 2 : 1;
+  if (lane == 0) mbar_expect_tx(bar, bytes * nant * nrow);
+  if (lane < 2 * A) {
+    const int half = lane / A, t = lane % A;
+    if (t < nant && half < nrow)
+      bulk_load(smem_u32(slot + half * kTwHalfB + t * (N + L) * 4),
+                row_ptr<LOG2N, false>(p, f, c * A + t, witem_symbol(p, pilot_here, d0, ia + half)),
+                bytes, bar, pol);
   }
 }
 
 // P += conj(H) Y for one symbol of the step (half 0: .x, half 1: .y) into
-// the 64 accumulator columns at tp (column 2c, 2c + 1 = subcarrier
-// lane + 32 c), as four FMAs per subcarrier.
+// the 64 accumulator columns at tp (columns 2c, 2c + 1 for the subcarrier of
+// register c), as four FMAs per subcarrier.
 template <int HALF, int QC = 16>
 __device__ __forceinline__ void twin_mrc(const float2 (&re)[32], const float2 (&im)[32],
                                          const float2 (&h)[32], uint32_t tp) {
@@ -231,7 +280,7 @@ __device__ __forceinline__ void twin_mrc(const float2 (&re)[32], const float2 (&
 
 // P += conj(H) Y for both symbols of a step into the 128 interleaved
 // columns at tp (4c: Re a, 4c + 1: Re b, 4c + 2: Im a, 4c + 3: Im b for
-// subcarrier lane + 32 c): the symbols' values are already packed pairs, so
+// the subcarrier of register c): the symbols' values are already packed pairs, so
 // four packed FMAs per subcarrier, in the scalar form's order of operations.
 __device__ __forceinline__ void twin_mrc2(const float2 (&re)[32], const float2 (&im)[32],
                                           const float2 (&h)[32], uint32_t tp) {
@@ -269,8 +318,10 @@ __device__ __forceinline__ int twin_block_col(int it, bool pilot, bool* pair, in
 
 template <int LOG2N>
 __global__ void __launch_bounds__(kTwThreads, 1) twin_kernel(const KParams p) {
-  static_assert(LOG2N == 10, "the two-symbol kernel is written for N = 1024");
+  static_assert(LOG2N >= 7 && LOG2N <= 10, "the two-symbol kernel covers N = 128 .. 1024");
   constexpr int N = 1 << LOG2N;
+  constexpr int L = N / 32;     // lanes of an antenna's FFT team
+  constexpr int A = 32 / L;     // antennas of a warp step (teams)
   constexpr int NW = kTwWarps;
   constexpr int NT = kTwThreads;
   constexpr int OWN = kTwOwn;
@@ -282,6 +333,8 @@ __global__ void __launch_bounds__(kTwThreads, 1) twin_kernel(const KParams p) {
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
   const int lane = tid & 31;
+  const int team = lane / L;    // antenna of the chunk
+  const int jt = lane % L;      // FFT team thread
   const TwLayout lay = make_twlayout();
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem) + warp * kMaxSlots;
   uint32_t* tmem_base = reinterpret_cast<uint32_t*>(smem + kWTmemAddr);
@@ -352,9 +405,8 @@ __global__ void __launch_bounds__(kTwThreads, 1) twin_kernel(const KParams p) {
       int is = slot;
       for (int s = 0; s < K && to_issue > 0; ++s, --to_issue) {
         const int ia = 2 * ipi;
-        twin_issue(p, f, warp + ic * NW, witem_symbol(p, pilot_here, d0, ia),
-                   ia + 1 < items ? witem_symbol(p, pilot_here, d0, ia + 1) : -1,
-                   stage + is * slot_bytes, smem_u32(&bars[is]), pol, lane);
+        twin_issue<LOG2N>(p, f, warp + ic * NW, pilot_here, d0, items, ia, stage + is * slot_bytes,
+                          smem_u32(&bars[is]), pol, lane);
         // test hook: the first staging phase of block 0 also waits for 16
         // bytes that no copy delivers, so its bounded wait runs out
         if (p.fault == 1 && blockIdx.x == 0 && warp == 0 && g == 0 && s == 0 && lane == 0)
@@ -368,28 +420,33 @@ __global__ void __launch_bounds__(kTwThreads, 1) twin_kernel(const KParams p) {
       }
     }
     for (int lc = 0; lc < nch; ++lc) {
-      const int m = warp + lc * NW;
+      const int m = (warp + lc * NW) * A + team;   // this lane's antenna
+      const bool valid = m < p.M;                  // a chunk's last teams may have none
       const size_t hrow = (static_cast<size_t>(f) * p.Mtot + p.m0 + blockIdx.y * p.shard_y + m) * N;
       float2 h[32];
       if (!pilot_here) {
+        // channel written in group 0 (zero for a team without an antenna, so
+        // that its stale rows add nothing)
 #pragma unroll
-        for (int e = 0; e < 32; ++e) h[e] = p.H_out[hrow + lane + 32 * e];
+        for (int e = 0; e < 32; ++e)
+          h[e] = valid ? p.H_out[hrow + bin_of<LOG2N>(jt, e)] : make_float2(0.f, 0.f);
       }
       for (int ip = 0; ip < npairs; ++ip) {
         float2 re[32], im[32];
         wait_slot(smem_u32(&bars[slot]), phase, abort_flag, p.status);
         // both rows; a missing second row leaves earlier samples in the slot
         // (finite integers), whose transform is not used
-        const uint32_t* sa = reinterpret_cast<const uint32_t*>(stage + slot * slot_bytes);
-        const uint32_t* sb = sa + kTwRow / 4;
+        const uint32_t* sa =
+            reinterpret_cast<const uint32_t*>(stage + slot * slot_bytes) + team * (N + L);
+        const uint32_t* sb = sa + kTwHalfB / 4;
         {
 #pragma unroll
           for (int r = 0; r < 32; ++r) {
             // sc16 -> float v + 2^23 + 32768 exactly: sign bits flipped to
             // offset binary, each half placed under the exponent bytes of
             // 2^23 (the offset leaves where pass 1 first adds two samples)
-            const uint32_t ua = sa[lane + 32 * r] ^ 0x80008000u;
-            const uint32_t ub = sb[lane + 32 * r] ^ 0x80008000u;
+            const uint32_t ua = sa[jt + L * r] ^ 0x80008000u;
+            const uint32_t ub = sb[jt + L * r] ^ 0x80008000u;
             re[r] = make_float2(__uint_as_float(__byte_perm(ua, 0x4b000000u, 0x7610)),
                                 __uint_as_float(__byte_perm(ub, 0x4b000000u, 0x7610)));
             im[r] = make_float2(__uint_as_float(__byte_perm(ua, 0x4b000000u, 0x7632)),
@@ -402,7 +459,7 @@ __global__ void __launch_bounds__(kTwThreads, 1) twin_kernel(const KParams p) {
           slot = 0;
           phase ^= 1;
         }
-        // pass 1: 32-point DFTs over n1 (n = lane + 32 n1)
+        // pass 1: 32-point DFTs over n1 (n = jt + L n1)
         twin_dft32_sr<true>(re, im);
         // every lane is done with the exchange of the previous step (and with
         // this step's slot): transpose in one round of 16-byte stores, rows
@@ -415,37 +472,57 @@ __global__ void __launch_bounds__(kTwThreads, 1) twin_kernel(const KParams p) {
             *reinterpret_cast<float4*>(wrow + 16 * r) = make_float4(re[r].x, re[r].y, im[r].x, im[r].y);
         }
         __syncwarp();
+        // row R = lane holds the pass-1 outputs k1 of team R / L, its thread
+        // n2 = R % L; this lane reads k1 = jt + L i, n2 = 0 .. L - 1 of its
+        // team into register i L + n2
+        if constexpr (L == 32) {
 #pragma unroll
-        for (int r = 0; r < 32; ++r) {
-          const float4 v = *reinterpret_cast<const float4*>(
-              (r < 16 ? yslot : reinterpret_cast<const unsigned char*>(ex)) + (r & 15) * kTwXRow + 16 * lane);
-          re[r] = make_float2(v.x, v.y);
-          im[r] = make_float2(v.z, v.w);
+          for (int r = 0; r < 32; ++r) {
+            const float4 v = *reinterpret_cast<const float4*>(
+                (r < 16 ? yslot : reinterpret_cast<const unsigned char*>(ex)) + (r & 15) * kTwXRow + 16 * lane);
+            re[r] = make_float2(v.x, v.y);
+            im[r] = make_float2(v.z, v.w);
+          }
+        } else {
+          // a team's L rows lie in one of the two places (L divides 16)
+          const unsigned char* trow = (team * L < 16 ? yslot : reinterpret_cast<const unsigned char*>(ex)) +
+                                      ((team * L) & 15) * kTwXRow + 16 * jt;
+#pragma unroll
+          for (int i = 0; i < 32 / L; ++i) {
+#pragma unroll
+            for (int n2 = 0; n2 < L; ++n2) {
+              const float4 v = *reinterpret_cast<const float4*>(trow + n2 * kTwXRow + 16 * L * i);
+              re[i * L + n2] = make_float2(v.x, v.y);
+              im[i * L + n2] = make_float2(v.z, v.w);
+            }
+          }
         }
         __syncwarp();
         if (to_issue > 0 && !*abort_flag) {
           ++issued;
           fence_proxy_async();
           const int ia = 2 * ipi;
-          twin_issue(p, f, warp + ic * NW, witem_symbol(p, pilot_here, d0, ia),
-                     ia + 1 < items ? witem_symbol(p, pilot_here, d0, ia + 1) : -1,
-                     yslot, ybar, pol, lane);
+          twin_issue<LOG2N>(p, f, warp + ic * NW, pilot_here, d0, items, ia, yslot, ybar, pol, lane);
           --to_issue;
           if (++ipi == npairs) {
             ipi = 0;
             ++ic;
           }
         }
-        // pass twiddles W_1024^(n2 k1), n2 = r, k1 = lane
+        // pass twiddles W_N^(n2 k1) of register i L + n2, k1 = jt + L i
 #pragma unroll
-        for (int r = 1; r < 32; ++r) {
-          const float2 w = tws[r * 32 + lane];
-          const float2 xr = re[r], xi = im[r];
-          re[r] = __ffma2_rn(xi, f2(-w.y), __fmul2_rn(xr, f2(w.x)));
-          im[r] = __ffma2_rn(xr, f2(w.y), __fmul2_rn(xi, f2(w.x)));
+        for (int i = 0; i < 32 / L; ++i) {
+#pragma unroll
+          for (int n2 = 1; n2 < L; ++n2) {
+            const float2 w = tws[n2 * 32 + jt + L * i];
+            const int e = i * L + n2;
+            const float2 xr = re[e], xi = im[e];
+            re[e] = __ffma2_rn(xi, f2(-w.y), __fmul2_rn(xr, f2(w.x)));
+            im[e] = __ffma2_rn(xr, f2(w.y), __fmul2_rn(xi, f2(w.x)));
+          }
         }
-        // pass 2: 32-point DFTs over n2; register e holds bin lane + 32 e
-        twin_dft32_sr<false>(re, im);
+        // pass 2: radix-L DFTs over n2; register e holds bin bin_of(jt, e)
+        twin_pass2<L>(re, im);
         const int ia = 2 * ip;
         if (pilot_here && ip == 0) {
           // first row: the pilot.  LS estimate H = Y conj(X) / |X|^2 (1/sqrt(N)
@@ -453,10 +530,10 @@ __global__ void __launch_bounds__(kTwThreads, 1) twin_kernel(const KParams p) {
           // energy
 #pragma unroll
           for (int e = 0; e < 32; ++e) {
-            const int k = lane + 32 * e;
+            const int k = bin_of<LOG2N>(jt, e);
             const float2 hv = cmul(make_float2(re[e].x, im[e].x), __ldg(p.xinv + k));
-            h[e] = hv;
-            if (energy_here) p.H_out[hrow + k] = hv;
+            h[e] = valid ? hv : make_float2(0.f, 0.f);
+            if (valid && energy_here) p.H_out[hrow + k] = hv;
           }
           if (energy_here) {
             float acc[OWN];
@@ -491,20 +568,20 @@ __global__ void __launch_bounds__(kTwThreads, 1) twin_kernel(const KParams p) {
     if (energy_here) {
       // warps w and w + 4 share a lane quarter: warp w < 4 adds the other's
       // columns in tensor memory, then four warps go through shared memory
-      float* RE = reinterpret_cast<float*>(smem + lay.warp_off);   // [4][N]
+      float* RE = reinterpret_cast<float*>(smem + lay.warp_off);   // [4][A][N]
       if (warp < 4) {
         float e[OWN], e2[OWN];
         TmE::ld(tE, e);
         TmE::ld(tE + kTwTmemWarp, e2);
         tmem_wait_ld();
 #pragma unroll
-        for (int cc = 0; cc < OWN; ++cc) RE[warp * N + lane + 32 * cc] = e[cc] + e2[cc];
+        for (int cc = 0; cc < OWN; ++cc) RE[(warp * A + team) * N + bin_of<LOG2N>(jt, cc)] = e[cc] + e2[cc];
       }
       __syncthreads();
       for (int k = tid; k < N; k += NT) {
         float E = 0.f;
 #pragma unroll
-        for (int w = 0; w < 4; ++w) E += RE[w * N + k];
+        for (int w = 0; w < 4 * A; ++w) E += RE[w * N + k];
         if (p.mode == kModePartial) {
           p.E_out[(static_cast<size_t>(blockIdx.y) * gridDim.x + f) * N + k] = E;
         } else {
@@ -517,7 +594,7 @@ __global__ void __launch_bounds__(kTwThreads, 1) twin_kernel(const KParams p) {
       __syncthreads();
     }
     // warps w < 4 add warp w + 4's sums (same lane quarter) in tensor
-    // memory and write both to shared memory: [4][nd][N]
+    // memory and write both to shared memory: [4][A][nd][N]
     float2* RP = reinterpret_cast<float2*>(smem + lay.warp_off);
     const int dlc = kTwDg;
     for (int dl0 = 0; dl0 < nd; dl0 += dlc) {
@@ -526,7 +603,7 @@ __global__ void __launch_bounds__(kTwThreads, 1) twin_kernel(const KParams p) {
         const int it = dl0 + j + (pilot_here ? 1 : 0);
         bool pr;
         const uint32_t tb = tP + twin_block_col(it, pilot_here, &pr, items);
-        float2* dst = RP + static_cast<size_t>(warp * dlc + j) * N;
+        float2* dst = RP + static_cast<size_t>((warp * A + team) * dlc + j) * N;
         if (pr) {
           const int hf = it & 1;
 #pragma unroll
@@ -537,7 +614,7 @@ __global__ void __launch_bounds__(kTwThreads, 1) twin_kernel(const KParams p) {
             tmem_wait_ld();
 #pragma unroll
             for (int i = 0; i < 8; ++i)
-              dst[lane + 32 * (q0 / 4 + i)] =
+              dst[bin_of<LOG2N>(jt, q0 / 4 + i)] =
                   make_float2(hf ? t[4 * i + 1] + t2[4 * i + 1] : t[4 * i] + t2[4 * i],
                               hf ? t[4 * i + 3] + t2[4 * i + 3] : t[4 * i + 2] + t2[4 * i + 2]);
           }
@@ -550,17 +627,17 @@ __global__ void __launch_bounds__(kTwThreads, 1) twin_kernel(const KParams p) {
             tmem_wait_ld();
 #pragma unroll
             for (int i = 0; i < 16; ++i)
-              dst[lane + 32 * (q0 / 2 + i)] = make_float2(t[2 * i] + t2[2 * i], t[2 * i + 1] + t2[2 * i + 1]);
+              dst[bin_of<LOG2N>(jt, q0 / 2 + i)] = make_float2(t[2 * i] + t2[2 * i], t[2 * i + 1] + t2[2 * i + 1]);
           }
         }
       }
       __syncthreads();
       for (int idx = tid; idx < n * N; idx += NT) {
-        const int j = idx >> 10;
+        const int j = idx >> LOG2N;
         const int k = idx & (N - 1);
         float2 s = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int w = 0; w < 4; ++w) s = cadd(s, RP[static_cast<size_t>(w * dlc + j) * N + k]);
+        for (int w = 0; w < 4 * A; ++w) s = cadd(s, RP[static_cast<size_t>(w * dlc + j) * N + k]);
         const int dl = dl0 + j;
         if (p.mode == kModePartial) {
           p.P_out[((static_cast<size_t>(blockIdx.y) * gridDim.x + f) * p.D + d0 + dl) * N + k] =

@@ -144,6 +144,17 @@ def test_two_symbol_kernel_groupings(L, M, S, pilot_idx):
     run_and_check(L, sweep_config(M, 1024).replace(S=S, pilot_idx=pilot_idx), F=2)
 
 
+@pytest.mark.parametrize("M,N,S,pilot_idx", [
+    (32, 512, 14, 0), (37, 512, 5, 4), (71, 512, 17, 16), (40, 512, 2, 1),
+    (128, 256, 14, 0), (131, 256, 9, 3), (158, 256, 4, 0)])
+def test_two_symbol_kernel_antenna_teams(L, M, N, S, pilot_idx):
+    """N = 512 with 32 or more antennas and N = 256 with 128 or more run the
+    two-symbol kernel with 2 or 4 antennas per warp step (lane teams of 16 or
+    8 lanes, a radix-16 or radix-8 second pass): ragged antenna counts leave
+    teams of the last step idle, with the step pairings of every group."""
+    run_and_check(L, sweep_config(M, N).replace(S=S, pilot_idx=pilot_idx), F=2)
+
+
 @pytest.mark.parametrize("M,S,pilot_idx", [
     (1, 2, 0), (5, 3, 2), (4, 4, 0), (13, 5, 4), (8, 9, 0), (20, 14, 7), (9, 17, 16)])
 def test_two_symbol_pair_kernel_groupings(L, M, S, pilot_idx):
@@ -154,14 +165,15 @@ def test_two_symbol_pair_kernel_groupings(L, M, S, pilot_idx):
     run_and_check(L, sweep_config(M, 2048).replace(S=S, pilot_idx=pilot_idx), F=2)
 
 
-@pytest.mark.parametrize("N,S,pilot_idx", [(1024, 17, 5), (1024, 6, 0), (2048, 17, 16), (2048, 5, 2)])
+@pytest.mark.parametrize("N,S,pilot_idx", [(1024, 17, 5), (1024, 6, 0), (2048, 17, 16), (2048, 5, 2),
+                                             (512, 11, 10)])
 def test_two_symbol_kernel_group_layers(L, N, S, pilot_idx):
     """Both two-symbol kernels: the one-launch antenna split of a small batch
     gives every data-symbol group its own block (each transforms the pilot,
     group 0 alone writes H and the energy): against the oracle, and H equal
     to the unsplit call's."""
     import torch
-    cfg = sweep_config(16, N).replace(S=S, pilot_idx=pilot_idx)
+    cfg = sweep_config(40 if N == 512 else 16, N).replace(S=S, pilot_idx=pilot_idx)
     F, G = 2, 2
     b = synth.generate(cfg, frame_ids=range(F))
     plan = make_plan(L, cfg, max_frames=4)
@@ -387,8 +399,9 @@ def test_batch_split_small_batch(L, name, F):
 @pytest.mark.parametrize("N,fmt", [(2048, "fc32"), (512, "sc16")])
 def test_batch_split_other_kernels(L, N, fmt):
     """The shard pass of the warp-specialised kernel (N = 2048 from fc32 rows)
-    and of the per-warp kernel with two antennas per lane team (N = 512):
-    split and unsplit small batches both meet the oracle bars, H equal."""
+    and of the two-symbol kernel with two antennas per warp step (N = 512,
+    64 antennas): split and unsplit small batches both meet the oracle bars,
+    H equal (the plan picks one kernel for all its launches)."""
     import torch
     cfg = sweep_config(16, N).replace(fmt=fmt, M=64 if N == 512 else 16)
     b = synth.generate(cfg, frame_ids=range(2))
