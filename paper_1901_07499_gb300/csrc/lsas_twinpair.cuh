@@ -21,11 +21,13 @@
 //     kept in registers, |H|^2 added to the channel energy (Sec. III); data
 //     symbols: P += conj(H) Y in tensor memory (MRC, Sec. II-C), for two data
 //     symbols as four packed FMAs per subcarrier on interleaved columns.
-// Four barriers of the pair's 64 threads order a step: the first follows the
-// reads of the step's slot and (in program order) every read of the previous
-// step, so it also frees the previous step's slot, which is refilled there
-// for the step after this one; then middle write -> read, middle read ->
-// final write, final write -> read.
+// Three barriers of the pair's 64 threads order a step: the first follows
+// the reads of the step's slot and (in program order) every read of the
+// previous step, so it also frees the previous step's slot, which is
+// refilled there for the step after this one; then middle write -> read and
+// final write -> read.  Middle read -> final write needs only the warp's own
+// order: each warp writes its final-exchange outputs over the cells that it
+// alone read in the middle exchange.
 // Data-symbol groups as in the N = 1024 two-symbol kernel (the pilot with
 // three data symbols, then four); at a group's end warp w < 4 adds the sums
 // of warp w + 4 (same lane quarter, same subcarriers) in tensor memory, the
@@ -48,9 +50,10 @@ constexpr int kTpRow = kTpN * 4;             // one CP-stripped sc16 row
 // rw) at row rw, column jw of [32][65] 16-byte entries (one pad per row);
 // rows 0..15 in the slot just read, rows 16..31 in the exchange region
 constexpr int kTpMRow = 65 * 16;
-// final exchange: element (a, r, b) of writer j = 32 a + b, output r, at
-// [a][r][b]; a < 4 in the slot, a >= 4 in the exchange region
-constexpr int kTpFHalf = 4 * 8 * 32 * 16;
+// final exchange: element (a, r, b) of writer j = 32 a + b (a = w + 2 i for
+// warp w of the pair), output r, in the middle layout at row
+// (8 i + r) ^ (bit 2 of b), column 2 b + w: the cells warp w itself read in
+// the middle exchange (column parity w), without bank conflicts
 constexpr int kTpSlotB = 16 * kTpMRow;       // 16,640 B: two rows, or half an exchange
 constexpr int kTpTwl = 7 * 256;              // last-pass twiddles W_2048^(j r), r = 1..7
 
@@ -293,24 +296,33 @@ __global__ void __launch_bounds__(kTpThreads, 1) twinpair_kernel(const KParams p
           for (int i = 0; i < 4; ++i) tp_twiddle(re[i * 8 + rr], im[i * 8 + rr], w);
         }
         tp_dft8x4(re, im);
-        bar_sync(pbar, 64);   // B2: the middle reads are done
-        // final exchange: output r of j = jt + 64 i = 32 a + b at [a][r][b]
+        // final exchange: output r of j = jt + 64 i = 32 a + b (a = w + 2 i,
+        // w = jt >> 5 the warp of the pair) goes to row R = (8 i + r) ^ t,
+        // column 2 b + w of the middle layout (t = bit 2 of b spreads a
+        // quarter-warp's 16-byte cells over all banks).  Warp w writes only
+        // the column-parity-w cells that it alone read in the middle
+        // exchange, so its own reads need to be done, not its partner's
+        __syncwarp();
+        const int tq = (jt >> 2) & 1;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          const int a = (jt >> 5) + 2 * i;
 #pragma unroll
-          for (int r = 0; r < 8; ++r)
-            *reinterpret_cast<float4*>((i < 2 ? yslot : X) + (((a & 3) * 8 + r) * 32 + (jt & 31)) * 16) =
+          for (int r = 0; r < 8; ++r) {
+            const int R = (8 * i + r) ^ tq;
+            *reinterpret_cast<float4*>((i < 2 ? yslot : X) + ((R & 15) * 65 + 2 * (jt & 31) + (jt >> 5)) * 16) =
                 make_float4(re[i * 8 + r].x, re[i * 8 + r].y, im[i * 8 + r].x, im[i * 8 + r].y);
+          }
         }
-        bar_sync(pbar, 64);   // B3
+        bar_sync(pbar, 64);   // B2
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const int a = (jt >> 5) + 2 * i;   // this thread's j = jt + 64 i = 32 a + (jt & 31)
 #pragma unroll
           for (int r = 0; r < 8; ++r) {
+            // output a of j' = 32 r + b, written by warp r & 1 at its i' = r >> 1
+            const int R = (8 * (r >> 1) + a) ^ tq;
             const float4 v = *reinterpret_cast<const float4*>(
-                (r < 4 ? yslot : X) + (((r & 3) * 8 + a) * 32 + (jt & 31)) * 16);
+                (r < 4 ? yslot : X) + ((R & 15) * 65 + 2 * (jt & 31) + (r & 1)) * 16);
             re[i * 8 + r] = make_float2(v.x, v.y);
             im[i * 8 + r] = make_float2(v.z, v.w);
             if (r > 0) tp_twiddle(re[i * 8 + r], im[i * 8 + r], twl[(r - 1) * 256 + jt + 64 * i]);
