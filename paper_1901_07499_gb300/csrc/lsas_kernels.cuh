@@ -888,12 +888,26 @@ __device__ __forceinline__ void wait_slot(uint32_t bar, uint32_t parity,
 }
 
 // Level of one axis value: boundaries at or below v (ties go up).
+// Level of one axis: the number of decision thresholds at or below v (a tie
+// goes to the upper level).  The compares are independent and summed
+// pairwise for the constellation's threshold count (1, 3, 7 or 15), so the
+// slicer is a short tree rather than a chain of dependent additions.
+template <int T>
+__device__ __forceinline__ int count_ge(float v, const float* thr) {
+  if constexpr (T == 1) {
+    return v >= thr[0] ? 1 : 0;
+  } else {
+    constexpr int H = T / 2;
+    return count_ge<H>(v, thr) + count_ge<T - H>(v, thr + H);
+  }
+}
 __device__ __forceinline__ int axis_level(float v, const KParams& p) {
-  int l = 0;
-#pragma unroll
-  for (int b = 0; b < kMaxThresholds; ++b)
-    if (b < p.nthr) l += (v >= p.thr[b]) ? 1 : 0;
-  return l;
+  switch (p.nthr) {
+    case 1: return count_ge<1>(v, p.thr);
+    case 3: return count_ge<3>(v, p.thr);
+    case 7: return count_ge<7>(v, p.thr);
+    default: return count_ge<kMaxThresholds>(v, p.thr);
+  }
 }
 __device__ __forceinline__ uint32_t gray(int l) { return static_cast<uint32_t>(l ^ (l >> 1)); }
 

@@ -593,62 +593,88 @@ __global__ void __launch_bounds__(kTwThreads, 1) twin_kernel(const KParams p) {
       }
       __syncthreads();
     }
-    // warps w < 4 add warp w + 4's sums (same lane quarter) in tensor
-    // memory and write both to shared memory: [4][A][nd][N]
+    // the group's data items in tensor memory, block by block (a step's
+    // pair of items interleaved in 128 columns, or an item alone in 64):
+    // the two warps of a lane quarter take alternate blocks, add both
+    // warps' sums and write them to shared memory: [4][A][nd][N]
+    static_assert(kTwDg0 <= kTwDg, "a group's data items fit one reduction");
     float2* RP = reinterpret_cast<float2*>(smem + lay.warp_off);
     const int dlc = kTwDg;
-    for (int dl0 = 0; dl0 < nd; dl0 += dlc) {
-      const int n = min(dlc, nd - dl0);
-      for (int j = 0; j < n && warp < 4; ++j) {
-        const int it = dl0 + j + (pilot_here ? 1 : 0);
+    const int dl0 = 0;
+    const int n = nd;
+    {
+      const uint32_t tfirst = tE - static_cast<uint32_t>((warp >> 2) * kTwTmemWarp);   // first warp's columns
+      const int j0 = pilot_here ? 1 : 0;
+      int blk = 0;
+      for (int it = j0; it < items; ++blk) {
         bool pr;
-        const uint32_t tb = tP + twin_block_col(it, pilot_here, &pr, items);
-        float2* dst = RP + static_cast<size_t>((warp * A + team) * dlc + j) * N;
-        if (pr) {
-          const int hf = it & 1;
+        const uint32_t tb = tfirst + (tP - tE) + twin_block_col(it, pilot_here, &pr, items);
+        if ((blk & 1) == (warp >> 2)) {
+          float2* dst = RP + static_cast<size_t>(((warp & 3) * A + team) * dlc + (it - j0)) * N;
+          if (pr) {
 #pragma unroll
-          for (int q0 = 0; q0 < 128; q0 += 32) {
-            float t[32], t2[32];
-            Tmem<32>::ld(tb + q0, t);
-            Tmem<32>::ld(tb + kTwTmemWarp + q0, t2);
-            tmem_wait_ld();
+            for (int q0 = 0; q0 < 128; q0 += 32) {
+              float t[32], t2[32];
+              Tmem<32>::ld(tb + q0, t);
+              Tmem<32>::ld(tb + kTwTmemWarp + q0, t2);
+              tmem_wait_ld();
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
-              dst[bin_of<LOG2N>(jt, q0 / 4 + i)] =
-                  make_float2(hf ? t[4 * i + 1] + t2[4 * i + 1] : t[4 * i] + t2[4 * i],
-                              hf ? t[4 * i + 3] + t2[4 * i + 3] : t[4 * i + 2] + t2[4 * i + 2]);
-          }
-        } else {
+              for (int i = 0; i < 8; ++i) {
+                const int k = bin_of<LOG2N>(jt, q0 / 4 + i);
+                dst[k] = make_float2(t[4 * i] + t2[4 * i], t[4 * i + 2] + t2[4 * i + 2]);
+                dst[N + k] = make_float2(t[4 * i + 1] + t2[4 * i + 1], t[4 * i + 3] + t2[4 * i + 3]);
+              }
+            }
+          } else {
 #pragma unroll
-          for (int q0 = 0; q0 < 2 * OWN; q0 += 32) {
-            float t[32], t2[32];
-            Tmem<32>::ld(tb + q0, t);
-            Tmem<32>::ld(tb + kTwTmemWarp + q0, t2);
-            tmem_wait_ld();
+            for (int q0 = 0; q0 < 2 * OWN; q0 += 32) {
+              float t[32], t2[32];
+              Tmem<32>::ld(tb + q0, t);
+              Tmem<32>::ld(tb + kTwTmemWarp + q0, t2);
+              tmem_wait_ld();
 #pragma unroll
-            for (int i = 0; i < 16; ++i)
-              dst[bin_of<LOG2N>(jt, q0 / 2 + i)] = make_float2(t[2 * i] + t2[2 * i], t[2 * i + 1] + t2[2 * i + 1]);
+              for (int i = 0; i < 16; ++i)
+                dst[bin_of<LOG2N>(jt, q0 / 2 + i)] = make_float2(t[2 * i] + t2[2 * i], t[2 * i + 1] + t2[2 * i + 1]);
+            }
           }
         }
+        it += pr ? 2 : 1;
       }
+    }
+    {
       __syncthreads();
-      for (int idx = tid; idx < n * N; idx += NT) {
-        const int j = idx >> LOG2N;
-        const int k = idx & (N - 1);
-        float2 s = make_float2(0.f, 0.f);
+      // four items per thread at a time: their shared-memory sums are all
+      // loaded before the first is demapped
+      for (int idx0 = tid; idx0 < n * N; idx0 += 4 * NT) {
+        float2 sv[4];
 #pragma unroll
-        for (int w = 0; w < 4 * A; ++w) s = cadd(s, RP[static_cast<size_t>(w * dlc + j) * N + k]);
-        const int dl = dl0 + j;
-        if (p.mode == kModePartial) {
-          p.P_out[((static_cast<size_t>(blockIdx.y) * gridDim.x + f) * p.D + d0 + dl) * N + k] =
-              make_float2(s.x * p.inv_sqrtN, s.y * p.inv_sqrtN);
-        } else {
-          const float ie = ie_s[k];
-          const float2 z = (ie != 0.f) ? make_float2(s.x * ie, s.y * ie) : make_float2(0.f, 0.f);
-          if (p.eq) p.eq[(static_cast<size_t>(f) * p.D + d0 + dl) * N + k] = z;
-          uint32_t code = gray(axis_level(z.x, p));
-          if (p.axes == 2) code = (code << p.wbits) | gray(axis_level(z.y, p));
-          codes[dl * N + k] = static_cast<uint8_t>(code);
+        for (int u = 0; u < 4; ++u) {
+          const int idx = min(idx0 + u * NT, n * N - 1);
+          const int j = idx >> LOG2N;
+          const int k = idx & (N - 1);
+          sv[u] = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int w = 0; w < 4 * A; ++w) sv[u] = cadd(sv[u], RP[static_cast<size_t>(w * dlc + j) * N + k]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int idx = idx0 + u * NT;
+          if (idx >= n * N) break;
+          const int j = idx >> LOG2N;
+          const int k = idx & (N - 1);
+          const float2 s = sv[u];
+          const int dl = dl0 + j;
+          if (p.mode == kModePartial) {
+            p.P_out[((static_cast<size_t>(blockIdx.y) * gridDim.x + f) * p.D + d0 + dl) * N + k] =
+                make_float2(s.x * p.inv_sqrtN, s.y * p.inv_sqrtN);
+          } else {
+            const float ie = ie_s[k];
+            const float2 z = (ie != 0.f) ? make_float2(s.x * ie, s.y * ie) : make_float2(0.f, 0.f);
+            if (p.eq) p.eq[(static_cast<size_t>(f) * p.D + d0 + dl) * N + k] = z;
+            uint32_t code = gray(axis_level(z.x, p));
+            if (p.axes == 2) code = (code << p.wbits) | gray(axis_level(z.y, p));
+            codes[dl * N + k] = static_cast<uint8_t>(code);
+          }
         }
       }
       __syncthreads();

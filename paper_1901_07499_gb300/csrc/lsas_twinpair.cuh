@@ -398,15 +398,20 @@ __global__ void __launch_bounds__(kTpThreads, 1) twinpair_kernel(const KParams p
       __syncthreads();
     }
     {
+      // the group's data items in tensor memory, block by block (a step's
+      // pair of items interleaved in 128 columns, or an item alone in 64):
+      // the two warps of a lane quarter (pairs q and q + 2) take alternate
+      // blocks, add both warps' sums and write them to shared memory
       float2* RP = reinterpret_cast<float2*>(smem + lay.pair_off);   // [2][kTwDg][N]
-      if (warp < 4) {
-        for (int j = 0; j < nd; ++j) {
-          const int it = j + (pilot_here ? 1 : 0);
-          bool pr;
-          const uint32_t tb = tP + twin_block_col(it, pilot_here, &pr, items);
-          float2* dst = RP + static_cast<size_t>(q * kTwDg + j) * N;
+      const uint32_t tfirst = tE - static_cast<uint32_t>((warp >> 2) * kTwTmemWarp);   // first warp's columns
+      const int j0 = pilot_here ? 1 : 0;
+      int blk = 0;
+      for (int it = j0; it < items; ++blk) {
+        bool pr;
+        const uint32_t tb = tfirst + (tP - tE) + twin_block_col(it, pilot_here, &pr, items);
+        if ((blk & 1) == (warp >> 2)) {
+          float2* dst = RP + static_cast<size_t>((q & 1) * kTwDg + (it - j0)) * N;
           if (pr) {
-            const int hf = it & 1;
 #pragma unroll
             for (int q0 = 0; q0 < 128; q0 += 32) {
               float t[32], t2[32];
@@ -414,10 +419,11 @@ __global__ void __launch_bounds__(kTpThreads, 1) twinpair_kernel(const KParams p
               Tmem<32>::ld(tb + kTwTmemWarp + q0, t2);
               tmem_wait_ld();
 #pragma unroll
-              for (int i = 0; i < 8; ++i)
-                dst[bin_of<LOG2N>(jt, q0 / 4 + i)] =
-                    make_float2(hf ? t[4 * i + 1] + t2[4 * i + 1] : t[4 * i] + t2[4 * i],
-                                hf ? t[4 * i + 3] + t2[4 * i + 3] : t[4 * i + 2] + t2[4 * i + 2]);
+              for (int i = 0; i < 8; ++i) {
+                const int k = bin_of<LOG2N>(jt, q0 / 4 + i);
+                dst[k] = make_float2(t[4 * i] + t2[4 * i], t[4 * i + 2] + t2[4 * i + 2]);
+                dst[N + k] = make_float2(t[4 * i + 1] + t2[4 * i + 1], t[4 * i + 3] + t2[4 * i + 3]);
+              }
             }
           } else {
 #pragma unroll
@@ -433,23 +439,38 @@ __global__ void __launch_bounds__(kTpThreads, 1) twinpair_kernel(const KParams p
             }
           }
         }
+        it += pr ? 2 : 1;
       }
       __syncthreads();
-      for (int idx = threadIdx.x; idx < nd * N; idx += kTpThreads) {
-        const int dl = idx >> LOG2N;
-        const int k = idx & (N - 1);
-        const float2 s = cadd(RP[static_cast<size_t>(dl) * N + k],
-                              RP[static_cast<size_t>(kTwDg + dl) * N + k]);
-        if (p.mode == kModePartial) {
-          p.P_out[((static_cast<size_t>(blockIdx.y) * gridDim.x + f) * p.D + d0 + dl) * N + k] =
-              make_float2(s.x * p.inv_sqrtN, s.y * p.inv_sqrtN);
-        } else {
-          const float ie = ie_s[k];
-          const float2 z = (ie != 0.f) ? make_float2(s.x * ie, s.y * ie) : make_float2(0.f, 0.f);
-          if (p.eq) p.eq[(static_cast<size_t>(f) * p.D + d0 + dl) * N + k] = z;
-          uint32_t code = gray(axis_level(z.x, p));
-          if (p.axes == 2) code = (code << p.wbits) | gray(axis_level(z.y, p));
-          codes[dl * N + k] = static_cast<uint8_t>(code);
+      // four items per thread at a time: their shared-memory sums are all
+      // loaded before the first is demapped
+      for (int idx0 = threadIdx.x; idx0 < nd * N; idx0 += 4 * kTpThreads) {
+        float2 sv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int idx = min(idx0 + u * kTpThreads, nd * N - 1);
+          const int dl = idx >> LOG2N;
+          const int k = idx & (N - 1);
+          sv[u] = cadd(RP[static_cast<size_t>(dl) * N + k], RP[static_cast<size_t>(kTwDg + dl) * N + k]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int idx = idx0 + u * kTpThreads;
+          if (idx >= nd * N) break;
+          const int dl = idx >> LOG2N;
+          const int k = idx & (N - 1);
+          const float2 s = sv[u];
+          if (p.mode == kModePartial) {
+            p.P_out[((static_cast<size_t>(blockIdx.y) * gridDim.x + f) * p.D + d0 + dl) * N + k] =
+                make_float2(s.x * p.inv_sqrtN, s.y * p.inv_sqrtN);
+          } else {
+            const float ie = ie_s[k];
+            const float2 z = (ie != 0.f) ? make_float2(s.x * ie, s.y * ie) : make_float2(0.f, 0.f);
+            if (p.eq) p.eq[(static_cast<size_t>(f) * p.D + d0 + dl) * N + k] = z;
+            uint32_t code = gray(axis_level(z.x, p));
+            if (p.axes == 2) code = (code << p.wbits) | gray(axis_level(z.y, p));
+            codes[dl * N + k] = static_cast<uint8_t>(code);
+          }
         }
       }
       __syncthreads();
