@@ -36,6 +36,8 @@
 // split).
 #pragma once
 
+#include <type_traits>
+
 #include "lsas_kernels.cuh"
 #include "lsas_warp.cuh"
 #include "lsas_twin.cuh"
@@ -443,35 +445,45 @@ __global__ void __launch_bounds__(kTpThreads, 1) twinpair_kernel(const KParams p
       }
       __syncthreads();
       // four items per thread at a time: their shared-memory sums are all
-      // loaded before the first is demapped
-      for (int idx0 = threadIdx.x; idx0 < nd * N; idx0 += 4 * kTpThreads) {
-        float2 sv[4];
+      // loaded before the first is demapped; one copy of the loop per
+      // constellation, so that the slicer inside it has no branches
+      auto demap_items = [&](auto tcount) {
+        constexpr int T = decltype(tcount)::value;
+        for (int idx0 = threadIdx.x; idx0 < nd * N; idx0 += 4 * kTpThreads) {
+          float2 sv[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int idx = min(idx0 + u * kTpThreads, nd * N - 1);
-          const int dl = idx >> LOG2N;
-          const int k = idx & (N - 1);
-          sv[u] = cadd(RP[static_cast<size_t>(dl) * N + k], RP[static_cast<size_t>(kTwDg + dl) * N + k]);
-        }
+          for (int u = 0; u < 4; ++u) {
+            const int idx = min(idx0 + u * kTpThreads, nd * N - 1);
+            const int dl = idx >> LOG2N;
+            const int k = idx & (N - 1);
+            sv[u] = cadd(RP[static_cast<size_t>(dl) * N + k], RP[static_cast<size_t>(kTwDg + dl) * N + k]);
+          }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int idx = idx0 + u * kTpThreads;
-          if (idx >= nd * N) break;
-          const int dl = idx >> LOG2N;
-          const int k = idx & (N - 1);
-          const float2 s = sv[u];
-          if (p.mode == kModePartial) {
-            p.P_out[((static_cast<size_t>(blockIdx.y) * gridDim.x + f) * p.D + d0 + dl) * N + k] =
-                make_float2(s.x * p.inv_sqrtN, s.y * p.inv_sqrtN);
-          } else {
-            const float ie = ie_s[k];
-            const float2 z = (ie != 0.f) ? make_float2(s.x * ie, s.y * ie) : make_float2(0.f, 0.f);
-            if (p.eq) p.eq[(static_cast<size_t>(f) * p.D + d0 + dl) * N + k] = z;
-            uint32_t code = gray(axis_level(z.x, p));
-            if (p.axes == 2) code = (code << p.wbits) | gray(axis_level(z.y, p));
-            codes[dl * N + k] = static_cast<uint8_t>(code);
+          for (int u = 0; u < 4; ++u) {
+            const int idx = idx0 + u * kTpThreads;
+            if (idx >= nd * N) break;
+            const int dl = idx >> LOG2N;
+            const int k = idx & (N - 1);
+            const float2 s = sv[u];
+            if (p.mode == kModePartial) {
+              p.P_out[((static_cast<size_t>(blockIdx.y) * gridDim.x + f) * p.D + d0 + dl) * N + k] =
+                  make_float2(s.x * p.inv_sqrtN, s.y * p.inv_sqrtN);
+            } else {
+              const float ie = ie_s[k];
+              const float2 z = (ie != 0.f) ? make_float2(s.x * ie, s.y * ie) : make_float2(0.f, 0.f);
+              if (p.eq) p.eq[(static_cast<size_t>(f) * p.D + d0 + dl) * N + k] = z;
+              uint32_t code = gray(count_ge<T>(z.x, p.thr));
+              if (p.axes == 2) code = (code << p.wbits) | gray(count_ge<T>(z.y, p.thr));
+              codes[dl * N + k] = static_cast<uint8_t>(code);
+            }
           }
         }
+      };
+      switch (p.nthr) {
+        case 1: demap_items(std::integral_constant<int, 1>{}); break;
+        case 3: demap_items(std::integral_constant<int, 3>{}); break;
+        case 7: demap_items(std::integral_constant<int, 7>{}); break;
+        default: demap_items(std::integral_constant<int, kMaxThresholds>{}); break;
       }
       __syncthreads();
     }
