@@ -444,22 +444,22 @@ __global__ void __launch_bounds__(kTpThreads, 1) twinpair_kernel(const KParams p
         it += pr ? 2 : 1;
       }
       __syncthreads();
-      // four items per thread at a time: their shared-memory sums are all
+      // eight items per thread at a time: their shared-memory sums are all
       // loaded before the first is demapped; one copy of the loop per
       // constellation, so that the slicer inside it has no branches
       auto demap_items = [&](auto tcount) {
         constexpr int T = decltype(tcount)::value;
-        for (int idx0 = threadIdx.x; idx0 < nd * N; idx0 += 4 * kTpThreads) {
-          float2 sv[4];
+        for (int idx0 = threadIdx.x; idx0 < nd * N; idx0 += 8 * kTpThreads) {
+          float2 sv[8];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
+          for (int u = 0; u < 8; ++u) {
             const int idx = min(idx0 + u * kTpThreads, nd * N - 1);
             const int dl = idx >> LOG2N;
             const int k = idx & (N - 1);
             sv[u] = cadd(RP[static_cast<size_t>(dl) * N + k], RP[static_cast<size_t>(kTwDg + dl) * N + k]);
           }
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
+          for (int u = 0; u < 8; ++u) {
             const int idx = idx0 + u * kTpThreads;
             if (idx >= nd * N) break;
             const int dl = idx >> LOG2N;
