@@ -9,6 +9,8 @@
 // fused kernel does: Gray slicer, packed bits, optional z.
 #include <cfloat>
 
+#include <type_traits>
+
 #include "lsas_kernels.cuh"
 
 namespace lsas {
@@ -59,18 +61,30 @@ __global__ void __launch_bounds__(kCombineThreads) combine_kernel(const KParams 
       E[4 * j + 3] += e.w;
     }
   }
-  uint64_t acc = 0;
+  // one copy of the slicing per constellation, so that it has no branches
+  auto codes_of = [&](auto tcount) {
+    constexpr int T = decltype(tcount)::value;
+    uint64_t a = 0;
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    // zero or non-finite energy: z = 0 and the frame is flagged
-    const bool ok = (E[j] > 0.f) && (E[j] <= FLT_MAX);
-    if (!ok) latch(p.status, kStDevice);
-    const float ie = ok ? 1.0f / E[j] : 0.f;
-    const float2 z = ok ? make_float2(P[j].x * ie, P[j].y * ie) : make_float2(0.f, 0.f);
-    if (p.eq) p.eq[f * dn + r * 8 + j] = z;
-    uint32_t code = gray(axis_level(z.x, p));
-    if (p.axes == 2) code = (code << p.wbits) | gray(axis_level(z.y, p));
-    acc = (acc << p.q) | code;
+    for (int j = 0; j < 8; ++j) {
+      // zero or non-finite energy: z = 0 and the frame is flagged
+      const bool ok = (E[j] > 0.f) && (E[j] <= FLT_MAX);
+      if (!ok) latch(p.status, kStDevice);
+      const float ie = ok ? 1.0f / E[j] : 0.f;
+      const float2 z = ok ? make_float2(P[j].x * ie, P[j].y * ie) : make_float2(0.f, 0.f);
+      if (p.eq) p.eq[f * dn + r * 8 + j] = z;
+      uint32_t code = gray(count_ge<T>(z.x, p.thr));
+      if (p.axes == 2) code = (code << p.wbits) | gray(count_ge<T>(z.y, p.thr));
+      a = (a << p.q) | code;
+    }
+    return a;
+  };
+  uint64_t acc;
+  switch (p.nthr) {
+    case 1: acc = codes_of(std::integral_constant<int, 1>{}); break;
+    case 3: acc = codes_of(std::integral_constant<int, 3>{}); break;
+    case 7: acc = codes_of(std::integral_constant<int, 7>{}); break;
+    default: acc = codes_of(std::integral_constant<int, kMaxThresholds>{}); break;
   }
   uint8_t* dst = p.bits + f * (dn * p.q / 8) + r * p.q;
   for (int j = 0; j < p.q; ++j) dst[j] = static_cast<uint8_t>(acc >> (8 * (p.q - 1 - j)));
