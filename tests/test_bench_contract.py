@@ -24,6 +24,7 @@ sys.path.insert(0, ROOT)
 
 import bench  # noqa: E402
 import synth  # noqa: E402
+from synth.frames import sweep_config  # noqa: E402
 
 
 def test_reference_arm_json_line():
@@ -86,3 +87,23 @@ def test_sweep_shapes_cover_the_grid():
     scale = synth.CONFIGS["scale"]
     for c in shapes:
         assert (c.S, c.Q, c.fmt, c.pilot_idx) == (scale.S, scale.Q, scale.fmt, scale.pilot_idx)
+
+
+@pytest.mark.parametrize("M,N,fmt,kernel", [
+    (64, 1024, "sc16", "twin_kernel"), (8, 1024, "sc16", "twin_kernel"),
+    (32, 512, "sc16", "twin_kernel"), (31, 512, "sc16", "warp_kernel"),
+    (128, 256, "sc16", "twin_kernel"), (127, 256, "sc16", "warp_kernel"),
+    (128, 128, "sc16", "warp_kernel"), (128, 64, "sc16", "warp_kernel"),
+    (8, 2048, "sc16", "twinpair_kernel"), (64, 1024, "fc32", "warp_kernel"),
+    (64, 2048, "fc32", "frame_kernel")])
+def test_fused_kernel_name_follows_the_plan(monkeypatch, M, N, fmt, kernel):
+    """The kernel the benchmark names (and whose traffic entry it reads) is the
+    one the plan picks: two symbols per step from sc16 rows at N = 1024 and
+    2048, at N = 512 from 32 antennas and at N = 256 from 128; one symbol per
+    step otherwise; LSAS_FUSED_KERNEL=warp keeps one symbol per step."""
+    monkeypatch.delenv("LSAS_FUSED_KERNEL", raising=False)
+    cfg = sweep_config(M, N).replace(fmt=fmt)
+    assert bench.fused_kernel_name(cfg).split(" ")[0] == kernel
+    monkeypatch.setenv("LSAS_FUSED_KERNEL", "warp")
+    one = {"twin_kernel": "warp_kernel", "twinpair_kernel": "pair_kernel"}.get(kernel, kernel)
+    assert bench.fused_kernel_name(cfg).split(" ")[0] == one
