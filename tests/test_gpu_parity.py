@@ -208,9 +208,13 @@ def test_pilot_not_first_n2048(L, pilot_idx):
     run_and_check(L, sweep_config(12, 2048).replace(pilot_idx=pilot_idx), F=2)
 
 
+@pytest.mark.parametrize("N", [256, 1024, 2048])
 @pytest.mark.parametrize("Q", [2, 4, 64, 256])
-def test_qam_orders(L, Q):
-    run_and_check(L, sweep_config(16, 256).replace(Q=Q, snr_db=40.0), F=2)
+def test_qam_orders(L, Q, N):
+    """Every constellation through each fused receiver the plan picks at 16
+    antennas: the one-symbol kernel (N = 256) and the two-symbol kernels
+    (N = 1024, 2048), whose demap has one copy per constellation."""
+    run_and_check(L, sweep_config(16, N).replace(Q=Q, snr_db=40.0), F=2)
 
 
 @pytest.mark.parametrize("cp", [17, 1, 0])
