@@ -38,13 +38,15 @@ def make_plan(L, cfg, max_frames=1024):
                   max_frames=max_frames, pilot=synth.frames.pilot_sequence(cfg))
 
 
-def run_and_check(L, cfg, F=None, want_eq=True, pilot=None):
+def run_and_check(L, cfg, F=None, want_eq=True, pilot=None, split=True):
     import torch
     ids = range(F if F is not None else cfg.F)
     b = synth.generate(cfg, frame_ids=ids, pilot=pilot)
     plan = make_plan(L, cfg)
     if pilot is not None:
         plan.set_pilot(pilot)
+    if not split:
+        plan.set_batch_split(False)
     x = to_torch_frames(b)
     H, bits, eq = plan.run_frame(x, want_eq=want_eq)
     plan.sync()
@@ -208,13 +210,16 @@ def test_pilot_not_first_n2048(L, pilot_idx):
     run_and_check(L, sweep_config(12, 2048).replace(pilot_idx=pilot_idx), F=2)
 
 
+@pytest.mark.parametrize("split", [True, False])
 @pytest.mark.parametrize("N", [256, 1024, 2048])
 @pytest.mark.parametrize("Q", [2, 4, 64, 256])
-def test_qam_orders(L, Q, N):
+def test_qam_orders(L, Q, N, split):
     """Every constellation through each fused receiver the plan picks at 16
     antennas: the one-symbol kernel (N = 256) and the two-symbol kernels
-    (N = 1024, 2048), whose demap has one copy per constellation."""
-    run_and_check(L, sweep_config(16, N).replace(Q=Q, snr_db=40.0), F=2)
+    (N = 1024, 2048), whose demap has one copy per constellation.  A small
+    batch runs split into antenna shards (the combine kernel slices) unless
+    the split is off (the fused kernel slices)."""
+    run_and_check(L, sweep_config(16, N).replace(Q=Q, snr_db=40.0), F=2, split=split)
 
 
 @pytest.mark.parametrize("cp", [17, 1, 0])
