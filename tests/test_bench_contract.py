@@ -107,3 +107,30 @@ def test_fused_kernel_name_follows_the_plan(monkeypatch, M, N, fmt, kernel):
     monkeypatch.setenv("LSAS_FUSED_KERNEL", "warp")
     one = {"twin_kernel": "warp_kernel", "twinpair_kernel": "pair_kernel"}.get(kernel, kernel)
     assert bench.fused_kernel_name(cfg).split(" ")[0] == one
+
+
+def test_kernel_hashes_cover_their_includes():
+    """Each fused kernel's source hash (which decides whether a committed ncu
+    traffic figure still describes the kernel) covers the file that defines
+    the kernel and every local header it includes, directly or not."""
+    import re
+    csrc = bench.CSRC
+
+    def text(name):
+        with open(os.path.join(csrc, name)) as fh:
+            return fh.read()
+
+    def includes(name):
+        return re.findall(r'^#include "([^"]+)"', text(name), re.M)
+
+    for kernel, files in bench.KERNEL_SRC.items():
+        defining = [f for f in os.listdir(csrc) if f.endswith((".cuh", ".cu"))
+                    and re.search(r"__global__.*\b%s\(" % kernel, text(f))]
+        assert len(defining) == 1, (kernel, defining)
+        closure, todo = set(), [defining[0]]
+        while todo:
+            f = todo.pop()
+            if f not in closure:
+                closure.add(f)
+                todo.extend(includes(f))
+        assert set(files) == closure, (kernel, sorted(files), sorted(closure))
