@@ -523,7 +523,11 @@ lsas_status run_split_tail(lsas_plan p, const void* d_in, int f0, int nf, int G,
   k.M = p->M / G;
   k.shard_y = k.M;
   k.grid_y = G;
-  k.group_z = 0;
+  // small batches: one block per data-symbol group as well (each repeats
+  // the pilot transform), so a frame's groups also run side by side, as in
+  // the one-launch static split
+  k.group_z = ((p->N <= 1024 || p->fmt == LSAS_IN_SC16) && p->geo.groups > 1 &&
+               nf * G * 2 <= p->sms) ? 1 : 0;
   k.chunks = (k.M + p->geo.Af - 1) / p->geo.Af;
   k.mode = kModePartial;
   k.use_tma = tma_ok(p, in) ? 1 : 0;
